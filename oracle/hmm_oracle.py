@@ -1,0 +1,706 @@
+"""Plain, slow FP64 CPU oracle for the HMM hot path.
+
+TEST INFRASTRUCTURE ONLY.  Nothing in the product package imports this file;
+only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py`` (its CPU
+baseline and ``--impl reference`` arm) may import or run it.  It shares no
+code with the CUDA path.
+
+Everything here is the plain definition from the paper (libhmm,
+arXiv 2605.29208), evaluated in float64 with numpy/scipy library primitives
+(``logaddexp``-free: the log-sum-exp is written out as the paper defines it).
+Citations name the paper's section and equation numbers:
+
+  Sec. 3.2  log-space forward-backward, Eq. 1 (init) and Eq. 2 (recursion);
+            the backward pass and smoothed probabilities "analogously".
+  Sec. 3.1  notation: gamma_t(j), xi_t(i,j).
+  Sec. 3.3  Viterbi, Eq. 3-4 with the backpointer psi_t(j).
+  Sec. 3.4  posterior decoding q_t = argmax_j gamma_t(j).
+  Sec. 4    weighted M-step, Eq. 5 (N_j, ybar_j) and Eq. 6 (argmax).
+  Sec. 4.1  closed forms (Gaussian, Poisson, von Mises mean direction).
+  Sec. 4.2  Newton-Raphson: Gamma (Eq. 7-8), Beta (Eq. 9-10), Weibull
+            (Eq. 11), von Mises kappa (Eq. 12), negative binomial (text).
+  Sec. 4.3  ECME for Student-t: Eq. 13 (scale mixture), Eq. 14 (u-tilde),
+            Eq. 15-16 (CM-step 1), Eq. 17-19 (CM-step 2 for nu).
+  Sec. 4.4  state-collapse guard (N_j < 1e-8 keeps the parameters).
+  Sec. 4.5  diagonal Gaussian (Eq. 20-21), full covariance (Eq. 22-24).
+
+Where the paper is silent the readings used are listed in the module
+constants and functions below (transition/initial M-step, tie breaks,
+support of each family, Newton stopping rule, negative-binomial score,
+the Student-t nu equation, Weibull seed).
+
+Parity status: every function here is pinned by the not-gpu tests in
+``tests/test_oracle_*.py`` (brute-force path enumeration, invariants,
+closed forms, scipy.stats fits, score equations).  None is unpinned.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+from scipy import linalg as sla
+from scipy import special as sp
+
+# --------------------------------------------------------------------------
+# Readings where the paper is silent (also listed in the design notes)
+# --------------------------------------------------------------------------
+COLLAPSE_EPS = 1e-8          # Sec. 4.4: skip the M-step for state j if N_j < eps
+TIKHONOV_EPS = 1e-6          # Sec. 4.5: Sigma + eps I for the full covariance
+NEWTON_TOL = 1e-10           # |delta| <= tol * max(1, |theta|) stops Newton
+NEWTON_MAXIT = 50
+NU_TOL = 1e-6                # Sec. 4.3: |d nu| < 1e-6 stops the nu Newton
+NU_MIN, NU_MAX = 0.5, 1e4    # reading: nu kept in [0.5, 1e4]
+NEGBIN_RMAX = 1e6            # reading: no finite MLE when var <= mean
+KAPPA_MAX = 1e6              # reading: R -> 1 gives kappa -> inf
+
+FAMILIES = ("gauss", "poisson", "gamma", "beta", "weibull", "negbin",
+            "student_t", "vonmises", "diag_gauss", "full_gauss")
+
+
+@dataclass
+class Model:
+    """lambda = (pi, A, B) of Sec. 3.1 with the emission family of every
+    state equal to ``family`` and parameters ``params[name][j]``."""
+    family: str
+    pi: np.ndarray            # [N]
+    A: np.ndarray             # [N, N] row-stochastic
+    params: dict = field(default_factory=dict)
+
+    @property
+    def n_states(self) -> int:
+        return self.A.shape[0]
+
+    def copy(self) -> "Model":
+        return Model(self.family, self.pi.copy(), self.A.copy(),
+                     {k: np.array(v, dtype=np.float64, copy=True)
+                      for k, v in self.params.items()})
+
+
+# --------------------------------------------------------------------------
+# log-sum-exp exactly as Sec. 3.2 defines it: max + log sum exp(x - max)
+# --------------------------------------------------------------------------
+def lse(x: np.ndarray, axis: int) -> np.ndarray:
+    m = np.max(x, axis=axis, keepdims=True)
+    finite = np.isfinite(m)
+    m0 = np.where(finite, m, 0.0)
+    with np.errstate(divide="ignore"):
+        out = m0 + np.log(np.sum(np.exp(x - m0), axis=axis, keepdims=True))
+    out = np.where(finite, out, m)          # all -inf stays -inf
+    return np.squeeze(out, axis=axis)
+
+
+# --------------------------------------------------------------------------
+# Emission log-densities log b_j(y_t) -> [T, N]
+# --------------------------------------------------------------------------
+def _is_count(y):
+    return (y >= 0) & (np.floor(y) == y)
+
+
+def emission_logpdf(model: Model, y: np.ndarray) -> np.ndarray:
+    """log b_j(y_t) for every t and state j (densities of Sec. 4.1-4.5).
+
+    Scalar families take y of shape [T]; the multivariate ones [T, D].
+    Observations outside a family's support give -inf (reading).
+    """
+    f, p = model.family, model.params
+    y = np.asarray(y, dtype=np.float64)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        if f == "gauss":        # Sec. 4.1, N(mu, sigma^2)
+            mu, s2 = p["mu"], p["sigma2"]
+            yy = y[:, None]
+            return -0.5 * np.log(2 * np.pi * s2) - (yy - mu) ** 2 / (2 * s2)
+        if f == "poisson":      # Sec. 4.1
+            lam = p["lam"]
+            yy = y[:, None]
+            out = yy * np.log(lam) - lam - sp.gammaln(yy + 1)
+            return np.where(_is_count(yy), out, -np.inf)
+        if f == "gamma":        # Sec. 4.2, rate parameterisation (beta = rate)
+            a, b = p["alpha"], p["beta"]
+            yy = y[:, None]
+            out = a * np.log(b) + (a - 1) * np.log(yy) - b * yy - sp.gammaln(a)
+            return np.where(yy > 0, out, -np.inf)
+        if f == "beta":         # Sec. 4.2
+            a, b = p["a"], p["b"]
+            yy = y[:, None]
+            out = (a - 1) * np.log(yy) + (b - 1) * np.log1p(-yy) - sp.betaln(a, b)
+            return np.where((yy > 0) & (yy < 1), out, -np.inf)
+        if f == "weibull":      # Sec. 4.2, shape k, scale lambda
+            k, lam = p["k"], p["lam"]
+            yy = y[:, None]
+            out = (np.log(k) - k * np.log(lam) + (k - 1) * np.log(yy)
+                   - (yy / lam) ** k)
+            return np.where(yy > 0, out, -np.inf)
+        if f == "negbin":       # Sec. 4.2, p = r / (r + mean)
+            r, pp = p["r"], p["p"]
+            yy = y[:, None]
+            out = (sp.gammaln(yy + r) - sp.gammaln(r) - sp.gammaln(yy + 1)
+                   + r * np.log(pp) + yy * np.log1p(-pp))
+            return np.where(_is_count(yy), out, -np.inf)
+        if f == "student_t":    # Sec. 4.3, location-scale t
+            mu, s2, nu = p["mu"], p["sigma2"], p["nu"]
+            yy = y[:, None]
+            return (sp.gammaln((nu + 1) / 2) - sp.gammaln(nu / 2)
+                    - 0.5 * np.log(nu * np.pi * s2)
+                    - (nu + 1) / 2 * np.log1p((yy - mu) ** 2 / (nu * s2)))
+        if f == "vonmises":     # Sec. 4.1-4.2, log(2 pi I0(k)) = log 2pi + log i0e(k) + k
+            mu, kap = p["mu"], p["kappa"]
+            yy = y[:, None]
+            return (kap * np.cos(yy - mu) - np.log(2 * np.pi)
+                    - (np.log(sp.i0e(kap)) + kap))
+        if f == "diag_gauss":   # Sec. 4.5, Eq. 20
+            mu, var = p["mu"], p["var"]          # [N, D]
+            d = y[:, None, :] - mu[None]
+            return np.sum(-0.5 * np.log(2 * np.pi * var)[None]
+                          - d ** 2 / (2 * var[None]), axis=2)
+        if f == "full_gauss":   # Sec. 4.5, Eq. 22 through the Cholesky factor
+            mu, cov = p["mu"], p["cov"]          # [N, D], [N, D, D]
+            T, D = y.shape
+            out = np.empty((T, mu.shape[0]))
+            for j in range(mu.shape[0]):
+                L = np.linalg.cholesky(cov[j])
+                z = sla.solve_triangular(L, (y - mu[j]).T, lower=True)
+                out[:, j] = (-0.5 * D * np.log(2 * np.pi)
+                             - np.sum(np.log(np.diag(L)))
+                             - 0.5 * np.sum(z * z, axis=0))
+            return out
+    raise ValueError(f"unknown family {f!r}")
+
+
+# --------------------------------------------------------------------------
+# Forward / backward in log space (Sec. 3.2)
+# --------------------------------------------------------------------------
+def forward_log(logpi, logA, logb):
+    """alpha-hat_t(j) by Eq. 1 and Eq. 2.  logb: [T, N]."""
+    T, N = logb.shape
+    alpha = np.empty((T, N))
+    alpha[0] = logpi + logb[0]                                   # Eq. 1
+    for t in range(1, T):                                        # Eq. 2
+        alpha[t] = lse(alpha[t - 1][:, None] + logA, axis=0) + logb[t]
+    return alpha
+
+
+def backward_log(logA, logb):
+    """beta-hat_t(i) = log P(y_{t+1..T} | q_t = i): beta-hat_T = 0 and
+    beta-hat_t(i) = lse_j[log a_ij + log b_j(y_{t+1}) + beta-hat_{t+1}(j)]
+    (the 'analogous' backward recursion of Sec. 3.2)."""
+    T, N = logb.shape
+    beta = np.empty((T, N))
+    beta[T - 1] = 0.0
+    for t in range(T - 2, -1, -1):
+        beta[t] = lse(logA + (logb[t + 1] + beta[t + 1])[None, :], axis=1)
+    return beta
+
+
+def forward_backward_logb(logpi, logA, logb):
+    """logL, gamma_t(j), sum_t xi_t(i,j) (Sec. 3.1 definitions) from a
+    log-emission table."""
+    alpha = forward_log(logpi, logA, logb)
+    beta = backward_log(logA, logb)
+    logL = float(lse(alpha[-1], axis=0))
+    gamma = np.exp(alpha + beta - logL)
+    T, N = logb.shape
+    xi_sum = np.zeros((N, N))
+    for t in range(T - 1):
+        xi_sum += np.exp(alpha[t][:, None] + logA
+                         + (logb[t + 1] + beta[t + 1])[None, :] - logL)
+    return dict(logL=logL, gamma=gamma, xi_sum=xi_sum, alpha=alpha, beta=beta)
+
+
+def _logs(model: Model):
+    with np.errstate(divide="ignore"):
+        return np.log(model.pi), np.log(model.A)
+
+
+def forward_backward(model: Model, y):
+    logpi, logA = _logs(model)
+    return forward_backward_logb(logpi, logA, emission_logpdf(model, y))
+
+
+def posterior_decode(gamma):
+    """Sec. 3.4: argmax_j gamma_t(j); ties go to the lowest j (reading)."""
+    return np.argmax(gamma, axis=1).astype(np.int32)
+
+
+# --------------------------------------------------------------------------
+# Viterbi (Sec. 3.3)
+# --------------------------------------------------------------------------
+def viterbi_logb(logpi, logA, logb):
+    """Max-plus recursion of Eq. 3-4 in FP64 with backpointers.
+
+    Ties (reading): scanning i upward with a strict '>' keeps the lowest
+    predecessor index; the final state is the lowest index attaining the
+    maximum.  Returns (path [T] int32, score float)."""
+    T, N = logb.shape
+    delta = logpi + logb[0]
+    psi = np.zeros((T, N), dtype=np.int32)
+    for t in range(1, T):
+        cand = delta[:, None] + logA                   # [i, j]
+        psi[t] = np.argmax(cand, axis=0)               # first max = lowest i
+        delta = cand[psi[t], np.arange(N)] + logb[t]
+    q = np.empty(T, dtype=np.int32)
+    q[T - 1] = int(np.argmax(delta))
+    for t in range(T - 1, 0, -1):
+        q[t - 1] = psi[t, q[t]]
+    return q, float(delta[q[T - 1]])
+
+
+def viterbi(model: Model, y):
+    logpi, logA = _logs(model)
+    return viterbi_logb(logpi, logA, emission_logpdf(model, y))
+
+
+def viterbi_gaps(logpi, logA, logb):
+    """FP64 best-minus-second-best margins of every Viterbi decision, used
+    to excuse path differences at near-ties.  Returns (path, score,
+    step_gap [T, N], final_gap) where step_gap[t, j] is the margin of the
+    predecessor choice psi_t(j)."""
+    T, N = logb.shape
+    delta = logpi + logb[0]
+    psi = np.zeros((T, N), dtype=np.int32)
+    gap = np.full((T, N), np.inf)
+    for t in range(1, T):
+        cand = delta[:, None] + logA
+        psi[t] = np.argmax(cand, axis=0)
+        srt = np.sort(cand, axis=0)
+        if N > 1:
+            gap[t] = srt[-1] - srt[-2]
+        delta = cand[psi[t], np.arange(N)] + logb[t]
+    q = np.empty(T, dtype=np.int32)
+    q[T - 1] = int(np.argmax(delta))
+    fs = np.sort(delta)
+    final_gap = float(fs[-1] - fs[-2]) if N > 1 else np.inf
+    for t in range(T - 1, 0, -1):
+        q[t - 1] = psi[t, q[t]]
+    return q, float(delta[q[T - 1]]), gap, final_gap
+
+
+def viterbi_fp32(logpi32, logA32, logb32):
+    """Viterbi in float32 with a fixed operation order, for bit-exact
+    comparison of decoded paths (reading of Sec. 3.3 for a single-precision
+    device).  Only IEEE additions, subtractions and comparisons occur:
+
+      delta_1(j) = logpi(j) + logb_1(j)
+      for t >= 2, every j: scan i = 0..N-1 upward,
+          c = delta_{t-1}(i) + logA(i, j); keep c if c > best (strict)
+      delta_t(j) = best + logb_t(j)
+      after every step m_t = max_j delta_t(j) and, if m_t is finite,
+      delta_t(j) <- delta_t(j) - m_t, with m_t added to an FP64 score.
+    The final state is the lowest j with delta_T(j) == max_j delta_T(j).
+    Returns (path int32 [T], score float64)."""
+    f32 = np.float32
+    logpi32 = np.asarray(logpi32, dtype=f32)
+    logA32 = np.asarray(logA32, dtype=f32)
+    logb32 = np.asarray(logb32, dtype=f32)
+    T, N = logb32.shape
+    psi = np.zeros((T, N), dtype=np.int32)
+    d = (logpi32 + logb32[0]).astype(f32)
+    off = 0.0
+    m = d.max()
+    if np.isfinite(m):
+        d = (d - m).astype(f32)
+        off += float(m)
+    for t in range(1, T):
+        # c(i, j) = delta_{t-1}(i) + logA(i, j) in float32; the first
+        # maximum over i (lowest index) is what a strict '>' scan keeps.
+        cand = (d[:, None] + logA32).astype(f32)
+        psi[t] = np.argmax(cand, axis=0)
+        best = cand[psi[t], np.arange(N)]
+        nd = (best + logb32[t]).astype(f32)
+        m = nd.max()
+        if np.isfinite(m):
+            nd = (nd - m).astype(f32)
+            off += float(m)
+        d = nd
+    q = np.empty(T, dtype=np.int32)
+    q[T - 1] = int(np.argmax(d))
+    score = off + float(d[q[T - 1]])
+    for t in range(T - 1, 0, -1):
+        q[t - 1] = psi[t, q[t]]
+    return q, score
+
+
+# --------------------------------------------------------------------------
+# Special functions used by the M-steps (library routines)
+# --------------------------------------------------------------------------
+def digamma(x):
+    return sp.digamma(x)
+
+
+def trigamma(x):
+    return sp.polygamma(1, x)
+
+
+def bessel_ratio(kappa):
+    """A(kappa) = I1(kappa) / I0(kappa) (Sec. 4.2), through the
+    exponentially scaled Bessel functions so that large kappa is safe."""
+    return sp.i1e(kappa) / sp.i0e(kappa)
+
+
+# --------------------------------------------------------------------------
+# Weighted M-steps for one state (Sec. 4), w = gamma_t(j) over the
+# concatenated sequences of one model, y the matching observations.
+# --------------------------------------------------------------------------
+def _newton_done(old, new):
+    return abs(new - old) <= NEWTON_TOL * max(1.0, abs(old))
+
+
+def mstep_gauss(w, y, cur):
+    """Sec. 4.1: mu = ybar, sigma^2 = N^-1 sum w (y - mu)^2 (two-pass)."""
+    Nj = w.sum()
+    mu = np.sum(w * y) / Nj
+    s2 = np.sum(w * (y - mu) ** 2) / Nj
+    return dict(mu=mu, sigma2=s2)
+
+
+def mstep_poisson(w, y, cur):
+    """Sec. 4.1: lambda = ybar."""
+    return dict(lam=np.sum(w * y) / w.sum())
+
+
+def mstep_gamma(w, y, cur):
+    """Sec. 4.2, Eq. 7-8: Newton on the shape from the MOM seed
+    ybar^2 / sigma^2, rate = shape / ybar.  (The N_j factors of Eq. 7 and
+    Eq. 8 cancel in the update.)"""
+    Nj = w.sum()
+    ybar = np.sum(w * y) / Nj
+    mlog = np.sum(w * np.log(y)) / Nj
+    c = np.log(ybar) - mlog
+    var = np.sum(w * (y - ybar) ** 2) / Nj
+    a = ybar * ybar / var
+    iters = 0
+    for iters in range(1, NEWTON_MAXIT + 1):
+        s = np.log(a) - digamma(a) - c
+        ds = 1.0 / a - trigamma(a)
+        step = s / ds
+        new = a - step
+        while new <= 0:
+            step *= 0.5
+            new = a - step
+        done = _newton_done(a, new)
+        a = new
+        if done:
+            break
+    return dict(alpha=a, beta=a / ybar, _iters=iters)
+
+
+def mstep_beta(w, y, cur):
+    """Sec. 4.2, Eq. 9-10: joint Newton on
+    psi(a) - psi(a+b) = mean log y, psi(b) - psi(a+b) = mean log(1-y)
+    with the trigamma Jacobian, from the MOM seeds of the text.
+    Reading: if the MOM seed is not positive, start from (1, 1)."""
+    Nj = w.sum()
+    ybar = np.sum(w * y) / Nj
+    var = np.sum(w * (y - ybar) ** 2) / Nj
+    m1 = np.sum(w * np.log(y)) / Nj
+    m2 = np.sum(w * np.log1p(-y)) / Nj
+    k = ybar * (1 - ybar) / var - 1
+    a, b = (ybar * k, (1 - ybar) * k) if k > 0 else (1.0, 1.0)
+    iters = 0
+    for iters in range(1, NEWTON_MAXIT + 1):
+        pab = digamma(a + b)
+        F = np.array([digamma(a) - pab - m1, digamma(b) - pab - m2])
+        tab = trigamma(a + b)
+        J = np.array([[trigamma(a) - tab, -tab], [-tab, trigamma(b) - tab]])
+        step = np.linalg.solve(J, F)
+        na, nb = a - step[0], b - step[1]
+        while na <= 0 or nb <= 0:
+            step *= 0.5
+            na, nb = a - step[0], b - step[1]
+        done = _newton_done(a, na) and _newton_done(b, nb)
+        a, b = na, nb
+        if done:
+            break
+    return dict(a=a, b=b, _iters=iters)
+
+
+def mstep_weibull(w, y, cur):
+    """Sec. 4.2, Eq. 11: Newton on
+    f(k) = 1/k + mean log y - sum w y^k log y / sum w y^k, with
+    f'(k) = -1/k^2 - (S2 S0 - S1^2) / S0^2, S_r = sum w y^k (log y)^r;
+    scale = (N^-1 sum w y^k)^(1/k).  Reading for the 'MOM seed': log Y of a
+    Weibull has standard deviation pi / (k sqrt 6), so
+    k0 = pi / (sqrt 6 * weighted sd of log y)."""
+    Nj = w.sum()
+    ly = np.log(y)
+    mlog = np.sum(w * ly) / Nj
+    sdlog = math.sqrt(np.sum(w * (ly - mlog) ** 2) / Nj)
+    k = math.pi / (math.sqrt(6.0) * sdlog)
+    lmax = ly.max()
+
+    def sums(k):
+        e = np.exp(k * (ly - lmax))            # y^k / ymax^k, ratios invariant
+        return np.sum(w * e), np.sum(w * e * ly), np.sum(w * e * ly * ly)
+
+    iters = 0
+    for iters in range(1, NEWTON_MAXIT + 1):
+        S0, S1, S2 = sums(k)
+        f = 1.0 / k + mlog - S1 / S0
+        df = -1.0 / (k * k) - (S2 * S0 - S1 * S1) / (S0 * S0)
+        step = f / df
+        new = k - step
+        while new <= 0:
+            step *= 0.5
+            new = k - step
+        done = _newton_done(k, new)
+        k = new
+        if done:
+            break
+    S0 = np.sum(w * np.exp(k * ly))
+    lam = (S0 / Nj) ** (1.0 / k)
+    return dict(k=k, lam=lam, _iters=iters)
+
+
+def mstep_negbin(w, y, cur):
+    """Sec. 4.2 (negative binomial).  The paper gives no score; reading:
+    with p = r / (r + ybar) profiled out, Newton on
+      g(r)  = sum w [psi(y+r) - psi(r)] + N log(r / (r + ybar)) = 0,
+      g'(r) = sum w [psi'(y+r) - psi'(r)] + N (1/r - 1/(r + ybar)),
+    seeded at ybar^2 / (var - ybar); when var <= ybar there is no finite
+    maximiser and r = 1e6.  Steps are halved to keep r > 0, r <= 1e6."""
+    Nj = w.sum()
+    ybar = np.sum(w * y) / Nj
+    var = np.sum(w * (y - ybar) ** 2) / Nj
+    iters = 0
+    if var <= ybar:
+        r = NEGBIN_RMAX
+    else:
+        r = ybar * ybar / (var - ybar)
+        for iters in range(1, NEWTON_MAXIT + 1):
+            g = np.sum(w * (digamma(y + r) - digamma(r))) + Nj * np.log(r / (r + ybar))
+            dg = (np.sum(w * (trigamma(y + r) - trigamma(r)))
+                  + Nj * (1.0 / r - 1.0 / (r + ybar)))
+            step = g / dg
+            new = r - step
+            while new <= 0:
+                step *= 0.5
+                new = r - step
+            new = min(new, NEGBIN_RMAX)
+            done = _newton_done(r, new)
+            r = new
+            if done:
+                break
+    return dict(r=r, p=r / (r + ybar), _iters=iters)
+
+
+def mstep_vonmises(w, y, cur):
+    """Sec. 4.1 mean direction mu = atan2(sum w sin y, sum w cos y);
+    Sec. 4.2 Eq. 12: Newton on A(kappa) = Rbar from the seed
+    Rbar (2 - Rbar^2) / (1 - Rbar^2)."""
+    Nj = w.sum()
+    C, S = np.sum(w * np.cos(y)), np.sum(w * np.sin(y))
+    mu = math.atan2(S, C)
+    R = math.hypot(C, S) / Nj
+    if R >= 1.0:
+        return dict(mu=mu, kappa=KAPPA_MAX, _iters=0)
+    k = R * (2 - R * R) / (1 - R * R)
+    iters = 0
+    for iters in range(1, NEWTON_MAXIT + 1):
+        A = bessel_ratio(k)
+        dA = 1 - A * A - A / k
+        step = (A - R) / dA
+        new = k - step
+        while new <= 0:
+            step *= 0.5
+            new = k - step
+        new = min(new, KAPPA_MAX)
+        done = _newton_done(k, new)
+        k = new
+        if done:
+            break
+    return dict(mu=mu, kappa=k, _iters=iters)
+
+
+def student_t_utilde(y, mu, s2, nu):
+    """Eq. 14: u_t = (nu + 1) / (nu + (y - mu)^2 / sigma^2)."""
+    return (nu + 1) / (nu + (y - mu) ** 2 / s2)
+
+
+def mstep_student_t(w, y, cur, nu_mode="ecm"):
+    """Sec. 4.3.  E-step weights u_t from the current (mu0, sigma0^2, nu0)
+    (Eq. 14); CM-step 1 (Eq. 15-16) with sigma^2 divided by N_j and the new
+    mu; CM-step 2: Newton on the nu score with the Hessian of Eq. 19 until
+    |d nu| < 1e-6.
+
+    nu_mode='ecm' (default reading): the score of Eq. 18 plus the constant
+    (N/2)[psi((nu0+1)/2) - log((nu0+1)/2)] that E[log U | y] contributes in
+    the ECM equation for nu; Eq. 17-18 as printed omit it, which biases nu
+    upward.  nu_mode='paper_literal' uses Eq. 18 exactly as printed.
+    nu is kept in [0.5, 1e4] (reading)."""
+    mu0, s20, nu0 = cur["mu"], cur["sigma2"], cur["nu"]
+    Nj = w.sum()
+    u = student_t_utilde(y, mu0, s20, nu0)
+    wu = w * u
+    mu = np.sum(wu * y) / np.sum(wu)                      # Eq. 15
+    s2 = np.sum(wu * (y - mu) ** 2) / Nj                  # Eq. 16
+    C = np.sum(w * (np.log(u) - u))
+    if nu_mode == "ecm":
+        C += Nj * (digamma((nu0 + 1) / 2) - np.log((nu0 + 1) / 2))
+    elif nu_mode != "paper_literal":
+        raise ValueError(nu_mode)
+    nu = nu0
+    iters = 0
+    for iters in range(1, NEWTON_MAXIT + 1):
+        g = 0.5 * Nj * (np.log(nu / 2) + 1 - digamma(nu / 2)) + 0.5 * C   # Eq. 18
+        h = 0.25 * Nj * (2.0 / nu - trigamma(nu / 2))                     # Eq. 19
+        dnu = -g / h
+        new = min(max(nu + dnu, NU_MIN), NU_MAX)
+        done = abs(new - nu) < NU_TOL
+        nu = new
+        if done:
+            break
+    return dict(mu=mu, sigma2=s2, nu=nu, _iters=iters)
+
+
+def mstep_diag_gauss(w, y, cur):
+    """Sec. 4.5, Eq. 21: D independent weighted Gaussian updates."""
+    Nj = w.sum()
+    mu = np.sum(w[:, None] * y, axis=0) / Nj
+    var = np.sum(w[:, None] * (y - mu) ** 2, axis=0) / Nj
+    return dict(mu=mu, var=var)
+
+
+def mstep_full_gauss(w, y, cur):
+    """Sec. 4.5, Eq. 23-24: weighted mean and covariance + eps I."""
+    Nj = w.sum()
+    mu = np.sum(w[:, None] * y, axis=0) / Nj
+    d = y - mu
+    cov = (w[:, None] * d).T @ d / Nj + TIKHONOV_EPS * np.eye(y.shape[1])
+    return dict(mu=mu, cov=cov)
+
+
+MSTEP = dict(gauss=mstep_gauss, poisson=mstep_poisson, gamma=mstep_gamma,
+             beta=mstep_beta, weibull=mstep_weibull, negbin=mstep_negbin,
+             student_t=mstep_student_t, vonmises=mstep_vonmises,
+             diag_gauss=mstep_diag_gauss, full_gauss=mstep_full_gauss)
+
+
+def _state_params(model: Model, j: int) -> dict:
+    return {k: v[j] for k, v in model.params.items()}
+
+
+def mstep_emission(model: Model, W: np.ndarray, y: np.ndarray, nu_mode="ecm"):
+    """Eq. 6 for every state with the Sec. 4.4 collapse guard.
+    W: [T_total, N] occupancies, y: observations of the same rows."""
+    new = model.copy()
+    iters = np.zeros(model.n_states, dtype=np.int64)
+    for j in range(model.n_states):
+        w = W[:, j]
+        if w.sum() < COLLAPSE_EPS:              # Sec. 4.4: keep theta_j
+            continue
+        fn = MSTEP[model.family]
+        kw = dict(nu_mode=nu_mode) if model.family == "student_t" else {}
+        res = fn(w, y, _state_params(model, j), **kw)
+        iters[j] = res.pop("_iters", 0)
+        for k, v in res.items():
+            new.params[k][j] = v
+    return new, iters
+
+
+def mstep_transitions(model: Model, xi_sum, gamma1_sum, n_seq):
+    """Reading (the paper names Baum-Welch but prints no transition update):
+    a_ij = sum xi(i,j) / sum_j' xi(i,j') (the denominator equals
+    sum_{t<T} gamma_t(i)); a row whose denominator is below 1e-8 is kept
+    (the Sec. 4.4 rule applied to rows); pi_j = mean over the model's
+    sequences of gamma_1(j)."""
+    A = model.A.copy()
+    den = xi_sum.sum(axis=1)
+    for i in range(model.n_states):
+        if den[i] >= COLLAPSE_EPS:
+            A[i] = xi_sum[i] / den[i]
+    pi = gamma1_sum / n_seq
+    return pi, A
+
+
+# --------------------------------------------------------------------------
+# One Baum-Welch iteration over a packed ragged batch of several models
+# --------------------------------------------------------------------------
+def split_batch(values, offsets):
+    return [values[offsets[s]:offsets[s + 1]] for s in range(len(offsets) - 1)]
+
+
+def estep(models, values, offsets, model_id):
+    """Per model: per-sequence logL, occupancies of every row of its data,
+    sum of xi, sum of gamma_1 and the number of sequences."""
+    seqs = split_batch(values, offsets)
+    out = []
+    for m, model in enumerate(models):
+        idx = [s for s in range(len(seqs)) if model_id[s] == m]
+        N = model.n_states
+        res = dict(seq=idx, logL=[], W=[], Y=[], xi_sum=np.zeros((N, N)),
+                   gamma1_sum=np.zeros(N), n_seq=len(idx))
+        for s in idx:
+            fb = forward_backward(model, seqs[s])
+            res["logL"].append(fb["logL"])
+            res["W"].append(fb["gamma"])
+            res["Y"].append(seqs[s])
+            res["xi_sum"] += fb["xi_sum"]
+            res["gamma1_sum"] += fb["gamma"][0]
+        out.append(res)
+    return out
+
+
+def em_iteration(models, values, offsets, model_id, nu_mode="ecm"):
+    """E-step with the current models, then the M-step of Sec. 4 for the
+    emissions and the transition/initial reading.  Returns
+    (new_models, logL per sequence [S] under the OLD models)."""
+    S = len(offsets) - 1
+    logL = np.zeros(S)
+    new_models = []
+    for model, res in zip(models, estep(models, values, offsets, model_id)):
+        for s, ll in zip(res["seq"], res["logL"]):
+            logL[s] = ll
+        if res["n_seq"] == 0:
+            new_models.append(model.copy())
+            continue
+        W = np.concatenate(res["W"], axis=0)
+        Y = np.concatenate(res["Y"], axis=0)
+        new, _ = mstep_emission(model, W, Y, nu_mode=nu_mode)
+        new.pi, new.A = mstep_transitions(model, res["xi_sum"],
+                                          res["gamma1_sum"], res["n_seq"])
+        new_models.append(new)
+    return new_models, logL
+
+
+def fit(models, values, offsets, model_id, n_iter, nu_mode="ecm"):
+    """n_iter Baum-Welch iterations; returns (models, logL trace
+    [n_iter, S]) where row k holds the logL under the models entering
+    iteration k."""
+    trace = []
+    for _ in range(n_iter):
+        models, ll = em_iteration(models, values, offsets, model_id, nu_mode)
+        trace.append(ll)
+    return models, np.array(trace)
+
+
+def batch_loglik(models, values, offsets, model_id):
+    seqs = split_batch(values, offsets)
+    return np.array([forward_backward(models[model_id[s]], seqs[s])["logL"]
+                     for s in range(len(seqs))])
+
+
+# --------------------------------------------------------------------------
+# Brute force over all N^T state paths (tiny N, T) -- pins the recursions
+# --------------------------------------------------------------------------
+def brute_force(logpi, logA, logb):
+    """Enumerate every path q in [N]^T: returns logL, gamma, sum xi, the
+    MAP path (lowest path in lexicographic order among exact ties) and its
+    score.  Exponential cost; N <= 3, T <= 8 only."""
+    import itertools
+    T, N = logb.shape
+    paths = np.array(list(itertools.product(range(N), repeat=T)))
+    lp = logpi[paths[:, 0]] + logb[0, paths[:, 0]]
+    for t in range(1, T):
+        lp = lp + logA[paths[:, t - 1], paths[:, t]] + logb[t, paths[:, t]]
+    logL = float(lse(lp, axis=0))
+    post = np.exp(lp - logL)
+    gamma = np.zeros((T, N))
+    xi = np.zeros((N, N))
+    for t in range(T):
+        np.add.at(gamma[t], paths[:, t], post)
+    for t in range(T - 1):
+        np.add.at(xi, (paths[:, t], paths[:, t + 1]), post)
+    best = int(np.argmax(lp))
+    return dict(logL=logL, gamma=gamma, xi_sum=xi,
+                map_path=paths[best].astype(np.int32), map_score=float(lp[best]),
+                all_scores=lp, paths=paths)
