@@ -1,0 +1,240 @@
+/*
+ * hmmgpu -- C ABI of the GB300 (sm_103a) hidden-Markov-model hot path.
+ *
+ * The library implements, on one GPU, the data-parallel hot path of the HMM
+ * method of "libhmm: A Modern C++20 Library for Hidden Markov Models with
+ * Correct MLE Emission M-Steps" (arXiv 2605.29208):
+ *   - emission log-densities log b_j(y_t)              (paper Sec. 4.1-4.5)
+ *   - log-space forward / backward recursions           (Sec. 3.2, Eq. 1-2)
+ *   - posteriors gamma_t(j), xi_t(i,j)                  (Sec. 3.1, 3.4)
+ *   - weighted sufficient statistics and the M-steps    (Sec. 4, Eq. 5-24)
+ *   - Baum-Welch iterations (fit)
+ *   - max-plus Viterbi with backpointer traceback       (Sec. 3.3, Eq. 3-4)
+ *
+ * Conventions (every entry point):
+ *   - Returns hmm_status; never throws or aborts across the ABI.  On error
+ *     hmm_last_error() gives a thread-local message.
+ *   - Pointers named d_* / inside hmm_batch are DEVICE pointers owned by the
+ *     caller (e.g. torch.Tensor.data_ptr()); pointers named h_* are host
+ *     pointers owned by the caller.  Handles (hmm_ctx, hmm_model, hmm_stats,
+ *     hmm_plan) are owned by the library: create/destroy pairs.
+ *   - Work is enqueued on the given CUDA stream (0 = legacy default stream);
+ *     device outputs are valid once that stream has synchronised.  Calls
+ *     that return host data synchronise the stream themselves.
+ *   - Asynchronous numeric problems (NaN observations, zero-probability
+ *     sequences) are reported through the per-sequence log-likelihood
+ *     (-inf or NaN) and hmm_ctx_status().
+ *
+ * Layouts:
+ *   - Packed ragged batch: values[total_T * dim] row-major float32 (all
+ *     sequences concatenated), offsets[n_seq + 1] int64 (sequence s covers
+ *     rows offsets[s] .. offsets[s+1]-1; offsets[0] = 0,
+ *     offsets[n_seq] = total_T, non-decreasing), model_id[n_seq] int32 in
+ *     [0, n_models).  Empty sequences (length 0) are allowed and get
+ *     log-likelihood 0.
+ *   - Per-time-step outputs (gamma, logb) are [total_T][n_states] row-major
+ *     float32 in the same row order as the batch.
+ *   - Parameter blob (float64, host): the models one after another; model m
+ *     holds pi[N], A[N][N] (row-stochastic, a_ij = P(q_{t+1}=j | q_t=i)),
+ *     then for each state j its family parameters (hmm_family_param_count).
+ */
+#ifndef HMMGPU_H
+#define HMMGPU_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  HMM_OK = 0,
+  HMM_E_ARG = 1,          /* invalid argument (null pointer, bad size, bad family) */
+  HMM_E_NOMEM = 2,        /* device or host allocation failed                       */
+  HMM_E_CUDA = 3,         /* a CUDA runtime call failed (message has the details)   */
+  HMM_E_NUMERIC = 4,      /* non-finite result detected                              */
+  HMM_E_TIMEOUT = 5,      /* a bounded device wait expired                           */
+  HMM_E_BUSY = 6,         /* server queue full                                       */
+  HMM_E_NOTREADY = 7,     /* server request still pending                            */
+  HMM_E_UNSUPPORTED = 8   /* valid request outside what this build implements        */
+} hmm_status;
+
+/* Emission families (paper Sec. 4).  Parameters per state, in blob order:
+ *   HMM_GAUSS       mu, sigma2                          (Sec. 4.1)
+ *   HMM_POISSON     lambda                              (Sec. 4.1)
+ *   HMM_GAMMA       alpha (shape), beta (RATE)          (Sec. 4.2, Eq. 7-8)
+ *   HMM_BETA        a, b                                (Sec. 4.2, Eq. 9-10)
+ *   HMM_WEIBULL     k (shape), lambda (scale)           (Sec. 4.2, Eq. 11)
+ *   HMM_NEGBIN      r, p     (mean r(1-p)/p)            (Sec. 4.2)
+ *   HMM_STUDENT_T   mu, sigma2, nu                      (Sec. 4.3, Eq. 13-19)
+ *   HMM_VONMISES    mu, kappa                           (Sec. 4.1-4.2, Eq. 12)
+ *   HMM_DIAG_GAUSS  mu[D], var[D]                       (Sec. 4.5, Eq. 20-21)
+ *   HMM_FULL_GAUSS  mu[D], cov[D][D]                    (Sec. 4.5, Eq. 22-24)
+ * Observations outside a family's support (y <= 0 for Gamma/Weibull,
+ * y outside (0,1) for Beta, non-integer or negative counts) have density 0. */
+typedef enum {
+  HMM_GAUSS = 0, HMM_POISSON = 1, HMM_GAMMA = 2, HMM_BETA = 3, HMM_WEIBULL = 4,
+  HMM_NEGBIN = 5, HMM_STUDENT_T = 6, HMM_VONMISES = 7, HMM_DIAG_GAUSS = 8,
+  HMM_FULL_GAUSS = 9
+} hmm_family;
+
+typedef struct hmm_ctx_s* hmm_ctx;       /* device + workspace            */
+typedef struct hmm_model_s* hmm_model;   /* M models x N states on device */
+typedef struct hmm_stats_s* hmm_stats;   /* FP64 sufficient statistics    */
+typedef struct hmm_plan_s* hmm_plan;     /* host-side schedule of a batch */
+
+typedef struct {
+  const float* values;        /* device [total_T * dim]                        */
+  const int64_t* offsets;     /* device [n_seq + 1]                            */
+  const int32_t* model_id;    /* device [n_seq]                                */
+  int64_t n_seq;
+  int64_t total_T;
+  int32_t dim;                /* 1 for scalar families, D for multivariate     */
+  hmm_plan plan;              /* optional (may be NULL): a plan made by
+                                 hmm_plan_create for exactly this batch; without
+                                 one each call copies offsets/model_id to the
+                                 host and plans on the fly (synchronous).     */
+} hmm_batch;
+
+/* Options of the M-step (paper Sec. 4).  Zero-initialised fields take the
+ * defaults given in brackets. */
+typedef struct {
+  double collapse_eps;   /* [1e-8]  Sec. 4.4: N_j below this keeps theta_j      */
+  double tikhonov_eps;   /* [1e-6]  Sec. 4.5: Sigma + eps I                     */
+  int32_t newton_maxit;  /* [50]    Newton iterations (Gamma/Beta/Weibull/...)  */
+  double newton_tol;     /* [1e-10] |d theta| <= tol * max(1, |theta|)          */
+  int32_t nu_mode;       /* [0]     Student-t nu equation: 0 = ECM equation with
+                                    the E[log U] constant, 1 = Eq. 18 as printed */
+  int32_t update_transitions; /* [1 when the struct is NULL] 0 keeps pi and A    */
+} hmm_mstep_opts;
+
+typedef struct {
+  int32_t max_iter;      /* number of Baum-Welch iterations                      */
+  double tol;            /* stop when |dlogL| <= tol * |logL| (0: run max_iter)  */
+  hmm_mstep_opts mstep;
+} hmm_fit_opts;
+
+/* ---------------------------------------------------------------- basics */
+const char* hmm_status_string(hmm_status s);
+/* Thread-local text of the last error raised by a call on this thread. */
+const char* hmm_last_error(void);
+/* Library version string. */
+const char* hmm_version(void);
+
+/* Number of float64 parameters of ONE state of a family with dimension dim
+ * (see hmm_family); -1 for an unknown family. */
+int32_t hmm_family_param_count(int32_t family, int32_t dim);
+/* Total size in float64 values of the parameter blob of n_models models. */
+int64_t hmm_param_blob_size(int32_t n_models, int32_t n_states, int32_t dim,
+                            const int32_t* h_family);
+
+/* ------------------------------------------------------------ context */
+/* Creates a context on CUDA device `device`.  workspace_bytes is an initial
+ * reservation (0: grow on demand).  The context owns its scratch memory. */
+hmm_status hmm_ctx_create(int device, size_t workspace_bytes, hmm_ctx* out);
+hmm_status hmm_ctx_destroy(hmm_ctx ctx);
+/* Sticky device-side status word (HMM_OK or the first error raised by a
+ * kernel since the last call); synchronises `stream`, then clears it. */
+hmm_status hmm_ctx_status(hmm_ctx ctx, void* stream);
+
+/* -------------------------------------------------------------- models */
+/* n_models models of n_states states with observation dimension dim; the
+ * family of model m is h_family[m] (host array).  Multivariate families need
+ * dim >= 1, scalar families dim == 1.  State counts up to 1024. */
+hmm_status hmm_model_create(hmm_ctx ctx, int32_t n_models, int32_t n_states,
+                            int32_t dim, const int32_t* h_family, hmm_model* out);
+hmm_status hmm_model_destroy(hmm_model model);
+/* Copies the float64 parameter blob (layout above, n_values entries) to the
+ * device and refreshes the derived single-precision tables. */
+hmm_status hmm_model_set_params(hmm_model model, const double* h_blob, int64_t n_values);
+/* Copies the current parameters back (synchronises the model's last stream). */
+hmm_status hmm_model_get_params(hmm_model model, double* h_blob, int64_t n_values);
+
+/* ---------------------------------------------------------------- plans */
+/* Builds the schedule of a batch (processing order by family and length,
+ * the per-model sequence lists used for the deterministic reductions).
+ * h_offsets / h_model_id are host copies of the batch arrays. */
+hmm_status hmm_plan_create(hmm_ctx ctx, hmm_model model, const hmm_batch* batch,
+                           const int64_t* h_offsets, const int32_t* h_model_id,
+                           hmm_plan* out);
+hmm_status hmm_plan_destroy(hmm_plan plan);
+
+/* ------------------------------------------------------------ inference */
+/* Emission log-densities log b_j(y_t) (natural log) of every row of the batch
+ * under the model of its sequence: d_logb [total_T][n_states].
+ * Paper Sec. 4.1-4.5 (densities), used by Eq. 1-4. */
+hmm_status hmm_emission_logpdf(hmm_ctx ctx, hmm_model model, const hmm_batch* batch,
+                               float* d_logb, void* stream);
+
+/* Forward-backward in log space (Sec. 3.2, Eq. 1-2): per-sequence
+ * log-likelihood d_loglik[n_seq] (float64, natural log), and optionally the
+ * occupancies gamma_t(j) (d_gamma [total_T][n_states], may be NULL) and the
+ * posterior decoding argmax_j gamma_t(j) (Sec. 3.4; d_post_path [total_T]
+ * int32, may be NULL; ties -> lowest j).  d_logb may be NULL (emissions
+ * evaluated in the kernel from the model) or a [total_T][n_states] natural-log
+ * table that replaces the model's emissions. */
+hmm_status hmm_forward_backward(hmm_ctx ctx, hmm_model model, const hmm_batch* batch,
+                                const float* d_logb, float* d_gamma,
+                                int32_t* d_post_path, double* d_loglik, void* stream);
+
+/* Max-plus Viterbi (Sec. 3.3, Eq. 3-4) with backpointer traceback:
+ * d_path [total_T] int32 states, d_score [n_seq] float64 (natural log of the
+ * best path's joint probability).  Ties: lowest predecessor index, lowest
+ * final state.  d_logb as in hmm_forward_backward; with a table the decode
+ * uses only float32 additions, subtractions and comparisons of that table and
+ * the model's float32 log pi / log A. */
+hmm_status hmm_viterbi(hmm_ctx ctx, hmm_model model, const hmm_batch* batch,
+                       const float* d_logb, int32_t* d_path, double* d_score,
+                       void* stream);
+
+/* ------------------------------------------------------------ training */
+hmm_status hmm_stats_create(hmm_ctx ctx, hmm_model model, hmm_stats* out);
+hmm_status hmm_stats_destroy(hmm_stats stats);
+/* Layout of the canonical statistics returned by hmm_stats_get, per model m
+ * (float64): n_seq, sum of logL, then per state j: gamma1_j (sum over
+ * sequences of gamma_1(j)), then the N x N matrix sum_t xi_t(i,j), then per
+ * state j the family sums (Sec. 4, weights gamma_t(j)):
+ *   GAUSS     W, Wy, Wy^2         POISSON  W, Wy
+ *   GAMMA     W, Wy, W log y, Wy^2
+ *   BETA      W, Wy, Wy^2, W log y, W log(1-y)
+ *   WEIBULL   W, W log y, W (log y)^2
+ *   NEGBIN    W, Wy, Wy^2
+ *   STUDENT_T W, Wu, Wuy, Wuy^2, W(log u - u)   (u of Eq. 14, current params)
+ *   VONMISES  W, W cos y, W sin y
+ *   DIAG_GAUSS W, Wy_d (D), Wy_d^2 (D)
+ *   FULL_GAUSS W, Wy_d (D), Wy_d y_e (D*D)
+ * where W = sum_t gamma_t(j) (x) and x the named function of y_t. */
+int64_t hmm_stats_size(hmm_stats stats);
+hmm_status hmm_stats_get(hmm_stats stats, double* h_out, int64_t n_values);
+
+/* E-step over a batch (Sec. 3.2 + Sec. 4, Eq. 5): fills `stats` with the
+ * weighted sufficient statistics of every model and writes per-sequence
+ * log-likelihoods to d_loglik [n_seq] (may be NULL).  The reductions are in
+ * a fixed order (bitwise reproducible). */
+hmm_status hmm_estep_stats(hmm_ctx ctx, hmm_model model, const hmm_batch* batch,
+                           hmm_stats stats, double* d_loglik, void* stream);
+
+/* M-step (Sec. 4, Eq. 6 with the closed forms, Newton-Raphson and ECM
+ * steps of Sec. 4.1-4.5, the Sec. 4.4 collapse guard, and the transition /
+ * initial-distribution update) from `stats`, in place on `model`.
+ * `batch` is needed only by families whose Newton step re-reads the data
+ * (Weibull shape, negative-binomial r); it may be NULL otherwise.  opts may
+ * be NULL for the defaults. */
+hmm_status hmm_mstep(hmm_ctx ctx, hmm_model model, hmm_stats stats,
+                     const hmm_batch* batch, const hmm_mstep_opts* opts, void* stream);
+
+/* max_iter Baum-Welch iterations (E-step, then M-step) on the batch, in place
+ * on `model`.  h_loglik_trace (host, may be NULL) receives, for every
+ * iteration k, the sum of log-likelihoods of each model under the parameters
+ * entering iteration k: [max_iter][n_models].  *iters_done (may be NULL) gets
+ * the number of iterations run.  The iterations run as one captured CUDA
+ * graph replay per iteration when tol == 0. */
+hmm_status hmm_fit(hmm_ctx ctx, hmm_model model, const hmm_batch* batch,
+                   const hmm_fit_opts* opts, double* h_loglik_trace,
+                   int32_t* iters_done, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HMMGPU_H */

@@ -1,0 +1,286 @@
+"""hmmgpu: the data-parallel HMM hot path (Baum-Welch and Viterbi) on a
+GB300 GPU (sm_103a), behind a C ABI (include/hmmgpu.h).
+
+This module is argument marshalling only: every step of the computation
+runs in the CUDA kernels of ``libhmmgpu.so``.  PyTorch supplies device
+memory and streams.  There is no CPU fallback: importing the wrappers on a
+machine without the built library, or calling them without a GPU, raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+
+from . import _lib
+from ._lib import FAMILY, HmmError, check
+
+__all__ = ["Context", "Model", "Batch", "FAMILY", "HmmError", "blob_from_model",
+           "model_from_blob"]
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _ptr(t):
+    return C.c_void_p(0 if t is None else t.data_ptr())
+
+
+def _stream(stream):
+    torch = _torch()
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream)
+
+
+PARAM_ORDER = {
+    "gauss": ("mu", "sigma2"), "poisson": ("lam",), "gamma": ("alpha", "beta"),
+    "beta": ("a", "b"), "weibull": ("k", "lam"), "negbin": ("r", "p"),
+    "student_t": ("mu", "sigma2", "nu"), "vonmises": ("mu", "kappa"),
+    "diag_gauss": ("mu", "var"), "full_gauss": ("mu", "cov"),
+}
+
+
+def blob_from_model(model: dict) -> np.ndarray:
+    """Flattens a model dict {family, pi, A, params} into the C-ABI blob
+    (pi, A, then per state its family parameters)."""
+    N = len(model["pi"])
+    parts = [np.asarray(model["pi"], np.float64).ravel(), np.asarray(model["A"], np.float64).ravel()]
+    fam = model["family"]
+    per_state = []
+    for j in range(N):
+        for name in PARAM_ORDER[fam]:
+            per_state.append(np.asarray(model["params"][name][j], np.float64).ravel())
+    parts.extend(per_state)
+    return np.concatenate(parts)
+
+
+def model_from_blob(blob: np.ndarray, family: str, N: int, D: int = 1) -> tuple[dict, int]:
+    """Inverse of blob_from_model; returns (model, values consumed)."""
+    q = 0
+    pi = blob[q:q + N].copy(); q += N
+    A = blob[q:q + N * N].reshape(N, N).copy(); q += N * N
+    names = PARAM_ORDER[family]
+    sizes = {"mu": D if family in ("diag_gauss", "full_gauss") else 1,
+             "var": D, "cov": D * D}
+    params = {n: [] for n in names}
+    for j in range(N):
+        for n in names:
+            k = sizes.get(n, 1) if family in ("diag_gauss", "full_gauss") else 1
+            v = blob[q:q + k]; q += k
+            params[n].append(v.reshape(D, D) if n == "cov" else (v if k > 1 else v[0]))
+    params = {n: np.array(v) for n, v in params.items()}
+    return dict(family=family, pi=pi, A=A, params=params), q
+
+
+class Context:
+    """A CUDA device context of the library (owns its scratch memory)."""
+
+    def __init__(self, device: int = 0, workspace_bytes: int = 0):
+        self.lib = _lib.load()
+        h = C.c_void_p()
+        check(self.lib.hmm_ctx_create(device, workspace_bytes, C.byref(h)))
+        self.h = h
+        self.device = device
+
+    def close(self):
+        if self.h:
+            self.lib.hmm_ctx_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def status(self, stream=None):
+        return self.lib.hmm_ctx_status(self.h, _stream(stream))
+
+
+class Model:
+    """M models x N states on the device; ``models`` is a list of model dicts
+    that share N (and D)."""
+
+    def __init__(self, ctx: Context, models: list[dict]):
+        self.ctx, self.lib = ctx, ctx.lib
+        self.families = [m["family"] for m in models]
+        self.N = len(models[0]["pi"])
+        mu = models[0]["params"].get("mu")
+        self.D = (np.asarray(mu).shape[1] if self.families[0] in ("diag_gauss", "full_gauss") else 1)
+        fam = np.array([FAMILY[f] for f in self.families], np.int32)
+        h = C.c_void_p()
+        check(self.lib.hmm_model_create(ctx.h, len(models), self.N, self.D,
+                                        fam.ctypes.data_as(C.c_void_p), C.byref(h)))
+        self.h = h
+        self._fam = fam
+        self.set(models)
+
+    @property
+    def n_models(self):
+        return len(self.families)
+
+    def blob_size(self):
+        return self.lib.hmm_param_blob_size(self.n_models, self.N, self.D,
+                                            self._fam.ctypes.data_as(C.c_void_p))
+
+    def set(self, models: list[dict]):
+        blob = np.concatenate([blob_from_model(m) for m in models])
+        check(self.lib.hmm_model_set_params(self.h, blob.ctypes.data_as(C.c_void_p), blob.size))
+
+    def get(self) -> list[dict]:
+        n = self.blob_size()
+        blob = np.empty(n, np.float64)
+        check(self.lib.hmm_model_get_params(self.h, blob.ctypes.data_as(C.c_void_p), n))
+        out, q = [], 0
+        for f in self.families:
+            m, used = model_from_blob(blob[q:], f, self.N, self.D)
+            out.append(m)
+            q += used
+        return out
+
+    def close(self):
+        if self.h:
+            self.lib.hmm_model_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """A packed ragged batch resident on the device (float32 values, int64
+    offsets, int32 model ids) with an optional plan."""
+
+    def __init__(self, values, offsets, model_id, device="cuda", dim=1):
+        torch = _torch()
+        self.values = torch.as_tensor(np.asarray(values, np.float32)).to(device).contiguous()
+        self.offsets = torch.as_tensor(np.asarray(offsets, np.int64)).to(device).contiguous()
+        self.model_id = torch.as_tensor(np.asarray(model_id, np.int32)).to(device).contiguous()
+        self.h_offsets = np.ascontiguousarray(offsets, np.int64)
+        self.h_model_id = np.ascontiguousarray(model_id, np.int32)
+        self.n_seq = len(self.h_offsets) - 1
+        self.total_T = int(self.h_offsets[-1]) if self.n_seq >= 0 else 0
+        self.dim = dim
+        self.plan = None
+        self._lib = None
+
+    def c(self):
+        return _lib.hmm_batch(self.values.data_ptr() if self.values.numel() else None,
+                              self.offsets.data_ptr(), self.model_id.data_ptr() if self.n_seq else None,
+                              self.n_seq, self.total_T, self.dim, self.plan)
+
+    def make_plan(self, ctx: Context, model: Model):
+        b = self.c()
+        h = C.c_void_p()
+        check(ctx.lib.hmm_plan_create(ctx.h, model.h, C.byref(b),
+                                      self.h_offsets.ctypes.data_as(C.c_void_p),
+                                      self.h_model_id.ctypes.data_as(C.c_void_p), C.byref(h)))
+        self.plan = h
+        self._lib = ctx.lib
+        return self
+
+    def __del__(self):
+        try:
+            if self.plan and self._lib:
+                self._lib.hmm_plan_destroy(self.plan)
+        except Exception:
+            pass
+
+
+# ------------------------------------------------------------------ calls
+def emission_logpdf(ctx, model, batch, out=None, stream=None):
+    torch = _torch()
+    if out is None:
+        out = torch.empty((batch.total_T, model.N), dtype=torch.float32, device=batch.values.device)
+    b = batch.c()
+    check(ctx.lib.hmm_emission_logpdf(ctx.h, model.h, C.byref(b), _ptr(out), _stream(stream)))
+    return out
+
+
+def forward_backward(ctx, model, batch, logb=None, want_gamma=True, want_path=False, stream=None):
+    torch = _torch()
+    dev = batch.values.device
+    ll = torch.empty(batch.n_seq, dtype=torch.float64, device=dev)
+    gamma = torch.empty((batch.total_T, model.N), dtype=torch.float32, device=dev) if want_gamma else None
+    path = torch.empty(batch.total_T, dtype=torch.int32, device=dev) if want_path else None
+    b = batch.c()
+    check(ctx.lib.hmm_forward_backward(ctx.h, model.h, C.byref(b), _ptr(logb), _ptr(gamma), _ptr(path),
+                                       _ptr(ll), _stream(stream)))
+    return ll, gamma, path
+
+
+def viterbi(ctx, model, batch, logb=None, stream=None):
+    torch = _torch()
+    dev = batch.values.device
+    path = torch.empty(batch.total_T, dtype=torch.int32, device=dev)
+    score = torch.empty(batch.n_seq, dtype=torch.float64, device=dev)
+    b = batch.c()
+    check(ctx.lib.hmm_viterbi(ctx.h, model.h, C.byref(b), _ptr(logb), _ptr(path), _ptr(score),
+                              _stream(stream)))
+    return path, score
+
+
+class Stats:
+    def __init__(self, ctx, model):
+        self.lib = ctx.lib
+        h = C.c_void_p()
+        check(self.lib.hmm_stats_create(ctx.h, model.h, C.byref(h)))
+        self.h = h
+
+    def get(self) -> np.ndarray:
+        n = self.lib.hmm_stats_size(self.h)
+        out = np.empty(n, np.float64)
+        check(self.lib.hmm_stats_get(self.h, out.ctypes.data_as(C.c_void_p), n))
+        return out
+
+    def __del__(self):
+        try:
+            self.lib.hmm_stats_destroy(self.h)
+        except Exception:
+            pass
+
+
+def estep_stats(ctx, model, batch, stats=None, stream=None):
+    torch = _torch()
+    stats = stats or Stats(ctx, model)
+    ll = torch.empty(batch.n_seq, dtype=torch.float64, device=batch.values.device)
+    b = batch.c()
+    check(ctx.lib.hmm_estep_stats(ctx.h, model.h, C.byref(b), stats.h, _ptr(ll), _stream(stream)))
+    return stats, ll
+
+
+def mstep_opts(nu_mode=0, update_transitions=1, **kw):
+    o = _lib.hmm_mstep_opts()
+    o.collapse_eps = kw.get("collapse_eps", 0.0)
+    o.tikhonov_eps = kw.get("tikhonov_eps", 0.0)
+    o.newton_maxit = kw.get("newton_maxit", 0)
+    o.newton_tol = kw.get("newton_tol", 0.0)
+    o.nu_mode = nu_mode
+    o.update_transitions = update_transitions
+    return o
+
+
+def mstep(ctx, model, stats, batch=None, opts=None, stream=None):
+    o = opts or mstep_opts()
+    b = batch.c() if batch is not None else None
+    check(ctx.lib.hmm_mstep(ctx.h, model.h, stats.h, C.byref(b) if b is not None else None,
+                            C.byref(o), _stream(stream)))
+
+
+def fit(ctx, model, batch, n_iter, tol=0.0, opts=None, stream=None):
+    o = _lib.hmm_fit_opts()
+    o.max_iter = n_iter
+    o.tol = tol
+    o.mstep = opts or mstep_opts()
+    trace = np.zeros((max(n_iter, 1), model.n_models), np.float64)
+    done = C.c_int32(0)
+    b = batch.c()
+    check(ctx.lib.hmm_fit(ctx.h, model.h, C.byref(b), C.byref(o), trace.ctypes.data_as(C.c_void_p),
+                          C.byref(done), _stream(stream)))
+    return trace[:done.value], done.value

@@ -1,0 +1,107 @@
+"""ctypes declarations of the hmmgpu C ABI (include/hmmgpu.h)."""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+from . import build as _build
+
+HMM_OK = 0
+STATUS_NAMES = {0: "HMM_OK", 1: "HMM_E_ARG", 2: "HMM_E_NOMEM", 3: "HMM_E_CUDA",
+                4: "HMM_E_NUMERIC", 5: "HMM_E_TIMEOUT", 6: "HMM_E_BUSY",
+                7: "HMM_E_NOTREADY", 8: "HMM_E_UNSUPPORTED"}
+
+FAMILY = {"gauss": 0, "poisson": 1, "gamma": 2, "beta": 3, "weibull": 4, "negbin": 5,
+          "student_t": 6, "vonmises": 7, "diag_gauss": 8, "full_gauss": 9}
+
+
+class hmm_batch(C.Structure):
+    _fields_ = [("values", C.c_void_p), ("offsets", C.c_void_p), ("model_id", C.c_void_p),
+                ("n_seq", C.c_int64), ("total_T", C.c_int64), ("dim", C.c_int32),
+                ("plan", C.c_void_p)]
+
+
+class hmm_mstep_opts(C.Structure):
+    _fields_ = [("collapse_eps", C.c_double), ("tikhonov_eps", C.c_double),
+                ("newton_maxit", C.c_int32), ("newton_tol", C.c_double),
+                ("nu_mode", C.c_int32), ("update_transitions", C.c_int32)]
+
+
+class hmm_fit_opts(C.Structure):
+    _fields_ = [("max_iter", C.c_int32), ("tol", C.c_double), ("mstep", hmm_mstep_opts)]
+
+
+# name -> (restype, argtypes)
+_SIGS = {
+    "hmm_status_string": (C.c_char_p, [C.c_int]),
+    "hmm_last_error": (C.c_char_p, []),
+    "hmm_version": (C.c_char_p, []),
+    "hmm_family_param_count": (C.c_int32, [C.c_int32, C.c_int32]),
+    "hmm_param_blob_size": (C.c_int64, [C.c_int32, C.c_int32, C.c_int32, C.c_void_p]),
+    "hmm_ctx_create": (C.c_int, [C.c_int, C.c_size_t, C.POINTER(C.c_void_p)]),
+    "hmm_ctx_destroy": (C.c_int, [C.c_void_p]),
+    "hmm_ctx_status": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "hmm_model_create": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_int32, C.c_void_p,
+                                   C.POINTER(C.c_void_p)]),
+    "hmm_model_destroy": (C.c_int, [C.c_void_p]),
+    "hmm_model_set_params": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64]),
+    "hmm_model_get_params": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64]),
+    "hmm_plan_create": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(hmm_batch), C.c_void_p,
+                                  C.c_void_p, C.POINTER(C.c_void_p)]),
+    "hmm_plan_destroy": (C.c_int, [C.c_void_p]),
+    "hmm_emission_logpdf": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(hmm_batch), C.c_void_p,
+                                      C.c_void_p]),
+    "hmm_forward_backward": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(hmm_batch), C.c_void_p,
+                                       C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "hmm_viterbi": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(hmm_batch), C.c_void_p,
+                              C.c_void_p, C.c_void_p, C.c_void_p]),
+    "hmm_stats_create": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_void_p)]),
+    "hmm_stats_destroy": (C.c_int, [C.c_void_p]),
+    "hmm_stats_size": (C.c_int64, [C.c_void_p]),
+    "hmm_stats_get": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64]),
+    "hmm_estep_stats": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(hmm_batch), C.c_void_p,
+                                  C.c_void_p, C.c_void_p]),
+    "hmm_mstep": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(hmm_batch),
+                            C.POINTER(hmm_mstep_opts), C.c_void_p]),
+    "hmm_fit": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(hmm_batch), C.POINTER(hmm_fit_opts),
+                          C.c_void_p, C.POINTER(C.c_int32), C.c_void_p]),
+}
+
+# every symbol the header declares (checked by the not-gpu tests)
+EXPORTED = tuple(_SIGS)
+
+_lib = None
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = False):
+    """Loads libhmmgpu.so; raises if it has not been built (no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = lib_path()
+    if not os.path.exists(path):
+        if not build_if_missing:
+            raise ImportError(f"hmmgpu library not built ({path}); run paper_2605_29208_gb300.build.build()")
+        _build.build()
+    lib = C.CDLL(path)
+    for name, (res, args) in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+class HmmError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+def check(status: int):
+    if status != HMM_OK:
+        raise HmmError(status, _lib.hmm_last_error().decode())

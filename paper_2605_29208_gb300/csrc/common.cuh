@@ -1,0 +1,204 @@
+// Shared device-side definitions of the hmmgpu library (sm_103a).
+//
+// Units: inside the kernels every log-quantity is kept in base 2
+// (log2 b_j(y), log2 a_ij) so that exponentials are single ex2 operations;
+// results leave the library in natural-log units (x ln 2 in float64).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/hmmgpu.h"
+
+namespace hmm {
+
+constexpr double kLn2 = 0.69314718055994530942;
+constexpr double kLog2e = 1.44269504088896340736;
+constexpr float kLog2ef = 1.44269504088896340736f;
+constexpr float kLn2f = 0.69314718055994530942f;
+
+// Emission coefficients per (model, state), float32, log2 units.
+constexpr int KC = 8;
+// Sufficient-statistic slots per state accumulated by the E-step kernels
+// (family sums, slot NST-1 holds gamma_1).
+constexpr int NST = 6;
+// Negative-binomial log2 table: lgamma(y+r) - lgamma(r) - lgamma(y+1) in
+// log2 units for integer y < NB_YMAX, computed in float64 per (model, state).
+constexpr int NB_YMAX = 512;
+// log2(y!) table for integer y < LF_YMAX (Poisson), float64 -> float32.
+constexpr int LF_YMAX = 1024;
+
+// Device status word bits (sticky, read by hmm_ctx_status).
+enum : int {
+  ST_NUMERIC = 1,      // non-finite value met in a recursion
+  ST_TIMEOUT = 2,      // bounded wait expired
+  ST_ARG = 4           // inconsistent batch (offsets) seen by a kernel
+};
+
+// Read-only view of the device-resident models used by all kernels.
+struct ModelView {
+  int M;              // models
+  int N;              // states (real)
+  int NP;             // states padded to the kernel size (>= N)
+  int D;              // observation dimension
+  const int* family;  // [M]
+  const float* A32;   // [M][NP][NP] linear a_ij (padded entries 0)
+  const float* logA2; // [M][NP][NP] log2 a_ij (-inf for 0)
+  const float* logAe; // [M][NP][NP] ln a_ij as float32 (table-mode Viterbi)
+  const float* pi32;  // [M][NP]
+  const float* logpi2;// [M][NP]
+  const float* logpie;// [M][NP]
+  const float* coef;  // [M][NP][KC]
+  const float* nbtab; // [M][NP][NB_YMAX] or nullptr
+  const float* lfact2;// [LF_YMAX] log2(y!)
+};
+
+__device__ __forceinline__ float ex2f(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+__device__ __forceinline__ float rcpf(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// floor(log2(x)) of a positive normal float from its exponent bits; for 0
+// and denormals it gives -127 (the value is only used to pick a shift).
+__device__ __forceinline__ float ilog2f(float x) {
+  return (float)(int)((__float_as_uint(x) >> 23) & 0xffu) - 127.0f;
+}
+
+// Reads an NP-float row of shared memory (16-byte aligned for NP >= 4).
+template <int NP>
+__device__ __forceinline__ void load_row(const float* src, float* dst) {
+  if constexpr (NP % 4 == 0) {
+#pragma unroll
+    for (int i = 0; i < NP; i += 4) {
+      const float4 t4 = *reinterpret_cast<const float4*>(src + i);
+      dst[i] = t4.x;
+      dst[i + 1] = t4.y;
+      dst[i + 2] = t4.z;
+      dst[i + 3] = t4.w;
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < NP; i += 2) {
+      const float2 t2 = *reinterpret_cast<const float2*>(src + i);
+      dst[i] = t2.x;
+      dst[i + 1] = t2.y;
+    }
+  }
+}
+
+template <int W>
+__device__ __forceinline__ float group_max(float v) {
+#pragma unroll
+  for (int o = W / 2; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o, W));
+  return v;
+}
+
+template <int W>
+__device__ __forceinline__ float group_sum(float v) {
+#pragma unroll
+  for (int o = W / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o, W);
+  return v;
+}
+
+__device__ __forceinline__ void set_status(int* status, int bit) {
+  if (status) atomicOr(status, bit);
+}
+
+// ---------------------------------------------------------------------------
+// Emission evaluation.  Per time step a few "features" of y_t are computed
+// once and shared by all states; each state then costs 2-5 FP32 operations.
+// ---------------------------------------------------------------------------
+struct Feat {
+  float y;      // observation
+  float a;      // family feature 1 (see feat_of)
+  float b;      // family feature 2
+  bool ok;      // y inside the family's support
+};
+
+__device__ __forceinline__ bool is_count(float y) { return y >= 0.f && floorf(y) == y; }
+
+__device__ __forceinline__ Feat feat_of(int fam, float y, const float* __restrict__ lfact2) {
+  Feat f;
+  f.y = y;
+  f.a = 0.f;
+  f.b = 0.f;
+  f.ok = true;
+  switch (fam) {
+    case HMM_GAUSS:
+    case HMM_STUDENT_T:
+      f.ok = (y == y);
+      break;
+    case HMM_POISSON:
+    case HMM_NEGBIN: {
+      f.ok = is_count(y);
+      if (f.ok) {
+        int yi = (int)fminf(y, 2.0e9f);
+        f.a = (yi < LF_YMAX) ? __ldg(lfact2 + yi) : lgammaf(y + 1.0f) * kLog2ef;  // log2 y!
+      }
+      break;
+    }
+    case HMM_GAMMA:
+    case HMM_WEIBULL:
+      f.ok = y > 0.f;
+      f.a = log2f(y);
+      break;
+    case HMM_BETA:
+      f.ok = (y > 0.f) && (y < 1.f);
+      f.a = log2f(y);
+      f.b = log2f(1.0f - y);
+      break;
+    case HMM_VONMISES:
+      f.ok = (y == y);
+      sincosf(y, &f.b, &f.a);  // a = cos y, b = sin y
+      break;
+    default:
+      break;
+  }
+  return f;
+}
+
+// log2 b_j(y) of one state from its coefficients c[0..KC) (log2 units).
+// For the negative binomial `nbt` points at the state's table.
+__device__ __forceinline__ float emis_log2(int fam, const Feat& f, const float* c,
+                                           const float* __restrict__ nbt) {
+  switch (fam) {
+    case HMM_GAUSS: {            // c2 - ((y - mu) * c1)^2
+      float z = (f.y - c[0]) * c[1];
+      return fmaf(-z, z, c[2]);
+    }
+    case HMM_POISSON:            // y log2 lam - lam log2e - log2 y!
+      return fmaf(f.y, c[0], c[1]) - f.a;
+    case HMM_GAMMA:              // (alpha-1) log2 y - beta log2e y + const
+      return fmaf(c[0], f.a, fmaf(c[1], f.y, c[2]));
+    case HMM_BETA:
+      return fmaf(c[0], f.a, fmaf(c[1], f.b, c[2]));
+    case HMM_WEIBULL: {          // (k-1) log2 y + const - log2e * 2^(k log2 y - k log2 lam)
+      float e = ex2f(fmaf(c[1], f.a, c[2]));
+      return fmaf(c[0], f.a, fmaf(-kLog2ef, e, c[3]));
+    }
+    case HMM_NEGBIN: {           // table(y) + y log2(1-p) + r log2 p  (table holds -log2 y!)
+      int yi = (int)fminf(f.y, 2.0e9f);
+      float lg = (yi < NB_YMAX) ? __ldg(nbt + yi)
+                                : (lgammaf(f.y + c[2]) - c[3] - lgammaf(f.y + 1.0f)) * kLog2ef;
+      return lg + fmaf(f.y, c[0], c[1]);
+    }
+    case HMM_STUDENT_T: {        // const - (nu+1)/2 log2(1 + (y-mu)^2 / (nu sigma2))
+      float d = f.y - c[0];
+      float q = fmaf(d * c[1], d, 1.0f);
+      return fmaf(c[2], log2f(q), c[3]);
+    }
+    case HMM_VONMISES:           // kappa cos(y - mu) log2e + const
+      return fmaf(c[0], f.a, fmaf(c[1], f.b, c[2]));
+    default:
+      return 0.f;
+  }
+}
+
+}  // namespace hmm

@@ -1,0 +1,923 @@
+// Implementation of the hmmgpu C ABI (include/hmmgpu.h): contexts, models,
+// plans, the inference entry points and the Baum-Welch loop.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "launch.h"
+#include "runtime.h"
+
+namespace hmm {
+
+static thread_local std::string g_last_error;
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+template <class F>
+static hmm_status guarded(F&& f) {
+  try {
+    f();
+    return HMM_OK;
+  } catch (const Error& e) {
+    set_error(e.msg);
+    return e.st;
+  } catch (const std::exception& e) {
+    set_error(e.what());
+    return HMM_E_ARG;
+  } catch (...) {
+    set_error("unknown exception");
+    return HMM_E_ARG;
+  }
+}
+
+static int padded_states(int N) {
+  int np = 2;
+  while (np < N) np *= 2;
+  return np;
+}
+
+static int scalar_param_count(int fam) {
+  switch (fam) {
+    case HMM_GAUSS: return 2;
+    case HMM_POISSON: return 1;
+    case HMM_GAMMA: return 2;
+    case HMM_BETA: return 2;
+    case HMM_WEIBULL: return 2;
+    case HMM_NEGBIN: return 2;
+    case HMM_STUDENT_T: return 3;
+    case HMM_VONMISES: return 2;
+    default: return -1;
+  }
+}
+
+static int param_count(int fam, int D) {
+  if (fam == HMM_DIAG_GAUSS) return 2 * D;
+  if (fam == HMM_FULL_GAUSS) return D + D * D;
+  return scalar_param_count(fam);
+}
+
+static cudaStream_t S(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+// ---------------------------------------------------------------- kernels
+__global__ void post_path_kernel(const float* __restrict__ gamma, int64_t total_T, int N,
+                                 int32_t* __restrict__ path) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= total_T) return;
+  const float* g = gamma + t * N;
+  float best = g[0];
+  int arg = 0;
+  for (int j = 1; j < N; ++j)
+    if (g[j] > best) {
+      best = g[j];
+      arg = j;
+    }
+  path[t] = arg;
+}
+
+__global__ void trace_gather_kernel(const double* __restrict__ rec, int RS, int M,
+                                    double* __restrict__ trace, int* __restrict__ it) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  const int k = *it;
+  if (m < M) trace[(size_t)k * M + m] = rec[(size_t)m * RS + 1];
+}
+
+__global__ void bump_kernel(int* it) { *it += 1; }
+
+// Single-state emission log-densities of a whole batch (natural log).
+__global__ void emission_kernel(ModelView mv, const float* __restrict__ y, const int64_t* __restrict__ offsets,
+                                const int32_t* __restrict__ model_id, float* __restrict__ logb) {
+  const int s = blockIdx.x;
+  const int64_t b = offsets[s], e = offsets[s + 1];
+  const int m = model_id[s];
+  const int fam = mv.family[m];
+  const int N = mv.N, NP = mv.NP;
+  for (int64_t idx = threadIdx.x; idx < (e - b) * N; idx += blockDim.x) {
+    const int64_t t = b + idx / N;
+    const int k = (int)(idx % N);
+    const Feat f = feat_of(fam, y[t], mv.lfact2);
+    const float* c = mv.coef + ((size_t)m * NP + k) * KC;
+    const float* nbt = mv.nbtab ? mv.nbtab + ((size_t)m * NP + k) * NB_YMAX : nullptr;
+    const float l2 = f.ok ? emis_log2(fam, f, c, nbt) : -INFINITY;
+    logb[t * N + k] = l2 * kLn2f;
+  }
+}
+
+}  // namespace hmm
+
+using namespace hmm;
+
+// ================================================================ model views
+ModelBufs hmm_model_s::bufs() const {
+  ModelBufs b;
+  b.M = M;
+  b.N = N;
+  b.NP = NP;
+  b.D = D;
+  b.P = P;
+  b.family = family.as<int>();
+  b.pi = pi.as<double>();
+  b.A = A.as<double>();
+  b.theta = theta.as<double>();
+  b.A32 = A32.as<float>();
+  b.logA2 = logA2.as<float>();
+  b.logAe = logAe.as<float>();
+  b.pi32 = pi32.as<float>();
+  b.logpi2 = logpi2.as<float>();
+  b.logpie = logpie.as<float>();
+  b.coef = coef.as<float>();
+  b.nbtab = any_negbin ? nbtab.as<float>() : nullptr;
+  b.lfact2 = lfact2.as<float>();
+  return b;
+}
+
+ModelView hmm_model_s::view() const {
+  ModelView v;
+  v.M = M;
+  v.N = N;
+  v.NP = NP;
+  v.D = D;
+  v.family = family.as<int>();
+  v.A32 = A32.as<float>();
+  v.logA2 = logA2.as<float>();
+  v.logAe = logAe.as<float>();
+  v.pi32 = pi32.as<float>();
+  v.logpi2 = logpi2.as<float>();
+  v.logpie = logpie.as<float>();
+  v.coef = coef.as<float>();
+  v.nbtab = any_negbin ? nbtab.as<float>() : nullptr;
+  v.lfact2 = lfact2.as<float>();
+  return v;
+}
+
+// ================================================================ helpers
+namespace {
+
+void check_batch(hmm_model model, const hmm_batch* b) {
+  HMM_REQUIRE(b != nullptr, "batch is NULL");
+  HMM_REQUIRE(b->n_seq >= 0 && b->total_T >= 0, "negative batch sizes");
+  HMM_REQUIRE(b->n_seq < (1ll << 31) && b->total_T < (1ll << 40), "batch too large");
+  HMM_REQUIRE(b->offsets != nullptr && b->model_id != nullptr, "batch arrays are NULL");
+  HMM_REQUIRE(b->total_T == 0 || b->values != nullptr, "batch values are NULL");
+  HMM_REQUIRE(b->dim == model->D, "batch dim does not match the model");
+}
+
+// Builds a plan from host arrays.
+hmm_plan make_plan(hmm_ctx ctx, hmm_model model, const hmm_batch* b, const int64_t* ho,
+                   const int32_t* hm) {
+  const int64_t S = b->n_seq;
+  HMM_REQUIRE(S == 0 || (ho && hm), "host offsets/model_id needed for a plan");
+  if (S > 0) {
+    HMM_REQUIRE(ho[0] == 0, "offsets[0] must be 0");
+    HMM_REQUIRE(ho[S] == b->total_T, "offsets[n_seq] must equal total_T");
+  }
+  int64_t maxT = 0;
+  for (int64_t s = 0; s < S; ++s) {
+    HMM_REQUIRE(ho[s + 1] >= ho[s], "offsets must be non-decreasing");
+    HMM_REQUIRE(ho[s + 1] - ho[s] < (1ll << 30), "sequence longer than 2^30");
+    HMM_REQUIRE(hm[s] >= 0 && hm[s] < model->M, "model_id out of range");
+    maxT = std::max(maxT, ho[s + 1] - ho[s]);
+  }
+  auto* p = new hmm_plan_s();
+  try {
+    p->ctx = ctx;
+    p->n_seq = S;
+    p->total_T = b->total_T;
+    p->M = model->M;
+    p->max_T = maxT;
+    std::vector<int32_t> order(S), bym(S);
+    std::iota(order.begin(), order.end(), 0);
+    std::iota(bym.begin(), bym.end(), 0);
+    // processing order: family, then length descending (longest first)
+    std::stable_sort(order.begin(), order.end(), [&](int32_t x, int32_t y) {
+      const int fx = model->h_family[hm[x]], fy = model->h_family[hm[y]];
+      if (fx != fy) return fx < fy;
+      return (ho[x + 1] - ho[x]) > (ho[y + 1] - ho[y]);
+    });
+    std::stable_sort(bym.begin(), bym.end(), [&](int32_t x, int32_t y) { return hm[x] < hm[y]; });
+    const int CH = 64;
+    std::vector<int32_t> lo, hi, mptr(model->M + 1, 0);
+    int64_t q = 0;
+    for (int m = 0; m < model->M; ++m) {
+      mptr[m] = (int32_t)lo.size();
+      int64_t e = q;
+      while (e < S && hm[bym[e]] == m) ++e;
+      for (int64_t c = q; c < e; c += CH) {
+        lo.push_back((int32_t)c);
+        hi.push_back((int32_t)std::min<int64_t>(c + CH, e));
+      }
+      q = e;
+    }
+    mptr[model->M] = (int32_t)lo.size();
+    p->n_chunks = (int)lo.size();
+    p->order.ensure(std::max<int64_t>(S, 1) * 4);
+    p->seq_by_model.ensure(std::max<int64_t>(S, 1) * 4);
+    p->chunk_lo.ensure(std::max<size_t>(lo.size(), 1) * 4);
+    p->chunk_hi.ensure(std::max<size_t>(lo.size(), 1) * 4);
+    p->model_chunk_ptr.ensure(mptr.size() * 4);
+    if (S) {
+      HMM_CUDA(cudaMemcpy(p->order.p, order.data(), S * 4, cudaMemcpyHostToDevice));
+      HMM_CUDA(cudaMemcpy(p->seq_by_model.p, bym.data(), S * 4, cudaMemcpyHostToDevice));
+    }
+    if (!lo.empty()) {
+      HMM_CUDA(cudaMemcpy(p->chunk_lo.p, lo.data(), lo.size() * 4, cudaMemcpyHostToDevice));
+      HMM_CUDA(cudaMemcpy(p->chunk_hi.p, hi.data(), hi.size() * 4, cudaMemcpyHostToDevice));
+    }
+    HMM_CUDA(cudaMemcpy(p->model_chunk_ptr.p, mptr.data(), mptr.size() * 4, cudaMemcpyHostToDevice));
+    p->h_order = std::move(order);
+  } catch (...) {
+    p->order.release();
+    p->seq_by_model.release();
+    p->chunk_lo.release();
+    p->chunk_hi.release();
+    p->model_chunk_ptr.release();
+    delete p;
+    throw;
+  }
+  return p;
+}
+
+void destroy_plan(hmm_plan p) {
+  if (!p) return;
+  p->order.release();
+  p->seq_by_model.release();
+  p->chunk_lo.release();
+  p->chunk_hi.release();
+  p->model_chunk_ptr.release();
+  delete p;
+}
+
+// A plan for the batch: the caller's, or a temporary one built from host
+// copies of offsets and model_id (synchronous).
+struct PlanRef {
+  hmm_plan p = nullptr;
+  bool owned = false;
+  ~PlanRef() {
+    if (owned) destroy_plan(p);
+  }
+};
+
+void get_plan(hmm_ctx ctx, hmm_model model, const hmm_batch* b, cudaStream_t st, PlanRef& ref) {
+  if (b->plan) {
+    HMM_REQUIRE(b->plan->n_seq == b->n_seq && b->plan->total_T == b->total_T && b->plan->M == model->M,
+                "plan does not match the batch");
+    ref.p = b->plan;
+    ref.owned = false;
+    return;
+  }
+  std::vector<int64_t> ho(b->n_seq + 1);
+  std::vector<int32_t> hm(std::max<int64_t>(b->n_seq, 1));
+  HMM_CUDA(cudaStreamSynchronize(st));
+  HMM_CUDA(cudaMemcpy(ho.data(), b->offsets, (b->n_seq + 1) * 8, cudaMemcpyDeviceToHost));
+  if (b->n_seq) HMM_CUDA(cudaMemcpy(hm.data(), b->model_id, b->n_seq * 4, cudaMemcpyDeviceToHost));
+  ref.p = make_plan(ctx, model, b, ho.data(), hm.data());
+  ref.owned = true;
+}
+
+void require_small(hmm_model model) {
+  if (model->NP > 32)
+    throw Error{HMM_E_UNSUPPORTED, "state counts above 32 are not supported by this build"};
+  if (model->any_mv)
+    throw Error{HMM_E_UNSUPPORTED, "multivariate families need an emission table (d_logb)"};
+}
+
+// The fused E-step over a batch.  gamma (optional) receives [total_T][N].
+void run_estep(hmm_ctx ctx, hmm_model model, const hmm_batch* b, hmm_plan plan, const float* logb,
+               float* gamma, double* loglik, bool want_stats, hmm_stats stats, cudaStream_t st) {
+  const int NP = model->NP;
+  if (model->NP > 32) throw Error{HMM_E_UNSUPPORTED, "state counts above 32 are not supported"};
+  if (model->any_mv && !logb)
+    throw Error{HMM_E_UNSUPPORTED, "multivariate families need an emission table (d_logb)"};
+  const int64_t S = b->n_seq;
+  ctx->scratch.ensure(std::max<int64_t>(b->total_T, 1) * NP * 4 + 64);
+  const int F = NP + NST;
+  ctx->partials.ensure(std::max<int64_t>(S, 1) * 2 * NP * F * 4);
+  double* ll = loglik;
+  if (!ll) {
+    ctx->loglik.ensure(std::max<int64_t>(S, 1) * 8);
+    ll = ctx->loglik.as<double>();
+  }
+  if (S == 0) return;
+  EStepArgs a;
+  a.y = b->values;
+  a.logb = logb;
+  a.offsets = b->offsets;
+  a.model_id = b->model_id;
+  a.order = plan->order.as<int32_t>();
+  a.n_seq = (int32_t)S;
+  const int G = default_estep_G(NP, S, ctx->n_sm);
+  a.n_items = (int32_t)((S + estep_seqs_per_item(G) - 1) / estep_seqs_per_item(G));
+  a.mv = model->view();
+  a.scratch = ctx->scratch.as<float>();
+  a.gamma = gamma;
+  a.partials = ctx->partials.as<float>();
+  a.loglik = ll;
+  a.work_counter = ctx->counters;
+  a.status = ctx->status;
+  a.want_stats = want_stats ? 1 : 0;
+  HMM_CUDA(cudaMemsetAsync(ctx->counters, 0, sizeof(int), st));
+  HMM_CUDA(launch_estep_small(NP, G, a, logb ? 1 : 0, ctx->n_sm, st));
+  if (want_stats) {
+    const int RS = rec_size(NP);
+    ctx->chunk_rec.ensure((size_t)std::max(plan->n_chunks, 1) * RS * 8);
+    if (plan->n_chunks > 0) {
+      reduce_estep_l1<<<plan->n_chunks, 256, 0, st>>>(a.partials, ll, plan->seq_by_model.as<int32_t>(),
+                                                     plan->chunk_lo.as<int32_t>(), plan->chunk_hi.as<int32_t>(),
+                                                     NP, ctx->chunk_rec.as<double>());
+      HMM_CUDA(cudaGetLastError());
+    }
+    reduce_chunks_l2<<<model->M, 256, 0, st>>>(ctx->chunk_rec.as<double>(), plan->model_chunk_ptr.as<int32_t>(),
+                                               RS, stats->rec.as<double>());
+    HMM_CUDA(cudaGetLastError());
+    stats->valid = true;
+  }
+}
+
+MStepOpts to_opts(const hmm_mstep_opts* o) {
+  MStepOpts r;
+  r.collapse_eps = (o && o->collapse_eps > 0) ? o->collapse_eps : 1e-8;
+  r.tikhonov_eps = (o && o->tikhonov_eps > 0) ? o->tikhonov_eps : 1e-6;
+  r.newton_maxit = (o && o->newton_maxit > 0) ? o->newton_maxit : 50;
+  r.newton_tol = (o && o->newton_tol > 0) ? o->newton_tol : 1e-10;
+  r.nu_mode = o ? o->nu_mode : 0;
+  r.update_transitions = o ? o->update_transitions : 1;
+  return r;
+}
+
+void run_mstep(hmm_ctx ctx, hmm_model model, hmm_stats stats, const MStepOpts& o, cudaStream_t st) {
+  if (model->any_negbin || model->any_weibull)
+    throw Error{HMM_E_UNSUPPORTED, "Weibull / negative-binomial M-steps are not in this build"};
+  if (model->any_mv) throw Error{HMM_E_UNSUPPORTED, "multivariate M-steps are not in this build"};
+  mstep_kernel<<<model->M, model->NP, 0, st>>>(model->bufs(), stats->rec.as<double>(), o);
+  HMM_CUDA(cudaGetLastError());
+}
+
+}  // namespace
+
+// ================================================================ C ABI
+extern "C" {
+
+const char* hmm_status_string(hmm_status s) {
+  switch (s) {
+    case HMM_OK: return "ok";
+    case HMM_E_ARG: return "invalid argument";
+    case HMM_E_NOMEM: return "out of memory";
+    case HMM_E_CUDA: return "CUDA error";
+    case HMM_E_NUMERIC: return "non-finite result";
+    case HMM_E_TIMEOUT: return "device wait timed out";
+    case HMM_E_BUSY: return "queue full";
+    case HMM_E_NOTREADY: return "not ready";
+    case HMM_E_UNSUPPORTED: return "unsupported";
+  }
+  return "unknown status";
+}
+
+const char* hmm_last_error(void) { return g_last_error.c_str(); }
+const char* hmm_version(void) { return "hmmgpu 0.1 (sm_103a)"; }
+
+int32_t hmm_family_param_count(int32_t family, int32_t dim) {
+  if (family < 0 || family > HMM_FULL_GAUSS) return -1;
+  if (family >= HMM_DIAG_GAUSS && dim < 1) return -1;
+  return param_count(family, dim);
+}
+
+int64_t hmm_param_blob_size(int32_t n_models, int32_t n_states, int32_t dim, const int32_t* h_family) {
+  if (n_models <= 0 || n_states <= 0 || !h_family) return -1;
+  int64_t tot = 0;
+  for (int m = 0; m < n_models; ++m) {
+    const int pc = hmm_family_param_count(h_family[m], dim);
+    if (pc < 0) return -1;
+    tot += n_states + (int64_t)n_states * n_states + (int64_t)n_states * pc;
+  }
+  return tot;
+}
+
+hmm_status hmm_ctx_create(int device, size_t workspace_bytes, hmm_ctx* out) {
+  return guarded([&] {
+    HMM_REQUIRE(out != nullptr, "out is NULL");
+    *out = nullptr;
+    int ndev = 0;
+    HMM_CUDA(cudaGetDeviceCount(&ndev));
+    HMM_REQUIRE(device >= 0 && device < ndev, "no such CUDA device");
+    HMM_CUDA(cudaSetDevice(device));
+    auto* c = new hmm_ctx_s();
+    c->device = device;
+    cudaError_t e = cudaDeviceGetAttribute(&c->n_sm, cudaDevAttrMultiProcessorCount, device);
+    if (e == cudaSuccess) e = cudaMalloc(&c->status, sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&c->counters, 64 * sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(c->status, 0, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(c->counters, 0, 64 * sizeof(int));
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->work_stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+      if (c->status) cudaFree(c->status);
+      if (c->counters) cudaFree(c->counters);
+      delete c;
+      throw Error{HMM_E_CUDA, std::string("context setup: ") + cudaGetErrorString(e)};
+    }
+    if (workspace_bytes) c->scratch.ensure(workspace_bytes);
+    *out = c;
+  });
+}
+
+hmm_status hmm_ctx_destroy(hmm_ctx ctx) {
+  return guarded([&] {
+    if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    cudaDeviceSynchronize();
+    ctx->scratch.release();
+    ctx->partials.release();
+    ctx->chunk_rec.release();
+    ctx->loglik.release();
+    ctx->psi.release();
+    ctx->gamma.release();
+    ctx->dp_part.release();
+    ctx->trace.release();
+    cudaFree(ctx->status);
+    cudaFree(ctx->counters);
+    if (ctx->work_stream) cudaStreamDestroy(ctx->work_stream);
+    delete ctx;
+  });
+}
+
+hmm_status hmm_ctx_status(hmm_ctx ctx, void* stream) {
+  int v = 0;
+  hmm_status st = guarded([&] {
+    HMM_REQUIRE(ctx != nullptr, "ctx is NULL");
+    HMM_CUDA(cudaStreamSynchronize(S(stream)));
+    HMM_CUDA(cudaMemcpy(&v, ctx->status, sizeof(int), cudaMemcpyDeviceToHost));
+    HMM_CUDA(cudaMemset(ctx->status, 0, sizeof(int)));
+  });
+  if (st != HMM_OK) return st;
+  if (v & ST_TIMEOUT) return HMM_E_TIMEOUT;
+  if (v & ST_NUMERIC) return HMM_E_NUMERIC;
+  if (v & ST_ARG) return HMM_E_ARG;
+  return HMM_OK;
+}
+
+hmm_status hmm_model_create(hmm_ctx ctx, int32_t n_models, int32_t n_states, int32_t dim,
+                            const int32_t* h_family, hmm_model* out) {
+  return guarded([&] {
+    HMM_REQUIRE(ctx && out && h_family, "NULL argument");
+    *out = nullptr;
+    HMM_REQUIRE(n_models >= 1 && n_states >= 1 && n_states <= 1024 && dim >= 1, "bad model sizes");
+    auto* m = new hmm_model_s();
+    try {
+      m->ctx = ctx;
+      m->M = n_models;
+      m->N = n_states;
+      m->NP = padded_states(n_states);
+      m->D = dim;
+      m->h_family.assign(h_family, h_family + n_models);
+      int P = 1;
+      for (int i = 0; i < n_models; ++i) {
+        const int f = h_family[i];
+        HMM_REQUIRE(f >= 0 && f <= HMM_FULL_GAUSS, "unknown family");
+        const bool mv = f == HMM_DIAG_GAUSS || f == HMM_FULL_GAUSS;
+        HMM_REQUIRE(mv || dim == 1, "scalar families need dim == 1");
+        m->any_negbin |= f == HMM_NEGBIN;
+        m->any_weibull |= f == HMM_WEIBULL;
+        m->any_mv |= mv;
+        P = std::max(P, param_count(f, dim));
+      }
+      m->P = P;
+      const size_t M = n_models, NP = m->NP;
+      m->family.ensure(M * 4);
+      m->pi.ensure(M * NP * 8);
+      m->A.ensure(M * NP * NP * 8);
+      m->theta.ensure(M * NP * P * 8);
+      m->A32.ensure(M * NP * NP * 4);
+      m->logA2.ensure(M * NP * NP * 4);
+      m->logAe.ensure(M * NP * NP * 4);
+      m->pi32.ensure(M * NP * 4);
+      m->logpi2.ensure(M * NP * 4);
+      m->logpie.ensure(M * NP * 4);
+      m->coef.ensure(M * NP * KC * 4);
+      if (m->any_negbin) m->nbtab.ensure(M * NP * NB_YMAX * 4);
+      m->lfact2.ensure(LF_YMAX * 4);
+      HMM_CUDA(cudaMemcpy(m->family.p, h_family, M * 4, cudaMemcpyHostToDevice));
+      HMM_CUDA(cudaMemset(m->pi.p, 0, M * NP * 8));
+      HMM_CUDA(cudaMemset(m->A.p, 0, M * NP * NP * 8));
+      HMM_CUDA(cudaMemset(m->theta.p, 0, M * NP * P * 8));
+      HMM_CUDA(cudaMemset(m->coef.p, 0, M * NP * KC * 4));
+      lfact_kernel<<<(LF_YMAX + 255) / 256, 256>>>(m->lfact2.as<float>());
+      HMM_CUDA(cudaGetLastError());
+      HMM_CUDA(cudaDeviceSynchronize());
+    } catch (...) {
+      for (auto* b : {&m->family, &m->pi, &m->A, &m->theta, &m->A32, &m->logA2, &m->logAe, &m->pi32,
+                      &m->logpi2, &m->logpie, &m->coef, &m->nbtab, &m->lfact2})
+        b->release();
+      delete m;
+      throw;
+    }
+    *out = m;
+  });
+}
+
+hmm_status hmm_model_destroy(hmm_model m) {
+  return guarded([&] {
+    if (!m) return;
+    for (auto* b : {&m->family, &m->pi, &m->A, &m->theta, &m->A32, &m->logA2, &m->logAe, &m->pi32,
+                    &m->logpi2, &m->logpie, &m->coef, &m->nbtab, &m->lfact2})
+      b->release();
+    delete m;
+  });
+}
+
+hmm_status hmm_model_set_params(hmm_model model, const double* h_blob, int64_t n_values) {
+  return guarded([&] {
+    HMM_REQUIRE(model && h_blob, "NULL argument");
+    const int M = model->M, N = model->N, NP = model->NP, P = model->P, D = model->D;
+    const int64_t need = hmm_param_blob_size(M, N, D, model->h_family.data());
+    HMM_REQUIRE(n_values == need, "parameter blob has the wrong size");
+    std::vector<double> pi((size_t)M * NP, 0.0), A((size_t)M * NP * NP, 0.0), th((size_t)M * NP * P, 0.0);
+    const double* q = h_blob;
+    for (int m = 0; m < M; ++m) {
+      const int pc = param_count(model->h_family[m], D);
+      double psum = 0.0;
+      for (int j = 0; j < N; ++j) {
+        HMM_REQUIRE(q[j] >= 0.0 && std::isfinite(q[j]), "pi must be finite and >= 0");
+        pi[(size_t)m * NP + j] = q[j];
+        psum += q[j];
+      }
+      HMM_REQUIRE(std::fabs(psum - 1.0) < 1e-6, "pi must sum to 1");
+      q += N;
+      for (int i = 0; i < N; ++i) {
+        double rs = 0.0;
+        for (int j = 0; j < N; ++j) {
+          HMM_REQUIRE(q[j] >= 0.0 && std::isfinite(q[j]), "A must be finite and >= 0");
+          A[((size_t)m * NP + i) * NP + j] = q[j];
+          rs += q[j];
+        }
+        HMM_REQUIRE(std::fabs(rs - 1.0) < 1e-6, "rows of A must sum to 1");
+        q += N;
+      }
+      for (int j = 0; j < N; ++j) {
+        for (int z = 0; z < pc; ++z) {
+          HMM_REQUIRE(std::isfinite(q[z]), "parameters must be finite");
+          th[((size_t)m * NP + j) * P + z] = q[z];
+        }
+        q += pc;
+      }
+    }
+    HMM_CUDA(cudaMemcpy(model->pi.p, pi.data(), pi.size() * 8, cudaMemcpyHostToDevice));
+    HMM_CUDA(cudaMemcpy(model->A.p, A.data(), A.size() * 8, cudaMemcpyHostToDevice));
+    HMM_CUDA(cudaMemcpy(model->theta.p, th.data(), th.size() * 8, cudaMemcpyHostToDevice));
+    const int n = M * NP;
+    derive_kernel<<<(n + 127) / 128, 128>>>(model->bufs());
+    HMM_CUDA(cudaGetLastError());
+    HMM_CUDA(cudaDeviceSynchronize());
+  });
+}
+
+hmm_status hmm_model_get_params(hmm_model model, double* h_blob, int64_t n_values) {
+  return guarded([&] {
+    HMM_REQUIRE(model && h_blob, "NULL argument");
+    const int M = model->M, N = model->N, NP = model->NP, P = model->P, D = model->D;
+    const int64_t need = hmm_param_blob_size(M, N, D, model->h_family.data());
+    HMM_REQUIRE(n_values == need, "parameter blob has the wrong size");
+    HMM_CUDA(cudaDeviceSynchronize());
+    std::vector<double> pi((size_t)M * NP), A((size_t)M * NP * NP), th((size_t)M * NP * P);
+    HMM_CUDA(cudaMemcpy(pi.data(), model->pi.p, pi.size() * 8, cudaMemcpyDeviceToHost));
+    HMM_CUDA(cudaMemcpy(A.data(), model->A.p, A.size() * 8, cudaMemcpyDeviceToHost));
+    HMM_CUDA(cudaMemcpy(th.data(), model->theta.p, th.size() * 8, cudaMemcpyDeviceToHost));
+    double* q = h_blob;
+    for (int m = 0; m < M; ++m) {
+      const int pc = param_count(model->h_family[m], D);
+      for (int j = 0; j < N; ++j) *q++ = pi[(size_t)m * NP + j];
+      for (int i = 0; i < N; ++i)
+        for (int j = 0; j < N; ++j) *q++ = A[((size_t)m * NP + i) * NP + j];
+      for (int j = 0; j < N; ++j)
+        for (int z = 0; z < pc; ++z) *q++ = th[((size_t)m * NP + j) * P + z];
+    }
+  });
+}
+
+hmm_status hmm_plan_create(hmm_ctx ctx, hmm_model model, const hmm_batch* batch, const int64_t* h_offsets,
+                           const int32_t* h_model_id, hmm_plan* out) {
+  return guarded([&] {
+    HMM_REQUIRE(ctx && model && batch && out, "NULL argument");
+    *out = nullptr;
+    check_batch(model, batch);
+    *out = make_plan(ctx, model, batch, h_offsets, h_model_id);
+  });
+}
+
+hmm_status hmm_plan_destroy(hmm_plan plan) {
+  return guarded([&] { destroy_plan(plan); });
+}
+
+hmm_status hmm_emission_logpdf(hmm_ctx ctx, hmm_model model, const hmm_batch* batch, float* d_logb,
+                               void* stream) {
+  return guarded([&] {
+    HMM_REQUIRE(ctx && model && d_logb, "NULL argument");
+    check_batch(model, batch);
+    if (model->any_mv) throw Error{HMM_E_UNSUPPORTED, "multivariate emissions are not in this build"};
+    if (batch->n_seq == 0) return;
+    emission_kernel<<<(unsigned)batch->n_seq, 128, 0, S(stream)>>>(model->view(), batch->values, batch->offsets,
+                                                                   batch->model_id, d_logb);
+    HMM_CUDA(cudaGetLastError());
+  });
+}
+
+hmm_status hmm_forward_backward(hmm_ctx ctx, hmm_model model, const hmm_batch* batch, const float* d_logb,
+                                float* d_gamma, int32_t* d_post_path, double* d_loglik, void* stream) {
+  return guarded([&] {
+    HMM_REQUIRE(ctx && model && d_loglik, "NULL argument");
+    check_batch(model, batch);
+    PlanRef pr;
+    get_plan(ctx, model, batch, S(stream), pr);
+    float* gamma = d_gamma;
+    if (!gamma && d_post_path) {
+      ctx->gamma.ensure(std::max<int64_t>(batch->total_T, 1) * model->N * 4);
+      gamma = ctx->gamma.as<float>();
+    }
+    run_estep(ctx, model, batch, pr.p, d_logb, gamma, d_loglik, false, nullptr, S(stream));
+    if (d_post_path && batch->total_T > 0) {
+      const unsigned blocks = (unsigned)((batch->total_T + 255) / 256);
+      post_path_kernel<<<blocks, 256, 0, S(stream)>>>(gamma, batch->total_T, model->N, d_post_path);
+      HMM_CUDA(cudaGetLastError());
+    }
+    if (pr.owned) HMM_CUDA(cudaStreamSynchronize(S(stream)));
+  });
+}
+
+hmm_status hmm_viterbi(hmm_ctx ctx, hmm_model model, const hmm_batch* batch, const float* d_logb,
+                       int32_t* d_path, double* d_score, void* stream) {
+  return guarded([&] {
+    HMM_REQUIRE(ctx && model && d_path && d_score, "NULL argument");
+    check_batch(model, batch);
+    if (model->NP > 32) throw Error{HMM_E_UNSUPPORTED, "state counts above 32 are not supported"};
+    if (model->any_mv && !d_logb)
+      throw Error{HMM_E_UNSUPPORTED, "multivariate families need an emission table (d_logb)"};
+    PlanRef pr;
+    get_plan(ctx, model, batch, S(stream), pr);
+    const int64_t Sn = batch->n_seq;
+    if (Sn == 0) return;
+    const int NP = model->NP;
+    ctx->psi.ensure(std::max<int64_t>(batch->total_T, 1) * NP + 64);
+    VitArgs a;
+    a.y = batch->values;
+    a.logb = d_logb;
+    a.offsets = batch->offsets;
+    a.model_id = batch->model_id;
+    a.order = pr.p->order.as<int32_t>();
+    a.n_seq = (int32_t)Sn;
+    const int G = default_viterbi_G(NP, Sn, ctx->n_sm);
+    a.n_items = (int32_t)((Sn + viterbi_seqs_per_item(G) - 1) / viterbi_seqs_per_item(G));
+    a.mv = model->view();
+    a.psi = ctx->psi.as<uint8_t>();
+    a.path = d_path;
+    a.score = d_score;
+    a.work_counter = ctx->counters + 1;
+    a.status = ctx->status;
+    HMM_CUDA(cudaMemsetAsync(ctx->counters + 1, 0, sizeof(int), S(stream)));
+    HMM_CUDA(launch_viterbi_small(NP, G, a, d_logb ? 1 : 0, ctx->n_sm, S(stream)));
+    if (pr.owned) HMM_CUDA(cudaStreamSynchronize(S(stream)));
+  });
+}
+
+hmm_status hmm_stats_create(hmm_ctx ctx, hmm_model model, hmm_stats* out) {
+  return guarded([&] {
+    HMM_REQUIRE(ctx && model && out, "NULL argument");
+    auto* s = new hmm_stats_s();
+    s->model = model;
+    try {
+      s->rec.ensure((size_t)model->M * rec_size(model->NP) * 8);
+      HMM_CUDA(cudaMemset(s->rec.p, 0, (size_t)model->M * rec_size(model->NP) * 8));
+    } catch (...) {
+      s->rec.release();
+      delete s;
+      throw;
+    }
+    *out = s;
+  });
+}
+
+hmm_status hmm_stats_destroy(hmm_stats stats) {
+  return guarded([&] {
+    if (!stats) return;
+    stats->rec.release();
+    delete stats;
+  });
+}
+
+static int canon_fam_count(int fam, int D) {
+  switch (fam) {
+    case HMM_GAUSS: return 3;
+    case HMM_POISSON: return 2;
+    case HMM_GAMMA: return 4;
+    case HMM_BETA: return 5;
+    case HMM_WEIBULL: return 3;
+    case HMM_NEGBIN: return 3;
+    case HMM_STUDENT_T: return 5;
+    case HMM_VONMISES: return 3;
+    case HMM_DIAG_GAUSS: return 1 + 2 * D;
+    case HMM_FULL_GAUSS: return 1 + D + D * D;
+  }
+  return 0;
+}
+
+int64_t hmm_stats_size(hmm_stats stats) {
+  if (!stats) return -1;
+  const hmm_model m = stats->model;
+  int64_t tot = 0;
+  for (int i = 0; i < m->M; ++i)
+    tot += 2 + m->N + (int64_t)m->N * m->N + (int64_t)m->N * canon_fam_count(m->h_family[i], m->D);
+  return tot;
+}
+
+hmm_status hmm_stats_get(hmm_stats stats, double* h_out, int64_t n_values) {
+  return guarded([&] {
+    HMM_REQUIRE(stats && h_out, "NULL argument");
+    HMM_REQUIRE(n_values == hmm_stats_size(stats), "output has the wrong size");
+    HMM_REQUIRE(stats->valid, "statistics were never computed");
+    const hmm_model md = stats->model;
+    const int M = md->M, N = md->N, NP = md->NP, RS = rec_size(NP);
+    HMM_CUDA(cudaDeviceSynchronize());
+    std::vector<double> rec((size_t)M * RS), A((size_t)M * NP * NP);
+    std::vector<float> coef((size_t)M * NP * KC);
+    HMM_CUDA(cudaMemcpy(rec.data(), stats->rec.p, rec.size() * 8, cudaMemcpyDeviceToHost));
+    HMM_CUDA(cudaMemcpy(A.data(), md->A.p, A.size() * 8, cudaMemcpyDeviceToHost));
+    HMM_CUDA(cudaMemcpy(coef.data(), md->coef.p, coef.size() * 4, cudaMemcpyDeviceToHost));
+    double* q = h_out;
+    for (int m = 0; m < M; ++m) {
+      const double* R = rec.data() + (size_t)m * RS;
+      *q++ = R[0];
+      *q++ = R[1];
+      for (int j = 0; j < N; ++j) *q++ = R[rec_g1(NP) + j];
+      for (int i = 0; i < N; ++i)
+        for (int j = 0; j < N; ++j)
+          *q++ = A[((size_t)m * NP + i) * NP + j] * R[rec_xi(NP) + i * NP + j];
+      const int fam = md->h_family[m];
+      for (int j = 0; j < N; ++j) {
+        const double* St = R + rec_st(NP) + j * (NST - 1);
+        const double c0 = coef[((size_t)m * NP + j) * KC];
+        const double W = St[0];
+        switch (fam) {
+          case HMM_GAUSS:   // shifted by c0: sum w d, sum w d^2 -> raw moments
+            q[0] = W;
+            q[1] = St[1] + c0 * W;
+            q[2] = St[2] + 2 * c0 * St[1] + c0 * c0 * W;
+            break;
+          case HMM_POISSON:
+            q[0] = W;
+            q[1] = St[1];
+            break;
+          case HMM_GAMMA:
+            q[0] = W;
+            q[1] = St[1];
+            q[2] = St[2] * kLn2;
+            q[3] = St[3];
+            break;
+          case HMM_BETA:
+            q[0] = W;
+            q[1] = St[1];
+            q[2] = St[2];
+            q[3] = St[3] * kLn2;
+            q[4] = St[4] * kLn2;
+            break;
+          case HMM_WEIBULL:
+            q[0] = W;
+            q[1] = St[1] * kLn2;
+            q[2] = St[2] * kLn2 * kLn2;
+            break;
+          case HMM_NEGBIN:
+            q[0] = W;
+            q[1] = St[1];
+            q[2] = St[2];
+            break;
+          case HMM_STUDENT_T:
+            q[0] = W;
+            q[1] = St[1];
+            q[2] = St[2] + c0 * St[1];
+            q[3] = St[3] + 2 * c0 * St[2] + c0 * c0 * St[1];
+            q[4] = St[4];
+            break;
+          case HMM_VONMISES:
+            q[0] = W;
+            q[1] = St[1];
+            q[2] = St[2];
+            break;
+          default:
+            for (int z = 0; z < canon_fam_count(fam, md->D); ++z) q[z] = 0.0;
+            q[0] = W;
+            break;
+        }
+        q += canon_fam_count(fam, md->D);
+      }
+    }
+  });
+}
+
+hmm_status hmm_estep_stats(hmm_ctx ctx, hmm_model model, const hmm_batch* batch, hmm_stats stats,
+                           double* d_loglik, void* stream) {
+  return guarded([&] {
+    HMM_REQUIRE(ctx && model && stats, "NULL argument");
+    HMM_REQUIRE(stats->model == model, "stats belong to another model");
+    check_batch(model, batch);
+    require_small(model);
+    PlanRef pr;
+    get_plan(ctx, model, batch, S(stream), pr);
+    run_estep(ctx, model, batch, pr.p, nullptr, nullptr, d_loglik, true, stats, S(stream));
+    if (pr.owned) HMM_CUDA(cudaStreamSynchronize(S(stream)));
+  });
+}
+
+hmm_status hmm_mstep(hmm_ctx ctx, hmm_model model, hmm_stats stats, const hmm_batch* batch,
+                     const hmm_mstep_opts* opts, void* stream) {
+  (void)batch;
+  return guarded([&] {
+    HMM_REQUIRE(ctx && model && stats, "NULL argument");
+    HMM_REQUIRE(stats->model == model, "stats belong to another model");
+    HMM_REQUIRE(stats->valid, "statistics were never computed");
+    run_mstep(ctx, model, stats, to_opts(opts), S(stream));
+  });
+}
+
+hmm_status hmm_fit(hmm_ctx ctx, hmm_model model, const hmm_batch* batch, const hmm_fit_opts* opts,
+                   double* h_loglik_trace, int32_t* iters_done, void* stream) {
+  return guarded([&] {
+    HMM_REQUIRE(ctx && model && opts, "NULL argument");
+    HMM_REQUIRE(opts->max_iter >= 0, "max_iter must be >= 0");
+    check_batch(model, batch);
+    require_small(model);
+    // The iterations run on the context's own non-blocking stream (a graph
+    // cannot be captured on the legacy default stream); the caller's stream
+    // is drained first and the call returns after the loop has finished.
+    HMM_CUDA(cudaStreamSynchronize(S(stream)));
+    cudaStream_t st = ctx->work_stream;
+    PlanRef pr;
+    get_plan(ctx, model, batch, st, pr);
+    hmm_stats stats = nullptr;
+    hmm_status s0 = hmm_stats_create(ctx, model, &stats);
+    if (s0 != HMM_OK) throw Error{s0, hmm_last_error()};
+    struct StatsGuard {
+      hmm_stats s;
+      ~StatsGuard() { hmm_stats_destroy(s); }
+    } sg{stats};
+    const MStepOpts mo = to_opts(&opts->mstep);
+    const int M = model->M, RS = rec_size(model->NP);
+    const int iters = opts->max_iter;
+    ctx->trace.ensure((size_t)std::max(iters, 1) * M * 8 + 64);
+    int* it_dev = reinterpret_cast<int*>(ctx->trace.as<char>() + (size_t)std::max(iters, 1) * M * 8);
+    HMM_CUDA(cudaMemsetAsync(it_dev, 0, sizeof(int), st));
+    // make every buffer the iteration needs exist before any capture
+    run_estep(ctx, model, batch, pr.p, nullptr, nullptr, nullptr, true, stats, st);
+    HMM_CUDA(cudaStreamSynchronize(st));
+    auto one_iter = [&]() {
+      run_estep(ctx, model, batch, pr.p, nullptr, nullptr, nullptr, true, stats, st);
+      trace_gather_kernel<<<(M + 255) / 256, 256, 0, st>>>(stats->rec.as<double>(), RS, M,
+                                                          ctx->trace.as<double>(), it_dev);
+      HMM_CUDA(cudaGetLastError());
+      run_mstep(ctx, model, stats, mo, st);
+      bump_kernel<<<1, 1, 0, st>>>(it_dev);
+      HMM_CUDA(cudaGetLastError());
+    };
+    int done = 0;
+    if (opts->tol <= 0.0 && iters > 0) {
+      cudaGraph_t graph = nullptr;
+      cudaGraphExec_t exec = nullptr;
+      HMM_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+      try {
+        one_iter();
+      } catch (...) {
+        cudaStreamEndCapture(st, &graph);
+        if (graph) cudaGraphDestroy(graph);
+        throw;
+      }
+      HMM_CUDA(cudaStreamEndCapture(st, &graph));
+      cudaError_t e = cudaGraphInstantiate(&exec, graph, 0);
+      cudaGraphDestroy(graph);
+      if (e != cudaSuccess) throw Error{HMM_E_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e)};
+      for (int k = 0; k < iters; ++k) {
+        e = cudaGraphLaunch(exec, st);
+        if (e != cudaSuccess) break;
+      }
+      cudaGraphExecDestroy(exec);
+      if (e != cudaSuccess) throw Error{HMM_E_CUDA, std::string("graph launch: ") + cudaGetErrorString(e)};
+      done = iters;
+    } else {
+      double prev = 0.0;
+      std::vector<double> row(M);
+      for (int k = 0; k < iters; ++k) {
+        one_iter();
+        ++done;
+        HMM_CUDA(cudaMemcpyAsync(row.data(), ctx->trace.as<double>() + (size_t)k * M, M * 8,
+                                 cudaMemcpyDeviceToHost, st));
+        HMM_CUDA(cudaStreamSynchronize(st));
+        double tot = 0.0;
+        for (double v : row) tot += v;
+        if (k > 0 && std::fabs(tot - prev) <= opts->tol * std::fabs(tot)) break;
+        prev = tot;
+      }
+    }
+    if (h_loglik_trace && done > 0) {
+      HMM_CUDA(cudaMemcpyAsync(h_loglik_trace, ctx->trace.p, (size_t)done * M * 8, cudaMemcpyDeviceToHost, st));
+    }
+    HMM_CUDA(cudaStreamSynchronize(st));
+    if (iters_done) *iters_done = done;
+  });
+}
+
+}  // extern "C"

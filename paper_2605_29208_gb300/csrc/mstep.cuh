@@ -1,0 +1,384 @@
+// Cross-sequence reductions, the M-step (paper Sec. 4) and the derived
+// single-precision tables used by the inference kernels.
+#pragma once
+
+#include "common.cuh"
+#include "special.cuh"
+
+namespace hmm {
+
+// ---------------------------------------------------------------------------
+// Mutable device model (float64 master parameters + derived float32 tables)
+// ---------------------------------------------------------------------------
+struct ModelBufs {
+  int M, N, NP, D, P;       // P: float64 parameters per state (theta stride)
+  int* family;              // [M]
+  double* pi;               // [M][NP]
+  double* A;                // [M][NP][NP]
+  double* theta;            // [M][NP][P]
+  float* A32;
+  float* logA2;
+  float* logAe;
+  float* pi32;
+  float* logpi2;
+  float* logpie;
+  float* coef;              // [M][NP][KC]
+  float* nbtab;             // [M][NP][NB_YMAX] or nullptr
+  float* lfact2;            // [LF_YMAX]
+};
+
+// Record of one model's sufficient statistics after the E-step reduction
+// (float64, internal layout):
+//   [0] number of sequences, [1] sum of log-likelihoods,
+//   [2, 2+NP) gamma_1 sums,
+//   [2+NP, 2+NP+NP*NP) X(i,j) = sum_t v(i) o(j)/Z  (xi without the a_ij factor),
+//   then NP x (NST-1) family sums (the E-step's shifted / log2 forms).
+__host__ __device__ inline int rec_size(int NP) { return 2 + NP + NP * NP + NP * (NST - 1); }
+__host__ __device__ inline int rec_g1(int) { return 2; }
+__host__ __device__ inline int rec_xi(int NP) { return 2 + NP; }
+__host__ __device__ inline int rec_st(int NP) { return 2 + NP + NP * NP; }
+
+struct MStepOpts {
+  double collapse_eps;
+  double tikhonov_eps;
+  int newton_maxit;
+  double newton_tol;
+  int nu_mode;
+  int update_transitions;
+};
+
+// Level 1: chunk c of the model-sorted sequence list -> float64 record.
+// Each field sums the chunk's sequences in list order (fixed order).
+__global__ void reduce_estep_l1(const float* __restrict__ partials, const double* __restrict__ loglik,
+                                const int32_t* __restrict__ seq_by_model,
+                                const int32_t* __restrict__ chunk_lo, const int32_t* __restrict__ chunk_hi,
+                                int NP, double* __restrict__ chunk_rec) {
+  const int c = blockIdx.x;
+  const int lo = chunk_lo[c], hi = chunk_hi[c];
+  const int F = NP + NST;
+  const int RS = rec_size(NP);
+  double* out = chunk_rec + (size_t)c * RS;
+  for (int f = threadIdx.x; f < RS; f += blockDim.x) {
+    double acc = 0.0;
+    if (f == 0) {
+      acc = (double)(hi - lo);
+    } else if (f == 1) {
+      for (int q = lo; q < hi; ++q) acc += loglik[seq_by_model[q]];
+    } else if (f < rec_xi(NP)) {
+      const int k = f - rec_g1(NP);
+      for (int q = lo; q < hi; ++q) {
+        const size_t s = seq_by_model[q];
+        acc += (double)partials[((s * 2 + 1) * NP + k) * F + NP + NST - 1];
+      }
+    } else if (f < rec_st(NP)) {
+      const int i = (f - rec_xi(NP)) / NP, j = (f - rec_xi(NP)) % NP;
+      for (int q = lo; q < hi; ++q) {
+        const size_t s = seq_by_model[q];
+        // forward chains accumulate xi with state j as the owned index
+        acc += (double)partials[((s * 2 + 0) * NP + j) * F + i];
+        acc += (double)partials[((s * 2 + 1) * NP + i) * F + j];
+      }
+    } else {
+      const int k = (f - rec_st(NP)) / (NST - 1), z = (f - rec_st(NP)) % (NST - 1);
+      for (int q = lo; q < hi; ++q) {
+        const size_t s = seq_by_model[q];
+        acc += (double)partials[((s * 2 + 0) * NP + k) * F + NP + z];
+        acc += (double)partials[((s * 2 + 1) * NP + k) * F + NP + z];
+      }
+    }
+    out[f] = acc;
+  }
+}
+
+// Level 2: a model's chunk records in order -> the model's record.
+__global__ void reduce_chunks_l2(const double* __restrict__ chunk_rec,
+                                 const int32_t* __restrict__ model_chunk_ptr, int RS,
+                                 double* __restrict__ rec) {
+  const int m = blockIdx.x;
+  const int c0 = model_chunk_ptr[m], c1 = model_chunk_ptr[m + 1];
+  for (int f = threadIdx.x; f < RS; f += blockDim.x) {
+    double acc = 0.0;
+    for (int c = c0; c < c1; ++c) acc += chunk_rec[(size_t)c * RS + f];
+    rec[(size_t)m * RS + f] = acc;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Derived float32 tables of one state (log2 units for the E-step kernels).
+// ---------------------------------------------------------------------------
+__device__ inline void derive_coef(int fam, const double* th, float* c, float* nbt) {
+#pragma unroll
+  for (int z = 0; z < KC; ++z) c[z] = 0.f;
+  const double L2E = kLog2e;
+  switch (fam) {
+    case HMM_GAUSS: {
+      const double mu = th[0], s2 = th[1];
+      c[0] = (float)mu;
+      c[1] = (float)sqrt(L2E / (2.0 * s2));
+      c[2] = (float)(-0.5 * log2(2.0 * 3.14159265358979323846 * s2));
+      break;
+    }
+    case HMM_POISSON: {
+      const double lam = th[0];
+      c[0] = (float)log2(lam);
+      c[1] = (float)(-lam * L2E);
+      break;
+    }
+    case HMM_GAMMA: {
+      const double a = th[0], b = th[1];
+      c[0] = (float)(a - 1.0);
+      c[1] = (float)(-b * L2E);
+      c[2] = (float)((a * log(b) - lgamma(a)) * L2E);
+      break;
+    }
+    case HMM_BETA: {
+      const double a = th[0], b = th[1];
+      c[0] = (float)(a - 1.0);
+      c[1] = (float)(b - 1.0);
+      c[2] = (float)(-(lgamma(a) + lgamma(b) - lgamma(a + b)) * L2E);
+      break;
+    }
+    case HMM_WEIBULL: {
+      const double k = th[0], lam = th[1];
+      c[0] = (float)(k - 1.0);
+      c[1] = (float)k;
+      c[2] = (float)(-k * log2(lam));
+      c[3] = (float)((log(k) - k * log(lam)) * L2E);
+      break;
+    }
+    case HMM_NEGBIN: {
+      const double r = th[0], p = th[1];
+      c[0] = (float)log2(1.0 - p);
+      c[1] = (float)(r * log2(p));
+      c[2] = (float)r;
+      c[3] = (float)lgamma(r);
+      if (nbt) {
+        // T(y) = [lgamma(y+r) - lgamma(r) - lgamma(y+1)] log2 e by the
+        // recurrence T(y) = T(y-1) + log((r + y - 1) / y)
+        double acc = 0.0;
+        nbt[0] = 0.f;
+        for (int y = 1; y < NB_YMAX; ++y) {
+          acc += log((r + y - 1.0) / (double)y);
+          nbt[y] = (float)(acc * L2E);
+        }
+      }
+      break;
+    }
+    case HMM_STUDENT_T: {
+      const double mu = th[0], s2 = th[1], nu = th[2];
+      c[0] = (float)mu;
+      c[1] = (float)(1.0 / (nu * s2));
+      c[2] = (float)(-(nu + 1.0) / 2.0);
+      c[3] = (float)((lgamma((nu + 1.0) / 2.0) - lgamma(nu / 2.0) -
+                      0.5 * log(nu * 3.14159265358979323846 * s2)) * L2E);
+      c[4] = (float)((nu + 1.0) / nu);
+      c[5] = (float)log2((nu + 1.0) / nu);
+      break;
+    }
+    case HMM_VONMISES: {
+      const double mu = th[0], k = th[1];
+      c[0] = (float)(k * cos(mu) * L2E);
+      c[1] = (float)(k * sin(mu) * L2E);
+      c[2] = (float)(-(log(2.0 * 3.14159265358979323846) + log_i0_d(k)) * L2E);
+      break;
+    }
+    default:
+      break;
+  }
+}
+
+// One thread per (model, state row): refresh every derived table of the row.
+__device__ inline void derive_row(const ModelBufs& mb, int m, int k) {
+  const int NP = mb.NP, N = mb.N;
+  const size_t row = ((size_t)m * NP + k) * NP;
+  for (int j = 0; j < NP; ++j) {
+    const double a = (k < N && j < N) ? mb.A[row + j] : 0.0;
+    mb.A32[row + j] = (float)a;
+    mb.logA2[row + j] = a > 0.0 ? (float)log2(a) : -INFINITY;
+    mb.logAe[row + j] = a > 0.0 ? (float)log(a) : -INFINITY;
+  }
+  const double p = k < N ? mb.pi[(size_t)m * NP + k] : 0.0;
+  mb.pi32[(size_t)m * NP + k] = (float)p;
+  mb.logpi2[(size_t)m * NP + k] = p > 0.0 ? (float)log2(p) : -INFINITY;
+  mb.logpie[(size_t)m * NP + k] = p > 0.0 ? (float)log(p) : -INFINITY;
+  if (k < N) {
+    float* nbt = mb.nbtab ? mb.nbtab + ((size_t)m * NP + k) * NB_YMAX : nullptr;
+    derive_coef(mb.family[m], mb.theta + ((size_t)m * NP + k) * mb.P,
+                mb.coef + ((size_t)m * NP + k) * KC, mb.family[m] == HMM_NEGBIN ? nbt : nullptr);
+  }
+}
+
+__global__ void derive_kernel(ModelBufs mb) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= mb.M * mb.NP) return;
+  derive_row(mb, idx / mb.NP, idx % mb.NP);
+}
+
+__global__ void lfact_kernel(float* lfact2) {
+  const int y = blockIdx.x * blockDim.x + threadIdx.x;
+  if (y < LF_YMAX) lfact2[y] = (float)(lgamma((double)y + 1.0) * kLog2e);
+}
+
+// ---------------------------------------------------------------------------
+// Newton-Raphson and ECM updates (float64), mirroring Sec. 4.1-4.3.
+// ---------------------------------------------------------------------------
+__device__ inline bool newton_done(double old, double nw, double tol) {
+  return fabs(nw - old) <= tol * fmax(1.0, fabs(old));
+}
+
+// Gamma shape by Eq. 7-8 from the MOM seed; c = log ybar - mean log y.
+__device__ inline double gamma_shape(double ybar, double var, double c, const MStepOpts& o) {
+  double a = (var > 0.0) ? ybar * ybar / var : 0.5 / c;
+  for (int it = 0; it < o.newton_maxit; ++it) {
+    const double s = log(a) - digamma_d(a) - c;
+    const double ds = 1.0 / a - trigamma_d(a);
+    double step = s / ds;
+    double nw = a - step;
+    while (nw <= 0.0) {
+      step *= 0.5;
+      nw = a - step;
+    }
+    const bool done = newton_done(a, nw, o.newton_tol);
+    a = nw;
+    if (done) break;
+  }
+  return a;
+}
+
+__device__ inline void beta_fit(double ybar, double var, double m1, double m2, const MStepOpts& o,
+                                double* pa, double* pb) {
+  const double kk = ybar * (1.0 - ybar) / var - 1.0;
+  double a = kk > 0.0 ? ybar * kk : 1.0, b = kk > 0.0 ? (1.0 - ybar) * kk : 1.0;
+  for (int it = 0; it < o.newton_maxit; ++it) {
+    const double pab = digamma_d(a + b), tab = trigamma_d(a + b);
+    const double F0 = digamma_d(a) - pab - m1, F1 = digamma_d(b) - pab - m2;
+    const double J00 = trigamma_d(a) - tab, J01 = -tab, J11 = trigamma_d(b) - tab;
+    const double det = J00 * J11 - J01 * J01;
+    double s0 = (J11 * F0 - J01 * F1) / det, s1 = (J00 * F1 - J01 * F0) / det;
+    double na = a - s0, nb = b - s1;
+    while (na <= 0.0 || nb <= 0.0) {
+      s0 *= 0.5;
+      s1 *= 0.5;
+      na = a - s0;
+      nb = b - s1;
+    }
+    const bool done = newton_done(a, na, o.newton_tol) && newton_done(b, nb, o.newton_tol);
+    a = na;
+    b = nb;
+    if (done) break;
+  }
+  *pa = a;
+  *pb = b;
+}
+
+__device__ inline double vonmises_kappa(double R, const MStepOpts& o) {
+  if (R >= 1.0) return 1e6;
+  double k = R * (2.0 - R * R) / (1.0 - R * R);
+  for (int it = 0; it < o.newton_maxit; ++it) {
+    const double A = bessel_ratio_d(k);
+    const double dA = 1.0 - A * A - A / k;
+    double step = (A - R) / dA;
+    double nw = k - step;
+    while (nw <= 0.0) {
+      step *= 0.5;
+      nw = k - step;
+    }
+    nw = fmin(nw, 1e6);
+    const bool done = newton_done(k, nw, o.newton_tol);
+    k = nw;
+    if (done) break;
+  }
+  return k;
+}
+
+// CM-step 2 of Sec. 4.3 (Eq. 18-19): Newton on nu with C = sum w(log u - u)
+// (+ the E[log U] constant in the ECM reading), |d nu| < 1e-6, nu in [0.5, 1e4].
+__device__ inline double student_nu(double W, double C, double nu0, const MStepOpts& o) {
+  if (o.nu_mode == 0) C += W * (digamma_d(0.5 * (nu0 + 1.0)) - log(0.5 * (nu0 + 1.0)));
+  double nu = nu0;
+  for (int it = 0; it < o.newton_maxit; ++it) {
+    const double g = 0.5 * W * (log(0.5 * nu) + 1.0 - digamma_d(0.5 * nu)) + 0.5 * C;
+    const double h = 0.25 * W * (2.0 / nu - trigamma_d(0.5 * nu));
+    const double nw = fmin(fmax(nu - g / h, 0.5), 1e4);
+    const bool done = fabs(nw - nu) < 1e-6;
+    nu = nw;
+    if (done) break;
+  }
+  return nu;
+}
+
+// One block per model, one thread per state: emission M-step of state k
+// (Sec. 4 with the collapse guard of Sec. 4.4), transition row k and pi_k,
+// then the derived tables of row k.  Families whose Newton step needs data
+// passes (Weibull, negative binomial) get their seed here and are finished by
+// the data-pass kernels.
+__global__ void mstep_kernel(ModelBufs mb, const double* __restrict__ rec, MStepOpts o) {
+  const int m = blockIdx.x, k = threadIdx.x;
+  const int NP = mb.NP, N = mb.N;
+  if (k >= NP) return;
+  const double* R = rec + (size_t)m * rec_size(NP);
+  const int fam = mb.family[m];
+  if (k < N) {
+    double* th = mb.theta + ((size_t)m * NP + k) * mb.P;
+    const double* S = R + rec_st(NP) + k * (NST - 1);
+    const double W = S[0];
+    const float* cf = mb.coef + ((size_t)m * NP + k) * KC;   // current shifts
+    if (W >= o.collapse_eps) {
+      switch (fam) {
+        case HMM_GAUSS: {
+          const double d1 = S[1] / W;
+          th[0] = (double)cf[0] + d1;
+          th[1] = fmax(S[2] / W - d1 * d1, 0.0);
+          break;
+        }
+        case HMM_POISSON:
+          th[0] = S[1] / W;
+          break;
+        case HMM_GAMMA: {
+          const double ybar = S[1] / W, mlog = S[2] * kLn2 / W;
+          const double var = S[3] / W - ybar * ybar;
+          const double a = gamma_shape(ybar, var, log(ybar) - mlog, o);
+          th[0] = a;
+          th[1] = a / ybar;
+          break;
+        }
+        case HMM_BETA: {
+          const double ybar = S[1] / W, var = S[2] / W - ybar * ybar;
+          beta_fit(ybar, var, S[3] * kLn2 / W, S[4] * kLn2 / W, o, &th[0], &th[1]);
+          break;
+        }
+        case HMM_STUDENT_T: {
+          const double Su = S[1], Sud = S[2], Sud2 = S[3];
+          const double d1 = Sud / Su;
+          const double nu0 = th[2];
+          th[0] = (double)cf[0] + d1;                 // Eq. 15
+          th[1] = (Sud2 - Sud * d1) / W;              // Eq. 16 (divides by N_j)
+          th[2] = student_nu(W, S[4], nu0, o);        // Eq. 18-19
+          break;
+        }
+        case HMM_VONMISES: {
+          const double C = S[1], Sn = S[2];
+          th[0] = atan2(Sn, C);
+          th[1] = vonmises_kappa(hypot(C, Sn) / W, o);
+          break;
+        }
+        default:
+          break;
+      }
+    }
+    if (o.update_transitions) {
+      double* Arow = mb.A + ((size_t)m * NP + k) * NP;
+      const double* X = R + rec_xi(NP) + k * NP;
+      double den = 0.0;
+      for (int j = 0; j < N; ++j) den += Arow[j] * X[j];
+      if (den >= o.collapse_eps)
+        for (int j = 0; j < N; ++j) Arow[j] = Arow[j] * X[j] / den;
+      const double ns = R[0];
+      if (ns > 0.0) mb.pi[(size_t)m * NP + k] = R[rec_g1(NP) + k] / ns;
+    }
+  }
+  __syncthreads();
+  derive_row(mb, m, k);
+}
+
+}  // namespace hmm

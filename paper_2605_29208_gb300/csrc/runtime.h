@@ -1,0 +1,109 @@
+// Host-side runtime objects of the hmmgpu library: error handling, the
+// context workspace, device models and batch plans.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "../../include/hmmgpu.h"
+#include "common.cuh"
+#include "mstep.cuh"
+
+namespace hmm {
+
+void set_error(const std::string& msg);
+
+struct Error {
+  hmm_status st;
+  std::string msg;
+};
+
+#define HMM_CUDA(call)                                                              \
+  do {                                                                              \
+    cudaError_t e_ = (call);                                                        \
+    if (e_ != cudaSuccess)                                                          \
+      throw ::hmm::Error{HMM_E_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)}; \
+  } while (0)
+
+#define HMM_REQUIRE(cond, msg)                                            \
+  do {                                                                    \
+    if (!(cond)) throw ::hmm::Error{HMM_E_ARG, std::string(msg)};         \
+  } while (0)
+
+// A growable device buffer owned by the library.
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  void ensure(size_t n) {
+    if (n <= bytes) return;
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+    cudaError_t e = cudaMalloc(&p, n);
+    if (e != cudaSuccess) {
+      p = nullptr;
+      throw Error{HMM_E_NOMEM, "cudaMalloc(" + std::to_string(n) + "): " + cudaGetErrorString(e)};
+    }
+    bytes = n;
+  }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+  }
+  template <class T>
+  T* as() const {
+    return reinterpret_cast<T*>(p);
+  }
+};
+
+}  // namespace hmm
+
+struct hmm_ctx_s {
+  int device = 0;
+  int n_sm = 0;
+  int* status = nullptr;         // device status word
+  int* counters = nullptr;       // device work counters [64]
+  cudaStream_t work_stream = nullptr;  // non-blocking stream for captured loops
+  hmm::DevBuf scratch;           // [total_T][NP] float recurrence rows
+  hmm::DevBuf partials;          // per-sequence float32 partial sums
+  hmm::DevBuf chunk_rec;         // float64 chunk records
+  hmm::DevBuf loglik;            // float64 per-sequence logL (internal)
+  hmm::DevBuf psi;               // Viterbi backpointers
+  hmm::DevBuf gamma;             // gamma rows for the data passes
+  hmm::DevBuf dp_part;           // data-pass partials
+  hmm::DevBuf trace;             // float64 logL trace of hmm_fit
+};
+
+struct hmm_model_s {
+  hmm_ctx ctx = nullptr;
+  int M = 0, N = 0, NP = 0, D = 1, P = 0;
+  std::vector<int32_t> h_family;
+  bool any_negbin = false, any_weibull = false, any_mv = false;
+  hmm::DevBuf family, pi, A, theta, A32, logA2, logAe, pi32, logpi2, logpie, coef, nbtab, lfact2;
+  hmm::ModelBufs bufs() const;
+  hmm::ModelView view() const;
+};
+
+struct hmm_stats_s {
+  hmm_model model = nullptr;
+  hmm::DevBuf rec;               // [M][rec_size(NP)] float64
+  bool valid = false;
+};
+
+struct hmm_plan_s {
+  hmm_ctx ctx = nullptr;
+  int64_t n_seq = 0, total_T = 0;
+  int M = 0;
+  int64_t max_T = 0;
+  hmm::DevBuf order;             // [S] int32 processing order
+  hmm::DevBuf seq_by_model;      // [S] int32
+  hmm::DevBuf chunk_lo, chunk_hi;// [n_chunks] int32
+  hmm::DevBuf model_chunk_ptr;   // [M+1] int32
+  int n_chunks = 0;
+  std::vector<int32_t> h_order;
+};

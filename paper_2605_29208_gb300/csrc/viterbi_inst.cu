@@ -1,0 +1,75 @@
+// Instantiations and launcher of the small-N Viterbi kernel.
+#include "launch.h"
+
+namespace hmm {
+
+namespace {
+
+template <int NP, int G>
+cudaError_t launch_one(const VitArgs& a, int table_mode, int n_sm, cudaStream_t st) {
+  constexpr int WPB = kWarpsPerBlock;
+  const size_t smem = sizeof(VitSmem<VitCfg<NP, G>>) * WPB;
+  auto kern = viterbi_small_kernel<NP, G, WPB>;
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  int per_sm = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, WPB * 32, smem);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) per_sm = 1;
+  const int want = (a.n_items + WPB - 1) / WPB;
+  int grid = per_sm * n_sm;
+  if (want < grid) grid = want;
+  if (grid < 1) grid = 1;
+  kern<<<grid, WPB * 32, smem, st>>>(a, table_mode);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+bool viterbi_small_supported(int NP, int G) {
+  switch (NP) {
+    case 2: return G == 1 || G == 2;
+    case 4: return G == 1 || G == 2 || G == 4;
+    case 8: return G == 2 || G == 4 || G == 8;
+    case 16: return G == 4 || G == 8 || G == 16;
+    case 32: return G == 16;
+    default: return false;
+  }
+}
+
+int default_viterbi_G(int NP, int64_t n_seq, int n_sm) {
+  if (NP == 32) return 16;
+  int G = NP >= 8 ? NP / 4 : (NP == 4 ? 1 : 1);
+  while (G < 16 && G < NP && viterbi_small_supported(NP, 2 * G)) {
+    const double warps = (double)n_seq / (32 / G);
+    if (warps >= 8.0 * n_sm) break;
+    G *= 2;
+  }
+  return G;
+}
+
+cudaError_t launch_viterbi_small(int NP, int G, const VitArgs& a, int table_mode, int n_sm,
+                                 cudaStream_t st) {
+#define HMM_CASE(np, g) \
+  if (NP == np && G == g) return launch_one<np, g>(a, table_mode, n_sm, st);
+  HMM_CASE(2, 1)
+  HMM_CASE(2, 2)
+  HMM_CASE(4, 1)
+  HMM_CASE(4, 2)
+  HMM_CASE(4, 4)
+  HMM_CASE(8, 2)
+  HMM_CASE(8, 4)
+  HMM_CASE(8, 8)
+  HMM_CASE(16, 4)
+  HMM_CASE(16, 8)
+  HMM_CASE(16, 16)
+  HMM_CASE(32, 16)
+#undef HMM_CASE
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace hmm
