@@ -1,0 +1,370 @@
+#!/usr/bin/env python3
+"""Benchmark of the HMM hot path on one GB300 (or N GPUs, one process each).
+
+Workload (the paper-shaped "plain method at GPU scale" configuration): N = 16
+states, 4096 sequences of T = 2000 float32 observations, one Gamma-emission
+model with Dirichlet(1) transition rows, synthetic seeded data.  One step =
+one Baum-Welch iteration (fused E-step: emissions, forward, backward,
+occupancies, xi and sufficient statistics; fixed-order float64 reductions;
+M-step with the Gamma Newton-Raphson) followed by one Viterbi decode of the
+whole batch with the updated model.  The metric counts N^2 * sum(T) cell
+updates for the iteration and again for the decode.
+
+Timing: CUDA events on the launching stream around every step, W untimed
+warm-up steps, the L2 cache flushed (a 256 MiB write) before each timed
+step outside the events, GPU clocks sampled with nvidia-smi during the timed
+steps.  The dominant kernel (the fused E-step) is timed separately by the
+library's event hooks on its own stream for the roofline entry.
+
+--impl reference times the CPU checker (oracle/) on a bounded sample of the
+same workload, for the driver's ratio.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_STATES, N_SEQ, T_LEN = 16, 4096, 2000
+METRIC = "Baum-Welch N^2 T cell-updates/s (EM iteration + Viterbi decode)"
+UNIT = "cell-updates/s"
+
+
+def args_parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--family", choices=["gamma", "student_t"], default="gamma")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-plain", action="store_true")
+    p.add_argument("--estep-lanes", type=int, default=0)
+    p.add_argument("--quick", action="store_true", help="small case for profiling runs")
+    return p.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def workload(args, rank):
+    from paper_2605_29208_gb300 import synth
+    n_seq, T = (256, 500) if args.quick else (N_SEQ, T_LEN)
+    # weak scaling: every rank holds its own full-size batch (seed per rank)
+    return synth.scale_workload(args.family, n_seq=n_seq, T=T, N=N_STATES,
+                                seed=synth.MASTER_SEED + 1 + 1000 * rank)
+
+
+def cells(offsets, N):
+    return float(N * N) * float(offsets[-1])
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+# ---------------------------------------------------------------- CPU side
+def oracle_step_sample(init, values, offsets, mid, n_sample):
+    """One EM iteration and one Viterbi decode of the first n_sample
+    sequences with the oracle; returns (seconds, cell updates)."""
+    from oracle import hmm_oracle as O
+    m = O.Model(init["family"], init["pi"].copy(), init["A"].copy(),
+                {k: v.copy() for k, v in init["params"].items()})
+    sub_off = offsets[:n_sample + 1]
+    sub_vals = values[:sub_off[-1]]
+    sub_mid = mid[:n_sample]
+    t0 = time.perf_counter()
+    new, _ = O.em_iteration([m], sub_vals, sub_off, sub_mid)
+    for s in range(n_sample):
+        O.viterbi(new[0], sub_vals[sub_off[s]:sub_off[s + 1]])
+    dt = time.perf_counter() - t0
+    return dt, 2.0 * cells(sub_off, len(init["pi"]))
+
+
+def cpu_baseline(init, values, offsets, mid, target_s=12.0):
+    n = 4
+    dt, c = oracle_step_sample(init, values, offsets, mid, n)
+    n2 = int(max(4, min(len(offsets) - 1, n * target_s / max(dt, 1e-3))))
+    dt, c = oracle_step_sample(init, values, offsets, mid, n2)
+    return dict(value=c / dt, unit=UNIT, cores=1, kind="oracle",
+                sample=f"first {n2} of {len(offsets) - 1} sequences (T={int(offsets[1] - offsets[0])}, "
+                       f"N={len(init['pi'])}), one EM iteration + one Viterbi decode, "
+                       f"numpy float64 single thread, {dt:.1f} s")
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    truth, init, values, offsets, mid = workload(args, 0)
+    n_sample = 8 if not args.quick else 4
+    for _ in range(args.warmup):
+        oracle_step_sample(init, values, offsets, mid, 2)
+    times, cs = [], 0.0
+    for _ in range(args.steps):
+        dt, c = oracle_step_sample(init, values, offsets, mid, n_sample)
+        times.append(dt)
+        cs = c
+    ms = 1e3 * float(np.mean(times))
+    value = cs / (ms / 1e3)
+    line = dict(impl="reference", metric=METRIC, value=value, unit=UNIT, n_gpus=args.gpus,
+                steps=args.steps, warmup=args.warmup, ms_per_step=ms, higher_is_better=True,
+                scaling="weak", vs_baseline=None, dtype="f64", data="synthetic",
+                config=dict(workload=f"{args.family} N={N_STATES} sample of {n_sample} x T={T_LEN}",
+                            n_seq_sample=n_sample, seq_len=T_LEN, n_states=N_STATES),
+                cpu_baseline=dict(value=value, unit=UNIT, cores=1, kind="oracle",
+                                  sample=f"{n_sample} sequences of the workload per step"),
+                e2e=dict(value=value, unit=UNIT, h2d_bytes_per_step=0, d2h_bytes_per_step=0))
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- GPU side
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.fh,
+                stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        try:
+            rows = [r.split(",") for r in open(self.path).read().strip().splitlines()]
+        except Exception:
+            return None
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[0]))
+                mx.append(float(r[1]))
+                for i, n in enumerate(names):
+                    if r[4 + i].strip().lower() == "active":
+                        reasons.add(n)
+            except Exception:
+                continue
+        if not sm:
+            return None
+        return dict(sm_mhz=statistics.median(sm), sm_max_mhz=max(mx), samples=len(sm),
+                    reasons=sorted(reasons))
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+def run_ours(args):
+    import torch
+    import paper_2605_29208_gb300 as H
+    from paper_2605_29208_gb300 import _lib
+    from paper_2605_29208_gb300.parallel import allreduce_stats
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    truth, init, values, offsets, mid = workload(args, rank)
+    ctx = H.Context(local)
+    if args.estep_lanes:
+        ctx.set_option(_lib.OPT_ESTEP_LANES, args.estep_lanes)
+    model = H.Model(ctx, [init])
+    batch = H.Batch(values, offsets, mid).make_plan(ctx, model)
+    stats = H.Stats(ctx, model)
+    dev = batch.values.device
+    S = batch.n_seq
+    ll = torch.empty(S, dtype=torch.float64, device=dev)
+    path = torch.empty(batch.total_T, dtype=torch.int32, device=dev)
+    score = torch.empty(S, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream()
+    flush_buf = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    opts = H.mstep_opts()
+    b = batch.c()
+    L = ctx.lib
+    import ctypes as C
+    sp = C.c_void_p(stream.cuda_stream)
+
+    record = stats.device_tensor() if dist is not None else None
+
+    def step():
+        H.check(L.hmm_estep_stats(ctx.h, model.h, C.byref(b), stats.h, C.c_void_p(ll.data_ptr()), sp))
+        if dist is not None:
+            allreduce_stats(record)        # the one exchange step of an iteration
+        H.check(L.hmm_mstep(ctx.h, model.h, stats.h, C.byref(b), C.byref(opts), sp))
+        H.check(L.hmm_viterbi(ctx.h, model.h, C.byref(b), None, C.c_void_p(path.data_ptr()),
+                              C.c_void_p(score.data_ptr()), sp))
+
+    def timed(fn, n, flush=True):
+        times = []
+        for _ in range(n):
+            if flush:
+                flush_buf.fill_(1)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            times.append((e0, e1))
+        torch.cuda.synchronize()
+        return [a.elapsed_time(b) for a, b in times]
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    ctx.profile(reset=True)
+    ctx.set_option(_lib.OPT_PROFILE, 1)
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        t_wall = time.perf_counter()
+        step_ms = timed(step, args.steps)
+        t_wall = time.perf_counter() - t_wall
+    ctx.set_option(_lib.OPT_PROFILE, 0)
+    prof = ctx.profile(reset=True)
+    ms = float(np.sum(step_ms)) / args.steps
+    if dist is not None:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    c_step = 2.0 * cells(offsets, N_STATES)
+    value = ws * c_step / (ms / 1e3)
+
+    # ---- end to end through the public API with host buffers
+    h_vals = torch.from_numpy(np.asarray(values, np.float32)).pin_memory()
+    h_off = torch.from_numpy(np.asarray(offsets, np.int64)).pin_memory()
+    h_mid = torch.from_numpy(np.asarray(mid, np.int32)).pin_memory()
+    h_path = torch.empty(batch.total_T, dtype=torch.int32).pin_memory()
+    h_ll = torch.empty(S, dtype=torch.float64).pin_memory()
+    h_score = torch.empty(S, dtype=torch.float64).pin_memory()
+
+    def e2e_step():
+        batch.values.copy_(h_vals, non_blocking=True)
+        batch.offsets.copy_(h_off, non_blocking=True)
+        batch.model_id.copy_(h_mid, non_blocking=True)
+        step()
+        h_path.copy_(path, non_blocking=True)
+        h_ll.copy_(ll, non_blocking=True)
+        h_score.copy_(score, non_blocking=True)
+
+    e2e_ms = float(np.mean(timed(e2e_step, max(2, args.steps // 2))))
+    h2d = h_vals.numel() * 4 + h_off.numel() * 8 + h_mid.numel() * 4
+    d2h = h_path.numel() * 4 + h_ll.numel() * 8 + h_score.numel() * 8
+
+    # ---- plain float32 log-space GPU path, same step otherwise
+    plain = None
+    if not args.no_plain:
+        ctx.set_option(_lib.OPT_PLAIN_ESTEP, 1)
+        step()
+        torch.cuda.synchronize()
+        ctx.set_option(_lib.OPT_PROFILE, 1)
+        pms = float(np.mean(timed(step, 2)))
+        ctx.set_option(_lib.OPT_PROFILE, 0)
+        pprof = ctx.profile(reset=True)
+        ctx.set_option(_lib.OPT_PLAIN_ESTEP, 0)
+        bw_plain = (pprof["plain"][0] + pprof["reduce"][0] + pprof["mstep"][0]) / 2
+        plain = dict(ms_per_step=pms, bw_ms=bw_plain, plain_estep_ms=pprof["plain"][0] / 2)
+
+    est_ms = prof["estep"][0] / max(prof["estep"][1], 1)
+    bw_ms = (prof["estep"][0] + prof["reduce"][0] + prof["mstep"][0]) / args.steps
+    vit_ms = prof["viterbi"][0] / max(prof["viterbi"][1], 1)
+    launches = sum(v[1] for v in prof.values())
+    # roofline of the fused E-step: 3 N^2 FP32 FMAs per (sequence, t)
+    # (forward mat-vec, backward mat-vec, xi accumulation) = 6 N^2 flop
+    pk = peaks()
+    sm_max = float(pk.get("sm_max_mhz", 2070.0))
+    alu_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12          # TFLOP/s, FP32 FMA
+    flops = 6.0 * N_STATES * N_STATES * float(offsets[-1])
+    achieved = flops / (est_ms / 1e3) / 1e12
+    roofline = dict(bound="alu", achieved=achieved, peak=alu_peak, unit="TFLOP/s",
+                    frac=achieved / alu_peak, traffic=None,
+                    kernel="estep_small_kernel (fused emission+forward+backward+gamma/xi+stats)",
+                    peak_note="FP32 FMA: 152 SMs x 128 lanes x 2 flop x max SM clock (derived)")
+    clocks = clk.summary() if rank == 0 else None
+    out = None
+    if rank == 0:
+        line = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=ws, steps=args.steps,
+                    warmup=max(args.warmup, 3), ms_per_step=ms, higher_is_better=True,
+                    scaling="weak", vs_baseline=None, dtype="f32", data="synthetic",
+                    config=dict(workload=f"{args.family} HMM, N={N_STATES} states, {S} sequences x "
+                                         f"T={int(offsets[1] - offsets[0])}, one EM iteration + Viterbi",
+                                family=args.family, n_states=N_STATES, n_seq_per_gpu=S,
+                                seq_len=int(offsets[1] - offsets[0]), global_batch=S * ws,
+                                parallelism=f"dp{ws}" if ws > 1 else "single GPU",
+                                cell_updates_per_step=c_step,
+                                l2="flushed before every timed step (256 MiB write, outside the events)"),
+                    clocks=clocks, e2e=dict(value=ws * c_step / (e2e_ms / 1e3), unit=UNIT,
+                                            ms_per_step=e2e_ms, h2d_bytes_per_step=h2d,
+                                            d2h_bytes_per_step=d2h),
+                    gpu_launches=launches * ws, roofline=roofline,
+                    breakdown=dict(estep_ms=est_ms, baum_welch_ms=bw_ms, viterbi_ms=vit_ms,
+                                   reduce_ms=prof["reduce"][0] / args.steps,
+                                   mstep_ms=prof["mstep"][0] / args.steps,
+                                   baum_welch_cell_updates_per_s=cells(offsets, N_STATES) / (bw_ms / 1e3),
+                                   wall_s=t_wall))
+        if plain:
+            line["plain_gpu"] = plain
+            line["vs_plain_gpu"] = plain["bw_ms"] / bw_ms
+        if not args.no_cpu_baseline and not args.quick:
+            line["cpu_baseline"] = cpu_baseline(init, values, offsets, mid)
+        out = line
+        print(json.dumps(out), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    return out
+
+
+def main():
+    args = args_parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

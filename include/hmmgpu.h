@@ -130,6 +130,28 @@ int64_t hmm_param_blob_size(int32_t n_models, int32_t n_states, int32_t dim,
                             const int32_t* h_family);
 
 /* ------------------------------------------------------------ context */
+/* Context options (hmm_ctx_set_option). */
+typedef enum {
+  HMM_OPT_PROFILE = 1,        /* 1: time every kernel launch with CUDA events on
+                                 its stream (read with hmm_ctx_profile_read)     */
+  HMM_OPT_ESTEP_LANES = 2,    /* lanes per chain of the small-N E-step, 0 = auto */
+  HMM_OPT_VITERBI_LANES = 3,  /* lanes per chain of the small-N Viterbi, 0 = auto */
+  HMM_OPT_PLAIN_ESTEP = 4     /* 1: run E-steps with the plain float32 log-space
+                                 kernels (straight log-sum-exp of Sec. 3.2, N^2
+                                 exponentials per step) -- the GPU baseline     */
+} hmm_option;
+
+/* Kernel timing slots of hmm_ctx_profile_read. */
+typedef enum {
+  HMM_KT_ESTEP = 0,           /* fused E-step kernel                     */
+  HMM_KT_REDUCE = 1,          /* fixed-order statistic reductions        */
+  HMM_KT_MSTEP = 2,           /* M-step + derived tables                 */
+  HMM_KT_VITERBI = 3,         /* Viterbi forward + traceback             */
+  HMM_KT_EMISSION = 4,        /* emission log-density tables             */
+  HMM_KT_PLAIN = 5,           /* plain float32 log-space E-step kernels  */
+  HMM_KT_SLOTS = 8
+} hmm_kernel_slot;
+
 /* Creates a context on CUDA device `device`.  workspace_bytes is an initial
  * reservation (0: grow on demand).  The context owns its scratch memory. */
 hmm_status hmm_ctx_create(int device, size_t workspace_bytes, hmm_ctx* out);
@@ -137,6 +159,15 @@ hmm_status hmm_ctx_destroy(hmm_ctx ctx);
 /* Sticky device-side status word (HMM_OK or the first error raised by a
  * kernel since the last call); synchronises `stream`, then clears it. */
 hmm_status hmm_ctx_status(hmm_ctx ctx, void* stream);
+
+/* Sets a context option (hmm_option); unknown keys give HMM_E_ARG. */
+hmm_status hmm_ctx_set_option(hmm_ctx ctx, int32_t key, int64_t value);
+/* Accumulated device milliseconds and launch counts per timing slot
+ * (h_ms / h_launches [n_slots], either may be NULL) of the launches recorded
+ * while HMM_OPT_PROFILE was on; waits for the recorded events.  reset != 0
+ * clears the totals.  Launches inside a graph capture are not timed. */
+hmm_status hmm_ctx_profile_read(hmm_ctx ctx, double* h_ms, int64_t* h_launches,
+                                int32_t n_slots, int32_t reset);
 
 /* -------------------------------------------------------------- models */
 /* n_models models of n_states states with observation dimension dim; the
@@ -207,6 +238,14 @@ hmm_status hmm_stats_destroy(hmm_stats stats);
  * where W = sum_t gamma_t(j) (x) and x the named function of y_t. */
 int64_t hmm_stats_size(hmm_stats stats);
 hmm_status hmm_stats_get(hmm_stats stats, double* h_out, int64_t n_values);
+
+/* Device view of the raw float64 statistic record behind `stats`
+ * (*d_values, *n_values).  Its layout is internal, but every entry is a sum
+ * over sequences, so records of the same model made on different GPUs from
+ * different sequences can be added element-wise (e.g. an all-reduce of
+ * data-parallel E-steps) before hmm_mstep.  The memory stays owned by the
+ * library and lives as long as `stats`. */
+hmm_status hmm_stats_device_buffer(hmm_stats stats, double** d_values, int64_t* n_values);
 
 /* E-step over a batch (Sec. 3.2 + Sec. 4, Eq. 5): fills `stats` with the
  * weighted sufficient statistics of every model and writes per-sequence

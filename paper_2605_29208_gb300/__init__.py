@@ -99,6 +99,17 @@ class Context:
     def status(self, stream=None):
         return self.lib.hmm_ctx_status(self.h, _stream(stream))
 
+    def set_option(self, key: int, value: int):
+        check(self.lib.hmm_ctx_set_option(self.h, key, value))
+
+    def profile(self, reset: bool = False) -> dict:
+        """{slot: (milliseconds, launches)} of the kernels timed so far."""
+        ms = np.zeros(8, np.float64)
+        n = np.zeros(8, np.int64)
+        check(self.lib.hmm_ctx_profile_read(self.h, ms.ctypes.data_as(C.c_void_p),
+                                            n.ctypes.data_as(C.c_void_p), 8, int(reset)))
+        return {name: (float(ms[i]), int(n[i])) for i, name in enumerate(_lib.KT_SLOTS)}
+
 
 class Model:
     """M models x N states on the device; ``models`` is a list of model dicts
@@ -232,6 +243,19 @@ class Stats:
         h = C.c_void_p()
         check(self.lib.hmm_stats_create(ctx.h, model.h, C.byref(h)))
         self.h = h
+
+    def device_tensor(self):
+        """The raw float64 statistic record as a torch tensor that aliases
+        the library's device memory (for cross-GPU sums)."""
+        torch = _torch()
+        ptr = C.c_void_p()
+        n = C.c_int64()
+        check(self.lib.hmm_stats_device_buffer(self.h, C.byref(ptr), C.byref(n)))
+
+        class _View:
+            __cuda_array_interface__ = dict(shape=(n.value,), typestr="<f8", data=(ptr.value, False),
+                                            version=2)
+        return torch.as_tensor(_View(), device="cuda")
 
     def get(self) -> np.ndarray:
         n = self.lib.hmm_stats_size(self.h)

@@ -11,6 +11,9 @@ STATUS_NAMES = {0: "HMM_OK", 1: "HMM_E_ARG", 2: "HMM_E_NOMEM", 3: "HMM_E_CUDA",
                 4: "HMM_E_NUMERIC", 5: "HMM_E_TIMEOUT", 6: "HMM_E_BUSY",
                 7: "HMM_E_NOTREADY", 8: "HMM_E_UNSUPPORTED"}
 
+OPT_PROFILE, OPT_ESTEP_LANES, OPT_VITERBI_LANES, OPT_PLAIN_ESTEP = 1, 2, 3, 4
+KT_SLOTS = ("estep", "reduce", "mstep", "viterbi", "emission", "plain", "slot6", "slot7")
+
 FAMILY = {"gauss": 0, "poisson": 1, "gamma": 2, "beta": 3, "weibull": 4, "negbin": 5,
           "student_t": 6, "vonmises": 7, "diag_gauss": 8, "full_gauss": 9}
 
@@ -41,6 +44,8 @@ _SIGS = {
     "hmm_ctx_create": (C.c_int, [C.c_int, C.c_size_t, C.POINTER(C.c_void_p)]),
     "hmm_ctx_destroy": (C.c_int, [C.c_void_p]),
     "hmm_ctx_status": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "hmm_ctx_set_option": (C.c_int, [C.c_void_p, C.c_int32, C.c_int64]),
+    "hmm_ctx_profile_read": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_int32]),
     "hmm_model_create": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_int32, C.c_void_p,
                                    C.POINTER(C.c_void_p)]),
     "hmm_model_destroy": (C.c_int, [C.c_void_p]),
@@ -59,6 +64,7 @@ _SIGS = {
     "hmm_stats_destroy": (C.c_int, [C.c_void_p]),
     "hmm_stats_size": (C.c_int64, [C.c_void_p]),
     "hmm_stats_get": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64]),
+    "hmm_stats_device_buffer": (C.c_int, [C.c_void_p, C.POINTER(C.c_void_p), C.POINTER(C.c_int64)]),
     "hmm_estep_stats": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(hmm_batch), C.c_void_p,
                                   C.c_void_p, C.c_void_p]),
     "hmm_mstep": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(hmm_batch),

@@ -1,34 +1,7 @@
-// Instantiations and launcher of the small-N fused E-step kernel.
+// Shape selection and dispatch of the small-N fused E-step kernel.
 #include "launch.h"
 
 namespace hmm {
-
-namespace {
-
-template <int NP, int G>
-cudaError_t launch_one(const EStepArgs& a, int table_mode, int n_sm, cudaStream_t st) {
-  constexpr int WPB = kWarpsPerBlock;
-  const size_t smem = sizeof(WarpSmem<SmallCfg<NP, G>>) * WPB;
-  auto kern = estep_small_kernel<NP, G, WPB>;
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
-  int per_sm = 0;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, WPB * 32, smem);
-  if (e != cudaSuccess) return e;
-  if (per_sm < 1) per_sm = 1;
-  const int want = (a.n_items + WPB - 1) / WPB;
-  int grid = per_sm * n_sm;
-  if (want < grid) grid = want;
-  if (grid < 1) grid = 1;
-  kern<<<grid, WPB * 32, smem, st>>>(a, table_mode);
-  return cudaGetLastError();
-}
-
-}  // namespace
 
 bool estep_small_supported(int NP, int G) {
   switch (NP) {
@@ -55,23 +28,16 @@ int default_estep_G(int NP, int64_t n_seq, int n_sm) {
   return G;
 }
 
-cudaError_t launch_estep_small(int NP, int G, const EStepArgs& a, int table_mode, int n_sm,
+cudaError_t launch_estep_small(int NP, int G, int mode, const EStepArgs& a, int fam, int n_sm,
                                cudaStream_t st) {
-#define HMM_CASE(np, g) \
-  if (NP == np && G == g) return launch_one<np, g>(a, table_mode, n_sm, st);
-  HMM_CASE(2, 1)
-  HMM_CASE(2, 2)
-  HMM_CASE(4, 1)
-  HMM_CASE(4, 2)
-  HMM_CASE(4, 4)
-  HMM_CASE(8, 2)
-  HMM_CASE(8, 4)
-  HMM_CASE(8, 8)
-  HMM_CASE(16, 4)
-  HMM_CASE(16, 8)
-  HMM_CASE(16, 16)
-  HMM_CASE(32, 16)
-#undef HMM_CASE
+  if (!estep_small_supported(NP, G)) return cudaErrorInvalidValue;
+  switch (NP) {
+    case 2:
+    case 4: return launch_estep_np2_4(NP, G, mode, a, fam, n_sm, st);
+    case 8: return launch_estep_np8(G, mode, a, fam, n_sm, st);
+    case 16: return launch_estep_np16(G, mode, a, fam, n_sm, st);
+    case 32: return launch_estep_np32(G, mode, a, fam, n_sm, st);
+  }
   return cudaErrorInvalidValue;
 }
 

@@ -36,6 +36,8 @@
 // fixed-order float64 kernel.
 #pragma once
 
+#include <type_traits>
+
 #include "common.cuh"
 
 namespace hmm {
@@ -58,7 +60,6 @@ struct EStepArgs {
   double* loglik;            // [S] or nullptr
   int* work_counter;
   int* status;
-  int want_stats;
 };
 
 template <int NP_, int G_>
@@ -69,9 +70,8 @@ struct SmallCfg {
   static constexpr int CPW = 32 / G;
   static constexpr int SPW = CPW / 2;
   static constexpr int F = NP + NST;
-  static constexpr int PD = 6;          // prefetch ring depth (iterations)
-  static constexpr int GAP = PD - 1;    // idle iterations between the phases
-  static constexpr int FLUSH = 64;      // inner accumulation length
+  static constexpr int PD = 6;          // prefetch ring depth (steps)
+  static constexpr int FLUSH = 64;      // inner accumulation length (steps)
   static_assert(NP % G == 0 && G <= 16 && (32 % G) == 0, "bad chain shape");
 };
 
@@ -83,6 +83,7 @@ struct alignas(16) WarpSmem {
   float oring[C::PD][C::CPW][C::NP];     // partner rows (phase 2) / logb rows (table)
   float lring[C::PD][C::CPW][C::NP];     // logb rows in table mode
   long long offf[C::SPW];                // forward offsets at the end of phase 1
+  float acc[C::R * C::F][32];            // outer sums, field-major / lane-minor
 };
 
 __device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
@@ -167,60 +168,23 @@ __device__ __forceinline__ void accumulate_stats(int fam, const Feat& f, const f
   }
 }
 
-// Role of a chain at warp iteration k.
-struct Role {
-  int t;        // time index, or -1 when idle
-  bool phase2;
-};
+// Mode bits of the E-step kernels (compile time).
+constexpr int MODE_STATS = 1;   // accumulate xi and the family sums
+constexpr int MODE_GAMMA = 2;   // write gamma_t(j) rows
 
-template <class C>
-__device__ __forceinline__ Role role_at(int k, int dir, int T, int h) {
-  Role r{-1, false};
-  if (T <= 0) return r;
-  if (dir == 0) {
-    if (k < h) r.t = k;
-    else if (k >= h + C::GAP && k < T + C::GAP) { r.t = k - C::GAP; r.phase2 = true; }
-  } else {
-    if (k < T - h) r.t = T - 1 - k;
-    else if (k >= h + C::GAP && k < 2 * h + C::GAP) { r.t = 2 * h + C::GAP - 1 - k; r.phase2 = true; }
-  }
-  return r;
+__device__ __forceinline__ float lg2a(float x) {
+  float y;
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
 }
 
-// Issue the prefetches that iteration kk needs into ring slot kk % PD.
-template <class C, int FAM>
-__device__ __forceinline__ void prefetch_iter(WarpSmem<C>& sm, const EStepArgs& a, int kk, int chain,
-                                              int sub, int dir, int T, int h, int64_t base) {
-  Role r = role_at<C>(kk, dir, T, h);
-  if (r.t < 0) return;
-  const int slot = kk % C::PD;
-  if constexpr (FAM == FAM_TABLE) {
-    const int N = a.mv.N;
-#pragma unroll
-    for (int q = 0; q < C::R; ++q) {
-      int k = sub * C::R + q;
-      if (k < N) cp_async4(&sm.lring[slot][chain][k], a.logb + (base + r.t) * N + k);
-    }
-  } else {
-    if (sub == 0) cp_async4(&sm.yring[slot][chain], a.y + base + r.t);
-  }
-  if (r.phase2) {
-    const float* src = a.scratch + (base + r.t) * C::NP + sub * C::R;
-    float* dst = &sm.oring[slot][chain][sub * C::R];
-    if constexpr (C::R % 4 == 0) {
-#pragma unroll
-      for (int q = 0; q < C::R; q += 4) cp_async16(dst + q, src + q);
-    } else if constexpr (C::R == 2) {
-      cp_async8(dst, src);
-    } else {
-      cp_async4(dst, src);
-    }
-  }
-}
-
-template <class C, int FAM>
+template <class C, int FAM, int MODE>
 __device__ void estep_item(WarpSmem<C>& sm, const EStepArgs& a, int item, int lane) {
   constexpr int NP = C::NP, G = C::G, R = C::R, F = C::F;
+  constexpr bool STATS = (MODE & MODE_STATS) != 0;
+  constexpr bool GAMMA = (MODE & MODE_GAMMA) != 0;
+  constexpr int NH = NP / 2;
+  constexpr int PD = C::PD;
   const int chain = lane / G, sub = lane % G;
   const int pair = chain >> 1, dir = chain & 1;
   const int slotseq = item * C::SPW + pair;
@@ -233,15 +197,22 @@ __device__ void estep_item(WarpSmem<C>& sm, const EStepArgs& a, int item, int la
   const int fam_rt = a.mv.family[m];
   const int N = a.mv.N;
   const int k0 = sub * R;
+  int fam = FAM;
+  if constexpr (FAM == FAM_ANY) fam = fam_rt;
 
-  // ---- model data of this chain
-  float Mb[NP][R];   // forward: a_{i, k0+r}; backward: a_{k0+r, i}
+  // ---- model data of this chain: pairs over the summation index i
+  float2 Mb[NH][R];   // forward: (a_{i,k}, a_{i+1,k}); backward: (a_{k,i}, a_{k,i+1})
   const float* Am = a.mv.A32 + (size_t)m * NP * NP;
 #pragma unroll
-  for (int i = 0; i < NP; ++i)
+  for (int i = 0; i < NH; ++i)
 #pragma unroll
-    for (int q = 0; q < R; ++q)
-      Mb[i][q] = dir == 0 ? __ldg(Am + i * NP + k0 + q) : __ldg(Am + (k0 + q) * NP + i);
+    for (int q = 0; q < R; ++q) {
+      const int k = k0 + q;
+      Mb[i][q] = dir == 0 ? make_float2(__ldg(Am + (2 * i) * NP + k), __ldg(Am + (2 * i + 1) * NP + k))
+                          : make_float2(__ldg(Am + k * NP + 2 * i), __ldg(Am + k * NP + 2 * i + 1));
+    }
+  constexpr bool NEED_NB = (FAM == HMM_NEGBIN || FAM == FAM_ANY);
+  constexpr bool NEED_C2 = (FAM == HMM_STUDENT_T || FAM == FAM_ANY);
   float init[R];
   float cf[R][4];
   float cf2[R][2];
@@ -253,84 +224,117 @@ __device__ void estep_item(WarpSmem<C>& sm, const EStepArgs& a, int item, int la
     const float* c = a.mv.coef + ((size_t)m * NP + k) * KC;
 #pragma unroll
     for (int z = 0; z < 4; ++z) cf[q][z] = __ldg(c + z);
-    cf2[q][0] = __ldg(c + 4);
-    cf2[q][1] = __ldg(c + 5);
-    nbt[q] = a.mv.nbtab ? a.mv.nbtab + ((size_t)m * NP + k) * NB_YMAX : nullptr;
+    cf2[q][0] = NEED_C2 ? __ldg(c + 4) : 0.f;
+    cf2[q][1] = NEED_C2 ? __ldg(c + 5) : 0.f;
+    nbt[q] = (NEED_NB && a.mv.nbtab) ? a.mv.nbtab + ((size_t)m * NP + k) * NB_YMAX : nullptr;
   }
 
-  // ---- iteration count of the warp
-  int kmax = T > 0 ? 2 * h + C::GAP : 0;
+  // ---- schedule: phase 1 runs n1 steps (forward t = 0..h-1, backward
+  // t = T-1..h), phase 2 runs n2 steps (forward t = h..T-1, backward
+  // t = h-1..0).  The warp runs the longest phase of its chains; shorter
+  // chains are masked.
+  const int n1 = T <= 0 ? 0 : (dir == 0 ? h : T - h);
+  const int n2 = T <= 0 ? 0 : (dir == 0 ? T - h : h);
+  const int dt = dir == 0 ? 1 : -1;
+  const int ta = dir == 0 ? 0 : T - 1;       // phase-1 start
+  const int tb = dir == 0 ? h : h - 1;       // phase-2 start
+  int K1 = h, K2 = h;
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) kmax = max(kmax, __shfl_xor_sync(0xffffffffu, kmax, o));
+  for (int o = 16; o > 0; o >>= 1) {
+    K1 = max(K1, __shfl_xor_sync(0xffffffffu, K1, o));
+    K2 = max(K2, __shfl_xor_sync(0xffffffffu, K2, o));
+  }
 
-  // ---- accumulators
-  float xi[R][NP];
+  // ---- accumulators (two-level: registers for <= FLUSH steps, then global)
+  float2 xi[R][NH];
   float st[R][NST];
 #pragma unroll
   for (int q = 0; q < R; ++q) {
 #pragma unroll
-    for (int i = 0; i < NP; ++i) xi[q][i] = 0.f;
+    for (int i = 0; i < NH; ++i) xi[q][i] = make_float2(0.f, 0.f);
 #pragma unroll
     for (int z = 0; z < NST; ++z) st[q][z] = 0.f;
   }
-  float* part = a.partials + ((size_t)(valid ? seq : 0) * 2 + dir) * NP * F + (size_t)k0 * F;
-  bool first_flush = true;
+  // Outer level of the two-level sums: per-lane slots in shared memory
+  // (conflict free), added every FLUSH steps; written to the per-sequence
+  // partials once at the end of the item.
+  if constexpr (STATS) {
+#pragma unroll
+    for (int f = 0; f < R * F; ++f) sm.acc[f][lane] = 0.f;
+  }
   auto flush = [&]() {
-    if (valid && a.want_stats) {
+    if constexpr (STATS) {
 #pragma unroll
       for (int q = 0; q < R; ++q) {
-        float* p = part + q * F;
 #pragma unroll
-        for (int i = 0; i < NP; ++i) {
-          p[i] = first_flush ? xi[q][i] : p[i] + xi[q][i];
-          xi[q][i] = 0.f;
+        for (int i = 0; i < NH; ++i) {
+          sm.acc[q * F + 2 * i][lane] += xi[q][i].x;
+          sm.acc[q * F + 2 * i + 1][lane] += xi[q][i].y;
+          xi[q][i] = make_float2(0.f, 0.f);
         }
 #pragma unroll
         for (int z = 0; z < NST; ++z) {
-          p[NP + z] = first_flush ? st[q][z] : p[NP + z] + st[q][z];
+          sm.acc[q * F + NP + z][lane] += st[q][z];
           st[q][z] = 0.f;
         }
       }
     }
-    first_flush = false;
   };
 
-  float v[R];
+  float v[R], gl[R];
 #pragma unroll
-  for (int q = 0; q < R; ++q) v[q] = 0.f;
+  for (int q = 0; q < R; ++q) {
+    v[q] = 0.f;
+    gl[q] = 0.f;
+  }
   long long off = 0;       // running log2 offset of this chain
   bool started = false;    // the chain has produced its first vector
+  const float* ybase = a.y + base;
+  const float* sbase = a.scratch + base * NP + k0;
+  float* wbase = a.scratch + base * NP + k0;
 
-  // ---- prologue prefetch (iterations 0 .. PD-2)
+  // prefetch of the step kk of the current phase into ring slot `slot`
+  auto prefetch = [&](int kk, int n, int t0, bool ph2, int slot) {
+    if (kk >= n) return;
+    const int t = t0 + dt * kk;
+    if constexpr (FAM == FAM_TABLE) {
 #pragma unroll
-  for (int kk = 0; kk < C::PD - 1; ++kk) {
-    if (kk < kmax) prefetch_iter<C, FAM>(sm, a, kk, chain, sub, dir, T, h, base);
-    cp_commit();
-  }
-
-  for (int k = 0; k < kmax; ++k) {
-    const Role r = role_at<C>(k, dir, T, h);
-    const bool active = r.t >= 0;
-    const bool p2 = active && r.phase2;
-    const int slot = k % C::PD;
-
-    // publish the previous vector for the mat-vec
-    if (active && started) {
-#pragma unroll
-      for (int q = 0; q < R; ++q) sm.xbuf[k & 1][chain][k0 + q] = v[q];
+      for (int q = 0; q < R; ++q)
+        if (k0 + q < N) cp_async4(&sm.lring[slot][chain][k0 + q], a.logb + (base + t) * N + k0 + q);
+    } else {
+      if (sub == 0) cp_async4(&sm.yring[slot][chain], ybase + t);
     }
-    cp_wait<C::PD - 2>();
-    __syncwarp();
-    // refill the slot consumed by iteration k-1 with the data of k+PD-1
-    if (k + C::PD - 1 < kmax) prefetch_iter<C, FAM>(sm, a, k + C::PD - 1, chain, sub, dir, T, h, base);
-    cp_commit();
+    if (ph2) {
+      const float* src = sbase + (int64_t)t * NP;
+      float* dst = &sm.oring[slot][chain][k0];
+      if constexpr (R % 4 == 0) {
+#pragma unroll
+        for (int q = 0; q < R; q += 4) cp_async16(dst + q, src + q);
+      } else if constexpr (R == 2) {
+        cp_async8(dst, src);
+      } else {
+        cp_async4(dst, src);
+      }
+    }
+  };
 
-    // Every lane runs the arithmetic below (idle chains on stale data) so that
-    // the chain-wide shuffles stay convergent; only active chains commit.
-    // ---- emission log2 b_k(y_t) for the owned states
+  // one recursion step of phase PH2 (false: phase 1) at warp iteration k
+  auto step = [&](auto ph2_tag, int k, int n, int t0, int& slot, int& pslot, int xb) {
+    constexpr bool PH2 = decltype(ph2_tag)::value;
+    const bool act = k < n;
+    const int t = t0 + dt * k;
+    if (act && started) {
+#pragma unroll
+      for (int q = 0; q < R; ++q) sm.xbuf[xb][chain][k0 + q] = v[q];
+    }
+    cp_wait<PD - 2>();
+    __syncwarp();
+    prefetch(k + PD - 1, n, t0, PH2, pslot);
+    cp_commit();
+    pslot = (pslot == PD - 1) ? 0 : pslot + 1;
+
+    // emission log2 b_k(y_t) of the owned states
     float lb[R];
-    int fam = FAM;
-    if constexpr (FAM == FAM_ANY) fam = fam_rt;
     Feat ft;
     if constexpr (FAM == FAM_TABLE) {
       ft.y = 0.f;
@@ -343,90 +347,103 @@ __device__ void estep_item(WarpSmem<C>& sm, const EStepArgs& a, int item, int la
     } else {
       ft = feat_of(fam, sm.yring[slot][chain], a.mv.lfact2);
 #pragma unroll
-      for (int q = 0; q < R; ++q)
-        lb[q] = (ft.ok && (k0 + q) < N) ? emis_log2(fam, ft, cf[q], nbt[q]) : -INFINITY;
+      for (int q = 0; q < R; ++q) {
+        const float e = emis_log2(fam, ft, cf[q], nbt[q]);
+        lb[q] = (ft.ok && (k0 + q) < N) ? e : -INFINITY;
+      }
     }
 
-    // ---- mat-vec s = M^T v_prev (or the initial vector)
+    // mat-vec s = M^T v_prev (or the initial vector), packed FP32x2 FMAs
     const bool first = !started;
+    float2 vin[NH];
+    load_row<NP>(&sm.xbuf[xb][chain][0], reinterpret_cast<float*>(vin));
     float s[R];
-    float vin[NP];
-    load_row<NP>(&sm.xbuf[k & 1][chain][0], vin);
 #pragma unroll
     for (int q = 0; q < R; ++q) {
-      float e0 = 0.f, e1 = 0.f;
+      float2 e0 = make_float2(0.f, 0.f), e1 = make_float2(0.f, 0.f);
 #pragma unroll
-      for (int i = 0; i < NP; i += 2) {
-        e0 = fmaf(vin[i], Mb[i][q], e0);
-        e1 = fmaf(vin[i + 1], Mb[i + 1][q], e1);
+      for (int i = 0; i < NH; i += 2) {
+        e0 = __ffma2_rn(vin[i], Mb[i][q], e0);
+        if (i + 1 < NH) e1 = __ffma2_rn(vin[i + 1], Mb[i + 1][q], e1);
       }
-      s[q] = first ? init[q] : e0 + e1;
+      s[q] = first ? init[q] : (e0.x + e0.y) + (e1.x + e1.y);
     }
 
-    // ---- phase 2: occupancies, xi and statistics
-    float o[R];
+    if constexpr (PH2) {
+      float o[R];
 #pragma unroll
-    for (int q = 0; q < R; ++q) o[q] = sm.oring[slot][chain][k0 + q];
-    float zl = 0.f;
+      for (int q = 0; q < R; ++q) o[q] = sm.oring[slot][chain][k0 + q];
+      float zl = 0.f;
 #pragma unroll
-    for (int q = 0; q < R; ++q) zl = fmaf(s[q], o[q], zl);
-    const float Z = group_sum<G>(p2 ? zl : 0.f);
-    if (p2) {
-      const bool bfirst = (dir == 1) && first_phase2_of_bwd(k, h, C::GAP);
-      if (bfirst && sub == 0) {
-        // log P(y) = log2 Z + O_bwd + O_fwd  (then x ln 2)
-        const long long of = sm.offf[pair];
-        double ll = (Z > 0.f) ? ((double)log2f(Z) + (double)(off + of)) * kLn2 : -INFINITY;
-        if (!(Z == Z)) {
-          ll = NAN;
-          set_status(a.status, ST_NUMERIC);
+      for (int q = 0; q < R; ++q) zl = fmaf(s[q], o[q], zl);
+      const float Z = group_sum<G>(zl);
+      const bool bfirst = (dir == 1) && (k == 0);
+      if (k == 0) {   // warp-uniform: log P(y) at the backward chain's first phase-2 step
+        if (bfirst && sub == 0 && act) {
+          const long long of = sm.offf[pair];
+          double ll = (Z > 0.f) ? ((double)log2f(Z) + (double)(off + of)) * kLn2 : -INFINITY;
+          if (!(Z == Z)) {
+            ll = NAN;
+            set_status(a.status, ST_NUMERIC);
+          }
+          if (a.loglik && valid) a.loglik[seq] = ll;
         }
-        if (a.loglik && valid) a.loglik[seq] = ll;
       }
-      const float rz = (Z > 0.f) ? 1.0f / Z : 0.f;
+      const float rz = (act && Z > 0.f) ? rcpf(Z) : 0.f;
       float w[R], g[R];
 #pragma unroll
       for (int q = 0; q < R; ++q) {
         w[q] = o[q] * rz;
         g[q] = s[q] * w[q];
+        gl[q] = act ? g[q] : gl[q];
       }
-      if (a.want_stats) {
-        if (!first && !bfirst) {
+      if constexpr (STATS) {
+       if (act) {
+        // xi between the previous and the current step (not at the
+        // backward's first phase-2 step: the forward chain counts that pair)
+        const float xs = (first || bfirst) ? 0.f : 1.f;
 #pragma unroll
-          for (int q = 0; q < R; ++q)
+        for (int q = 0; q < R; ++q) {
+          const float wq = w[q] * xs;
+          const float2 w2 = make_float2(wq, wq);
 #pragma unroll
-            for (int i = 0; i < NP; ++i) xi[q][i] = fmaf(vin[i], w[q], xi[q][i]);
+          for (int i = 0; i < NH; ++i) xi[q][i] = __ffma2_rn(vin[i], w2, xi[q][i]);
         }
 #pragma unroll
         for (int q = 0; q < R; ++q) {
-          const float gq = g[q];
-          st[q][0] += gq;
-          if constexpr (FAM != FAM_TABLE) accumulate_stats(fam, ft, cf[q], cf2[q], gq, st[q]);
-          if (dir == 1 && r.t == 0) st[q][NST - 1] += gq;
+          st[q][0] += g[q];
+          if constexpr (FAM != FAM_TABLE) accumulate_stats(fam, ft, cf[q], cf2[q], g[q], st[q]);
         }
+       }
       }
-      if (a.gamma) {
-        float* gr = a.gamma + (base + r.t) * (int64_t)N;
+      if constexpr (GAMMA) {
+        if (act) {
+          float* gr = a.gamma + (base + t) * (int64_t)N;
 #pragma unroll
-        for (int q = 0; q < R; ++q)
-          if (k0 + q < N) gr[k0 + q] = g[q];
+          for (int q = 0; q < R; ++q)
+            if (k0 + q < N) gr[k0 + q] = g[q];
+        }
       }
     }
 
-    // ---- new vector: v = s * 2^(lb - E), E = floor(max(lb + floor(log2 s)))
+    // new vector: v = s * 2^(lb - E), E = floor(max_j(lb_j + log2 s_j))
     float tm = -INFINITY;
 #pragma unroll
-    for (int q = 0; q < R; ++q) tm = fmaxf(tm, lb[q] + ilog2f(s[q]));
+    for (int q = 0; q < R; ++q) tm = fmaxf(tm, lb[q] + lg2a(s[q]));
     tm = group_max<G>(tm);
     const float E = (tm > -INFINITY) ? floorf(tm) : 0.f;
-    if (active) {
 #pragma unroll
-      for (int q = 0; q < R; ++q) v[q] = s[q] * ex2f(lb[q] - E);
+    for (int q = 0; q < R; ++q) {
+      const float nv = s[q] * ex2f(lb[q] - E);
+      v[q] = act ? nv : v[q];
+    }
+    if (act) {
       off += (long long)E;
       started = true;
-      if (!r.phase2) {
-        // store v_t for the partner's phase 2
-        float* dst = a.scratch + (base + r.t) * NP + k0;
+    }
+    if constexpr (!PH2) {
+      if (act) {
+        float* dst = wbase + (int64_t)t * NP;
         if constexpr (R % 4 == 0) {
 #pragma unroll
           for (int q = 0; q < R; q += 4)
@@ -437,12 +454,57 @@ __device__ void estep_item(WarpSmem<C>& sm, const EStepArgs& a, int item, int la
 #pragma unroll
           for (int q = 0; q < R; ++q) dst[q] = v[q];
         }
-        if (dir == 0 && r.t == h - 1 && sub == 0) sm.offf[pair] = off;
       }
     }
-    if ((k % C::FLUSH) == C::FLUSH - 1) flush();
+    slot = (slot == PD - 1) ? 0 : slot + 1;
+  };
+
+
+  // ---- phase 1
+  int slot = 0, pslot = PD - 1;
+#pragma unroll
+  for (int kk = 0; kk < PD - 1; ++kk) {
+    prefetch(kk, n1, ta, false, kk);
+    cp_commit();
+  }
+  int xb = 0;
+  for (int k = 0; k < K1; ++k) {
+    step(std::false_type{}, k, n1, ta, slot, pslot, xb);
+    xb ^= 1;
+    if ((k & (C::FLUSH - 1)) == C::FLUSH - 1) flush();
+  }
+  if (dir == 0 && sub == 0) sm.offf[pair] = off;
+  cp_wait<0>();
+  __syncwarp();   // phase-1 rows of both chains are visible from here on
+
+  // ---- phase 2
+  slot = 0;
+  pslot = PD - 1;
+#pragma unroll
+  for (int kk = 0; kk < PD - 1; ++kk) {
+    prefetch(kk, n2, tb, true, kk);
+    cp_commit();
+  }
+  for (int k = 0; k < K2; ++k) {
+    step(std::true_type{}, k, n2, tb, slot, pslot, xb);
+    xb ^= 1;
+    if ((k & (C::FLUSH - 1)) == C::FLUSH - 1) flush();
+  }
+  // gamma_1 (the backward chain's last occupancy) feeds the pi update
+  if constexpr (STATS) {
+    if (dir == 1 && T > 0) {
+#pragma unroll
+      for (int q = 0; q < R; ++q) st[q][NST - 1] += gl[q];
+    }
   }
   flush();
+  if constexpr (STATS) {
+    if (valid) {
+      float* part = a.partials + ((size_t)seq * 2 + dir) * NP * F + (size_t)k0 * F;
+#pragma unroll
+      for (int f = 0; f < R * F; ++f) part[f] = sm.acc[f][lane];
+    }
+  }
   cp_wait<0>();
   __syncwarp();
   if (valid && T == 0 && dir == 1 && sub == 0 && a.loglik) a.loglik[seq] = 0.0;
@@ -455,8 +517,13 @@ namespace hmm {
 // Persistent launch: warps pull work items (SPW sequences each) from a
 // global counter; items are laid out in the plan's order (family, then
 // length descending) so that consecutive items are alike.
-template <int NP, int G, int WPB>
-__global__ void __launch_bounds__(WPB * 32) estep_small_kernel(EStepArgs a, int table_mode) {
+// FAMK: one emission family for the whole launch, FAM_TABLE for a log b
+// table, or FAM_ANY for batches that mix families (the family is then
+// chosen per work item; warps straddling two families take the slower
+// per-step switch).  Specialised launches keep the register budget of the
+// common single-family case low.
+template <int NP, int G, int WPB, int MODE, int FAMK>
+__global__ void __launch_bounds__(WPB * 32) estep_small_kernel(EStepArgs a) {
   using C = SmallCfg<NP, G>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   WarpSmem<C>& sm = reinterpret_cast<WarpSmem<C>*>(smem_raw)[threadIdx.x >> 5];
@@ -466,25 +533,21 @@ __global__ void __launch_bounds__(WPB * 32) estep_small_kernel(EStepArgs a, int 
     if (lane == 0) item = atomicAdd(a.work_counter, 1);
     item = __shfl_sync(0xffffffffu, item, 0);
     if (item >= a.n_items) break;
-    if (table_mode) {
-      estep_item<C, FAM_TABLE>(sm, a, item, lane);
-      continue;
-    }
-    const int pair = (lane / G) >> 1;
-    const int slotseq = item * C::SPW + pair;
-    const int fam = slotseq < a.n_seq ? a.mv.family[a.model_id[a.order[slotseq]]] : -2;
-    const int fam0 = __shfl_sync(0xffffffffu, fam, 0);
-    const bool uniform = __all_sync(0xffffffffu, fam == fam0 || fam == -2);
-    switch (uniform ? fam0 : FAM_ANY) {
-      case HMM_GAUSS: estep_item<C, HMM_GAUSS>(sm, a, item, lane); break;
-      case HMM_POISSON: estep_item<C, HMM_POISSON>(sm, a, item, lane); break;
-      case HMM_GAMMA: estep_item<C, HMM_GAMMA>(sm, a, item, lane); break;
-      case HMM_BETA: estep_item<C, HMM_BETA>(sm, a, item, lane); break;
-      case HMM_WEIBULL: estep_item<C, HMM_WEIBULL>(sm, a, item, lane); break;
-      case HMM_NEGBIN: estep_item<C, HMM_NEGBIN>(sm, a, item, lane); break;
-      case HMM_STUDENT_T: estep_item<C, HMM_STUDENT_T>(sm, a, item, lane); break;
-      case HMM_VONMISES: estep_item<C, HMM_VONMISES>(sm, a, item, lane); break;
-      default: estep_item<C, FAM_ANY>(sm, a, item, lane); break;
+    if constexpr (FAMK != FAM_ANY) {
+      estep_item<C, FAMK, MODE>(sm, a, item, lane);
+    } else {
+      const int pair = (lane / G) >> 1;
+      const int slotseq = item * C::SPW + pair;
+      const int fam = slotseq < a.n_seq ? a.mv.family[a.model_id[a.order[slotseq]]] : -2;
+      const int fam0 = __shfl_sync(0xffffffffu, fam, 0);
+      const bool uniform = __all_sync(0xffffffffu, fam == fam0 || fam == -2);
+      switch (uniform ? fam0 : FAM_ANY) {
+        case HMM_GAUSS: estep_item<C, HMM_GAUSS, MODE>(sm, a, item, lane); break;
+        case HMM_POISSON: estep_item<C, HMM_POISSON, MODE>(sm, a, item, lane); break;
+        case HMM_NEGBIN: estep_item<C, HMM_NEGBIN, MODE>(sm, a, item, lane); break;
+        case HMM_VONMISES: estep_item<C, HMM_VONMISES, MODE>(sm, a, item, lane); break;
+        default: estep_item<C, FAM_ANY, MODE>(sm, a, item, lane); break;
+      }
     }
   }
 }

@@ -8,6 +8,7 @@
 #include <vector>
 
 #include "launch.h"
+#include "plain.cuh"
 #include "runtime.h"
 
 namespace hmm {
@@ -60,6 +61,39 @@ static int param_count(int fam, int D) {
 
 static cudaStream_t S(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 
+// Records a pair of CUDA events around the launches made in its scope when
+// the context's profiling option is on (not inside a graph capture).
+struct KTimer {
+  hmm_ctx ctx;
+  int slot;
+  cudaStream_t st;
+  cudaEvent_t e0 = nullptr;
+  static cudaEvent_t take(hmm_ctx c) {
+    if (!c->event_pool.empty()) {
+      cudaEvent_t e = c->event_pool.back();
+      c->event_pool.pop_back();
+      return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    return e;
+  }
+  KTimer(hmm_ctx c, int sl, cudaStream_t s) : ctx(c), slot(sl), st(s) {
+    if (!ctx || !ctx->profile) return;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return;
+    e0 = take(ctx);
+    if (e0) cudaEventRecord(e0, st);
+  }
+  ~KTimer() {
+    if (!e0) return;
+    cudaEvent_t e1 = take(ctx);
+    if (!e1) return;
+    cudaEventRecord(e1, st);
+    ctx->pending.push_back({slot, e0, e1});
+  }
+};
+
 // ---------------------------------------------------------------- kernels
 __global__ void post_path_kernel(const float* __restrict__ gamma, int64_t total_T, int N,
                                  int32_t* __restrict__ path) {
@@ -102,6 +136,28 @@ __global__ void emission_kernel(ModelView mv, const float* __restrict__ y, const
     const float l2 = f.ok ? emis_log2(fam, f, c, nbt) : -INFINITY;
     logb[t * N + k] = l2 * kLn2f;
   }
+}
+
+template <int NP>
+cudaError_t launch_plain_np(const PlainArgs& a, cudaStream_t st) {
+  const int spb = 4 * (32 / NP);
+  const unsigned grid = (unsigned)((a.n_seq + spb - 1) / spb);
+  plain_recursions_kernel<NP><<<grid, 128, 0, st>>>(a);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  plain_posterior_kernel<NP><<<grid, 128, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_plain(int NP, const PlainArgs& a, cudaStream_t st) {
+  switch (NP) {
+    case 2: return launch_plain_np<2>(a, st);
+    case 4: return launch_plain_np<4>(a, st);
+    case 8: return launch_plain_np<8>(a, st);
+    case 16: return launch_plain_np<16>(a, st);
+    case 32: return launch_plain_np<32>(a, st);
+  }
+  return cudaErrorInvalidValue;
 }
 
 }  // namespace hmm
@@ -225,6 +281,12 @@ hmm_plan make_plan(hmm_ctx ctx, hmm_model model, const hmm_batch* b, const int64
       HMM_CUDA(cudaMemcpy(p->chunk_hi.p, hi.data(), hi.size() * 4, cudaMemcpyHostToDevice));
     }
     HMM_CUDA(cudaMemcpy(p->model_chunk_ptr.p, mptr.data(), mptr.size() * 4, cudaMemcpyHostToDevice));
+    int uf = -2;
+    for (int64_t q2 = 0; q2 < S; ++q2) {
+      const int f = model->h_family[hm[q2]];
+      uf = (uf == -2 || uf == f) ? f : -1;
+    }
+    p->uniform_family = uf < 0 ? -1 : uf;
     p->h_order = std::move(order);
   } catch (...) {
     p->order.release();
@@ -299,6 +361,25 @@ void run_estep(hmm_ctx ctx, hmm_model model, const hmm_batch* b, hmm_plan plan, 
     ll = ctx->loglik.as<double>();
   }
   if (S == 0) return;
+  if (ctx->plain_estep) {
+    if (logb || gamma)
+      throw Error{HMM_E_UNSUPPORTED, "the plain path computes log-likelihoods and statistics only"};
+    ctx->plain_beta.ensure(std::max<int64_t>(b->total_T, 1) * NP * 4 + 64);
+    PlainArgs pa;
+    pa.y = b->values;
+    pa.offsets = b->offsets;
+    pa.model_id = b->model_id;
+    pa.n_seq = (int32_t)S;
+    pa.mv = model->view();
+    pa.alpha = ctx->scratch.as<float>();
+    pa.beta = ctx->plain_beta.as<float>();
+    pa.partials = ctx->partials.as<float>();
+    pa.loglik = ll;
+    {
+      KTimer kt(ctx, HMM_KT_PLAIN, st);
+      HMM_CUDA(launch_plain(NP, pa, st));
+    }
+  }
   EStepArgs a;
   a.y = b->values;
   a.logb = logb;
@@ -306,7 +387,8 @@ void run_estep(hmm_ctx ctx, hmm_model model, const hmm_batch* b, hmm_plan plan, 
   a.model_id = b->model_id;
   a.order = plan->order.as<int32_t>();
   a.n_seq = (int32_t)S;
-  const int G = default_estep_G(NP, S, ctx->n_sm);
+  int G = default_estep_G(NP, S, ctx->n_sm);
+  if (ctx->estep_lanes && estep_small_supported(NP, ctx->estep_lanes)) G = ctx->estep_lanes;
   a.n_items = (int32_t)((S + estep_seqs_per_item(G) - 1) / estep_seqs_per_item(G));
   a.mv = model->view();
   a.scratch = ctx->scratch.as<float>();
@@ -315,10 +397,15 @@ void run_estep(hmm_ctx ctx, hmm_model model, const hmm_batch* b, hmm_plan plan, 
   a.loglik = ll;
   a.work_counter = ctx->counters;
   a.status = ctx->status;
-  a.want_stats = want_stats ? 1 : 0;
-  HMM_CUDA(cudaMemsetAsync(ctx->counters, 0, sizeof(int), st));
-  HMM_CUDA(launch_estep_small(NP, G, a, logb ? 1 : 0, ctx->n_sm, st));
+  if (!ctx->plain_estep) {
+    HMM_CUDA(cudaMemsetAsync(ctx->counters, 0, sizeof(int), st));
+    KTimer kt(ctx, HMM_KT_ESTEP, st);
+    const int mode = (want_stats ? MODE_STATS : 0) | (gamma ? MODE_GAMMA : 0);
+    const int fam = logb ? FAM_TABLE : (plan->uniform_family >= 0 ? plan->uniform_family : FAM_ANY);
+    HMM_CUDA(launch_estep_small(NP, G, mode, a, fam, ctx->n_sm, st));
+  }
   if (want_stats) {
+    KTimer kt(ctx, HMM_KT_REDUCE, st);
     const int RS = rec_size(NP);
     ctx->chunk_rec.ensure((size_t)std::max(plan->n_chunks, 1) * RS * 8);
     if (plan->n_chunks > 0) {
@@ -349,6 +436,7 @@ void run_mstep(hmm_ctx ctx, hmm_model model, hmm_stats stats, const MStepOpts& o
   if (model->any_negbin || model->any_weibull)
     throw Error{HMM_E_UNSUPPORTED, "Weibull / negative-binomial M-steps are not in this build"};
   if (model->any_mv) throw Error{HMM_E_UNSUPPORTED, "multivariate M-steps are not in this build"};
+  KTimer kt(ctx, HMM_KT_MSTEP, st);
   mstep_kernel<<<model->M, model->NP, 0, st>>>(model->bufs(), stats->rec.as<double>(), o);
   HMM_CUDA(cudaGetLastError());
 }
@@ -436,6 +524,12 @@ hmm_status hmm_ctx_destroy(hmm_ctx ctx) {
     cudaFree(ctx->status);
     cudaFree(ctx->counters);
     if (ctx->work_stream) cudaStreamDestroy(ctx->work_stream);
+    for (auto& r : ctx->pending) {
+      cudaEventDestroy(r.e0);
+      cudaEventDestroy(r.e1);
+    }
+    for (auto e : ctx->event_pool) cudaEventDestroy(e);
+    ctx->plain_beta.release();
     delete ctx;
   });
 }
@@ -453,6 +547,47 @@ hmm_status hmm_ctx_status(hmm_ctx ctx, void* stream) {
   if (v & ST_NUMERIC) return HMM_E_NUMERIC;
   if (v & ST_ARG) return HMM_E_ARG;
   return HMM_OK;
+}
+
+hmm_status hmm_ctx_set_option(hmm_ctx ctx, int32_t key, int64_t value) {
+  return guarded([&] {
+    HMM_REQUIRE(ctx != nullptr, "ctx is NULL");
+    switch (key) {
+      case HMM_OPT_PROFILE: ctx->profile = value != 0; break;
+      case HMM_OPT_ESTEP_LANES: ctx->estep_lanes = (int)value; break;
+      case HMM_OPT_VITERBI_LANES: ctx->viterbi_lanes = (int)value; break;
+      case HMM_OPT_PLAIN_ESTEP: ctx->plain_estep = value != 0; break;
+      default: throw Error{HMM_E_ARG, "unknown option"};
+    }
+  });
+}
+
+hmm_status hmm_ctx_profile_read(hmm_ctx ctx, double* h_ms, int64_t* h_launches, int32_t n_slots,
+                                int32_t reset) {
+  return guarded([&] {
+    HMM_REQUIRE(ctx != nullptr, "ctx is NULL");
+    for (auto& r : ctx->pending) {
+      HMM_CUDA(cudaEventSynchronize(r.e1));
+      float ms = 0.f;
+      HMM_CUDA(cudaEventElapsedTime(&ms, r.e0, r.e1));
+      if (r.slot >= 0 && r.slot < HMM_KT_SLOTS) {
+        ctx->kt_ms[r.slot] += ms;
+        ctx->kt_n[r.slot] += 1;
+      }
+      ctx->event_pool.push_back(r.e0);
+      ctx->event_pool.push_back(r.e1);
+    }
+    ctx->pending.clear();
+    for (int i = 0; i < n_slots && i < HMM_KT_SLOTS; ++i) {
+      if (h_ms) h_ms[i] = ctx->kt_ms[i];
+      if (h_launches) h_launches[i] = ctx->kt_n[i];
+    }
+    if (reset)
+      for (int i = 0; i < HMM_KT_SLOTS; ++i) {
+        ctx->kt_ms[i] = 0.0;
+        ctx->kt_n[i] = 0;
+      }
+  });
 }
 
 hmm_status hmm_model_create(hmm_ctx ctx, int32_t n_models, int32_t n_states, int32_t dim,
@@ -614,6 +749,7 @@ hmm_status hmm_emission_logpdf(hmm_ctx ctx, hmm_model model, const hmm_batch* ba
     check_batch(model, batch);
     if (model->any_mv) throw Error{HMM_E_UNSUPPORTED, "multivariate emissions are not in this build"};
     if (batch->n_seq == 0) return;
+    KTimer kt(ctx, HMM_KT_EMISSION, S(stream));
     emission_kernel<<<(unsigned)batch->n_seq, 128, 0, S(stream)>>>(model->view(), batch->values, batch->offsets,
                                                                    batch->model_id, d_logb);
     HMM_CUDA(cudaGetLastError());
@@ -663,7 +799,8 @@ hmm_status hmm_viterbi(hmm_ctx ctx, hmm_model model, const hmm_batch* batch, con
     a.model_id = batch->model_id;
     a.order = pr.p->order.as<int32_t>();
     a.n_seq = (int32_t)Sn;
-    const int G = default_viterbi_G(NP, Sn, ctx->n_sm);
+    int G = default_viterbi_G(NP, Sn, ctx->n_sm);
+    if (ctx->viterbi_lanes && viterbi_small_supported(NP, ctx->viterbi_lanes)) G = ctx->viterbi_lanes;
     a.n_items = (int32_t)((Sn + viterbi_seqs_per_item(G) - 1) / viterbi_seqs_per_item(G));
     a.mv = model->view();
     a.psi = ctx->psi.as<uint8_t>();
@@ -672,7 +809,10 @@ hmm_status hmm_viterbi(hmm_ctx ctx, hmm_model model, const hmm_batch* batch, con
     a.work_counter = ctx->counters + 1;
     a.status = ctx->status;
     HMM_CUDA(cudaMemsetAsync(ctx->counters + 1, 0, sizeof(int), S(stream)));
-    HMM_CUDA(launch_viterbi_small(NP, G, a, d_logb ? 1 : 0, ctx->n_sm, S(stream)));
+    {
+      KTimer kt(ctx, HMM_KT_VITERBI, S(stream));
+      HMM_CUDA(launch_viterbi_small(NP, G, a, d_logb ? 1 : 0, ctx->n_sm, S(stream)));
+    }
     if (pr.owned) HMM_CUDA(cudaStreamSynchronize(S(stream)));
   });
 }
@@ -807,6 +947,14 @@ hmm_status hmm_stats_get(hmm_stats stats, double* h_out, int64_t n_values) {
         q += canon_fam_count(fam, md->D);
       }
     }
+  });
+}
+
+hmm_status hmm_stats_device_buffer(hmm_stats stats, double** d_values, int64_t* n_values) {
+  return guarded([&] {
+    HMM_REQUIRE(stats && d_values && n_values, "NULL argument");
+    *d_values = stats->rec.as<double>();
+    *n_values = (int64_t)stats->model->M * rec_size(stats->model->NP);
   });
 }
 

@@ -21,9 +21,17 @@ inline int viterbi_seqs_per_item(int G) { return 32 / G; }
 
 constexpr int kWarpsPerBlock = 4;
 
-cudaError_t launch_estep_small(int NP, int G, const EStepArgs& a, int table_mode, int n_sm,
+// mode: MODE_STATS | MODE_GAMMA (0 is treated as MODE_STATS); fam: the batch's
+// single family, FAM_TABLE (log b table) or FAM_ANY (mixed families)
+cudaError_t launch_estep_small(int NP, int G, int mode, const EStepArgs& a, int fam, int n_sm,
                                cudaStream_t st);
-cudaError_t launch_viterbi_small(int NP, int G, const VitArgs& a, int table_mode, int n_sm,
+// per-NP translation units
+cudaError_t launch_estep_np2_4(int NP, int G, int mode, const EStepArgs& a, int fam, int n_sm,
+                               cudaStream_t st);
+cudaError_t launch_estep_np8(int G, int mode, const EStepArgs& a, int fam, int n_sm, cudaStream_t st);
+cudaError_t launch_estep_np16(int G, int mode, const EStepArgs& a, int fam, int n_sm, cudaStream_t st);
+cudaError_t launch_estep_np32(int G, int mode, const EStepArgs& a, int fam, int n_sm, cudaStream_t st);
+cudaError_t launch_viterbi_small(int NP, int G, const VitArgs& a, int fam, int n_sm,
                                  cudaStream_t st);
 
 }  // namespace hmm

@@ -77,6 +77,21 @@ struct hmm_ctx_s {
   hmm::DevBuf gamma;             // gamma rows for the data passes
   hmm::DevBuf dp_part;           // data-pass partials
   hmm::DevBuf trace;             // float64 logL trace of hmm_fit
+  hmm::DevBuf plain_beta;        // beta-hat rows of the plain path
+  // options
+  int profile = 0;
+  int estep_lanes = 0;
+  int viterbi_lanes = 0;
+  int plain_estep = 0;
+  // kernel timing
+  struct Rec {
+    int slot;
+    cudaEvent_t e0, e1;
+  };
+  std::vector<Rec> pending;
+  std::vector<cudaEvent_t> event_pool;
+  double kt_ms[HMM_KT_SLOTS] = {0};
+  int64_t kt_n[HMM_KT_SLOTS] = {0};
 };
 
 struct hmm_model_s {
@@ -105,5 +120,6 @@ struct hmm_plan_s {
   hmm::DevBuf chunk_lo, chunk_hi;// [n_chunks] int32
   hmm::DevBuf model_chunk_ptr;   // [M+1] int32
   int n_chunks = 0;
+  int uniform_family = -1;       // the one family of all sequences, or -1
   std::vector<int32_t> h_order;
 };
