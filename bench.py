@@ -49,6 +49,7 @@ def args_parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-plain", action="store_true")
     p.add_argument("--estep-lanes", type=int, default=0)
+    p.add_argument("--viterbi-lanes", type=int, default=0)
     p.add_argument("--quick", action="store_true", help="small case for profiling runs")
     return p.parse_args()
 
@@ -211,6 +212,8 @@ def run_ours(args):
     ctx = H.Context(local)
     if args.estep_lanes:
         ctx.set_option(_lib.OPT_ESTEP_LANES, args.estep_lanes)
+    if args.viterbi_lanes:
+        ctx.set_option(_lib.OPT_VITERBI_LANES, args.viterbi_lanes)
     model = H.Model(ctx, [init])
     batch = H.Batch(values, offsets, mid).make_plan(ctx, model)
     stats = H.Stats(ctx, model)

@@ -15,14 +15,15 @@ bool estep_small_supported(int NP, int G) {
 }
 
 int default_estep_G(int NP, int64_t n_seq, int n_sm) {
-  // Narrowest chain (most states per lane) that still gives about eight
-  // warps per SM; wider chains when the sequences are too few.
+  // Four states per lane measured fastest at N = 16 (fewest instructions
+  // per state-step); wider chains only when the sequences would leave fewer
+  // than about four warps per SM.
   if (NP == 32) return 16;
   int G = NP >= 4 ? NP / 4 : 1;
   if (!estep_small_supported(NP, G)) G = 1;
   while (G < 16 && G < NP && estep_small_supported(NP, 2 * G)) {
     const double warps = (double)n_seq / (16 / G);
-    if (warps >= 8.0 * n_sm) break;
+    if (warps >= 4.0 * n_sm) break;
     G *= 2;
   }
   return G;

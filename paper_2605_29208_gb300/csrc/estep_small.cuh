@@ -255,6 +255,8 @@ __device__ void estep_item(WarpSmem<C>& sm, const EStepArgs& a, int item, int la
 #pragma unroll
     for (int z = 0; z < NST; ++z) st[q][z] = 0.f;
   }
+  long long off = 0;       // running log2 offset of this chain (outer part)
+  float offs = 0.f;        // inner part: integer-valued, exact below 2^24
   // Outer level of the two-level sums: per-lane slots in shared memory
   // (conflict free), added every FLUSH steps; written to the per-sequence
   // partials once at the end of the item.
@@ -263,6 +265,8 @@ __device__ void estep_item(WarpSmem<C>& sm, const EStepArgs& a, int item, int la
     for (int f = 0; f < R * F; ++f) sm.acc[f][lane] = 0.f;
   }
   auto flush = [&]() {
+    off += (long long)offs;
+    offs = 0.f;
     if constexpr (STATS) {
 #pragma unroll
       for (int q = 0; q < R; ++q) {
@@ -287,7 +291,6 @@ __device__ void estep_item(WarpSmem<C>& sm, const EStepArgs& a, int item, int la
     v[q] = 0.f;
     gl[q] = 0.f;
   }
-  long long off = 0;       // running log2 offset of this chain
   bool started = false;    // the chain has produced its first vector
   const float* ybase = a.y + base;
   const float* sbase = a.scratch + base * NP + k0;
@@ -348,8 +351,9 @@ __device__ void estep_item(WarpSmem<C>& sm, const EStepArgs& a, int item, int la
       ft = feat_of(fam, sm.yring[slot][chain], a.mv.lfact2);
 #pragma unroll
       for (int q = 0; q < R; ++q) {
+        // padding states carry a -inf constant (see derive_row)
         const float e = emis_log2(fam, ft, cf[q], nbt[q]);
-        lb[q] = (ft.ok && (k0 + q) < N) ? e : -INFINITY;
+        lb[q] = ft.ok ? e : -INFINITY;
       }
     }
 
@@ -381,7 +385,8 @@ __device__ void estep_item(WarpSmem<C>& sm, const EStepArgs& a, int item, int la
       if (k == 0) {   // warp-uniform: log P(y) at the backward chain's first phase-2 step
         if (bfirst && sub == 0 && act) {
           const long long of = sm.offf[pair];
-          double ll = (Z > 0.f) ? ((double)log2f(Z) + (double)(off + of)) * kLn2 : -INFINITY;
+          double ll = (Z > 0.f) ? ((double)log2f(Z) + (double)(off + (long long)offs + of)) * kLn2
+                                : -INFINITY;
           if (!(Z == Z)) {
             ll = NAN;
             set_status(a.status, ST_NUMERIC);
@@ -438,7 +443,7 @@ __device__ void estep_item(WarpSmem<C>& sm, const EStepArgs& a, int item, int la
       v[q] = act ? nv : v[q];
     }
     if (act) {
-      off += (long long)E;
+      offs += E;
       started = true;
     }
     if constexpr (!PH2) {
@@ -473,7 +478,7 @@ __device__ void estep_item(WarpSmem<C>& sm, const EStepArgs& a, int item, int la
     xb ^= 1;
     if ((k & (C::FLUSH - 1)) == C::FLUSH - 1) flush();
   }
-  if (dir == 0 && sub == 0) sm.offf[pair] = off;
+  if (dir == 0 && sub == 0) sm.offf[pair] = off + (long long)offs;
   cp_wait<0>();
   __syncwarp();   // phase-1 rows of both chains are visible from here on
 

@@ -187,6 +187,17 @@ __device__ inline void derive_coef(int fam, const double* th, float* c, float* n
   }
 }
 
+// Coefficient slot that enters log b additively (see emis_log2).
+__device__ inline int additive_slot(int fam) {
+  switch (fam) {
+    case HMM_POISSON:
+    case HMM_NEGBIN: return 1;
+    case HMM_WEIBULL:
+    case HMM_STUDENT_T: return 3;
+    default: return 2;
+  }
+}
+
 // One thread per (model, state row): refresh every derived table of the row.
 __device__ inline void derive_row(const ModelBufs& mb, int m, int k) {
   const int NP = mb.NP, N = mb.N;
@@ -205,6 +216,12 @@ __device__ inline void derive_row(const ModelBufs& mb, int m, int k) {
     float* nbt = mb.nbtab ? mb.nbtab + ((size_t)m * NP + k) * NB_YMAX : nullptr;
     derive_coef(mb.family[m], mb.theta + ((size_t)m * NP + k) * mb.P,
                 mb.coef + ((size_t)m * NP + k) * KC, mb.family[m] == HMM_NEGBIN ? nbt : nullptr);
+  } else {
+    // padding state: zero multipliers and a -inf additive constant give
+    // log b = -inf for every observation inside the support
+    float* c = mb.coef + ((size_t)m * NP + k) * KC;
+    for (int z = 0; z < KC; ++z) c[z] = 0.f;
+    c[additive_slot(mb.family[m])] = -INFINITY;
   }
 }
 

@@ -42,11 +42,14 @@ bool viterbi_small_supported(int NP, int G) {
 }
 
 int default_viterbi_G(int NP, int64_t n_seq, int n_sm) {
+  // Four states per lane unless the sequences would leave fewer than about
+  // two warps per SM (measured on the N = 16 x 4096 workload).
   if (NP == 32) return 16;
-  int G = NP >= 8 ? NP / 4 : (NP == 4 ? 1 : 1);
+  int G = NP >= 4 ? NP / 4 : 1;
+  if (!viterbi_small_supported(NP, G)) G = 1;
   while (G < 16 && G < NP && viterbi_small_supported(NP, 2 * G)) {
     const double warps = (double)n_seq / (32 / G);
-    if (warps >= 8.0 * n_sm) break;
+    if (warps >= 2.0 * n_sm) break;
     G *= 2;
   }
   return G;

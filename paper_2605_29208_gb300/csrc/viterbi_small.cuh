@@ -85,11 +85,13 @@ __device__ void viterbi_item(VitSmem<C>& sm, const VitArgs& a, int item, int lan
   constexpr bool TABLE = (FAM == FAM_TABLE);
   const float* La = (TABLE ? a.mv.logAe : a.mv.logA2) + (size_t)m * NP * NP;
 
-  float L[NP][R];
+  constexpr int NH = NP / 2;
+  float2 L[NH][R];   // (log a_{2h,k}, log a_{2h+1,k}) for the owned states k
 #pragma unroll
-  for (int i = 0; i < NP; ++i)
+  for (int i = 0; i < NH; ++i)
 #pragma unroll
-    for (int q = 0; q < R; ++q) L[i][q] = __ldg(La + i * NP + k0 + q);
+    for (int q = 0; q < R; ++q)
+      L[i][q] = make_float2(__ldg(La + (2 * i) * NP + k0 + q), __ldg(La + (2 * i + 1) * NP + k0 + q));
   float init[R], cf[R][4];
   const float* nbt[R];
 #pragma unroll
@@ -145,20 +147,34 @@ __device__ void viterbi_item(VitSmem<C>& sm, const VitArgs& a, int item, int lan
 #pragma unroll
       for (int q = 0; q < R; ++q) nd[q] = __fadd_rn(init[q], lb[q]);
     } else {
-      float vin[NP];
-      load_row<NP>(&sm.xbuf[k & 1][chain][0], vin);
+      float2 vin[NH];
+      load_row<NP>(&sm.xbuf[k & 1][chain][0], reinterpret_cast<float*>(vin));
 #pragma unroll
       for (int q = 0; q < R; ++q) {
-        float best = -INFINITY;
-        uint32_t arg = 0;
+        // candidates c_i = delta_{t-1}(i) + log a_iq (IEEE adds, two per
+        // instruction), then a pairwise tournament that keeps the right
+        // operand only when it is strictly larger: the winner is the lowest
+        // index attaining the maximum, as a strict '>' upward scan gives.
+        float cv[NP];
+        uint32_t ci[NP];
 #pragma unroll
-        for (int i = 0; i < NP; ++i) {
-          const float c = __fadd_rn(vin[i], L[i][q]);
-          if (c > best) {
-            best = c;
-            arg = (uint32_t)i;
-          }
+        for (int i = 0; i < NH; ++i) {
+          const float2 c2 = __fadd2_rn(vin[i], L[i][q]);
+          cv[2 * i] = c2.x;
+          cv[2 * i + 1] = c2.y;
+          ci[2 * i] = 2 * i;
+          ci[2 * i + 1] = 2 * i + 1;
         }
+#pragma unroll
+        for (int w = 1; w < NP; w <<= 1)
+#pragma unroll
+          for (int j = 0; j + w < NP; j += 2 * w) {
+            const bool take = cv[j + w] > cv[j];
+            cv[j] = take ? cv[j + w] : cv[j];
+            ci[j] = take ? ci[j + w] : ci[j];
+          }
+        const float best = cv[0];
+        const uint32_t arg = ci[0];
         nd[q] = __fadd_rn(best, lb[q]);
         arg4 |= arg << (8 * (q & 3));
         if ((q & 3) == 3 || q == R - 1) {
