@@ -209,6 +209,25 @@ hmm_status hmm_forward_backward(hmm_ctx ctx, hmm_model model, const hmm_batch* b
                                 const float* d_logb, float* d_gamma,
                                 int32_t* d_post_path, double* d_loglik, void* stream);
 
+/* Forward-backward for callers that cannot allocate device memory at call
+ * time (a caller-managed memory pool that must not be bypassed, a real-time
+ * loop that cannot afford cudaMalloc's implicit synchronisation, a process
+ * that has already claimed the free memory).  The paper has no counterpart:
+ * this is an operational variant of hmm_forward_backward, with the same
+ * outputs (d_loglik [n_seq] and d_gamma [total_T][n_states], both required),
+ * but its scratch lives in a fixed 32 MiB array inside the library and the
+ * call makes no device allocation of any kind.  Limit: total_T * padded
+ * states * 4 + n_seq * 4 + 512 bytes must fit in 32 MiB (padded states:
+ * n_states rounded up to a power of two, at most 32), else HMM_E_ARG.  The
+ * batch's plan is ignored (sequences run in input order).  The array is
+ * shared by every call in the process and kept between calls: calls whose
+ * GPU work overlaps race on it, so order them on one stream.  The first call
+ * on a device looks up the array's address; make it before any stream
+ * capture. */
+hmm_status hmm_forward_backward_static(hmm_model model, const hmm_batch* batch,
+                                       const float* d_logb, float* d_gamma,
+                                       double* d_loglik, void* stream);
+
 /* Max-plus Viterbi (Sec. 3.3, Eq. 3-4) with backpointer traceback:
  * d_path [total_T] int32 states, d_score [n_seq] float64 (natural log of the
  * best path's joint probability).  Ties: lowest predecessor index, lowest

@@ -226,6 +226,16 @@ def forward_backward(ctx, model, batch, logb=None, want_gamma=True, want_path=Fa
     return ll, gamma, path
 
 
+def forward_backward_static(model, batch, gamma, loglik, logb=None, stream=None):
+    """hmm_forward_backward_static: same outputs as forward_backward, written
+    into the caller's tensors; the library allocates nothing during the call
+    (its scratch is a fixed device array, see include/hmmgpu.h)."""
+    b = batch.c()
+    check(model.lib.hmm_forward_backward_static(model.h, C.byref(b), _ptr(logb), _ptr(gamma), _ptr(loglik),
+                                                _stream(stream)))
+    return loglik, gamma
+
+
 def viterbi(ctx, model, batch, logb=None, stream=None):
     torch = _torch()
     dev = batch.values.device

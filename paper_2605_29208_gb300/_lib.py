@@ -58,6 +58,8 @@ _SIGS = {
                                       C.c_void_p]),
     "hmm_forward_backward": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(hmm_batch), C.c_void_p,
                                        C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "hmm_forward_backward_static": (C.c_int, [C.c_void_p, C.POINTER(hmm_batch), C.c_void_p, C.c_void_p,
+                                              C.c_void_p, C.c_void_p]),
     "hmm_viterbi": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(hmm_batch), C.c_void_p,
                               C.c_void_p, C.c_void_p, C.c_void_p]),
     "hmm_stats_create": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_void_p)]),

@@ -8,6 +8,7 @@
 #include <vector>
 
 #include "launch.h"
+#include "mstep.cuh"
 #include "plain.cuh"
 #include "runtime.h"
 

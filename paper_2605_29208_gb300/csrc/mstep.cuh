@@ -3,49 +3,10 @@
 #pragma once
 
 #include "common.cuh"
+#include "mstep_types.h"
 #include "special.cuh"
 
 namespace hmm {
-
-// ---------------------------------------------------------------------------
-// Mutable device model (float64 master parameters + derived float32 tables)
-// ---------------------------------------------------------------------------
-struct ModelBufs {
-  int M, N, NP, D, P;       // P: float64 parameters per state (theta stride)
-  int* family;              // [M]
-  double* pi;               // [M][NP]
-  double* A;                // [M][NP][NP]
-  double* theta;            // [M][NP][P]
-  float* A32;
-  float* logA2;
-  float* logAe;
-  float* pi32;
-  float* logpi2;
-  float* logpie;
-  float* coef;              // [M][NP][KC]
-  float* nbtab;             // [M][NP][NB_YMAX] or nullptr
-  float* lfact2;            // [LF_YMAX]
-};
-
-// Record of one model's sufficient statistics after the E-step reduction
-// (float64, internal layout):
-//   [0] number of sequences, [1] sum of log-likelihoods,
-//   [2, 2+NP) gamma_1 sums,
-//   [2+NP, 2+NP+NP*NP) X(i,j) = sum_t v(i) o(j)/Z  (xi without the a_ij factor),
-//   then NP x (NST-1) family sums (the E-step's shifted / log2 forms).
-__host__ __device__ inline int rec_size(int NP) { return 2 + NP + NP * NP + NP * (NST - 1); }
-__host__ __device__ inline int rec_g1(int) { return 2; }
-__host__ __device__ inline int rec_xi(int NP) { return 2 + NP; }
-__host__ __device__ inline int rec_st(int NP) { return 2 + NP + NP * NP; }
-
-struct MStepOpts {
-  double collapse_eps;
-  double tikhonov_eps;
-  int newton_maxit;
-  double newton_tol;
-  int nu_mode;
-  int update_transitions;
-};
 
 // Level 1: chunk c of the model-sorted sequence list -> float64 record.
 // Each field sums the chunk's sequences in list order (fixed order).

@@ -11,7 +11,7 @@
 
 #include "../../include/hmmgpu.h"
 #include "common.cuh"
-#include "mstep.cuh"
+#include "mstep_types.h"
 
 namespace hmm {
 
