@@ -189,6 +189,24 @@ class ClockSampler:
                     reasons=sorted(reasons))
 
 
+def profiled_traffic(name, sources):
+    """DRAM bytes per launch from the committed ncu summary of a kernel, or
+    None when the kernel's sources changed since that capture."""
+    import hashlib
+    import re
+    try:
+        txt = open(os.path.join(ROOT, "profiles", name)).read()
+        h = hashlib.sha256()
+        for f in sources:
+            h.update(open(os.path.join(ROOT, "paper_2605_29208_gb300", "csrc", f), "rb").read())
+        sha = re.search(r"kernel_source_sha256_16: ([0-9a-f]+)", txt).group(1)
+        if sha != h.hexdigest()[:16]:
+            return None
+        return int(re.search(r"traffic_bytes_per_launch: (\d+)", txt).group(1))
+    except Exception:
+        return None
+
+
 def peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -322,8 +340,13 @@ def run_ours(args):
     alu_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12          # TFLOP/s, FP32 FMA
     flops = 6.0 * N_STATES * N_STATES * float(offsets[-1])
     achieved = flops / (est_ms / 1e3) / 1e12
+    traffic = profiled_traffic("estep_small_N16_S4096_T2000.md",
+                               ["estep_small.cuh", "estep_launch.cuh", "common.cuh"])
+    if args.quick or args.family != "gamma":
+        traffic = None
     roofline = dict(bound="alu", achieved=achieved, peak=alu_peak, unit="TFLOP/s",
-                    frac=achieved / alu_peak, traffic=None,
+                    frac=achieved / alu_peak, traffic=traffic,
+                    algorithmic_bytes=float(offsets[-1]) * (8.0 + 8.0 * N_STATES),
                     kernel="estep_small_kernel (fused emission+forward+backward+gamma/xi+stats)",
                     peak_note="FP32 FMA: 152 SMs x 128 lanes x 2 flop x max SM clock (derived)")
     clocks = clk.summary() if rank == 0 else None
