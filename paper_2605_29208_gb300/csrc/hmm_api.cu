@@ -398,6 +398,14 @@ void run_estep(hmm_ctx ctx, hmm_model model, const hmm_batch* b, hmm_plan plan, 
   a.loglik = ll;
   a.work_counter = ctx->counters;
   a.status = ctx->status;
+  const bool dpass = want_stats && stats && (model->any_negbin || model->any_weibull);
+  if (dpass && !gamma) {
+    // the Weibull / negative-binomial M-step re-reads the occupancies
+    stats->gamma.ensure(std::max<int64_t>(b->total_T, 1) * model->N * 4);
+    stats->gamma_T = b->total_T;
+    gamma = stats->gamma.as<float>();
+    a.gamma = gamma;
+  }
   if (!ctx->plain_estep) {
     HMM_CUDA(cudaMemsetAsync(ctx->counters, 0, sizeof(int), st));
     KTimer kt(ctx, HMM_KT_ESTEP, st);
@@ -433,12 +441,62 @@ MStepOpts to_opts(const hmm_mstep_opts* o) {
   return r;
 }
 
-void run_mstep(hmm_ctx ctx, hmm_model model, hmm_stats stats, const MStepOpts& o, cudaStream_t st) {
-  if (model->any_negbin || model->any_weibull)
-    throw Error{HMM_E_UNSUPPORTED, "Weibull / negative-binomial M-steps are not in this build"};
+// Buffers of the data-pass M-step (allocated before any graph capture).
+void prepare_mstep(hmm_model model, hmm_stats stats, const hmm_batch* b, hmm_plan plan) {
+  if (!(model->any_negbin || model->any_weibull) || !b || !plan) return;
+  const int RS = model->NP * 3;
+  stats->dps.ensure((size_t)model->M * model->NP * sizeof(DPState));
+  stats->dp_part.ensure((size_t)std::max<int64_t>(b->n_seq, 1) * RS * 4);
+  stats->dp_chunk.ensure((size_t)std::max(plan->n_chunks, 1) * RS * 8);
+  stats->dp_rec.ensure((size_t)model->M * RS * 8);
+}
+
+void run_mstep(hmm_ctx ctx, hmm_model model, hmm_stats stats, const MStepOpts& o, const hmm_batch* b,
+               hmm_plan plan, cudaStream_t st) {
   if (model->any_mv) throw Error{HMM_E_UNSUPPORTED, "multivariate M-steps are not in this build"};
+  const bool dpass = model->any_negbin || model->any_weibull;
+  DPState* dps = nullptr;
+  if (dpass) {
+    HMM_REQUIRE(b != nullptr && plan != nullptr, "Weibull / negative-binomial M-steps need the batch");
+    HMM_REQUIRE(stats->gamma_T == b->total_T, "the statistics were not made from this batch");
+    stats->dps.ensure((size_t)model->M * model->NP * sizeof(DPState));
+    dps = stats->dps.as<DPState>();
+  }
+  {
+    KTimer kt(ctx, HMM_KT_MSTEP, st);
+    mstep_kernel<<<model->M, model->NP, 0, st>>>(model->bufs(), stats->rec.as<double>(), o, dps);
+    HMM_CUDA(cudaGetLastError());
+  }
+  if (!dpass || b->n_seq == 0) return;
+  // Newton steps that re-read the data: a fixed number of passes
+  // (converged states skip their work), then the Weibull scale pass
+  const int NP = model->NP, RS = NP * 3;
+  const int64_t S = b->n_seq;
+  stats->dp_part.ensure((size_t)S * RS * 4);
+  stats->dp_chunk.ensure((size_t)std::max(plan->n_chunks, 1) * RS * 8);
+  stats->dp_rec.ensure((size_t)model->M * RS * 8);
+  const int passes = std::min(o.newton_maxit, 24);   // + one final pass
+  const unsigned blocks = (unsigned)((S * 32 + 255) / 256);
+  const int nthr = model->M * NP;
   KTimer kt(ctx, HMM_KT_MSTEP, st);
-  mstep_kernel<<<model->M, model->NP, 0, st>>>(model->bufs(), stats->rec.as<double>(), o);
+  for (int it = 0; it <= passes; ++it) {
+    dp_sums_kernel<<<blocks, 256, 0, st>>>(model->bufs(), b->values, stats->gamma.as<float>(), b->offsets,
+                                           b->model_id, (int)S, dps, stats->dp_part.as<float>());
+    HMM_CUDA(cudaGetLastError());
+    if (plan->n_chunks > 0) {
+      reduce_records_l1<<<plan->n_chunks, 128, 0, st>>>(stats->dp_part.as<float>(), RS,
+                                                      plan->seq_by_model.as<int32_t>(), plan->chunk_lo.as<int32_t>(),
+                                                      plan->chunk_hi.as<int32_t>(), stats->dp_chunk.as<double>());
+      HMM_CUDA(cudaGetLastError());
+    }
+    reduce_chunks_l2<<<model->M, 128, 0, st>>>(stats->dp_chunk.as<double>(), plan->model_chunk_ptr.as<int32_t>(), RS,
+                                               stats->dp_rec.as<double>());
+    HMM_CUDA(cudaGetLastError());
+    dp_update_kernel<<<(nthr + 127) / 128, 128, 0, st>>>(model->bufs(), stats->dp_rec.as<double>(), dps, o,
+                                                         it == passes ? 1 : 0);
+    HMM_CUDA(cudaGetLastError());
+  }
+  dp_finish_kernel<<<(nthr + 127) / 128, 128, 0, st>>>(model->bufs());
   HMM_CUDA(cudaGetLastError());
 }
 
@@ -838,7 +896,8 @@ hmm_status hmm_stats_create(hmm_ctx ctx, hmm_model model, hmm_stats* out) {
 hmm_status hmm_stats_destroy(hmm_stats stats) {
   return guarded([&] {
     if (!stats) return;
-    stats->rec.release();
+    for (auto* bb : {&stats->rec, &stats->gamma, &stats->dps, &stats->dp_part, &stats->dp_chunk, &stats->dp_rec})
+      bb->release();
     delete stats;
   });
 }
@@ -975,12 +1034,17 @@ hmm_status hmm_estep_stats(hmm_ctx ctx, hmm_model model, const hmm_batch* batch,
 
 hmm_status hmm_mstep(hmm_ctx ctx, hmm_model model, hmm_stats stats, const hmm_batch* batch,
                      const hmm_mstep_opts* opts, void* stream) {
-  (void)batch;
   return guarded([&] {
     HMM_REQUIRE(ctx && model && stats, "NULL argument");
     HMM_REQUIRE(stats->model == model, "stats belong to another model");
     HMM_REQUIRE(stats->valid, "statistics were never computed");
-    run_mstep(ctx, model, stats, to_opts(opts), S(stream));
+    PlanRef pr;
+    if (batch && (model->any_negbin || model->any_weibull)) {
+      check_batch(model, batch);
+      get_plan(ctx, model, batch, S(stream), pr);
+    }
+    run_mstep(ctx, model, stats, to_opts(opts), batch, pr.p, S(stream));
+    if (pr.owned) HMM_CUDA(cudaStreamSynchronize(S(stream)));
   });
 }
 
@@ -1013,13 +1077,14 @@ hmm_status hmm_fit(hmm_ctx ctx, hmm_model model, const hmm_batch* batch, const h
     HMM_CUDA(cudaMemsetAsync(it_dev, 0, sizeof(int), st));
     // make every buffer the iteration needs exist before any capture
     run_estep(ctx, model, batch, pr.p, nullptr, nullptr, nullptr, true, stats, st);
+    prepare_mstep(model, stats, batch, pr.p);
     HMM_CUDA(cudaStreamSynchronize(st));
     auto one_iter = [&]() {
       run_estep(ctx, model, batch, pr.p, nullptr, nullptr, nullptr, true, stats, st);
       trace_gather_kernel<<<(M + 255) / 256, 256, 0, st>>>(stats->rec.as<double>(), RS, M,
                                                           ctx->trace.as<double>(), it_dev);
       HMM_CUDA(cudaGetLastError());
-      run_mstep(ctx, model, stats, mo, st);
+      run_mstep(ctx, model, stats, mo, batch, pr.p, st);
       bump_kernel<<<1, 1, 0, st>>>(it_dev);
       HMM_CUDA(cudaGetLastError());
     };

@@ -290,7 +290,7 @@ __device__ inline double student_nu(double W, double C, double nu0, const MStepO
 // then the derived tables of row k.  Families whose Newton step needs data
 // passes (Weibull, negative binomial) get their seed here and are finished by
 // the data-pass kernels.
-__global__ void mstep_kernel(ModelBufs mb, const double* __restrict__ rec, MStepOpts o) {
+__global__ void mstep_kernel(ModelBufs mb, const double* __restrict__ rec, MStepOpts o, DPState* dps) {
   const int m = blockIdx.x, k = threadIdx.x;
   const int NP = mb.NP, N = mb.N;
   if (k >= NP) return;
@@ -301,6 +301,7 @@ __global__ void mstep_kernel(ModelBufs mb, const double* __restrict__ rec, MStep
     const double* S = R + rec_st(NP) + k * (NST - 1);
     const double W = S[0];
     const float* cf = mb.coef + ((size_t)m * NP + k) * KC;   // current shifts
+    if (dps && (fam == HMM_WEIBULL || fam == HMM_NEGBIN)) dps[(size_t)m * NP + k].active = 0;
     if (W >= o.collapse_eps) {
       switch (fam) {
         case HMM_GAUSS: {
@@ -334,6 +335,39 @@ __global__ void mstep_kernel(ModelBufs mb, const double* __restrict__ rec, MStep
           th[2] = student_nu(W, S[4], nu0, o);        // Eq. 18-19
           break;
         }
+        case HMM_WEIBULL: {
+          // Eq. 11 reading: seed k0 = pi / (sqrt 6 sd(log y)); Newton runs in the
+          // data passes (dp_*), which also finish the scale
+          const double mlog = S[1] * kLn2 / W;
+          const double vlog = S[2] * kLn2 * kLn2 / W - mlog * mlog;
+          DPState& d = dps[(size_t)m * NP + k];
+          d.x = 3.14159265358979323846 / (sqrt(6.0) * sqrt(fmax(vlog, 1e-300)));
+          d.mlog = mlog;
+          d.W = W;
+          d.ybar = 0.0;
+          d.active = 1;
+          d.iters = 0;
+          break;
+        }
+        case HMM_NEGBIN: {
+          // profiled score (reading of Sec. 4.2): seed ybar^2 / (var - ybar)
+          const double ybar = S[1] / W, var = S[2] / W - ybar * ybar;
+          DPState& d = dps[(size_t)m * NP + k];
+          d.ybar = ybar;
+          d.W = W;
+          d.mlog = 0.0;
+          d.iters = 0;
+          if (var <= ybar) {
+            d.x = 1e6;
+            d.active = 0;
+            th[0] = 1e6;
+            th[1] = 1e6 / (1e6 + ybar);
+          } else {
+            d.x = ybar * ybar / (var - ybar);
+            d.active = 1;
+          }
+          break;
+        }
         case HMM_VONMISES: {
           const double C = S[1], Sn = S[2];
           th[0] = atan2(Sn, C);
@@ -357,6 +391,152 @@ __global__ void mstep_kernel(ModelBufs mb, const double* __restrict__ rec, MStep
   }
   __syncthreads();
   derive_row(mb, m, k);
+}
+
+// ---------------------------------------------------------------------------
+// Data passes for the Newton steps that need the observations again
+// (SURVEY S8): Weibull shape (Eq. 11) and negative-binomial r.
+// One warp per sequence, one lane per state, float32 sums over the sequence,
+// then the same fixed-order float64 chunk reductions as the E-step.
+// Per state three sums:
+//   Weibull  S0 = sum g e, S1 = sum g e u, S2 = sum g e u^2 with
+//            u = ln y - mlog, e = exp(k u)   (shift mlog cancels in Eq. 11)
+//   NegBin   D1 = sum g [psi(y + r) - psi(r)], D2 = sum g [psi'(y + r) - psi'(r)]
+// ---------------------------------------------------------------------------
+__global__ void dp_sums_kernel(ModelBufs mb, const float* __restrict__ y, const float* __restrict__ gamma,
+                               const int64_t* __restrict__ offsets, const int32_t* __restrict__ model_id,
+                               int n_seq, const DPState* __restrict__ dps, float* __restrict__ part) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (warp >= n_seq) return;
+  const int s = warp;
+  const int NP = mb.NP, N = mb.N;
+  const int m = model_id[s];
+  const int fam = mb.family[m];
+  float* out = part + (size_t)s * NP * 3;
+  const bool dpf = (fam == HMM_WEIBULL || fam == HMM_NEGBIN);
+  const DPState* d = dps + (size_t)m * NP;
+  const bool mine = dpf && lane < N && d[lane].active != 0;
+  const bool any = __any_sync(0xffffffffu, mine);
+  if (!any) {
+    if (lane < NP) {
+      out[lane * 3 + 0] = 0.f;
+      out[lane * 3 + 1] = 0.f;
+      out[lane * 3 + 2] = 0.f;
+    }
+    return;
+  }
+  const int64_t b = offsets[s], e = offsets[s + 1];
+  float a0 = 0.f, a1 = 0.f, a2 = 0.f;
+  if (mine) {
+    const float x = (float)d[lane].x;
+    if (fam == HMM_WEIBULL) {
+      const float ml = (float)d[lane].mlog;
+      for (int64_t t = b; t < e; ++t) {
+        const float g = gamma[t * N + lane];
+        const float yy = y[t];
+        if (!(yy > 0.f)) continue;
+        const float u = logf(yy) - ml;
+        const float w = g * expf(x * u);
+        a0 += w;
+        a1 = fmaf(w, u, a1);
+        a2 = fmaf(w * u, u, a2);
+      }
+    } else {
+      const float pr = digamma_f(x), tr = trigamma_f(x);
+      for (int64_t t = b; t < e; ++t) {
+        const float g = gamma[t * N + lane];
+        const float yy = y[t];
+        if (g == 0.f || yy == 0.f) continue;
+        a0 = fmaf(g, digamma_f(yy + x) - pr, a0);
+        a1 = fmaf(g, trigamma_f(yy + x) - tr, a1);
+      }
+    }
+  }
+  if (lane < NP) {
+    out[lane * 3 + 0] = a0;
+    out[lane * 3 + 1] = a1;
+    out[lane * 3 + 2] = a2;
+  }
+}
+
+// plain fixed-order sum of per-sequence records over a chunk of the
+// model-sorted sequence list
+__global__ void reduce_records_l1(const float* __restrict__ part, int RS, const int32_t* __restrict__ seq_by_model,
+                                  const int32_t* __restrict__ chunk_lo, const int32_t* __restrict__ chunk_hi,
+                                  double* __restrict__ chunk_rec) {
+  const int c = blockIdx.x;
+  const int lo = chunk_lo[c], hi = chunk_hi[c];
+  for (int f = threadIdx.x; f < RS; f += blockDim.x) {
+    double acc = 0.0;
+    for (int q = lo; q < hi; ++q) acc += (double)part[(size_t)seq_by_model[q] * RS + f];
+    chunk_rec[(size_t)c * RS + f] = acc;
+  }
+}
+
+// One Newton step per active (model, state); a converged Weibull state asks
+// for one more pass to get its scale.  The data-pass sums are float32, so the
+// iterate cannot settle below ~1e-7 relative: the stopping tolerance is
+// max(newton_tol, 1e-7).  With `final` set every Weibull state still running
+// takes its current shape and the scale of the last pass.
+__global__ void dp_update_kernel(ModelBufs mb, const double* __restrict__ rec, DPState* dps, MStepOpts o,
+                                 int final) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= mb.M * mb.NP) return;
+  const int m = idx / mb.NP, k = idx % mb.NP;
+  if (k >= mb.N) return;
+  DPState& d = dps[idx];
+  if (!d.active) return;
+  const int fam = mb.family[m];
+  const double* R = rec + (size_t)m * mb.NP * 3 + k * 3;
+  double* th = mb.theta + ((size_t)m * mb.NP + k) * mb.P;
+  const double tol = fmax(o.newton_tol, 1e-7);
+  if (fam == HMM_WEIBULL) {
+    const double S0 = R[0], S1 = R[1], S2 = R[2];
+    if (d.active == 2 || final) {   // scale from the converged (or last) shape
+      th[0] = d.x;
+      th[1] = exp(d.mlog + log(S0 / d.W) / d.x);
+      d.active = 0;
+      return;
+    }
+    const double kk = d.x;
+    const double f = 1.0 / kk - S1 / S0;
+    const double df = -1.0 / (kk * kk) - (S2 * S0 - S1 * S1) / (S0 * S0);
+    double step = f / df, nw = kk - step;
+    while (nw <= 0.0) {
+      step *= 0.5;
+      nw = kk - step;
+    }
+    d.iters++;
+    const bool done = newton_done(kk, nw, tol) || d.iters >= o.newton_maxit;
+    d.x = nw;
+    if (done) d.active = 2;
+  } else if (fam == HMM_NEGBIN) {
+    const double r = d.x, W = d.W, ybar = d.ybar;
+    const double g = R[0] + W * log(r / (r + ybar));
+    const double dg = R[1] + W * (1.0 / r - 1.0 / (r + ybar));
+    double step = g / dg, nw = r - step;
+    while (nw <= 0.0) {
+      step *= 0.5;
+      nw = r - step;
+    }
+    nw = fmin(nw, 1e6);
+    d.iters++;
+    const bool done = newton_done(r, nw, tol) || d.iters >= o.newton_maxit || final;
+    d.x = nw;
+    th[0] = nw;
+    th[1] = nw / (nw + ybar);
+    if (done) d.active = 0;
+  }
+}
+
+// refresh the derived tables after the data-pass Newton steps
+__global__ void dp_finish_kernel(ModelBufs mb) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= mb.M * mb.NP) return;
+  const int m = idx / mb.NP, k = idx % mb.NP;
+  const int fam = mb.family[m];
+  if (fam == HMM_WEIBULL || fam == HMM_NEGBIN) derive_row(mb, m, k);
 }
 
 }  // namespace hmm

@@ -46,4 +46,15 @@ struct MStepOpts {
   int update_transitions;
 };
 
+// Per-(model, state) Newton state of the families whose M-step re-reads the
+// data (Weibull shape, negative-binomial r).
+struct DPState {
+  double x;        // current iterate (k or r)
+  double ybar;     // weighted mean of y (negative binomial)
+  double mlog;     // weighted mean of log y (Weibull, the data-pass shift)
+  double W;        // sum of occupancies
+  int active;      // 1 while Newton runs, 2 when the Weibull scale still needs a pass
+  int iters;
+};
+
 }  // namespace hmm

@@ -108,6 +108,14 @@ struct hmm_stats_s {
   hmm_model model = nullptr;
   hmm::DevBuf rec;               // [M][rec_size(NP)] float64
   bool valid = false;
+  // data-pass families (Weibull, negative binomial): occupancies of the last
+  // E-step and the Newton state
+  hmm::DevBuf gamma;             // [total_T][N] float32
+  int64_t gamma_T = -1;          // total_T of the batch that wrote gamma
+  hmm::DevBuf dps;               // [M][NP] DPState
+  hmm::DevBuf dp_part;           // [S][NP][3] float32
+  hmm::DevBuf dp_chunk;          // [n_chunks][NP*3] float64
+  hmm::DevBuf dp_rec;            // [M][NP*3] float64
 };
 
 struct hmm_plan_s {

@@ -15,7 +15,7 @@ LL_RTOL = 1e-5
 GAMMA_ATOL = 1e-4
 PARAM_RTOL = 1e-4
 
-SCALAR = ("gauss", "poisson", "gamma", "beta", "student_t", "vonmises")
+SCALAR = ("gauss", "poisson", "gamma", "beta", "weibull", "negbin", "student_t", "vonmises")
 
 
 @pytest.fixture(scope="module")
@@ -150,6 +150,10 @@ def oracle_canonical_stats(models, values, offsets, mid):
                              (w * (np.log(u) - u)).sum()])
             elif f == "vonmises":
                 cols.append([w.sum(), (w * np.cos(Y)).sum(), (w * np.sin(Y)).sum()])
+            elif f == "weibull":
+                cols.append([w.sum(), (w * np.log(Y)).sum(), (w * np.log(Y) ** 2).sum()])
+            elif f == "negbin":
+                cols.append([w.sum(), (w * Y).sum(), (w * Y * Y).sum()])
         out.append(np.concatenate([[len(idx), ll], g1, xi.ravel(), np.ravel(cols)]))
     return np.concatenate(out)
 
@@ -190,13 +194,13 @@ def test_mstep_parity(H, ctx, family):
     model = H.Model(ctx, init)
     batch = H.Batch(values, offsets, mid)
     stats, _ = H.estep_stats(ctx, model, batch)
-    H.mstep(ctx, model, stats)
+    H.mstep(ctx, model, stats, batch=batch)
     got = model.get()
     ref, _ = O.em_iteration([om(m) for m in init], values, offsets, mid)
     assert_params_close(got, ref)
 
 
-@pytest.mark.parametrize("family", ["gauss", "gamma", "student_t"])
+@pytest.mark.parametrize("family", ["gauss", "gamma", "student_t", "weibull", "negbin", "vonmises"])
 def test_fit_parity(H, ctx, family):
     N = 4
     truth = synth.small_models(family, N, 1, seed=31)
