@@ -46,6 +46,9 @@ def args_parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--family", choices=["gamma", "student_t"], default="gamma")
+    p.add_argument("--workload", choices=["scale", "batching"], default="scale",
+                   help="scale: N=16 x 4096 x 2000 (the bench line); batching: 100k ragged "
+                        "sequences, N=8, 1024 mixed-family models")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-plain", action="store_true")
     p.add_argument("--estep-lanes", type=int, default=0)
@@ -63,6 +66,9 @@ def dist_env():
 
 def workload(args, rank):
     from paper_2605_29208_gb300 import synth
+    if args.workload == "batching":
+        truths, inits, values, offsets, mid = synth.batching_workload(seed=synth.MASTER_SEED + 2 + 1000 * rank)
+        return truths, inits, values, offsets, mid
     n_seq, T = (256, 500) if args.quick else (N_SEQ, T_LEN)
     # weak scaling: every rank holds its own full-size batch (seed per rank)
     return synth.scale_workload(args.family, n_seq=n_seq, T=T, N=N_STATES,
@@ -81,21 +87,25 @@ def host_cores():
 
 
 # ---------------------------------------------------------------- CPU side
+def _as_list(init):
+    return init if isinstance(init, list) else [init]
+
+
 def oracle_step_sample(init, values, offsets, mid, n_sample):
     """One EM iteration and one Viterbi decode of the first n_sample
     sequences with the oracle; returns (seconds, cell updates)."""
     from oracle import hmm_oracle as O
-    m = O.Model(init["family"], init["pi"].copy(), init["A"].copy(),
-                {k: v.copy() for k, v in init["params"].items()})
+    models = [O.Model(m["family"], m["pi"].copy(), m["A"].copy(),
+                      {k: v.copy() for k, v in m["params"].items()}) for m in _as_list(init)]
     sub_off = offsets[:n_sample + 1]
     sub_vals = values[:sub_off[-1]]
     sub_mid = mid[:n_sample]
     t0 = time.perf_counter()
-    new, _ = O.em_iteration([m], sub_vals, sub_off, sub_mid)
+    new, _ = O.em_iteration(models, sub_vals, sub_off, sub_mid)
     for s in range(n_sample):
-        O.viterbi(new[0], sub_vals[sub_off[s]:sub_off[s + 1]])
+        O.viterbi(new[sub_mid[s]], sub_vals[sub_off[s]:sub_off[s + 1]])
     dt = time.perf_counter() - t0
-    return dt, 2.0 * cells(sub_off, len(init["pi"]))
+    return dt, 2.0 * cells(sub_off, len(models[0].pi))
 
 
 def cpu_baseline(init, values, offsets, mid, target_s=12.0):
@@ -104,8 +114,8 @@ def cpu_baseline(init, values, offsets, mid, target_s=12.0):
     n2 = int(max(4, min(len(offsets) - 1, n * target_s / max(dt, 1e-3))))
     dt, c = oracle_step_sample(init, values, offsets, mid, n2)
     return dict(value=c / dt, unit=UNIT, cores=1, kind="oracle",
-                sample=f"first {n2} of {len(offsets) - 1} sequences (T={int(offsets[1] - offsets[0])}, "
-                       f"N={len(init['pi'])}), one EM iteration + one Viterbi decode, "
+                sample=f"first {n2} of {len(offsets) - 1} sequences ({int(offsets[n2])} time steps, "
+                       f"N={len(_as_list(init)[0]['pi'])}), one EM iteration + one Viterbi decode, "
                        f"numpy float64 single thread, {dt:.1f} s")
 
 
@@ -232,8 +242,11 @@ def run_ours(args):
         ctx.set_option(_lib.OPT_ESTEP_LANES, args.estep_lanes)
     if args.viterbi_lanes:
         ctx.set_option(_lib.OPT_VITERBI_LANES, args.viterbi_lanes)
-    model = H.Model(ctx, [init])
+    models = _as_list(init)
+    NS = len(models[0]["pi"])
+    model = H.Model(ctx, models)
     batch = H.Batch(values, offsets, mid).make_plan(ctx, model)
+    tuned_ms = batch.autotune(ctx, model) if not (args.estep_lanes or args.viterbi_lanes) else None
     stats = H.Stats(ctx, model)
     dev = batch.values.device
     S = batch.n_seq
@@ -291,7 +304,7 @@ def run_ours(args):
         t = torch.tensor([ms], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
-    c_step = 2.0 * cells(offsets, N_STATES)
+    c_step = 2.0 * cells(offsets, NS)
     value = ws * c_step / (ms / 1e3)
 
     # ---- end to end through the public API with host buffers
@@ -338,15 +351,15 @@ def run_ours(args):
     pk = peaks()
     sm_max = float(pk.get("sm_max_mhz", 2070.0))
     alu_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12          # TFLOP/s, FP32 FMA
-    flops = 6.0 * N_STATES * N_STATES * float(offsets[-1])
+    flops = 6.0 * NS * NS * float(offsets[-1])
     achieved = flops / (est_ms / 1e3) / 1e12
     traffic = profiled_traffic("estep_small_N16_S4096_T2000.md",
                                ["estep_small.cuh", "estep_launch.cuh", "common.cuh"])
-    if args.quick or args.family != "gamma":
+    if args.quick or args.family != "gamma" or args.workload != "scale":
         traffic = None
     roofline = dict(bound="alu", achieved=achieved, peak=alu_peak, unit="TFLOP/s",
                     frac=achieved / alu_peak, traffic=traffic,
-                    algorithmic_bytes=float(offsets[-1]) * (8.0 + 8.0 * N_STATES),
+                    algorithmic_bytes=float(offsets[-1]) * (8.0 + 8.0 * NS),
                     kernel="estep_small_kernel (fused emission+forward+backward+gamma/xi+stats)",
                     peak_note="FP32 FMA: 152 SMs x 128 lanes x 2 flop x max SM clock (derived)")
     clocks = clk.summary() if rank == 0 else None
@@ -355,10 +368,15 @@ def run_ours(args):
         line = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=ws, steps=args.steps,
                     warmup=max(args.warmup, 3), ms_per_step=ms, higher_is_better=True,
                     scaling="weak", vs_baseline=None, dtype="f32", data="synthetic",
-                    config=dict(workload=f"{args.family} HMM, N={N_STATES} states, {S} sequences x "
-                                         f"T={int(offsets[1] - offsets[0])}, one EM iteration + Viterbi",
-                                family=args.family, n_states=N_STATES, n_seq_per_gpu=S,
-                                seq_len=int(offsets[1] - offsets[0]), global_batch=S * ws,
+                    config=dict(workload=(f"{args.family} HMM, N={NS} states, {S} sequences x "
+                                          f"T={int(offsets[1] - offsets[0])}, one EM iteration + Viterbi"
+                                          if args.workload == "scale" else
+                                          f"batching: {S} ragged sequences (sum T = {int(offsets[-1])}), "
+                                          f"N={NS}, {len(models)} mixed-family models, one EM iteration + Viterbi"),
+                                family=args.family if args.workload == "scale" else "mixed",
+                                n_states=NS, n_seq_per_gpu=S, total_T=int(offsets[-1]),
+                                seq_len=int(offsets[1] - offsets[0]) if args.workload == "scale" else "ragged",
+                                global_batch=S * ws,
                                 parallelism=f"dp{ws}" if ws > 1 else "single GPU",
                                 cell_updates_per_step=c_step,
                                 l2="flushed before every timed step (256 MiB write, outside the events)"),
@@ -369,7 +387,8 @@ def run_ours(args):
                     breakdown=dict(estep_ms=est_ms, baum_welch_ms=bw_ms, viterbi_ms=vit_ms,
                                    reduce_ms=prof["reduce"][0] / args.steps,
                                    mstep_ms=prof["mstep"][0] / args.steps,
-                                   baum_welch_cell_updates_per_s=cells(offsets, N_STATES) / (bw_ms / 1e3),
+                                   baum_welch_cell_updates_per_s=cells(offsets, NS) / (bw_ms / 1e3),
+                                   autotune_ms=tuned_ms,
                                    wall_s=t_wall))
         if plain:
             line["plain_gpu"] = plain

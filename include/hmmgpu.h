@@ -190,6 +190,15 @@ hmm_status hmm_plan_create(hmm_ctx ctx, hmm_model model, const hmm_batch* batch,
                            const int64_t* h_offsets, const int32_t* h_model_id,
                            hmm_plan* out);
 hmm_status hmm_plan_destroy(hmm_plan plan);
+/* Autotuner: times the fused E-step and the Viterbi kernel at every chain
+ * width compiled for the model's state count on this batch (CUDA events on
+ * `stream`, one warm-up and one timed run each) and stores the fastest widths
+ * in batch->plan (which must be set), where every later call with that plan
+ * uses them.  hmm_fit runs it by itself on a caller's plan that was never
+ * tuned.  Synchronises `stream`.  h_ms (may be NULL) receives the measured
+ * E-step and Viterbi milliseconds of the chosen widths. */
+hmm_status hmm_plan_autotune(hmm_ctx ctx, hmm_model model, const hmm_batch* batch,
+                             double* h_ms, void* stream);
 
 /* ------------------------------------------------------------ inference */
 /* Emission log-densities log b_j(y_t) (natural log) of every row of the batch

@@ -196,6 +196,15 @@ class Batch:
         self._lib = ctx.lib
         return self
 
+    def autotune(self, ctx: Context, model: Model, stream=None):
+        """hmm_plan_autotune: pick the fastest chain widths for this batch;
+        returns the measured (E-step ms, Viterbi ms)."""
+        ms = np.zeros(2, np.float64)
+        b = self.c()
+        check(ctx.lib.hmm_plan_autotune(ctx.h, model.h, C.byref(b), ms.ctypes.data_as(C.c_void_p),
+                                        _stream(stream)))
+        return tuple(ms)
+
     def __del__(self):
         try:
             if self.plan and self._lib:

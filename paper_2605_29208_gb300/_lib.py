@@ -54,6 +54,7 @@ _SIGS = {
     "hmm_plan_create": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(hmm_batch), C.c_void_p,
                                   C.c_void_p, C.POINTER(C.c_void_p)]),
     "hmm_plan_destroy": (C.c_int, [C.c_void_p]),
+    "hmm_plan_autotune": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(hmm_batch), C.c_void_p, C.c_void_p]),
     "hmm_emission_logpdf": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(hmm_batch), C.c_void_p,
                                       C.c_void_p]),
     "hmm_forward_backward": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(hmm_batch), C.c_void_p,

@@ -136,14 +136,12 @@ __device__ __forceinline__ Feat feat_of(int fam, float y, const float* __restric
       f.ok = (y == y);
       break;
     case HMM_POISSON:
-    case HMM_NEGBIN: {
+    case HMM_NEGBIN:
+      // log2 y!, evaluated in registers: a table read here would put a
+      // dependent global load on the recursion's critical path every step
       f.ok = is_count(y);
-      if (f.ok) {
-        int yi = (int)fminf(y, 2.0e9f);
-        f.a = (yi < LF_YMAX) ? __ldg(lfact2 + yi) : lgammaf(y + 1.0f) * kLog2ef;  // log2 y!
-      }
+      f.a = f.ok ? lgammaf(y + 1.0f) * kLog2ef : 0.f;
       break;
-    }
     case HMM_GAMMA:
     case HMM_WEIBULL:
       f.ok = y > 0.f;
@@ -183,10 +181,9 @@ __device__ __forceinline__ float emis_log2(int fam, const Feat& f, const float* 
       float e = ex2f(fmaf(c[1], f.a, c[2]));
       return fmaf(c[0], f.a, fmaf(-kLog2ef, e, c[3]));
     }
-    case HMM_NEGBIN: {           // table(y) + y log2(1-p) + r log2 p  (table holds -log2 y!)
-      int yi = (int)fminf(f.y, 2.0e9f);
-      float lg = (yi < NB_YMAX) ? __ldg(nbt + yi)
-                                : (lgammaf(f.y + c[2]) - c[3] - lgammaf(f.y + 1.0f)) * kLog2ef;
+    case HMM_NEGBIN: {           // [lgamma(y+r) - lgamma(r)] log2 e - log2 y! + y log2(1-p) + r log2 p
+      (void)nbt;
+      const float lg = (lgammaf(f.y + c[2]) - c[3]) * kLog2ef - f.a;
       return lg + fmaf(f.y, c[0], c[1]);
     }
     case HMM_STUDENT_T: {        // const - (nu+1)/2 log2(1 + (y-mu)^2 / (nu sigma2))

@@ -70,7 +70,7 @@ struct SmallCfg {
   static constexpr int CPW = 32 / G;
   static constexpr int SPW = CPW / 2;
   static constexpr int F = NP + NST;
-  static constexpr int PD = 6;          // prefetch ring depth (steps)
+  static constexpr int PD = 8;          // prefetch ring depth (steps)
   static constexpr int FLUSH = 64;      // inner accumulation length (steps)
   static_assert(NP % G == 0 && G <= 16 && (32 % G) == 0, "bad chain shape");
 };
@@ -321,6 +321,29 @@ __device__ void estep_item(WarpSmem<C>& sm, const EStepArgs& a, int item, int la
     }
   };
 
+  // emission of the step whose data sit in ring slot `sl` -> lbn / ftn
+  float lbn[R];
+  Feat ftn;
+  auto emission = [&](int sl) {
+    if constexpr (FAM == FAM_TABLE) {
+      ftn.y = 0.f;
+      ftn.a = 0.f;
+      ftn.b = 0.f;
+      ftn.ok = true;
+#pragma unroll
+      for (int q = 0; q < R; ++q)
+        lbn[q] = (k0 + q < N) ? sm.lring[sl][chain][k0 + q] * kLog2ef : -INFINITY;
+    } else {
+      ftn = feat_of(fam, sm.yring[sl][chain], a.mv.lfact2);
+#pragma unroll
+      for (int q = 0; q < R; ++q) {
+        // padding states carry a -inf constant (see derive_row)
+        const float e = emis_log2(fam, ftn, cf[q], nbt[q]);
+        lbn[q] = ftn.ok ? e : -INFINITY;
+      }
+    }
+  };
+
   // one recursion step of phase PH2 (false: phase 1) at warp iteration k
   auto step = [&](auto ph2_tag, int k, int n, int t0, int& slot, int& pslot, int xb) {
     constexpr bool PH2 = decltype(ph2_tag)::value;
@@ -330,33 +353,19 @@ __device__ void estep_item(WarpSmem<C>& sm, const EStepArgs& a, int item, int la
 #pragma unroll
       for (int q = 0; q < R; ++q) sm.xbuf[xb][chain][k0 + q] = v[q];
     }
-    cp_wait<PD - 2>();
+    cp_wait<PD - 3>();      // this step's and the next step's data are in
     __syncwarp();
     prefetch(k + PD - 1, n, t0, PH2, pslot);
     cp_commit();
     pslot = (pslot == PD - 1) ? 0 : pslot + 1;
 
-    // emission log2 b_k(y_t) of the owned states
+    // emission log2 b_k(y_t) of the owned states: computed one step ahead
+    // (it does not depend on the recursion, so it overlaps the previous step)
     float lb[R];
-    Feat ft;
-    if constexpr (FAM == FAM_TABLE) {
-      ft.y = 0.f;
-      ft.a = 0.f;
-      ft.b = 0.f;
-      ft.ok = true;
 #pragma unroll
-      for (int q = 0; q < R; ++q)
-        lb[q] = (k0 + q < N) ? sm.lring[slot][chain][k0 + q] * kLog2ef : -INFINITY;
-    } else {
-      ft = feat_of(fam, sm.yring[slot][chain], a.mv.lfact2);
-#pragma unroll
-      for (int q = 0; q < R; ++q) {
-        // padding states carry a -inf constant (see derive_row)
-        const float e = emis_log2(fam, ft, cf[q], nbt[q]);
-        lb[q] = ft.ok ? e : -INFINITY;
-      }
-    }
-
+    for (int q = 0; q < R; ++q) lb[q] = lbn[q];
+    const Feat ft = ftn;
+    emission((slot == PD - 1) ? 0 : slot + 1);
     // mat-vec s = M^T v_prev (or the initial vector), packed FP32x2 FMAs
     const bool first = !started;
     float2 vin[NH];
@@ -473,6 +482,9 @@ __device__ void estep_item(WarpSmem<C>& sm, const EStepArgs& a, int item, int la
     cp_commit();
   }
   int xb = 0;
+  cp_wait<PD - 2>();
+  __syncwarp();
+  emission(0);
   for (int k = 0; k < K1; ++k) {
     step(std::false_type{}, k, n1, ta, slot, pslot, xb);
     xb ^= 1;
@@ -490,6 +502,9 @@ __device__ void estep_item(WarpSmem<C>& sm, const EStepArgs& a, int item, int la
     prefetch(kk, n2, tb, true, kk);
     cp_commit();
   }
+  cp_wait<PD - 2>();
+  __syncwarp();
+  emission(0);
   for (int k = 0; k < K2; ++k) {
     step(std::true_type{}, k, n2, tb, slot, pslot, xb);
     xb ^= 1;
@@ -523,10 +538,9 @@ namespace hmm {
 // global counter; items are laid out in the plan's order (family, then
 // length descending) so that consecutive items are alike.
 // FAMK: one emission family for the whole launch, FAM_TABLE for a log b
-// table, or FAM_ANY for batches that mix families (the family is then
-// chosen per work item; warps straddling two families take the slower
-// per-step switch).  Specialised launches keep the register budget of the
-// common single-family case low.
+// table, or FAM_ANY for batches that mix families (each work item then runs
+// the loop of its family; items mixing families switch per step).
+// Specialised launches keep the register budget of the single-family case low.
 template <int NP, int G, int WPB, int MODE, int FAMK>
 __global__ void __launch_bounds__(WPB * 32) estep_small_kernel(EStepArgs a) {
   using C = SmallCfg<NP, G>;
@@ -541,6 +555,8 @@ __global__ void __launch_bounds__(WPB * 32) estep_small_kernel(EStepArgs a) {
     if constexpr (FAMK != FAM_ANY) {
       estep_item<C, FAMK, MODE>(sm, a, item, lane);
     } else {
+      // mixed batch: a work item whose chains share one family runs that
+      // family's loop; items straddling two families switch per step
       const int pair = (lane / G) >> 1;
       const int slotseq = item * C::SPW + pair;
       const int fam = slotseq < a.n_seq ? a.mv.family[a.model_id[a.order[slotseq]]] : -2;
@@ -551,6 +567,7 @@ __global__ void __launch_bounds__(WPB * 32) estep_small_kernel(EStepArgs a) {
         case HMM_POISSON: estep_item<C, HMM_POISSON, MODE>(sm, a, item, lane); break;
         case HMM_NEGBIN: estep_item<C, HMM_NEGBIN, MODE>(sm, a, item, lane); break;
         case HMM_VONMISES: estep_item<C, HMM_VONMISES, MODE>(sm, a, item, lane); break;
+        case HMM_GAMMA: estep_item<C, HMM_GAMMA, MODE>(sm, a, item, lane); break;
         default: estep_item<C, FAM_ANY, MODE>(sm, a, item, lane); break;
       }
     }

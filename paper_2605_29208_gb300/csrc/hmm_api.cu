@@ -246,8 +246,16 @@ hmm_plan make_plan(hmm_ctx ctx, hmm_model model, const hmm_batch* b, const int64
     std::vector<int32_t> order(S), bym(S);
     std::iota(order.begin(), order.end(), 0);
     std::iota(bym.begin(), bym.end(), 0);
-    // processing order: family, then length descending (longest first)
+    // processing order: longest first in buckets of ~9% length (so that the
+    // persistent warps take the long sequences early), family inside a
+    // bucket (family-uniform warps), then exact length descending
+    auto bucket = [&](int32_t q) {
+      const int64_t L = ho[q + 1] - ho[q];
+      return L <= 0 ? -1 : (int)std::floor(8.0 * std::log2((double)L));
+    };
     std::stable_sort(order.begin(), order.end(), [&](int32_t x, int32_t y) {
+      const int bx = bucket(x), by = bucket(y);
+      if (bx != by) return bx > by;
       const int fx = model->h_family[hm[x]], fy = model->h_family[hm[y]];
       if (fx != fy) return fx < fy;
       return (ho[x + 1] - ho[x]) > (ho[y + 1] - ho[y]);
@@ -388,7 +396,7 @@ void run_estep(hmm_ctx ctx, hmm_model model, const hmm_batch* b, hmm_plan plan, 
   a.model_id = b->model_id;
   a.order = plan->order.as<int32_t>();
   a.n_seq = (int32_t)S;
-  int G = default_estep_G(NP, S, ctx->n_sm);
+  int G = plan->estep_G > 0 ? plan->estep_G : default_estep_G(NP, S, ctx->n_sm);
   if (ctx->estep_lanes && estep_small_supported(NP, ctx->estep_lanes)) G = ctx->estep_lanes;
   a.n_items = (int32_t)((S + estep_seqs_per_item(G) - 1) / estep_seqs_per_item(G));
   a.mv = model->view();
@@ -449,6 +457,8 @@ void prepare_mstep(hmm_model model, hmm_stats stats, const hmm_batch* b, hmm_pla
   stats->dp_part.ensure((size_t)std::max<int64_t>(b->n_seq, 1) * RS * 4);
   stats->dp_chunk.ensure((size_t)std::max(plan->n_chunks, 1) * RS * 8);
   stats->dp_rec.ensure((size_t)model->M * RS * 8);
+  if (model->any_negbin) stats->nb_d.ensure((size_t)model->M * model->NP * 2 * NB_YMAX * 4);
+  stats->dp_count.ensure(64 * sizeof(int));
 }
 
 void run_mstep(hmm_ctx ctx, hmm_model model, hmm_stats stats, const MStepOpts& o, const hmm_batch* b,
@@ -479,9 +489,21 @@ void run_mstep(hmm_ctx ctx, hmm_model model, hmm_stats stats, const MStepOpts& o
   const unsigned blocks = (unsigned)((S * 32 + 255) / 256);
   const int nthr = model->M * NP;
   KTimer kt(ctx, HMM_KT_MSTEP, st);
+  prepare_mstep(model, stats, b, plan);
+  // active-state counters, one per pass (the update of pass p fills p + 1);
+  // passes with no active state return at once
+  int* cnt = stats->dp_count.as<int>();
+  HMM_CUDA(cudaMemsetAsync(cnt, 0, (size_t)(passes + 2) * sizeof(int), st));
+  dp_count_kernel<<<(nthr + 127) / 128, 128, 0, st>>>(dps, nthr, cnt);
+  HMM_CUDA(cudaGetLastError());
   for (int it = 0; it <= passes; ++it) {
+    if (model->any_negbin) {
+      nb_table_kernel<<<(nthr + 127) / 128, 128, 0, st>>>(model->bufs(), dps, cnt + it, stats->nb_d.as<float>());
+      HMM_CUDA(cudaGetLastError());
+    }
     dp_sums_kernel<<<blocks, 256, 0, st>>>(model->bufs(), b->values, stats->gamma.as<float>(), b->offsets,
-                                           b->model_id, (int)S, dps, stats->dp_part.as<float>());
+                                           b->model_id, (int)S, dps, stats->nb_d.as<float>(), cnt + it,
+                                           stats->dp_part.as<float>());
     HMM_CUDA(cudaGetLastError());
     if (plan->n_chunks > 0) {
       reduce_records_l1<<<plan->n_chunks, 128, 0, st>>>(stats->dp_part.as<float>(), RS,
@@ -493,7 +515,7 @@ void run_mstep(hmm_ctx ctx, hmm_model model, hmm_stats stats, const MStepOpts& o
                                                stats->dp_rec.as<double>());
     HMM_CUDA(cudaGetLastError());
     dp_update_kernel<<<(nthr + 127) / 128, 128, 0, st>>>(model->bufs(), stats->dp_rec.as<double>(), dps, o,
-                                                         it == passes ? 1 : 0);
+                                                         it == passes ? 1 : 0, cnt + it, cnt + it + 1);
     HMM_CUDA(cudaGetLastError());
   }
   dp_finish_kernel<<<(nthr + 127) / 128, 128, 0, st>>>(model->bufs());
@@ -801,6 +823,85 @@ hmm_status hmm_plan_destroy(hmm_plan plan) {
   return guarded([&] { destroy_plan(plan); });
 }
 
+hmm_status hmm_plan_autotune(hmm_ctx ctx, hmm_model model, const hmm_batch* batch, double* h_ms, void* stream) {
+  return guarded([&] {
+    HMM_REQUIRE(ctx && model && batch && batch->plan, "NULL argument (the batch needs a plan)");
+    check_batch(model, batch);
+    hmm_plan plan = batch->plan;
+    HMM_REQUIRE(plan->n_seq == batch->n_seq && plan->total_T == batch->total_T, "plan does not match the batch");
+    if (model->NP > 32 || batch->n_seq == 0) return;
+    cudaStream_t st = S(stream);
+    const int NP = model->NP;
+    ctx->tune_out.ensure((size_t)std::max<int64_t>(batch->total_T, 1) * 4 + (size_t)batch->n_seq * 8 + 256);
+    int32_t* path = ctx->tune_out.as<int32_t>();
+    double* score = reinterpret_cast<double*>(ctx->tune_out.as<char>() +
+                                              (((size_t)std::max<int64_t>(batch->total_T, 1) * 4 + 255) & ~size_t(255)));
+    cudaEvent_t e0, e1;
+    HMM_CUDA(cudaEventCreate(&e0));
+    HMM_CUDA(cudaEventCreate(&e1));
+    struct Ev {
+      cudaEvent_t a, b;
+      ~Ev() {
+        cudaEventDestroy(a);
+        cudaEventDestroy(b);
+      }
+    } ev{e0, e1};
+    const int saved_e = ctx->estep_lanes, saved_v = ctx->viterbi_lanes, saved_p = ctx->plain_estep;
+    ctx->plain_estep = 0;
+    double best_e = 1e30, best_v = 1e30;
+    int g_e = 0, g_v = 0;
+    try {
+      for (int G = 1; G <= 16; G *= 2) {
+        if (estep_small_supported(NP, G)) {
+          ctx->estep_lanes = G;
+          float ms = 0.f;
+          for (int rep = 0; rep < 2; ++rep) {
+            HMM_CUDA(cudaEventRecord(e0, st));
+            run_estep(ctx, model, batch, plan, nullptr, nullptr, nullptr, false, nullptr, st);
+            HMM_CUDA(cudaEventRecord(e1, st));
+            HMM_CUDA(cudaEventSynchronize(e1));
+            HMM_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+          }
+          if (ms < best_e) {
+            best_e = ms;
+            g_e = G;
+          }
+        }
+        if (viterbi_small_supported(NP, G)) {
+          ctx->viterbi_lanes = G;
+          float ms = 0.f;
+          for (int rep = 0; rep < 2; ++rep) {
+            HMM_CUDA(cudaEventRecord(e0, st));
+            hmm_status vs = hmm_viterbi(ctx, model, batch, nullptr, path, score, stream);
+            if (vs != HMM_OK) throw Error{vs, hmm_last_error()};
+            HMM_CUDA(cudaEventRecord(e1, st));
+            HMM_CUDA(cudaEventSynchronize(e1));
+            HMM_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+          }
+          if (ms < best_v) {
+            best_v = ms;
+            g_v = G;
+          }
+        }
+      }
+    } catch (...) {
+      ctx->estep_lanes = saved_e;
+      ctx->viterbi_lanes = saved_v;
+      ctx->plain_estep = saved_p;
+      throw;
+    }
+    ctx->estep_lanes = saved_e;
+    ctx->viterbi_lanes = saved_v;
+    ctx->plain_estep = saved_p;
+    plan->estep_G = g_e;
+    plan->viterbi_G = g_v;
+    if (h_ms) {
+      h_ms[0] = best_e;
+      h_ms[1] = best_v;
+    }
+  });
+}
+
 hmm_status hmm_emission_logpdf(hmm_ctx ctx, hmm_model model, const hmm_batch* batch, float* d_logb,
                                void* stream) {
   return guarded([&] {
@@ -858,7 +959,7 @@ hmm_status hmm_viterbi(hmm_ctx ctx, hmm_model model, const hmm_batch* batch, con
     a.model_id = batch->model_id;
     a.order = pr.p->order.as<int32_t>();
     a.n_seq = (int32_t)Sn;
-    int G = default_viterbi_G(NP, Sn, ctx->n_sm);
+    int G = pr.p->viterbi_G > 0 ? pr.p->viterbi_G : default_viterbi_G(NP, Sn, ctx->n_sm);
     if (ctx->viterbi_lanes && viterbi_small_supported(NP, ctx->viterbi_lanes)) G = ctx->viterbi_lanes;
     a.n_items = (int32_t)((Sn + viterbi_seqs_per_item(G) - 1) / viterbi_seqs_per_item(G));
     a.mv = model->view();
@@ -870,7 +971,8 @@ hmm_status hmm_viterbi(hmm_ctx ctx, hmm_model model, const hmm_batch* batch, con
     HMM_CUDA(cudaMemsetAsync(ctx->counters + 1, 0, sizeof(int), S(stream)));
     {
       KTimer kt(ctx, HMM_KT_VITERBI, S(stream));
-      HMM_CUDA(launch_viterbi_small(NP, G, a, d_logb ? 1 : 0, ctx->n_sm, S(stream)));
+      const int fam = d_logb ? FAM_TABLE : (pr.p->uniform_family >= 0 ? pr.p->uniform_family : FAM_ANY);
+      HMM_CUDA(launch_viterbi_small(NP, G, a, fam, ctx->n_sm, S(stream)));
     }
     if (pr.owned) HMM_CUDA(cudaStreamSynchronize(S(stream)));
   });
@@ -896,7 +998,8 @@ hmm_status hmm_stats_create(hmm_ctx ctx, hmm_model model, hmm_stats* out) {
 hmm_status hmm_stats_destroy(hmm_stats stats) {
   return guarded([&] {
     if (!stats) return;
-    for (auto* bb : {&stats->rec, &stats->gamma, &stats->dps, &stats->dp_part, &stats->dp_chunk, &stats->dp_rec})
+    for (auto* bb : {&stats->rec, &stats->gamma, &stats->dps, &stats->dp_part, &stats->dp_chunk, &stats->dp_rec,
+                     &stats->nb_d, &stats->dp_count})
       bb->release();
     delete stats;
   });
@@ -1075,6 +1178,10 @@ hmm_status hmm_fit(hmm_ctx ctx, hmm_model model, const hmm_batch* batch, const h
     ctx->trace.ensure((size_t)std::max(iters, 1) * M * 8 + 64);
     int* it_dev = reinterpret_cast<int*>(ctx->trace.as<char>() + (size_t)std::max(iters, 1) * M * 8);
     HMM_CUDA(cudaMemsetAsync(it_dev, 0, sizeof(int), st));
+    if (!pr.owned && pr.p->estep_G == 0 && iters >= 3 && model->NP <= 32) {
+      hmm_status ts = hmm_plan_autotune(ctx, model, batch, nullptr, st);
+      if (ts != HMM_OK) throw Error{ts, hmm_last_error()};
+    }
     // make every buffer the iteration needs exist before any capture
     run_estep(ctx, model, batch, pr.p, nullptr, nullptr, nullptr, true, stats, st);
     prepare_mstep(model, stats, batch, pr.p);

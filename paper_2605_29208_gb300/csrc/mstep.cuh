@@ -182,6 +182,7 @@ __device__ inline void derive_row(const ModelBufs& mb, int m, int k) {
     // log b = -inf for every observation inside the support
     float* c = mb.coef + ((size_t)m * NP + k) * KC;
     for (int z = 0; z < KC; ++z) c[z] = 0.f;
+    if (mb.family[m] == HMM_NEGBIN) c[2] = 1.f;   // r = 1 keeps lgamma(y + r) finite
     c[additive_slot(mb.family[m])] = -INFINITY;
   }
 }
@@ -403,20 +404,29 @@ __global__ void mstep_kernel(ModelBufs mb, const double* __restrict__ rec, MStep
 //            u = ln y - mlog, e = exp(k u)   (shift mlog cancels in Eq. 11)
 //   NegBin   D1 = sum g [psi(y + r) - psi(r)], D2 = sum g [psi'(y + r) - psi'(r)]
 // ---------------------------------------------------------------------------
+// Lanes cover (time step, state) pairs: lane = tt * NP + k handles state k
+// at the steps t = b + tt, b + tt + TPW, ... (TPW = 32 / NP), so a warp reads
+// TPW consecutive occupancy rows per iteration; the TPW partial sums of a
+// state are combined with shuffles at the end.  Nothing runs once no state
+// of any model is active (count in *active_count).
 __global__ void dp_sums_kernel(ModelBufs mb, const float* __restrict__ y, const float* __restrict__ gamma,
                                const int64_t* __restrict__ offsets, const int32_t* __restrict__ model_id,
-                               int n_seq, const DPState* __restrict__ dps, float* __restrict__ part) {
+                               int n_seq, const DPState* __restrict__ dps, const float* __restrict__ nbd,
+                               const int* __restrict__ active_count, float* __restrict__ part) {
+  if (*active_count == 0) return;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (warp >= n_seq) return;
   const int s = warp;
   const int NP = mb.NP, N = mb.N;
+  const int TPW = 32 / NP;
+  const int tt = lane / NP, k = lane % NP;
   const int m = model_id[s];
   const int fam = mb.family[m];
   float* out = part + (size_t)s * NP * 3;
   const bool dpf = (fam == HMM_WEIBULL || fam == HMM_NEGBIN);
   const DPState* d = dps + (size_t)m * NP;
-  const bool mine = dpf && lane < N && d[lane].active != 0;
+  const bool mine = dpf && k < N && tt < TPW && d[k].active != 0;
   const bool any = __any_sync(0xffffffffu, mine);
   if (!any) {
     if (lane < NP) {
@@ -429,34 +439,94 @@ __global__ void dp_sums_kernel(ModelBufs mb, const float* __restrict__ y, const 
   const int64_t b = offsets[s], e = offsets[s + 1];
   float a0 = 0.f, a1 = 0.f, a2 = 0.f;
   if (mine) {
-    const float x = (float)d[lane].x;
+    const float x = (float)d[k].x;
+    float i0 = 0.f, i1 = 0.f, i2 = 0.f;
+    int cnt = 0;
     if (fam == HMM_WEIBULL) {
-      const float ml = (float)d[lane].mlog;
-      for (int64_t t = b; t < e; ++t) {
-        const float g = gamma[t * N + lane];
+      const float ml = (float)d[k].mlog;
+      for (int64_t t = b + tt; t < e; t += TPW) {
+        const float g = gamma[t * N + k];
         const float yy = y[t];
-        if (!(yy > 0.f)) continue;
         const float u = logf(yy) - ml;
-        const float w = g * expf(x * u);
-        a0 += w;
-        a1 = fmaf(w, u, a1);
-        a2 = fmaf(w * u, u, a2);
+        const float w = (yy > 0.f) ? g * expf(x * u) : 0.f;
+        i0 += w;
+        i1 = fmaf(w, u, i1);
+        i2 = fmaf(w * u, u, i2);
+        if (++cnt == 64) {       // two-level sums
+          a0 += i0;
+          a1 += i1;
+          a2 += i2;
+          i0 = i1 = i2 = 0.f;
+          cnt = 0;
+        }
       }
     } else {
-      const float pr = digamma_f(x), tr = trigamma_f(x);
-      for (int64_t t = b; t < e; ++t) {
-        const float g = gamma[t * N + lane];
+      // psi(y + r) - psi(r) and psi'(y + r) - psi'(r) from the float64-built
+      // per-state tables for y < NB_YMAX; float32 evaluation above (rare)
+      const float* T1 = nbd + ((size_t)m * NP + k) * 2 * NB_YMAX;
+      const float* T2 = T1 + NB_YMAX;
+      for (int64_t t = b + tt; t < e; t += TPW) {
+        const float g = gamma[t * N + k];
         const float yy = y[t];
-        if (g == 0.f || yy == 0.f) continue;
-        a0 = fmaf(g, digamma_f(yy + x) - pr, a0);
-        a1 = fmaf(g, trigamma_f(yy + x) - tr, a1);
+        const int yi = (int)fminf(yy, 2.0e9f);
+        float d1, d2;
+        if (yi < NB_YMAX) {
+          d1 = __ldg(T1 + yi);
+          d2 = __ldg(T2 + yi);
+        } else {
+          d1 = digamma_f(yy + x) - digamma_f(x);
+          d2 = trigamma_f(yy + x) - trigamma_f(x);
+        }
+        i0 = fmaf(g, d1, i0);
+        i1 = fmaf(g, d2, i1);
+        if (++cnt == 64) {
+          a0 += i0;
+          a1 += i1;
+          i0 = i1 = 0.f;
+          cnt = 0;
+        }
       }
     }
+    a0 += i0;
+    a1 += i1;
+    a2 += i2;
+  }
+  // combine the TPW lanes of each state (fixed xor order: deterministic)
+  for (int o = NP; o < 32; o <<= 1) {
+    a0 += __shfl_xor_sync(0xffffffffu, a0, o);
+    a1 += __shfl_xor_sync(0xffffffffu, a1, o);
+    a2 += __shfl_xor_sync(0xffffffffu, a2, o);
   }
   if (lane < NP) {
     out[lane * 3 + 0] = a0;
     out[lane * 3 + 1] = a1;
     out[lane * 3 + 2] = a2;
+  }
+}
+
+// Tables of psi(y + r) - psi(r) and psi'(y + r) - psi'(r) for integer
+// y < NB_YMAX at the current iterate r of every active negative-binomial
+// state, by the float64 recurrences psi(x + 1) = psi(x) + 1/x and
+// psi'(x + 1) = psi'(x) - 1/x^2 (exact up to rounding), stored as float32.
+__global__ void nb_table_kernel(ModelBufs mb, const DPState* __restrict__ dps, const int* __restrict__ active_count,
+                                float* __restrict__ nbd) {
+  if (*active_count == 0) return;
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= mb.M * mb.NP) return;
+  const int m = idx / mb.NP, k = idx % mb.NP;
+  if (k >= mb.N || mb.family[m] != HMM_NEGBIN || !dps[idx].active) return;
+  const double r = dps[idx].x;
+  float* T1 = nbd + (size_t)idx * 2 * NB_YMAX;
+  float* T2 = T1 + NB_YMAX;
+  double d1 = 0.0, d2 = 0.0;
+  T1[0] = 0.f;
+  T2[0] = 0.f;
+  for (int y = 1; y < NB_YMAX; ++y) {
+    const double x = r + (double)(y - 1);
+    d1 += 1.0 / x;
+    d2 -= 1.0 / (x * x);
+    T1[y] = (float)d1;
+    T2[y] = (float)d2;
   }
 }
 
@@ -477,10 +547,11 @@ __global__ void reduce_records_l1(const float* __restrict__ part, int RS, const 
 // One Newton step per active (model, state); a converged Weibull state asks
 // for one more pass to get its scale.  The data-pass sums are float32, so the
 // iterate cannot settle below ~1e-7 relative: the stopping tolerance is
-// max(newton_tol, 1e-7).  With `final` set every Weibull state still running
+// max(newton_tol, 1e-6).  With `final` set every Weibull state still running
 // takes its current shape and the scale of the last pass.
 __global__ void dp_update_kernel(ModelBufs mb, const double* __restrict__ rec, DPState* dps, MStepOpts o,
-                                 int final) {
+                                 int final, const int* __restrict__ active_now, int* __restrict__ active_next) {
+  if (*active_now == 0) return;
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= mb.M * mb.NP) return;
   const int m = idx / mb.NP, k = idx % mb.NP;
@@ -490,27 +561,27 @@ __global__ void dp_update_kernel(ModelBufs mb, const double* __restrict__ rec, D
   const int fam = mb.family[m];
   const double* R = rec + (size_t)m * mb.NP * 3 + k * 3;
   double* th = mb.theta + ((size_t)m * mb.NP + k) * mb.P;
-  const double tol = fmax(o.newton_tol, 1e-7);
+  const double tol = fmax(o.newton_tol, 1e-6);
   if (fam == HMM_WEIBULL) {
     const double S0 = R[0], S1 = R[1], S2 = R[2];
     if (d.active == 2 || final) {   // scale from the converged (or last) shape
       th[0] = d.x;
       th[1] = exp(d.mlog + log(S0 / d.W) / d.x);
       d.active = 0;
-      return;
+    } else {
+      const double kk = d.x;
+      const double f = 1.0 / kk - S1 / S0;
+      const double df = -1.0 / (kk * kk) - (S2 * S0 - S1 * S1) / (S0 * S0);
+      double step = f / df, nw = kk - step;
+      while (nw <= 0.0) {
+        step *= 0.5;
+        nw = kk - step;
+      }
+      d.iters++;
+      const bool done = newton_done(kk, nw, tol) || d.iters >= o.newton_maxit;
+      d.x = nw;
+      if (done) d.active = 2;
     }
-    const double kk = d.x;
-    const double f = 1.0 / kk - S1 / S0;
-    const double df = -1.0 / (kk * kk) - (S2 * S0 - S1 * S1) / (S0 * S0);
-    double step = f / df, nw = kk - step;
-    while (nw <= 0.0) {
-      step *= 0.5;
-      nw = kk - step;
-    }
-    d.iters++;
-    const bool done = newton_done(kk, nw, tol) || d.iters >= o.newton_maxit;
-    d.x = nw;
-    if (done) d.active = 2;
   } else if (fam == HMM_NEGBIN) {
     const double r = d.x, W = d.W, ybar = d.ybar;
     const double g = R[0] + W * log(r / (r + ybar));
@@ -528,6 +599,13 @@ __global__ void dp_update_kernel(ModelBufs mb, const double* __restrict__ rec, D
     th[1] = nw / (nw + ybar);
     if (done) d.active = 0;
   }
+  if (d.active) atomicAdd(active_next, 1);   // still running in the next pass
+}
+
+// number of active data-pass states after the seeding M-step
+__global__ void dp_count_kernel(const DPState* __restrict__ dps, int n, int* __restrict__ count) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx < n && dps[idx].active) atomicAdd(count, 1);
 }
 
 // refresh the derived tables after the data-pass Newton steps

@@ -78,6 +78,7 @@ struct hmm_ctx_s {
   hmm::DevBuf dp_part;           // data-pass partials
   hmm::DevBuf trace;             // float64 logL trace of hmm_fit
   hmm::DevBuf plain_beta;        // beta-hat rows of the plain path
+  hmm::DevBuf tune_out;          // outputs of the autotuner's trial runs
   // options
   int profile = 0;
   int estep_lanes = 0;
@@ -116,6 +117,8 @@ struct hmm_stats_s {
   hmm::DevBuf dp_part;           // [S][NP][3] float32
   hmm::DevBuf dp_chunk;          // [n_chunks][NP*3] float64
   hmm::DevBuf dp_rec;            // [M][NP*3] float64
+  hmm::DevBuf nb_d;              // [M][NP][2][NB_YMAX] float32 digamma tables
+  hmm::DevBuf dp_count;          // active-state counters of the passes
 };
 
 struct hmm_plan_s {
@@ -129,5 +132,7 @@ struct hmm_plan_s {
   hmm::DevBuf model_chunk_ptr;   // [M+1] int32
   int n_chunks = 0;
   int uniform_family = -1;       // the one family of all sequences, or -1
+  int estep_G = 0;               // chain widths chosen by hmm_plan_autotune (0: default)
+  int viterbi_G = 0;
   std::vector<int32_t> h_order;
 };

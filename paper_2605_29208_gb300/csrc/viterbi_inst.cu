@@ -5,11 +5,11 @@ namespace hmm {
 
 namespace {
 
-template <int NP, int G>
-cudaError_t launch_one(const VitArgs& a, int table_mode, int n_sm, cudaStream_t st) {
+template <int NP, int G, int FAMK>
+cudaError_t launch_fam(const VitArgs& a, int n_sm, cudaStream_t st) {
   constexpr int WPB = kWarpsPerBlock;
   const size_t smem = sizeof(VitSmem<VitCfg<NP, G>>) * WPB;
-  auto kern = viterbi_small_kernel<NP, G, WPB>;
+  auto kern = viterbi_small_kernel<NP, G, WPB, FAMK>;
   static bool attr_set = false;
   if (!attr_set) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -24,8 +24,24 @@ cudaError_t launch_one(const VitArgs& a, int table_mode, int n_sm, cudaStream_t 
   int grid = per_sm * n_sm;
   if (want < grid) grid = want;
   if (grid < 1) grid = 1;
-  kern<<<grid, WPB * 32, smem, st>>>(a, table_mode);
+  kern<<<grid, WPB * 32, smem, st>>>(a);
   return cudaGetLastError();
+}
+
+template <int NP, int G>
+cudaError_t launch_one(const VitArgs& a, int fam, int n_sm, cudaStream_t st) {
+  switch (fam) {
+    case FAM_TABLE: return launch_fam<NP, G, FAM_TABLE>(a, n_sm, st);
+    case HMM_GAUSS: return launch_fam<NP, G, HMM_GAUSS>(a, n_sm, st);
+    case HMM_POISSON: return launch_fam<NP, G, HMM_POISSON>(a, n_sm, st);
+    case HMM_GAMMA: return launch_fam<NP, G, HMM_GAMMA>(a, n_sm, st);
+    case HMM_BETA: return launch_fam<NP, G, HMM_BETA>(a, n_sm, st);
+    case HMM_WEIBULL: return launch_fam<NP, G, HMM_WEIBULL>(a, n_sm, st);
+    case HMM_NEGBIN: return launch_fam<NP, G, HMM_NEGBIN>(a, n_sm, st);
+    case HMM_STUDENT_T: return launch_fam<NP, G, HMM_STUDENT_T>(a, n_sm, st);
+    case HMM_VONMISES: return launch_fam<NP, G, HMM_VONMISES>(a, n_sm, st);
+    default: return launch_fam<NP, G, FAM_ANY>(a, n_sm, st);
+  }
 }
 
 }  // namespace
@@ -55,10 +71,10 @@ int default_viterbi_G(int NP, int64_t n_seq, int n_sm) {
   return G;
 }
 
-cudaError_t launch_viterbi_small(int NP, int G, const VitArgs& a, int table_mode, int n_sm,
+cudaError_t launch_viterbi_small(int NP, int G, const VitArgs& a, int fam, int n_sm,
                                  cudaStream_t st) {
 #define HMM_CASE(np, g) \
-  if (NP == np && G == g) return launch_one<np, g>(a, table_mode, n_sm, st);
+  if (NP == np && G == g) return launch_one<np, g>(a, fam, n_sm, st);
   HMM_CASE(2, 1)
   HMM_CASE(2, 2)
   HMM_CASE(4, 1)

@@ -40,7 +40,7 @@ struct VitCfg {
   static constexpr int G = G_;
   static constexpr int R = NP / G;
   static constexpr int CPW = 32 / G;
-  static constexpr int PD = 6;
+  static constexpr int PD = 8;
   static constexpr int TBCH = 64;
   static constexpr int TBB = TBCH * NP + 8;   // staged bytes per chain (+ alignment slack)
 };
@@ -119,28 +119,41 @@ __device__ void viterbi_item(VitSmem<C>& sm, const VitArgs& a, int item, int lan
   for (int q = 0; q < R; ++q) d[q] = -INFINITY;
   double off = 0.0;
   float off_in = 0.f;   // float32 inner sum of the shifts (<= 16 steps)
+  // emission of the step in ring slot sl, computed one step ahead of its use
+  float lbn[R];
+  auto emission = [&](int sl) {
+    if constexpr (TABLE) {
+#pragma unroll
+      for (int q = 0; q < R; ++q) lbn[q] = (k0 + q < N) ? sm.lring[sl][chain][k0 + q] : -INFINITY;
+    } else {
+      const Feat ft = feat_of(fam, sm.yring[sl][chain], a.mv.lfact2);
+#pragma unroll
+      for (int q = 0; q < R; ++q) {
+        const float e = emis_log2(fam, ft, cf[q], nbt[q]);
+        lbn[q] = ft.ok ? e : -INFINITY;
+      }
+    }
+  };
+  cp_wait<C::PD - 2>();
+  __syncwarp();
+  emission(0);
+  int slot = 0;
   for (int k = 0; k < kmax; ++k) {
     const bool active = k < T;
-    const int slot = k % C::PD;
     if (active && k > 0) {
 #pragma unroll
       for (int q = 0; q < R; ++q) sm.xbuf[k & 1][chain][k0 + q] = d[q];
     }
-    cp_wait<C::PD - 2>();
+    cp_wait<C::PD - 3>();
     __syncwarp();
     if (k + C::PD - 1 < kmax) vit_prefetch<C, FAM>(sm, a, k + C::PD - 1, chain, sub, T, base);
     cp_commit();
 
     float lb[R];
-    if constexpr (TABLE) {
 #pragma unroll
-      for (int q = 0; q < R; ++q) lb[q] = (k0 + q < N) ? sm.lring[slot][chain][k0 + q] : -INFINITY;
-    } else {
-      const Feat ft = feat_of(fam, sm.yring[slot][chain], a.mv.lfact2);
-#pragma unroll
-      for (int q = 0; q < R; ++q)
-        lb[q] = (ft.ok && (k0 + q) < N) ? emis_log2(fam, ft, cf[q], nbt[q]) : -INFINITY;
-    }
+    for (int q = 0; q < R; ++q) lb[q] = lbn[q];
+    slot = (slot == C::PD - 1) ? 0 : slot + 1;
+    emission(slot);
     uint32_t arg4 = 0;
     float nd[R];
     if (k == 0) {
@@ -254,8 +267,10 @@ __device__ void viterbi_item(VitSmem<C>& sm, const VitArgs& a, int item, int lan
   __syncwarp();
 }
 
-template <int NP, int G, int WPB>
-__global__ void __launch_bounds__(WPB * 32) viterbi_small_kernel(VitArgs a, int table_mode) {
+// FAMK as in the E-step: one family per launch, FAM_TABLE, or FAM_ANY
+// (per-item dispatch to the family's loop).
+template <int NP, int G, int WPB, int FAMK>
+__global__ void __launch_bounds__(WPB * 32) viterbi_small_kernel(VitArgs a) {
   using C = VitCfg<NP, G>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   VitSmem<C>& sm = reinterpret_cast<VitSmem<C>*>(smem_raw)[threadIdx.x >> 5];
@@ -265,24 +280,21 @@ __global__ void __launch_bounds__(WPB * 32) viterbi_small_kernel(VitArgs a, int 
     if (lane == 0) item = atomicAdd(a.work_counter, 1);
     item = __shfl_sync(0xffffffffu, item, 0);
     if (item >= a.n_items) break;
-    if (table_mode) {
-      viterbi_item<C, FAM_TABLE>(sm, a, item, lane);
-      continue;
-    }
-    const int slotseq = item * C::CPW + lane / G;
-    const int fam = slotseq < a.n_seq ? a.mv.family[a.model_id[a.order[slotseq]]] : -2;
-    const int fam0 = __shfl_sync(0xffffffffu, fam, 0);
-    const bool uniform = __all_sync(0xffffffffu, fam == fam0 || fam == -2);
-    switch (uniform ? fam0 : FAM_ANY) {
-      case HMM_GAUSS: viterbi_item<C, HMM_GAUSS>(sm, a, item, lane); break;
-      case HMM_POISSON: viterbi_item<C, HMM_POISSON>(sm, a, item, lane); break;
-      case HMM_GAMMA: viterbi_item<C, HMM_GAMMA>(sm, a, item, lane); break;
-      case HMM_BETA: viterbi_item<C, HMM_BETA>(sm, a, item, lane); break;
-      case HMM_WEIBULL: viterbi_item<C, HMM_WEIBULL>(sm, a, item, lane); break;
-      case HMM_NEGBIN: viterbi_item<C, HMM_NEGBIN>(sm, a, item, lane); break;
-      case HMM_STUDENT_T: viterbi_item<C, HMM_STUDENT_T>(sm, a, item, lane); break;
-      case HMM_VONMISES: viterbi_item<C, HMM_VONMISES>(sm, a, item, lane); break;
-      default: viterbi_item<C, FAM_ANY>(sm, a, item, lane); break;
+    if constexpr (FAMK != FAM_ANY) {
+      viterbi_item<C, FAMK>(sm, a, item, lane);
+    } else {
+      const int slotseq = item * C::CPW + lane / G;
+      const int fam = slotseq < a.n_seq ? a.mv.family[a.model_id[a.order[slotseq]]] : -2;
+      const int fam0 = __shfl_sync(0xffffffffu, fam, 0);
+      const bool uniform = __all_sync(0xffffffffu, fam == fam0 || fam == -2);
+      switch (uniform ? fam0 : FAM_ANY) {
+        case HMM_GAUSS: viterbi_item<C, HMM_GAUSS>(sm, a, item, lane); break;
+        case HMM_POISSON: viterbi_item<C, HMM_POISSON>(sm, a, item, lane); break;
+        case HMM_NEGBIN: viterbi_item<C, HMM_NEGBIN>(sm, a, item, lane); break;
+        case HMM_VONMISES: viterbi_item<C, HMM_VONMISES>(sm, a, item, lane); break;
+        case HMM_GAMMA: viterbi_item<C, HMM_GAMMA>(sm, a, item, lane); break;
+        default: viterbi_item<C, FAM_ANY>(sm, a, item, lane); break;
+      }
     }
   }
 }

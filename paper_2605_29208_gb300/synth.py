@@ -157,6 +157,59 @@ def pack(seqs):
     return values, offsets
 
 
+def _stack_params(models, family):
+    names = PARAM_NAMES[family]
+    return {n: np.stack([np.asarray(m["params"][n], np.float64) for m in models]) for n in names}
+
+
+def make_batch_many(seed, models, lengths, model_id):
+    """Same output as make_batch for many models at once: the hidden paths of
+    all sequences are simulated together (inverse CDF on each sequence's own
+    transition rows) and emissions drawn per family with gathered parameters."""
+    rng = np.random.default_rng(seed)
+    model_id = np.asarray(model_id, dtype=np.int32)
+    lengths = np.asarray(lengths, dtype=np.int64)
+    S = len(lengths)
+    N = len(models[0]["pi"])
+    cpi = np.cumsum(np.stack([m["pi"] for m in models]), axis=1)          # [M, N]
+    cA = np.cumsum(np.stack([m["A"] for m in models]), axis=2)            # [M, N, N]
+    Tmax = int(lengths.max()) if S else 0
+    offsets = np.zeros(S + 1, dtype=np.int64)
+    np.cumsum(lengths, out=offsets[1:])
+    states = np.empty(int(offsets[-1]), dtype=np.int64)
+    q = np.minimum((rng.random(S)[:, None] * cpi[model_id, -1:] >= cpi[model_id]).sum(1), N - 1)
+    alive = np.arange(S)
+    for t in range(Tmax):
+        alive = alive[lengths[alive] > t]
+        if t == 0:
+            cur = q[alive]
+        else:
+            rows = cA[model_id[alive], cur]
+            u = rng.random(len(alive))[:, None]
+            cur = np.minimum((u * rows[:, -1:] >= rows).sum(1), N - 1)
+        states[offsets[alive] + t] = cur
+        # keep `cur` aligned with the next step's survivors
+        keep = lengths[alive] > t + 1
+        cur = cur[keep]
+        alive = alive[keep]
+        if len(alive) == 0:
+            break
+    values = np.empty(len(states))
+    seq_of_row = np.repeat(np.arange(S), lengths)
+    mrow = model_id[seq_of_row]
+    for fam in sorted({m["family"] for m in models}):
+        fam_models = [i for i, m in enumerate(models) if m["family"] == fam]
+        sel = np.isin(mrow, fam_models)
+        if not sel.any():
+            continue
+        lm = np.searchsorted(np.array(fam_models), mrow[sel])
+        P = _stack_params([models[i] for i in fam_models], fam)
+        params = {n: v[lm, states[sel]] for n, v in P.items()}
+        fake = dict(family=fam, params={n: v for n, v in params.items()})
+        values[sel] = sample_emissions(rng, fake, np.arange(sel.sum()))
+    return to_f32_grid(values), offsets, model_id
+
+
 def make_batch(seed, models, lengths, model_id):
     """Simulate one sequence per entry of ``lengths`` from
     ``models[model_id[s]]``; returns (values, offsets, model_id)."""
@@ -225,7 +278,7 @@ BATCH_FAMILIES = ("gauss", "poisson", "negbin", "vonmises")
 
 
 def batching_workload(n_seq=100_000, n_models=1024, N=8, seed=MASTER_SEED + 2,
-                      median=500, sigma=1.0, tmin=50, tmax=20000):
+                      median=500, sigma=1.0, tmin=50, tmax=20000, families=BATCH_FAMILIES):
     """Ragged batch: lengths round(lognormal(log median, sigma)) clipped to
     [tmin, tmax]; n_models models, each with one family drawn uniformly from
     Gaussian / Poisson / negative binomial / von Mises for all its states;
@@ -233,16 +286,16 @@ def batching_workload(n_seq=100_000, n_models=1024, N=8, seed=MASTER_SEED + 2,
     rng = np.random.default_rng(seed)
     lengths = np.clip(np.round(rng.lognormal(np.log(median), sigma, n_seq)),
                       tmin, tmax).astype(np.int64)
-    fams = rng.integers(0, len(BATCH_FAMILIES), n_models)
+    fams = rng.integers(0, len(families), n_models)
     truths, inits = [], []
     for m in range(n_models):
-        fam = BATCH_FAMILIES[fams[m]]
+        fam = families[fams[m]]
         t = make_model(fam, np.full(N, 1.0 / N), dirichlet_rows(rng, N, 1.0),
                        **random_params(rng, fam, N))
         truths.append(t)
         inits.append(perturb(rng, t))
     model_id = rng.integers(0, n_models, n_seq).astype(np.int32)
-    values, offsets, mid = make_batch(seed + 100, truths, lengths, model_id)
+    values, offsets, mid = make_batch_many(seed + 100, truths, lengths, model_id)
     return truths, inits, values, offsets, mid
 
 

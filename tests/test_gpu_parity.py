@@ -290,3 +290,43 @@ def test_zero_probability_sequence(H, ctx):
     assert ll[0] == -np.inf
     ref = O.forward_backward(om(models[0]), values[4:6])["logL"]
     check_ll(ll[1:], np.array([ref]))
+
+
+def test_batching_mixed_families_ragged(H, ctx):
+    """The batching workload at reduced size: ragged lognormal lengths, 24
+    models of N = 8 states with Gaussian / Poisson / negative-binomial / von
+    Mises emissions in one persistent launch; per-sequence logL and one EM
+    iteration (all models) against the oracle."""
+    truths, inits, values, offsets, mid = synth.batching_workload(
+        n_seq=600, n_models=24, N=8, seed=77, median=100, tmin=10, tmax=1500)
+    model = H.Model(ctx, inits)
+    batch = H.Batch(values, offsets, mid).make_plan(ctx, model)
+    ll, _, _ = H.forward_backward(ctx, model, batch, want_gamma=False)
+    ll = ll.cpu().numpy()
+    oms = [om(m) for m in inits]
+    for s in range(0, 600, 7):
+        fb = O.forward_backward(oms[mid[s]], values[offsets[s]:offsets[s + 1]])
+        check_ll(np.array([ll[s]]), np.array([fb["logL"]]), s)
+    stats, _ = H.estep_stats(ctx, model, batch)
+    H.mstep(ctx, model, stats, batch=batch)
+    ref, _ = O.em_iteration(oms, values, offsets, mid)
+    assert_params_close(model.get(), ref)
+
+
+def test_autotune_keeps_results(H, ctx):
+    """The autotuner only changes chain widths: log-likelihoods before and
+    after tuning agree with each other and with the oracle."""
+    truths, inits, values, offsets, mid = synth.batching_workload(
+        n_seq=300, n_models=8, N=8, seed=78, median=80, tmin=5, tmax=3000)
+    model = H.Model(ctx, inits)
+    batch = H.Batch(values, offsets, mid).make_plan(ctx, model)
+    ll0, _, _ = H.forward_backward(ctx, model, batch, want_gamma=False)
+    ms = batch.autotune(ctx, model)
+    assert ms[0] > 0 and ms[1] > 0
+    ll1, _, _ = H.forward_backward(ctx, model, batch, want_gamma=False)
+    ll0, ll1 = ll0.cpu().numpy(), ll1.cpu().numpy()
+    np.testing.assert_allclose(ll1, ll0, rtol=2e-6, atol=1e-6)
+    oms = [om(m) for m in inits]
+    for s in range(0, 300, 17):
+        fb = O.forward_backward(oms[mid[s]], values[offsets[s]:offsets[s + 1]])
+        check_ll(np.array([ll1[s]]), np.array([fb["logL"]]), s)
