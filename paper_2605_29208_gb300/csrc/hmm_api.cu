@@ -9,6 +9,7 @@
 
 #include "launch.h"
 #include "mstep.cuh"
+#include "mv.cuh"
 #include "plain.cuh"
 #include "runtime.h"
 
@@ -290,6 +291,21 @@ hmm_plan make_plan(hmm_ctx ctx, hmm_model model, const hmm_batch* b, const int64
       HMM_CUDA(cudaMemcpy(p->chunk_hi.p, hi.data(), hi.size() * 4, cudaMemcpyHostToDevice));
     }
     HMM_CUDA(cudaMemcpy(p->model_chunk_ptr.p, mptr.data(), mptr.size() * 4, cudaMemcpyHostToDevice));
+    if (model->any_mv && S > 0) {
+      std::vector<int32_t> ts, tr;
+      for (int64_t q2 = 0; q2 < S; ++q2)
+        for (int64_t r = 0; r < ho[q2 + 1] - ho[q2]; r += 32) {
+          ts.push_back((int32_t)q2);
+          tr.push_back((int32_t)r);
+        }
+      p->n_tiles = (int)ts.size();
+      p->tile_seq.ensure(std::max<size_t>(ts.size(), 1) * 4);
+      p->tile_row.ensure(std::max<size_t>(tr.size(), 1) * 4);
+      if (!ts.empty()) {
+        HMM_CUDA(cudaMemcpy(p->tile_seq.p, ts.data(), ts.size() * 4, cudaMemcpyHostToDevice));
+        HMM_CUDA(cudaMemcpy(p->tile_row.p, tr.data(), tr.size() * 4, cudaMemcpyHostToDevice));
+      }
+    }
     int uf = -2;
     for (int64_t q2 = 0; q2 < S; ++q2) {
       const int f = model->h_family[hm[q2]];
@@ -316,6 +332,8 @@ void destroy_plan(hmm_plan p) {
   p->chunk_lo.release();
   p->chunk_hi.release();
   p->model_chunk_ptr.release();
+  p->tile_seq.release();
+  p->tile_row.release();
   delete p;
 }
 
@@ -349,8 +367,49 @@ void get_plan(hmm_ctx ctx, hmm_model model, const hmm_batch* b, cudaStream_t st,
 void require_small(hmm_model model) {
   if (model->NP > 32)
     throw Error{HMM_E_UNSUPPORTED, "state counts above 32 are not supported by this build"};
-  if (model->any_mv)
-    throw Error{HMM_E_UNSUPPORTED, "multivariate families need an emission table (d_logb)"};
+}
+
+// log b table of a multivariate model set over the batch (Sec. 4.5), in the
+// context's buffer: one block per 32-row tile of a sequence.
+const float* mv_table(hmm_ctx ctx, hmm_model model, const hmm_batch* b, hmm_plan plan, cudaStream_t st) {
+  ctx->mvlogb.ensure(std::max<int64_t>(b->total_T, 1) * model->N * 4);
+  if (plan->n_tiles > 0) {
+    KTimer kt(ctx, HMM_KT_EMISSION, st);
+    const size_t smem = (size_t)32 * model->D * 4;
+    mv_emission_kernel<<<(unsigned)plan->n_tiles, 128, smem, st>>>(
+        model->family.as<int>(), model->mvcoef.as<float>(), model->NP, model->N, model->D, model->KM, b->values,
+        b->offsets, b->model_id, plan->tile_seq.as<int32_t>(), plan->tile_row.as<int32_t>(),
+        ctx->mvlogb.as<float>());
+    HMM_CUDA(cudaGetLastError());
+  }
+  return ctx->mvlogb.as<float>();
+}
+
+// Shifted weighted moments of the multivariate families from the
+// occupancies in stats->gamma, reduced in fixed order into stats->mv_rec.
+void mv_statistics(hmm_ctx ctx, hmm_model model, const hmm_batch* b, hmm_plan plan, hmm_stats stats,
+                   cudaStream_t st) {
+  const int NP = model->NP, KS = model->KS, RS = NP * KS;
+  const int64_t S = b->n_seq;
+  stats->mv_part.ensure((size_t)std::max<int64_t>(S, 1) * RS * 4);
+  stats->mv_chunk.ensure((size_t)std::max(plan->n_chunks, 1) * RS * 8);
+  stats->mv_rec.ensure((size_t)model->M * RS * 8);
+  KTimer kt(ctx, HMM_KT_REDUCE, st);
+  if (S > 0) {
+    mv_stats_kernel<<<(unsigned)S, 128, 0, st>>>(model->family.as<int>(), model->mvcoef.as<float>(), NP, model->N,
+                                                 model->D, model->KM, KS, b->values, stats->gamma.as<float>(),
+                                                 b->offsets, b->model_id, stats->mv_part.as<float>());
+    HMM_CUDA(cudaGetLastError());
+  }
+  if (plan->n_chunks > 0) {
+    reduce_records_l1<<<plan->n_chunks, 128, 0, st>>>(stats->mv_part.as<float>(), RS, plan->seq_by_model.as<int32_t>(),
+                                                    plan->chunk_lo.as<int32_t>(), plan->chunk_hi.as<int32_t>(),
+                                                    stats->mv_chunk.as<double>());
+    HMM_CUDA(cudaGetLastError());
+  }
+  reduce_chunks_l2<<<model->M, 128, 0, st>>>(stats->mv_chunk.as<double>(), plan->model_chunk_ptr.as<int32_t>(), RS,
+                                             stats->mv_rec.as<double>());
+  HMM_CUDA(cudaGetLastError());
 }
 
 // The fused E-step over a batch.  gamma (optional) receives [total_T][N].
@@ -358,9 +417,11 @@ void run_estep(hmm_ctx ctx, hmm_model model, const hmm_batch* b, hmm_plan plan, 
                float* gamma, double* loglik, bool want_stats, hmm_stats stats, cudaStream_t st) {
   const int NP = model->NP;
   if (model->NP > 32) throw Error{HMM_E_UNSUPPORTED, "state counts above 32 are not supported"};
-  if (model->any_mv && !logb)
-    throw Error{HMM_E_UNSUPPORTED, "multivariate families need an emission table (d_logb)"};
+  if (model->any_mv && ctx->plain_estep)
+    throw Error{HMM_E_UNSUPPORTED, "the plain path covers the scalar families only"};
   const int64_t S = b->n_seq;
+  const bool mv_stats = want_stats && stats && model->any_mv;
+  if (model->any_mv && !logb) logb = mv_table(ctx, model, b, plan, st);
   ctx->scratch.ensure(std::max<int64_t>(b->total_T, 1) * NP * 4 + 64);
   const int F = NP + NST;
   ctx->partials.ensure(std::max<int64_t>(S, 1) * 2 * NP * F * 4);
@@ -406,9 +467,10 @@ void run_estep(hmm_ctx ctx, hmm_model model, const hmm_batch* b, hmm_plan plan, 
   a.loglik = ll;
   a.work_counter = ctx->counters;
   a.status = ctx->status;
-  const bool dpass = want_stats && stats && (model->any_negbin || model->any_weibull);
+  const bool dpass = want_stats && stats && (model->any_negbin || model->any_weibull || model->any_mv);
   if (dpass && !gamma) {
-    // the Weibull / negative-binomial M-step re-reads the occupancies
+    // the Weibull / negative-binomial M-steps re-read the occupancies, and
+    // the multivariate moments are formed from them
     stats->gamma.ensure(std::max<int64_t>(b->total_T, 1) * model->N * 4);
     stats->gamma_T = b->total_T;
     gamma = stats->gamma.as<float>();
@@ -434,6 +496,7 @@ void run_estep(hmm_ctx ctx, hmm_model model, const hmm_batch* b, hmm_plan plan, 
     reduce_chunks_l2<<<model->M, 256, 0, st>>>(ctx->chunk_rec.as<double>(), plan->model_chunk_ptr.as<int32_t>(),
                                                RS, stats->rec.as<double>());
     HMM_CUDA(cudaGetLastError());
+    if (mv_stats) mv_statistics(ctx, model, b, plan, stats, st);
     stats->valid = true;
   }
 }
@@ -463,7 +526,7 @@ void prepare_mstep(hmm_model model, hmm_stats stats, const hmm_batch* b, hmm_pla
 
 void run_mstep(hmm_ctx ctx, hmm_model model, hmm_stats stats, const MStepOpts& o, const hmm_batch* b,
                hmm_plan plan, cudaStream_t st) {
-  if (model->any_mv) throw Error{HMM_E_UNSUPPORTED, "multivariate M-steps are not in this build"};
+  if (model->any_mv) HMM_REQUIRE(stats->mv_rec.p != nullptr, "multivariate statistics were never computed");
   const bool dpass = model->any_negbin || model->any_weibull;
   DPState* dps = nullptr;
   if (dpass) {
@@ -476,6 +539,18 @@ void run_mstep(hmm_ctx ctx, hmm_model model, hmm_stats stats, const MStepOpts& o
     KTimer kt(ctx, HMM_KT_MSTEP, st);
     mstep_kernel<<<model->M, model->NP, 0, st>>>(model->bufs(), stats->rec.as<double>(), o, dps);
     HMM_CUDA(cudaGetLastError());
+    if (model->any_mv) {   // Sec. 4.5: means, (co)variances, then the new factors
+      const int n = model->M * model->NP;
+      mv_mstep_kernel<<<(n + 127) / 128, 128, 0, st>>>(model->family.as<int>(), model->theta.as<double>(),
+                                                       model->mvcoef.as<float>(), stats->mv_rec.as<double>(),
+                                                       model->M, model->NP, model->N, model->P, model->D, model->KM,
+                                                       model->KS, o.collapse_eps, o.tikhonov_eps);
+      HMM_CUDA(cudaGetLastError());
+      mv_derive_kernel<<<(n + 127) / 128, 128, 0, st>>>(model->family.as<int>(), model->theta.as<double>(),
+                                                        model->M, model->NP, model->N, model->P, model->D, model->KM,
+                                                        model->mvcoef.as<float>());
+      HMM_CUDA(cudaGetLastError());
+    }
   }
   if (!dpass || b->n_seq == 0) return;
   // Newton steps that re-read the data: a fixed number of passes
@@ -611,6 +686,8 @@ hmm_status hmm_ctx_destroy(hmm_ctx ctx) {
     }
     for (auto e : ctx->event_pool) cudaEventDestroy(e);
     ctx->plain_beta.release();
+    ctx->tune_out.release();
+    ctx->mvlogb.release();
     delete ctx;
   });
 }
@@ -696,6 +773,9 @@ hmm_status hmm_model_create(hmm_ctx ctx, int32_t n_models, int32_t n_states, int
         m->any_mv |= mv;
         P = std::max(P, param_count(f, dim));
       }
+      for (int i = 0; i < n_models; ++i)
+        HMM_REQUIRE(!m->any_mv || h_family[i] == HMM_DIAG_GAUSS || h_family[i] == HMM_FULL_GAUSS,
+                    "multivariate and scalar families cannot share a model set");
       m->P = P;
       const size_t M = n_models, NP = m->NP;
       m->family.ensure(M * 4);
@@ -710,6 +790,16 @@ hmm_status hmm_model_create(hmm_ctx ctx, int32_t n_models, int32_t n_states, int
       m->logpie.ensure(M * NP * 4);
       m->coef.ensure(M * NP * KC * 4);
       if (m->any_negbin) m->nbtab.ensure(M * NP * NB_YMAX * 4);
+      if (m->any_mv) {
+        HMM_REQUIRE(dim <= 32, "multivariate families support dim <= 32");
+        for (int i = 0; i < n_models; ++i)
+          if (h_family[i] == HMM_DIAG_GAUSS || h_family[i] == HMM_FULL_GAUSS) {
+            m->KM = std::max(m->KM, mv_coef_count(h_family[i], dim));
+            m->KS = std::max(m->KS, mv_stat_count(h_family[i], dim));
+          }
+        m->mvcoef.ensure(M * NP * m->KM * 4);
+        HMM_CUDA(cudaMemset(m->mvcoef.p, 0, M * NP * m->KM * 4));
+      }
       m->lfact2.ensure(LF_YMAX * 4);
       HMM_CUDA(cudaMemcpy(m->family.p, h_family, M * 4, cudaMemcpyHostToDevice));
       HMM_CUDA(cudaMemset(m->pi.p, 0, M * NP * 8));
@@ -721,7 +811,7 @@ hmm_status hmm_model_create(hmm_ctx ctx, int32_t n_models, int32_t n_states, int
       HMM_CUDA(cudaDeviceSynchronize());
     } catch (...) {
       for (auto* b : {&m->family, &m->pi, &m->A, &m->theta, &m->A32, &m->logA2, &m->logAe, &m->pi32,
-                      &m->logpi2, &m->logpie, &m->coef, &m->nbtab, &m->lfact2})
+                      &m->logpi2, &m->logpie, &m->coef, &m->nbtab, &m->lfact2, &m->mvcoef})
         b->release();
       delete m;
       throw;
@@ -734,7 +824,7 @@ hmm_status hmm_model_destroy(hmm_model m) {
   return guarded([&] {
     if (!m) return;
     for (auto* b : {&m->family, &m->pi, &m->A, &m->theta, &m->A32, &m->logA2, &m->logAe, &m->pi32,
-                    &m->logpi2, &m->logpie, &m->coef, &m->nbtab, &m->lfact2})
+                    &m->logpi2, &m->logpie, &m->coef, &m->nbtab, &m->lfact2, &m->mvcoef})
       b->release();
     delete m;
   });
@@ -782,6 +872,11 @@ hmm_status hmm_model_set_params(hmm_model model, const double* h_blob, int64_t n
     const int n = M * NP;
     derive_kernel<<<(n + 127) / 128, 128>>>(model->bufs());
     HMM_CUDA(cudaGetLastError());
+    if (model->any_mv) {
+      mv_derive_kernel<<<(n + 127) / 128, 128>>>(model->family.as<int>(), model->theta.as<double>(), M, NP, N, P, D,
+                                                 model->KM, model->mvcoef.as<float>());
+      HMM_CUDA(cudaGetLastError());
+    }
     HMM_CUDA(cudaDeviceSynchronize());
   });
 }
@@ -907,8 +1002,21 @@ hmm_status hmm_emission_logpdf(hmm_ctx ctx, hmm_model model, const hmm_batch* ba
   return guarded([&] {
     HMM_REQUIRE(ctx && model && d_logb, "NULL argument");
     check_batch(model, batch);
-    if (model->any_mv) throw Error{HMM_E_UNSUPPORTED, "multivariate emissions are not in this build"};
     if (batch->n_seq == 0) return;
+    if (model->any_mv) {
+      PlanRef pr;
+      get_plan(ctx, model, batch, S(stream), pr);
+      if (pr.p->n_tiles > 0) {
+        KTimer kt(ctx, HMM_KT_EMISSION, S(stream));
+        mv_emission_kernel<<<(unsigned)pr.p->n_tiles, 128, (size_t)32 * model->D * 4, S(stream)>>>(
+            model->family.as<int>(), model->mvcoef.as<float>(), model->NP, model->N, model->D, model->KM,
+            batch->values, batch->offsets, batch->model_id, pr.p->tile_seq.as<int32_t>(),
+            pr.p->tile_row.as<int32_t>(), d_logb);
+        HMM_CUDA(cudaGetLastError());
+      }
+      if (pr.owned) HMM_CUDA(cudaStreamSynchronize(S(stream)));
+      return;
+    }
     KTimer kt(ctx, HMM_KT_EMISSION, S(stream));
     emission_kernel<<<(unsigned)batch->n_seq, 128, 0, S(stream)>>>(model->view(), batch->values, batch->offsets,
                                                                    batch->model_id, d_logb);
@@ -944,12 +1052,11 @@ hmm_status hmm_viterbi(hmm_ctx ctx, hmm_model model, const hmm_batch* batch, con
     HMM_REQUIRE(ctx && model && d_path && d_score, "NULL argument");
     check_batch(model, batch);
     if (model->NP > 32) throw Error{HMM_E_UNSUPPORTED, "state counts above 32 are not supported"};
-    if (model->any_mv && !d_logb)
-      throw Error{HMM_E_UNSUPPORTED, "multivariate families need an emission table (d_logb)"};
     PlanRef pr;
     get_plan(ctx, model, batch, S(stream), pr);
     const int64_t Sn = batch->n_seq;
     if (Sn == 0) return;
+    if (model->any_mv && !d_logb) d_logb = mv_table(ctx, model, batch, pr.p, S(stream));
     const int NP = model->NP;
     ctx->psi.ensure(std::max<int64_t>(batch->total_T, 1) * NP + 64);
     VitArgs a;
@@ -999,7 +1106,7 @@ hmm_status hmm_stats_destroy(hmm_stats stats) {
   return guarded([&] {
     if (!stats) return;
     for (auto* bb : {&stats->rec, &stats->gamma, &stats->dps, &stats->dp_part, &stats->dp_chunk, &stats->dp_rec,
-                     &stats->nb_d, &stats->dp_count})
+                     &stats->nb_d, &stats->dp_count, &stats->mv_part, &stats->mv_chunk, &stats->mv_rec})
       bb->release();
     delete stats;
   });
@@ -1043,6 +1150,16 @@ hmm_status hmm_stats_get(hmm_stats stats, double* h_out, int64_t n_values) {
     HMM_CUDA(cudaMemcpy(rec.data(), stats->rec.p, rec.size() * 8, cudaMemcpyDeviceToHost));
     HMM_CUDA(cudaMemcpy(A.data(), md->A.p, A.size() * 8, cudaMemcpyDeviceToHost));
     HMM_CUDA(cudaMemcpy(coef.data(), md->coef.p, coef.size() * 4, cudaMemcpyDeviceToHost));
+    const int D = md->D, KM = md->KM, KS = md->KS;
+    std::vector<double> mrec;
+    std::vector<float> mvc;
+    if (md->any_mv) {
+      HMM_REQUIRE(stats->mv_rec.p != nullptr, "multivariate statistics were never computed");
+      mrec.resize((size_t)M * NP * KS);
+      mvc.resize((size_t)M * NP * KM);
+      HMM_CUDA(cudaMemcpy(mrec.data(), stats->mv_rec.p, mrec.size() * 8, cudaMemcpyDeviceToHost));
+      HMM_CUDA(cudaMemcpy(mvc.data(), md->mvcoef.p, mvc.size() * 4, cudaMemcpyDeviceToHost));
+    }
     double* q = h_out;
     for (int m = 0; m < M; ++m) {
       const double* R = rec.data() + (size_t)m * RS;
@@ -1102,6 +1219,26 @@ hmm_status hmm_stats_get(hmm_stats stats, double* h_out, int64_t n_values) {
             q[1] = St[1];
             q[2] = St[2];
             break;
+          case HMM_DIAG_GAUSS:
+          case HMM_FULL_GAUSS: {
+            // raw moments W, sum g y_d, then sum g y_d^2 or sum g y_d y_e from
+            // the moments shifted by the current mean c
+            const double* Rm = mrec.data() + ((size_t)m * NP + j) * KS;
+            const float* c = mvc.data() + ((size_t)m * NP + j) * KM;
+            const double Wm = Rm[0];
+            q[0] = Wm;
+            for (int d = 0; d < D; ++d) q[1 + d] = Rm[1 + d] + c[d] * Wm;
+            if (fam == HMM_DIAG_GAUSS) {
+              for (int d = 0; d < D; ++d)
+                q[1 + D + d] = Rm[1 + D + d] + 2.0 * c[d] * Rm[1 + d] + (double)c[d] * c[d] * Wm;
+            } else {
+              for (int d = 0; d < D; ++d)
+                for (int e = 0; e < D; ++e)
+                  q[1 + D + d * D + e] = Rm[1 + D + d * D + e] + c[d] * Rm[1 + e] + c[e] * Rm[1 + d] +
+                                         (double)c[d] * c[e] * Wm;
+            }
+            break;
+          }
           default:
             for (int z = 0; z < canon_fam_count(fam, md->D); ++z) q[z] = 0.0;
             q[0] = W;

@@ -1,0 +1,214 @@
+// Multivariate emission families of paper Sec. 4.5: diagonal Gaussian
+// (Eq. 20-21) and full-covariance Gaussian (Eq. 22-24).
+//
+// Emissions are evaluated into a float32 log b table that the fused E-step
+// and Viterbi kernels read (table mode).  Derived per-state tables (float32):
+//   diagonal: mu[D], h[D] = 1 / (2 var), c = -1/2 sum_d log(2 pi var_d)
+//   full:     mu[D], Linv[D][D] (inverse of the Cholesky factor of Sigma,
+//             lower triangular), c = -D/2 log 2 pi - sum_d log L_dd
+// so log b = c - sum_d h_d (y_d - mu_d)^2  or  c - 1/2 |Linv (y - mu)|^2.
+// The statistics are shifted moments around the current mean (float32
+// per sequence, two-level), reduced in fixed order in float64; the M-step
+// recovers mu = shift + S1 / W and the (co)variance, adds eps I (Sec. 4.5)
+// and refactors.
+#pragma once
+
+#include "common.cuh"
+#include "mstep_types.h"
+
+namespace hmm {
+
+__host__ __device__ inline int mv_coef_count(int fam, int D) {
+  return fam == HMM_DIAG_GAUSS ? 2 * D + 1 : D + D * D + 1;
+}
+// statistic slots per state: W, S1[D], then S2[D] (diagonal) or S2[D][D] (full)
+__host__ __device__ inline int mv_stat_count(int fam, int D) {
+  return fam == HMM_DIAG_GAUSS ? 1 + 2 * D : 1 + D + D * D;
+}
+
+// Derived tables of one (model, state) from theta (float64, device).
+__device__ inline void mv_derive_state(int fam, int D, const double* th, float* c) {
+  constexpr double L2PI = 1.83787706640934548356;   // log(2 pi)
+  if (fam == HMM_DIAG_GAUSS) {
+    double cc = 0.0;
+    for (int d = 0; d < D; ++d) {
+      const double mu = th[d], var = th[D + d];
+      c[d] = (float)mu;
+      c[D + d] = (float)(0.5 / var);
+      cc += -0.5 * (L2PI + log(var));
+    }
+    c[2 * D] = (float)cc;
+    return;
+  }
+  // full covariance: Cholesky Sigma = L L^T (float64), then Linv
+  double L[32 * 32], Li[32 * 32];
+  const double* S = th + D;
+  bool ok = D <= 32;
+  for (int i = 0; i < D && ok; ++i)
+    for (int j = 0; j <= i; ++j) {
+      double acc = S[i * D + j];
+      for (int k = 0; k < j; ++k) acc -= L[i * D + k] * L[j * D + k];
+      if (i == j) {
+        if (!(acc > 0.0)) {
+          ok = false;
+          break;
+        }
+        L[i * D + i] = sqrt(acc);
+      } else {
+        L[i * D + j] = acc / L[j * D + j];
+      }
+    }
+  for (int d = 0; d < D; ++d) c[d] = (float)th[d];
+  if (!ok) {   // not positive definite: density 0 everywhere
+    for (int z = 0; z < D * D; ++z) c[D + z] = 0.f;
+    c[D + D * D] = -INFINITY;
+    return;
+  }
+  double logdet = 0.0;
+  for (int i = 0; i < D; ++i) logdet += log(L[i * D + i]);
+  for (int i = 0; i < D; ++i) {
+    for (int j = 0; j < D; ++j) Li[i * D + j] = 0.0;
+    Li[i * D + i] = 1.0 / L[i * D + i];
+    for (int j = 0; j < i; ++j) {
+      double acc = 0.0;
+      for (int k = j; k < i; ++k) acc += L[i * D + k] * Li[k * D + j];
+      Li[i * D + j] = -acc / L[i * D + i];
+    }
+  }
+  for (int z = 0; z < D * D; ++z) c[D + z] = (float)Li[z];
+  c[D + D * D] = (float)(-0.5 * D * L2PI - logdet);
+}
+
+__global__ void mv_derive_kernel(const int* __restrict__ family, const double* __restrict__ theta, int M, int NP,
+                                 int N, int P, int D, int KM, float* __restrict__ mvc) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= M * NP) return;
+  const int m = idx / NP, k = idx % NP;
+  const int fam = family[m];
+  float* c = mvc + (size_t)idx * KM;
+  if (k >= N) {                      // padding state: log b = -inf
+    for (int z = 0; z < KM; ++z) c[z] = 0.f;
+    c[mv_coef_count(fam, D) - 1] = -INFINITY;
+    return;
+  }
+  mv_derive_state(fam, D, theta + (size_t)idx * P, c);
+}
+
+// log b_j(y_t) (natural log) for every row of the batch: one block per
+// (sequence, tile of 32 rows); threads stride over (row, state).
+__global__ void mv_emission_kernel(const int* __restrict__ family, const float* __restrict__ mvc, int NP, int N,
+                                   int D, int KM, const float* __restrict__ y, const int64_t* __restrict__ offsets,
+                                   const int32_t* __restrict__ model_id, const int32_t* __restrict__ tile_seq,
+                                   const int32_t* __restrict__ tile_row, float* __restrict__ logb) {
+  extern __shared__ float ys[];       // [32][D]
+  const int s = tile_seq[blockIdx.x];
+  const int64_t r0 = offsets[s] + tile_row[blockIdx.x];
+  const int64_t r1 = min(r0 + 32, offsets[s + 1]);
+  const int nr = (int)(r1 - r0);
+  const int m = model_id[s];
+  const int fam = family[m];
+  for (int z = threadIdx.x; z < nr * D; z += blockDim.x) ys[z] = y[r0 * D + z];
+  __syncthreads();
+  for (int z = threadIdx.x; z < nr * N; z += blockDim.x) {
+    const int r = z / N, k = z % N;
+    const float* c = mvc + ((size_t)m * NP + k) * KM;
+    const float* yr = ys + r * D;
+    float q = 0.f;
+    if (fam == HMM_DIAG_GAUSS) {
+      for (int d = 0; d < D; ++d) {
+        const float e = yr[d] - c[d];
+        q = fmaf(c[D + d] * e, e, q);
+      }
+      logb[(r0 + r) * N + k] = c[2 * D] - q;
+    } else {
+      const float* Li = c + D;
+      for (int i = 0; i < D; ++i) {
+        float zi = 0.f;
+        for (int j = 0; j <= i; ++j) zi = fmaf(Li[i * D + j], yr[j] - c[j], zi);
+        q = fmaf(zi, zi, q);
+      }
+      logb[(r0 + r) * N + k] = c[D + D * D] - 0.5f * q;
+    }
+  }
+}
+
+// Shifted weighted moments per sequence and state from the occupancies:
+// part[s][k][*] = W, sum g (y - mu), then sum g (y-mu)_d^2 (diagonal) or
+// sum g (y-mu)(y-mu)^T (full).  One block per sequence, one thread per
+// (state, slot); two-level float32 sums over t.
+__global__ void mv_stats_kernel(const int* __restrict__ family, const float* __restrict__ mvc, int NP, int N, int D,
+                                int KM, int KS, const float* __restrict__ y, const float* __restrict__ gamma,
+                                const int64_t* __restrict__ offsets, const int32_t* __restrict__ model_id,
+                                float* __restrict__ part) {
+  const int s = blockIdx.x;
+  const int64_t b = offsets[s], e = offsets[s + 1];
+  const int m = model_id[s];
+  const int fam = family[m];
+  const int total = NP * KS;
+  for (int f = threadIdx.x; f < total; f += blockDim.x) {
+    const int k = f / KS, z = f % KS;
+    float a = 0.f;
+    if (k < N && z < mv_stat_count(fam, D)) {   // a set mixing both families pads the diagonal records
+      const float* c = mvc + ((size_t)m * NP + k) * KM;
+      int d1 = -1, d2 = -1;
+      if (z >= 1 && z <= D) d1 = z - 1;
+      else if (z > D) {
+        if (fam == HMM_DIAG_GAUSS) d1 = d2 = z - 1 - D;
+        else {
+          d1 = (z - 1 - D) / D;
+          d2 = (z - 1 - D) % D;
+        }
+      }
+      const float mu1 = d1 >= 0 ? c[d1] : 0.f, mu2 = d2 >= 0 ? c[d2] : 0.f;
+      float in = 0.f;
+      int cnt = 0;
+      for (int64_t t = b; t < e; ++t) {
+        const float g = gamma[t * N + k];
+        float v = g;
+        if (d1 >= 0) v *= y[t * D + d1] - mu1;
+        if (d2 >= 0) v *= y[t * D + d2] - mu2;
+        in += v;
+        if (++cnt == 64) {
+          a += in;
+          in = 0.f;
+          cnt = 0;
+        }
+      }
+      a += in;
+    }
+    part[(size_t)s * total + f] = a;
+  }
+}
+
+// M-step of the multivariate families (one thread per (model, state)).
+__global__ void mv_mstep_kernel(const int* __restrict__ family, double* __restrict__ theta, const float* __restrict__ mvc,
+                                const double* __restrict__ rec, int M, int NP, int N, int P, int D, int KM, int KS,
+                                double collapse_eps, double tikhonov_eps) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= M * NP) return;
+  const int m = idx / NP, k = idx % NP;
+  if (k >= N) return;
+  const int fam = family[m];
+  if (fam != HMM_DIAG_GAUSS && fam != HMM_FULL_GAUSS) return;
+  const double* R = rec + (size_t)idx * KS;
+  const float* c = mvc + (size_t)idx * KM;
+  double* th = theta + (size_t)idx * P;
+  const double W = R[0];
+  if (W < collapse_eps) return;                        // Sec. 4.4
+  for (int d = 0; d < D; ++d) th[d] = (double)c[d] + R[1 + d] / W;
+  if (fam == HMM_DIAG_GAUSS) {                         // Eq. 21
+    for (int d = 0; d < D; ++d) {
+      const double m1 = R[1 + d] / W;
+      th[D + d] = fmax(R[1 + D + d] / W - m1 * m1, 1e-300);
+    }
+  } else {                                             // Eq. 23-24
+    for (int i = 0; i < D; ++i)
+      for (int j = 0; j < D; ++j) {
+        const double mi = R[1 + i] / W, mj = R[1 + j] / W;
+        const double cij = 0.5 * (R[1 + D + i * D + j] + R[1 + D + j * D + i]) / W - mi * mj;
+        th[D + i * D + j] = cij + (i == j ? tikhonov_eps : 0.0);
+      }
+  }
+}
+
+}  // namespace hmm

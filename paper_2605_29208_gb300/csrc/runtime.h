@@ -79,6 +79,7 @@ struct hmm_ctx_s {
   hmm::DevBuf trace;             // float64 logL trace of hmm_fit
   hmm::DevBuf plain_beta;        // beta-hat rows of the plain path
   hmm::DevBuf tune_out;          // outputs of the autotuner's trial runs
+  hmm::DevBuf mvlogb;            // [total_T][N] log b table of multivariate models
   // options
   int profile = 0;
   int estep_lanes = 0;
@@ -101,6 +102,8 @@ struct hmm_model_s {
   std::vector<int32_t> h_family;
   bool any_negbin = false, any_weibull = false, any_mv = false;
   hmm::DevBuf family, pi, A, theta, A32, logA2, logAe, pi32, logpi2, logpie, coef, nbtab, lfact2;
+  int KM = 0, KS = 0;            // multivariate coefficient / statistic slots per state
+  hmm::DevBuf mvcoef;            // [M][NP][KM] float32 (multivariate families)
   hmm::ModelBufs bufs() const;
   hmm::ModelView view() const;
 };
@@ -119,6 +122,9 @@ struct hmm_stats_s {
   hmm::DevBuf dp_rec;            // [M][NP*3] float64
   hmm::DevBuf nb_d;              // [M][NP][2][NB_YMAX] float32 digamma tables
   hmm::DevBuf dp_count;          // active-state counters of the passes
+  hmm::DevBuf mv_part;           // [S][NP][KS] float32 multivariate moments
+  hmm::DevBuf mv_chunk;          // [n_chunks][NP*KS] float64
+  hmm::DevBuf mv_rec;            // [M][NP*KS] float64
 };
 
 struct hmm_plan_s {
@@ -133,6 +139,8 @@ struct hmm_plan_s {
   int n_chunks = 0;
   int uniform_family = -1;       // the one family of all sequences, or -1
   int estep_G = 0;               // chain widths chosen by hmm_plan_autotune (0: default)
+  hmm::DevBuf tile_seq, tile_row;// 32-row tiles of the batch (multivariate emissions)
+  int n_tiles = 0;
   int viterbi_G = 0;
   std::vector<int32_t> h_order;
 };
