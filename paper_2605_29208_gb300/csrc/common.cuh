@@ -43,6 +43,7 @@ struct ModelView {
   int D;              // observation dimension
   const int* family;  // [M]
   const float* A32;   // [M][NP][NP] linear a_ij (padded entries 0)
+  const float* AT32;  // [M][NP][NP] transposed (padded N > 32 only)
   const float* logA2; // [M][NP][NP] log2 a_ij (-inf for 0)
   const float* logAe; // [M][NP][NP] ln a_ij as float32 (table-mode Viterbi)
   const float* pi32;  // [M][NP]

@@ -179,6 +179,7 @@ ModelBufs hmm_model_s::bufs() const {
   b.A = A.as<double>();
   b.theta = theta.as<double>();
   b.A32 = A32.as<float>();
+  b.AT32 = NP > 32 ? AT32.as<float>() : nullptr;
   b.logA2 = logA2.as<float>();
   b.logAe = logAe.as<float>();
   b.pi32 = pi32.as<float>();
@@ -198,6 +199,7 @@ ModelView hmm_model_s::view() const {
   v.D = D;
   v.family = family.as<int>();
   v.A32 = A32.as<float>();
+  v.AT32 = NP > 32 ? AT32.as<float>() : nullptr;
   v.logA2 = logA2.as<float>();
   v.logAe = logAe.as<float>();
   v.pi32 = pi32.as<float>();
@@ -306,6 +308,31 @@ hmm_plan make_plan(hmm_ctx ctx, hmm_model model, const hmm_batch* b, const int64
         HMM_CUDA(cudaMemcpy(p->tile_row.p, tr.data(), tr.size() * 4, cudaMemcpyHostToDevice));
       }
     }
+    if (model->NP > 32 && S > 0) {
+      // groups of LG_SB sequences of one model with similar lengths, the
+      // groups holding the longest sequences first
+      std::vector<int32_t> idx(S);
+      std::iota(idx.begin(), idx.end(), 0);
+      std::stable_sort(idx.begin(), idx.end(), [&](int32_t x, int32_t y) {
+        if (hm[x] != hm[y]) return hm[x] < hm[y];
+        return (ho[x + 1] - ho[x]) > (ho[y + 1] - ho[y]);
+      });
+      std::vector<std::vector<int32_t>> groups;
+      for (int64_t q2 = 0; q2 < S;) {
+        std::vector<int32_t> g(LG_SB, -1);
+        const int mq = hm[idx[q2]];
+        for (int c = 0; c < LG_SB && q2 < S && hm[idx[q2]] == mq; ++c) g[c] = idx[q2++];
+        groups.push_back(std::move(g));
+      }
+      std::stable_sort(groups.begin(), groups.end(), [&](const std::vector<int32_t>& x, const std::vector<int32_t>& y) {
+        return (ho[x[0] + 1] - ho[x[0]]) > (ho[y[0] + 1] - ho[y[0]]);
+      });
+      std::vector<int32_t> flat;
+      for (auto& g : groups) flat.insert(flat.end(), g.begin(), g.end());
+      p->n_groups = (int)groups.size();
+      p->lg_groups.ensure(flat.size() * 4);
+      HMM_CUDA(cudaMemcpy(p->lg_groups.p, flat.data(), flat.size() * 4, cudaMemcpyHostToDevice));
+    }
     int uf = -2;
     for (int64_t q2 = 0; q2 < S; ++q2) {
       const int f = model->h_family[hm[q2]];
@@ -334,6 +361,7 @@ void destroy_plan(hmm_plan p) {
   p->model_chunk_ptr.release();
   p->tile_seq.release();
   p->tile_row.release();
+  p->lg_groups.release();
   delete p;
 }
 
@@ -364,16 +392,19 @@ void get_plan(hmm_ctx ctx, hmm_model model, const hmm_batch* b, cudaStream_t st,
   ref.owned = true;
 }
 
-void require_small(hmm_model model) {
-  if (model->NP > 32)
-    throw Error{HMM_E_UNSUPPORTED, "state counts above 32 are not supported by this build"};
-}
-
-// log b table of a multivariate model set over the batch (Sec. 4.5), in the
-// context's buffer: one block per 32-row tile of a sequence.
+// log b table of the batch in the context's buffer: multivariate families
+// (Sec. 4.5) one block per 32-row tile of a sequence, scalar families one
+// block per sequence.
 const float* mv_table(hmm_ctx ctx, hmm_model model, const hmm_batch* b, hmm_plan plan, cudaStream_t st) {
   ctx->mvlogb.ensure(std::max<int64_t>(b->total_T, 1) * model->N * 4);
-  if (plan->n_tiles > 0) {
+  if (!model->any_mv) {
+    if (b->n_seq > 0) {
+      KTimer kt(ctx, HMM_KT_EMISSION, st);
+      emission_kernel<<<(unsigned)b->n_seq, 128, 0, st>>>(model->view(), b->values, b->offsets, b->model_id,
+                                                         ctx->mvlogb.as<float>());
+      HMM_CUDA(cudaGetLastError());
+    }
+  } else if (plan->n_tiles > 0) {
     KTimer kt(ctx, HMM_KT_EMISSION, st);
     const size_t smem = (size_t)32 * model->D * 4;
     mv_emission_kernel<<<(unsigned)plan->n_tiles, 128, smem, st>>>(
@@ -412,11 +443,82 @@ void mv_statistics(hmm_ctx ctx, hmm_model model, const hmm_batch* b, hmm_plan pl
   HMM_CUDA(cudaGetLastError());
 }
 
+// Large-N E-step (padded N > 32): emission table, forward and backward
+// recursions, posterior rows, then (for statistics) the per-sequence sums,
+// the xi blocks and the fixed-order reductions.
+void run_estep_large(hmm_ctx ctx, hmm_model model, const hmm_batch* b, hmm_plan plan, const float* logb,
+                     float* gamma, double* ll, bool want_stats, hmm_stats stats, cudaStream_t st) {
+  const int NP = model->NP, N = model->N;
+  const int64_t S = b->n_seq, TT = std::max<int64_t>(b->total_T, 1);
+  if (ctx->plain_estep) throw Error{HMM_E_UNSUPPORTED, "the plain path covers padded N <= 32"};
+  if (!logb) logb = mv_table(ctx, model, b, plan, st);
+  ctx->scratch.ensure(TT * NP * 4 + 64);
+  ctx->lg_bv.ensure(TT * NP * 4);
+  ctx->lg_off.ensure(TT * 2 * 8);
+  ctx->lg_rz.ensure(TT * 4);
+  if (!gamma) {
+    if (want_stats && stats) {
+      stats->gamma.ensure(TT * N * 4);
+      stats->gamma_T = b->total_T;
+      gamma = stats->gamma.as<float>();
+    } else {
+      ctx->gamma.ensure(TT * N * 4);
+      gamma = ctx->gamma.as<float>();
+    }
+  } else if (want_stats && stats && (model->any_mv || model->any_negbin || model->any_weibull)) {
+    throw Error{HMM_E_ARG, "statistics of these families keep their own occupancies"};
+  }
+  if (want_stats) {
+    ctx->partials.ensure((size_t)std::max<int64_t>(S, 1) * NP * NST * 4);
+    ctx->lg_xi.ensure((size_t)std::max(plan->n_chunks, 1) * NP * NP * 8);
+    ctx->chunk_rec.ensure((size_t)std::max(plan->n_chunks, 1) * rec_size(NP) * 8);
+  }
+  if (S == 0) return;
+  LargeArgs a{};
+  a.logb = logb;
+  a.offsets = b->offsets;
+  a.model_id = b->model_id;
+  a.groups = plan->lg_groups.as<int32_t>();
+  a.n_groups = plan->n_groups;
+  a.mv = model->view();
+  a.fv = ctx->scratch.as<float>();
+  a.bv = ctx->lg_bv.as<float>();
+  a.oa = ctx->lg_off.as<double>();
+  a.ob = ctx->lg_off.as<double>() + TT;
+  {
+    KTimer kt(ctx, HMM_KT_ESTEP, st);
+    HMM_CUDA(launch_large_fb(NP, a, st));
+  }
+  KTimer kt(ctx, HMM_KT_REDUCE, st);
+  HMM_CUDA(launch_large_post(a, NP, N, S, gamma, ctx->lg_rz.as<float>(), ll, ctx->status, st));
+  if (!want_stats) return;
+  const bool table_stats = model->any_mv;
+  HMM_CUDA(launch_large_stats(a, b->values, gamma, S, table_stats, ctx->partials.as<float>(), st));
+  HMM_CUDA(launch_large_xi(a, ctx->lg_rz.as<float>(), plan->seq_by_model.as<int32_t>(), plan->chunk_lo.as<int32_t>(),
+                           plan->chunk_hi.as<int32_t>(), plan->n_chunks, ctx->lg_xi.as<double>(), st));
+  HMM_CUDA(launch_large_reduce(ctx->partials.as<float>(), ll, ctx->lg_xi.as<double>(),
+                               plan->seq_by_model.as<int32_t>(), plan->chunk_lo.as<int32_t>(),
+                               plan->chunk_hi.as<int32_t>(), plan->n_chunks, NP, ctx->chunk_rec.as<double>(), st));
+  reduce_chunks_l2<<<model->M, 256, 0, st>>>(ctx->chunk_rec.as<double>(), plan->model_chunk_ptr.as<int32_t>(),
+                                             rec_size(NP), stats->rec.as<double>());
+  HMM_CUDA(cudaGetLastError());
+  if (model->any_mv) mv_statistics(ctx, model, b, plan, stats, st);
+  stats->valid = true;
+}
+
 // The fused E-step over a batch.  gamma (optional) receives [total_T][N].
 void run_estep(hmm_ctx ctx, hmm_model model, const hmm_batch* b, hmm_plan plan, const float* logb,
                float* gamma, double* loglik, bool want_stats, hmm_stats stats, cudaStream_t st) {
   const int NP = model->NP;
-  if (model->NP > 32) throw Error{HMM_E_UNSUPPORTED, "state counts above 32 are not supported"};
+  if (model->NP > 32) {
+    double* ll = loglik;
+    if (!ll) {
+      ctx->loglik.ensure(std::max<int64_t>(b->n_seq, 1) * 8);
+      ll = ctx->loglik.as<double>();
+    }
+    run_estep_large(ctx, model, b, plan, logb, gamma, ll, want_stats, stats, st);
+    return;
+  }
   if (model->any_mv && ctx->plain_estep)
     throw Error{HMM_E_UNSUPPORTED, "the plain path covers the scalar families only"};
   const int64_t S = b->n_seq;
@@ -528,6 +630,8 @@ void run_mstep(hmm_ctx ctx, hmm_model model, hmm_stats stats, const MStepOpts& o
                hmm_plan plan, cudaStream_t st) {
   if (model->any_mv) HMM_REQUIRE(stats->mv_rec.p != nullptr, "multivariate statistics were never computed");
   const bool dpass = model->any_negbin || model->any_weibull;
+  if (dpass && model->NP > 32)
+    throw Error{HMM_E_UNSUPPORTED, "Weibull / negative-binomial M-steps support padded N <= 32"};
   DPState* dps = nullptr;
   if (dpass) {
     HMM_REQUIRE(b != nullptr && plan != nullptr, "Weibull / negative-binomial M-steps need the batch");
@@ -688,6 +792,10 @@ hmm_status hmm_ctx_destroy(hmm_ctx ctx) {
     ctx->plain_beta.release();
     ctx->tune_out.release();
     ctx->mvlogb.release();
+    ctx->lg_bv.release();
+    ctx->lg_off.release();
+    ctx->lg_rz.release();
+    ctx->lg_xi.release();
     delete ctx;
   });
 }
@@ -783,6 +891,7 @@ hmm_status hmm_model_create(hmm_ctx ctx, int32_t n_models, int32_t n_states, int
       m->A.ensure(M * NP * NP * 8);
       m->theta.ensure(M * NP * P * 8);
       m->A32.ensure(M * NP * NP * 4);
+      if (NP > 32) m->AT32.ensure(M * NP * NP * 4);
       m->logA2.ensure(M * NP * NP * 4);
       m->logAe.ensure(M * NP * NP * 4);
       m->pi32.ensure(M * NP * 4);
@@ -810,7 +919,7 @@ hmm_status hmm_model_create(hmm_ctx ctx, int32_t n_models, int32_t n_states, int
       HMM_CUDA(cudaGetLastError());
       HMM_CUDA(cudaDeviceSynchronize());
     } catch (...) {
-      for (auto* b : {&m->family, &m->pi, &m->A, &m->theta, &m->A32, &m->logA2, &m->logAe, &m->pi32,
+      for (auto* b : {&m->family, &m->pi, &m->A, &m->theta, &m->A32, &m->AT32, &m->logA2, &m->logAe, &m->pi32,
                       &m->logpi2, &m->logpie, &m->coef, &m->nbtab, &m->lfact2, &m->mvcoef})
         b->release();
       delete m;
@@ -823,7 +932,7 @@ hmm_status hmm_model_create(hmm_ctx ctx, int32_t n_models, int32_t n_states, int
 hmm_status hmm_model_destroy(hmm_model m) {
   return guarded([&] {
     if (!m) return;
-    for (auto* b : {&m->family, &m->pi, &m->A, &m->theta, &m->A32, &m->logA2, &m->logAe, &m->pi32,
+    for (auto* b : {&m->family, &m->pi, &m->A, &m->theta, &m->A32, &m->AT32, &m->logA2, &m->logAe, &m->pi32,
                     &m->logpi2, &m->logpie, &m->coef, &m->nbtab, &m->lfact2, &m->mvcoef})
       b->release();
     delete m;
@@ -1051,11 +1160,30 @@ hmm_status hmm_viterbi(hmm_ctx ctx, hmm_model model, const hmm_batch* batch, con
   return guarded([&] {
     HMM_REQUIRE(ctx && model && d_path && d_score, "NULL argument");
     check_batch(model, batch);
-    if (model->NP > 32) throw Error{HMM_E_UNSUPPORTED, "state counts above 32 are not supported"};
     PlanRef pr;
     get_plan(ctx, model, batch, S(stream), pr);
     const int64_t Sn = batch->n_seq;
     if (Sn == 0) return;
+    if (model->NP > 32) {
+      if (!d_logb) d_logb = mv_table(ctx, model, batch, pr.p, S(stream));
+      ctx->psi.ensure(std::max<int64_t>(batch->total_T, 1) * model->NP * 2 + 64);
+      LargeArgs a{};
+      a.logb = d_logb;
+      a.offsets = batch->offsets;
+      a.model_id = batch->model_id;
+      a.groups = pr.p->lg_groups.as<int32_t>();
+      a.n_groups = pr.p->n_groups;
+      a.mv = model->view();
+      a.psi = ctx->psi.as<uint16_t>();
+      a.path = d_path;
+      a.score = d_score;
+      {
+        KTimer kt(ctx, HMM_KT_VITERBI, S(stream));
+        HMM_CUDA(launch_large_viterbi(model->NP, a, S(stream)));
+      }
+      if (pr.owned) HMM_CUDA(cudaStreamSynchronize(S(stream)));
+      return;
+    }
     if (model->any_mv && !d_logb) d_logb = mv_table(ctx, model, batch, pr.p, S(stream));
     const int NP = model->NP;
     ctx->psi.ensure(std::max<int64_t>(batch->total_T, 1) * NP + 64);
@@ -1264,7 +1392,6 @@ hmm_status hmm_estep_stats(hmm_ctx ctx, hmm_model model, const hmm_batch* batch,
     HMM_REQUIRE(ctx && model && stats, "NULL argument");
     HMM_REQUIRE(stats->model == model, "stats belong to another model");
     check_batch(model, batch);
-    require_small(model);
     PlanRef pr;
     get_plan(ctx, model, batch, S(stream), pr);
     run_estep(ctx, model, batch, pr.p, nullptr, nullptr, d_loglik, true, stats, S(stream));
@@ -1294,7 +1421,6 @@ hmm_status hmm_fit(hmm_ctx ctx, hmm_model model, const hmm_batch* batch, const h
     HMM_REQUIRE(ctx && model && opts, "NULL argument");
     HMM_REQUIRE(opts->max_iter >= 0, "max_iter must be >= 0");
     check_batch(model, batch);
-    require_small(model);
     // The iterations run on the context's own non-blocking stream (a graph
     // cannot be captured on the legacy default stream); the caller's stream
     // is drained first and the call returns after the loop has finished.

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include "estep_small.cuh"
+#include "large.cuh"
 #include "viterbi_small.cuh"
 
 namespace hmm {
@@ -33,5 +34,21 @@ cudaError_t launch_estep_np16(int G, int mode, const EStepArgs& a, int fam, int 
 cudaError_t launch_estep_np32(int G, int mode, const EStepArgs& a, int fam, int n_sm, cudaStream_t st);
 cudaError_t launch_viterbi_small(int NP, int G, const VitArgs& a, int fam, int n_sm,
                                  cudaStream_t st);
+// large-N kernels (padded N in {64, 128, 256, 512, 1024})
+cudaError_t launch_large_fb(int NP, const LargeArgs& a, cudaStream_t st);
+cudaError_t launch_large_viterbi(int NP, const LargeArgs& a, cudaStream_t st);
+// posterior rows: gamma [total_T][N], 1/Z_t [total_T], log-likelihoods
+cudaError_t launch_large_post(const LargeArgs& a, int NP, int N, int64_t n_seq, float* gamma, float* rz,
+                              double* loglik, int* status, cudaStream_t st);
+// per-sequence statistic partials [n_seq][NP][NST] (slot NST-1: gamma_1)
+cudaError_t launch_large_stats(const LargeArgs& a, const float* y, const float* gamma, int64_t n_seq, bool table,
+                               float* part, cudaStream_t st);
+// xi blocks per chunk [n_chunks][NP][NP] (float64, without the a_ij factor)
+cudaError_t launch_large_xi(const LargeArgs& a, const float* rz, const int32_t* seq_by_model, const int32_t* chunk_lo,
+                            const int32_t* chunk_hi, int n_chunks, double* xi_chunk, cudaStream_t st);
+// chunk records in the rec_size(NP) layout
+cudaError_t launch_large_reduce(const float* part, const double* loglik, const double* xi_chunk,
+                                const int32_t* seq_by_model, const int32_t* chunk_lo, const int32_t* chunk_hi,
+                                int n_chunks, int NP, double* chunk_rec, cudaStream_t st);
 
 }  // namespace hmm

@@ -166,6 +166,7 @@ __device__ inline void derive_row(const ModelBufs& mb, int m, int k) {
   for (int j = 0; j < NP; ++j) {
     const double a = (k < N && j < N) ? mb.A[row + j] : 0.0;
     mb.A32[row + j] = (float)a;
+    if (mb.AT32) mb.AT32[((size_t)m * NP + j) * NP + k] = (float)a;
     mb.logA2[row + j] = a > 0.0 ? (float)log2(a) : -INFINITY;
     mb.logAe[row + j] = a > 0.0 ? (float)log(a) : -INFINITY;
   }

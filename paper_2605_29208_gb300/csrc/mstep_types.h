@@ -16,6 +16,7 @@ struct ModelBufs {
   double* A;                // [M][NP][NP]
   double* theta;            // [M][NP][P]
   float* A32;
+  float* AT32;              // [M][NP][NP] transposed a_ij (padded N > 32 only, else nullptr)
   float* logA2;
   float* logAe;
   float* pi32;

@@ -79,7 +79,11 @@ struct hmm_ctx_s {
   hmm::DevBuf trace;             // float64 logL trace of hmm_fit
   hmm::DevBuf plain_beta;        // beta-hat rows of the plain path
   hmm::DevBuf tune_out;          // outputs of the autotuner's trial runs
-  hmm::DevBuf mvlogb;            // [total_T][N] log b table of multivariate models
+  hmm::DevBuf mvlogb;            // [total_T][N] log b table (multivariate and large-N models)
+  hmm::DevBuf lg_bv;             // [total_T][NP] large-N backward rows
+  hmm::DevBuf lg_off;            // [2][total_T] float64 log2 offsets (forward, backward)
+  hmm::DevBuf lg_rz;             // [total_T] 1 / Z_t
+  hmm::DevBuf lg_xi;             // [n_chunks][NP][NP] float64 xi blocks
   // options
   int profile = 0;
   int estep_lanes = 0;
@@ -101,7 +105,7 @@ struct hmm_model_s {
   int M = 0, N = 0, NP = 0, D = 1, P = 0;
   std::vector<int32_t> h_family;
   bool any_negbin = false, any_weibull = false, any_mv = false;
-  hmm::DevBuf family, pi, A, theta, A32, logA2, logAe, pi32, logpi2, logpie, coef, nbtab, lfact2;
+  hmm::DevBuf family, pi, A, theta, A32, AT32, logA2, logAe, pi32, logpi2, logpie, coef, nbtab, lfact2;
   int KM = 0, KS = 0;            // multivariate coefficient / statistic slots per state
   hmm::DevBuf mvcoef;            // [M][NP][KM] float32 (multivariate families)
   hmm::ModelBufs bufs() const;
@@ -141,6 +145,8 @@ struct hmm_plan_s {
   int estep_G = 0;               // chain widths chosen by hmm_plan_autotune (0: default)
   hmm::DevBuf tile_seq, tile_row;// 32-row tiles of the batch (multivariate emissions)
   int n_tiles = 0;
+  hmm::DevBuf lg_groups;         // [n_groups][LG_SB] large-N sequence groups (one model each)
+  int n_groups = 0;
   int viterbi_G = 0;
   std::vector<int32_t> h_order;
 };

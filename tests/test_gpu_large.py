@@ -1,0 +1,234 @@
+"""Parity of the large-N path (padded N = 64 ... 1024: float32 CUDA cores,
+groups of sequences in lock step, xi as a blocked outer-product sum) with
+the FP64 oracle.  Same bar as the small-N path: per-sequence logL 1e-5
+relative, occupancies 1e-4 absolute, M-step parameters 1e-4 relative,
+Viterbi bit-identical to the float32-mode oracle on a shared table."""
+import numpy as np
+import pytest
+
+from oracle import hmm_oracle as O
+from paper_2605_29208_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+LL_RTOL = 1e-5
+GAMMA_ATOL = 1e-4
+PARAM_RTOL = 1e-4
+
+LENGTHS = [1, 2, 0, 37, 130, 9, 64, 65, 11, 3]
+
+
+@pytest.fixture(scope="module")
+def H():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import paper_2605_29208_gb300 as H
+    from paper_2605_29208_gb300 import build
+    build.build()
+    return H
+
+
+@pytest.fixture(scope="module")
+def ctx(H):
+    return H.Context(0)
+
+
+def om(d):
+    return O.Model(d["family"], d["pi"].copy(), d["A"].copy(),
+                   {k: np.array(v, copy=True) for k, v in d["params"].items()})
+
+
+def check_fb(ll, gamma, models, values, offsets, mid, xi_ref=None):
+    for s in range(len(offsets) - 1):
+        y = values[offsets[s]:offsets[s + 1]]
+        if len(y) == 0:
+            assert ll[s] == 0.0
+            continue
+        fb = O.forward_backward(om(models[mid[s]]), np.asarray(y, np.float64))
+        assert abs(ll[s] - fb["logL"]) <= LL_RTOL * max(1.0, abs(fb["logL"])), (s, ll[s], fb["logL"])
+        np.testing.assert_allclose(gamma[offsets[s]:offsets[s + 1]], fb["gamma"], atol=GAMMA_ATOL, rtol=0)
+
+
+@pytest.mark.parametrize("family,N,conc", [("gauss", 33, 1.0), ("gauss", 64, 1.0), ("poisson", 100, 1.0),
+                                           ("gamma", 200, 1.0), ("gauss", 128, 0.1), ("vonmises", 300, 1.0)])
+def test_large_forward_backward(H, ctx, family, N, conc):
+    models = synth.small_models(family, N, 2, seed=600 + N, conc=conc)
+    mid = np.arange(len(LENGTHS)) % 2
+    values, offsets, mid = synth.make_batch(610 + N, models, LENGTHS, mid)
+    model = H.Model(ctx, models)
+    batch = H.Batch(values, offsets, mid)
+    ll, gamma, path = H.forward_backward(ctx, model, batch, want_path=True)
+    check_fb(ll.cpu().numpy(), gamma.cpu().numpy(), models, values, offsets, mid)
+
+
+def test_large_forward_backward_512_sparse(H, ctx):
+    """N = 512 with Dirichlet(0.1) rows (many transition probabilities far
+    below float32's normal range) and diagonal Gaussian emissions, D = 4."""
+    models = synth.small_models("diag_gauss", 512, 1, seed=5, conc=0.1, D=4)
+    lengths = [1, 40, 0, 97]
+    values, offsets, mid = synth.make_batch(15, models, lengths, np.zeros(len(lengths), np.int32))
+    values = values.reshape(-1, 4)
+    model = H.Model(ctx, models)
+    batch = H.Batch(values, offsets, mid, dim=4)
+    ll, gamma, _ = H.forward_backward(ctx, model, batch)
+    check_fb(ll.cpu().numpy(), gamma.cpu().numpy(), models, values, offsets, mid)
+
+
+@pytest.mark.parametrize("N", [64, 96, 256, 1024])
+def test_large_table_mode_xi(H, ctx, N):
+    """A shared float32 log b table: logL, gamma and the statistics'
+    transition sums against the oracle's xi."""
+    import torch
+    rng = np.random.default_rng(N)
+    models = synth.small_models("gauss", N, 1, seed=N, conc=0.5)
+    lengths = [1, 2, 17, 70] if N < 1024 else [1, 9, 23]
+    offsets = np.concatenate([[0], np.cumsum(lengths)]).astype(np.int64)
+    logb = rng.normal(-3, 2, (offsets[-1], N)).astype(np.float32)
+    mid = np.zeros(len(lengths), np.int32)
+    model = H.Model(ctx, models)
+    batch = H.Batch(np.zeros(offsets[-1]), offsets, mid)
+    ll, gamma, _ = H.forward_backward(ctx, model, batch, logb=torch.as_tensor(logb).cuda())
+    ll = ll.cpu().numpy()
+    gamma = gamma.cpu().numpy()
+    m = om(models[0])
+    for s in range(len(lengths)):
+        fb = O.forward_backward_logb(np.log(m.pi), np.log(m.A), logb[offsets[s]:offsets[s + 1]].astype(np.float64))
+        assert abs(ll[s] - fb["logL"]) <= LL_RTOL * max(1.0, abs(fb["logL"]))
+        np.testing.assert_allclose(gamma[offsets[s]:offsets[s + 1]], fb["gamma"], atol=GAMMA_ATOL)
+
+
+def oracle_stats(models, values, offsets, mid):
+    out = []
+    for m, model in enumerate(models):
+        o = om(model)
+        N = len(model["pi"])
+        idx = [s for s in range(len(offsets) - 1) if mid[s] == m]
+        g1, xi, ll = np.zeros(N), np.zeros((N, N)), 0.0
+        cols = np.zeros((N, 3))
+        for s in idx:
+            y = np.asarray(values[offsets[s]:offsets[s + 1]], np.float64)
+            if len(y) == 0:
+                continue
+            fb = O.forward_backward(o, y)
+            ll += fb["logL"]
+            g1 += fb["gamma"][0]
+            xi += fb["xi_sum"]
+            w = fb["gamma"]
+            cols += np.stack([w.sum(0), (w * y[:, None]).sum(0), (w * y[:, None] ** 2).sum(0)], axis=1)
+        out.append(np.concatenate([[len(idx), ll], g1, xi.ravel(), cols.ravel()]))
+    return np.concatenate(out)
+
+
+@pytest.mark.parametrize("N", [40, 128])
+def test_large_estep_stats(H, ctx, N):
+    models = synth.small_models("gauss", N, 2, seed=700 + N)
+    lengths = [50, 3, 0, 200, 120, 1, 77]
+    values, offsets, mid = synth.make_batch(701, models, lengths, np.arange(len(lengths)) % 2)
+    model = H.Model(ctx, models)
+    batch = H.Batch(values, offsets, mid)
+    stats, _ = H.estep_stats(ctx, model, batch)
+    got = stats.get()
+    ref = oracle_stats(models, values, offsets, mid)
+    np.testing.assert_allclose(got, ref, rtol=2e-5, atol=2e-4)
+
+
+def assert_params_close(got_models, ref_models, rtol):
+    for g, r in zip(got_models, ref_models):
+        np.testing.assert_allclose(g["pi"], r.pi, rtol=rtol, atol=1e-6)
+        np.testing.assert_allclose(g["A"], r.A, rtol=rtol, atol=1e-6)
+        for k, v in r.params.items():
+            np.testing.assert_allclose(g["params"][k], v, rtol=rtol, atol=1e-6, err_msg=f"{r.family}.{k}")
+
+
+@pytest.mark.parametrize("family,N,D", [("gauss", 40, 1), ("gamma", 70, 1), ("student_t", 64, 1),
+                                        ("diag_gauss", 64, 3), ("full_gauss", 33, 3)])
+def test_large_mstep(H, ctx, family, N, D):
+    truth = synth.small_models(family, N, 2, seed=800 + N, D=D)
+    lengths = [400, 250, 1, 333, 128, 90]
+    values, offsets, mid = synth.make_batch(801, truth, lengths, np.arange(len(lengths)) % 2)
+    if D > 1:
+        values = values.reshape(-1, D)
+    rng = np.random.default_rng(7)
+    init = [synth.perturb(rng, t) for t in truth]
+    model = H.Model(ctx, init)
+    batch = H.Batch(values, offsets, mid, dim=D)
+    stats, _ = H.estep_stats(ctx, model, batch)
+    H.mstep(ctx, model, stats, batch=batch)
+    ref, _ = O.em_iteration([om(m) for m in init], np.asarray(values, np.float64), offsets, mid)
+    assert_params_close(model.get(), ref, PARAM_RTOL)
+
+
+def test_large_fit(H, ctx):
+    truth = synth.small_models("gauss", 48, 1, seed=901)
+    lengths = [300, 200, 150, 64]
+    values, offsets, mid = synth.make_batch(902, truth, lengths, np.zeros(len(lengths), np.int32))
+    rng = np.random.default_rng(8)
+    init = [synth.perturb(rng, t) for t in truth]
+    model = H.Model(ctx, init)
+    batch = H.Batch(values, offsets, mid)
+    trace, done = H.fit(ctx, model, batch, n_iter=3)
+    assert done == 3
+    ref_models, ref_trace = O.fit([om(m) for m in init], values, offsets, mid, 3)
+    np.testing.assert_allclose(trace[:, 0], ref_trace.sum(axis=1), rtol=LL_RTOL)
+    assert_params_close(model.get(), ref_models, 5 * PARAM_RTOL)
+
+
+@pytest.mark.parametrize("N", [64, 100, 256, 600])
+def test_large_viterbi_bit_exact_table(H, ctx, N):
+    import torch
+    rng = np.random.default_rng(50 + N)
+    models = synth.small_models("gauss", N, 1, seed=N, conc=0.5)
+    lengths = [1, 2, 5, 64, 65, 129, 300]
+    offsets = np.concatenate([[0], np.cumsum(lengths)]).astype(np.int64)
+    logb = rng.normal(-2, 2, (offsets[-1], N)).astype(np.float32)
+    logb[10:20] = np.round(logb[10:20])       # exact ties
+    mid = np.zeros(len(lengths), np.int32)
+    model = H.Model(ctx, models)
+    batch = H.Batch(np.zeros(offsets[-1]), offsets, mid)
+    path, score = H.viterbi(ctx, model, batch, logb=torch.as_tensor(logb).cuda())
+    path = path.cpu().numpy()
+    score = score.cpu().numpy()
+    m = models[0]
+    lpi = np.log(m["pi"]).astype(np.float32)
+    lA = np.log(m["A"]).astype(np.float32)
+    for s in range(len(lengths)):
+        q, sc = O.viterbi_fp32(lpi, lA, logb[offsets[s]:offsets[s + 1]])
+        np.testing.assert_array_equal(path[offsets[s]:offsets[s + 1]], q)
+        assert abs(score[s] - sc) <= 1e-5 * max(1.0, abs(sc))
+
+
+@pytest.mark.parametrize("family,N", [("gauss", 70), ("poisson", 128)])
+def test_large_viterbi_vs_fp64(H, ctx, family, N):
+    models = synth.small_models(family, N, 2, seed=61 + N)
+    lengths = [1, 2, 40, 200, 0, 77]
+    values, offsets, mid = synth.make_batch(17, models, lengths, np.arange(len(lengths)) % 2)
+    model = H.Model(ctx, models)
+    batch = H.Batch(values, offsets, mid)
+    path, score = H.viterbi(ctx, model, batch)
+    path = path.cpu().numpy()
+    score = score.cpu().numpy()
+    for s in range(len(lengths)):
+        y = values[offsets[s]:offsets[s + 1]]
+        if len(y) == 0:
+            assert score[s] == 0.0
+            continue
+        o = om(models[mid[s]])
+        q, sc, gap, fgap = O.viterbi_gaps(np.log(o.pi), np.log(o.A), O.emission_logpdf(o, y))
+        g = path[offsets[s]:offsets[s + 1]]
+        assert abs(score[s] - sc) <= 1e-5 * max(1.0, abs(sc))
+        diff = np.nonzero(g != q)[0]
+        if len(diff):
+            t = diff[-1]
+            margin = fgap if t == len(y) - 1 else gap[t + 1, q[t + 1]]
+            assert margin < 1e-3, (s, t, margin)
+
+
+def test_large_weibull_mstep_unsupported(H, ctx):
+    models = synth.small_models("weibull", 40, 1, seed=3)
+    values, offsets, mid = synth.make_batch(3, models, [30, 20], np.zeros(2, np.int32))
+    model = H.Model(ctx, models)
+    batch = H.Batch(values, offsets, mid)
+    stats, _ = H.estep_stats(ctx, model, batch)
+    with pytest.raises(Exception):
+        H.mstep(ctx, model, stats, batch=batch)
