@@ -136,9 +136,17 @@ typedef enum {
                                  its stream (read with hmm_ctx_profile_read)     */
   HMM_OPT_ESTEP_LANES = 2,    /* lanes per chain of the small-N E-step, 0 = auto */
   HMM_OPT_VITERBI_LANES = 3,  /* lanes per chain of the small-N Viterbi, 0 = auto */
-  HMM_OPT_PLAIN_ESTEP = 4     /* 1: run E-steps with the plain float32 log-space
+  HMM_OPT_PLAIN_ESTEP = 4,    /* 1: run E-steps with the plain float32 log-space
                                  kernels (straight log-sum-exp of Sec. 3.2, N^2
                                  exponentials per step) -- the GPU baseline     */
+  HMM_OPT_TENSOR_RECURRENCE = 5 /* 1: padded N in {64, ..., 512} run the forward
+                                 and backward recursions (Eq. 2 in the shifted
+                                 exp-space form) as tcgen05 GEMMs with FP16
+                                 operands and FP32 accumulation; the shift and
+                                 the log-likelihood stay in float64.  0 (default):
+                                 float32 CUDA-core recursions.  The FP16 path's
+                                 error against float64 is larger than the float32
+                                 path's (about 1e-3 absolute on gamma).          */
 } hmm_option;
 
 /* Kernel timing slots of hmm_ctx_profile_read. */

@@ -332,6 +332,23 @@ hmm_plan make_plan(hmm_ctx ctx, hmm_model model, const hmm_batch* b, const int64
       p->n_groups = (int)groups.size();
       p->lg_groups.ensure(flat.size() * 4);
       HMM_CUDA(cudaMemcpy(p->lg_groups.p, flat.data(), flat.size() * 4, cudaMemcpyHostToDevice));
+      if (tc_supported(model->NP)) {
+        // tiles of the tensor-core recursions: tc_tile_rows() sequences of
+        // one model, longest first (the first entry of a tile is valid)
+        const int TR = tc_tile_rows();
+        std::vector<int32_t> tiles;
+        int nt = 0;
+        for (int64_t q2 = 0; q2 < S;) {
+          const int mq = hm[idx[q2]];
+          std::vector<int32_t> g(TR, -1);
+          for (int c = 0; c < TR && q2 < S && hm[idx[q2]] == mq; ++c) g[c] = idx[q2++];
+          tiles.insert(tiles.end(), g.begin(), g.end());
+          ++nt;
+        }
+        p->n_tc_tiles = nt;
+        p->tc_tiles.ensure(tiles.size() * 4);
+        HMM_CUDA(cudaMemcpy(p->tc_tiles.p, tiles.data(), tiles.size() * 4, cudaMemcpyHostToDevice));
+      }
     }
     int uf = -2;
     for (int64_t q2 = 0; q2 < S; ++q2) {
@@ -362,6 +379,7 @@ void destroy_plan(hmm_plan p) {
   p->tile_seq.release();
   p->tile_row.release();
   p->lg_groups.release();
+  p->tc_tiles.release();
   delete p;
 }
 
@@ -487,7 +505,10 @@ void run_estep_large(hmm_ctx ctx, hmm_model model, const hmm_batch* b, hmm_plan 
   a.ob = ctx->lg_off.as<double>() + TT;
   {
     KTimer kt(ctx, HMM_KT_ESTEP, st);
-    HMM_CUDA(launch_large_fb(NP, a, st));
+    if (ctx->tensor_rec && tc_supported(NP))
+      HMM_CUDA(launch_tc_fb(NP, a, plan->tc_tiles.as<int32_t>(), plan->n_tc_tiles, ctx->status, st));
+    else
+      HMM_CUDA(launch_large_fb(NP, a, st));
   }
   KTimer kt(ctx, HMM_KT_REDUCE, st);
   HMM_CUDA(launch_large_post(a, NP, N, S, gamma, ctx->lg_rz.as<float>(), ll, ctx->status, st));
@@ -823,6 +844,7 @@ hmm_status hmm_ctx_set_option(hmm_ctx ctx, int32_t key, int64_t value) {
       case HMM_OPT_ESTEP_LANES: ctx->estep_lanes = (int)value; break;
       case HMM_OPT_VITERBI_LANES: ctx->viterbi_lanes = (int)value; break;
       case HMM_OPT_PLAIN_ESTEP: ctx->plain_estep = value != 0; break;
+      case HMM_OPT_TENSOR_RECURRENCE: ctx->tensor_rec = value != 0; break;
       default: throw Error{HMM_E_ARG, "unknown option"};
     }
   });

@@ -37,6 +37,12 @@ cudaError_t launch_viterbi_small(int NP, int G, const VitArgs& a, int fam, int n
 // large-N kernels (padded N in {64, 128, 256, 512, 1024})
 cudaError_t launch_large_fb(int NP, const LargeArgs& a, cudaStream_t st);
 cudaError_t launch_large_viterbi(int NP, const LargeArgs& a, cudaStream_t st);
+// tensor-core recursions (tcgen05, FP16 operands): padded N in {64, ..., 512},
+// tiles of tc_tile_rows() sequences of one model; same outputs as launch_large_fb
+bool tc_supported(int NP);
+int tc_tile_rows();
+cudaError_t launch_tc_fb(int NP, const LargeArgs& a, const int32_t* tiles, int n_tiles, int* status,
+                         cudaStream_t st);
 // posterior rows: gamma [total_T][N], 1/Z_t [total_T], log-likelihoods
 cudaError_t launch_large_post(const LargeArgs& a, int NP, int N, int64_t n_seq, float* gamma, float* rz,
                               double* loglik, int* status, cudaStream_t st);

@@ -89,6 +89,7 @@ struct hmm_ctx_s {
   int estep_lanes = 0;
   int viterbi_lanes = 0;
   int plain_estep = 0;
+  int tensor_rec = 0;            // HMM_OPT_TENSOR_RECURRENCE
   // kernel timing
   struct Rec {
     int slot;
@@ -147,6 +148,8 @@ struct hmm_plan_s {
   int n_tiles = 0;
   hmm::DevBuf lg_groups;         // [n_groups][LG_SB] large-N sequence groups (one model each)
   int n_groups = 0;
+  hmm::DevBuf tc_tiles;          // [n_tc_tiles][tc_tile_rows()] tiles of the tensor-core recursions
+  int n_tc_tiles = 0;
   int viterbi_G = 0;
   std::vector<int32_t> h_order;
 };
