@@ -46,7 +46,7 @@ def args_parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--family", choices=["gamma", "student_t"], default="gamma")
-    p.add_argument("--workload", choices=["scale", "batching"], default="scale",
+    p.add_argument("--workload", choices=["scale", "batching", "precision"], default="scale",
                    help="scale: N=16 x 4096 x 2000 (the bench line); batching: 100k ragged "
                         "sequences, N=8, 1024 mixed-family models")
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -403,10 +403,114 @@ def run_ours(args):
     return out
 
 
+def run_precision(args):
+    """Large dense N: N = 512, Dirichlet(0.1) rows, 1024 sequences x T = 4096,
+    diagonal Gaussian D = 32.  One EM iteration + Viterbi with the tensor-core
+    recursions, against the same step with the float32 CUDA-core recursions."""
+    import ctypes as C
+    import torch
+    import paper_2605_29208_gb300 as H
+    from paper_2605_29208_gb300 import _lib, synth
+    n_seq, T = (128, 512) if args.quick else (1024, 4096)
+    truth, init, values, offsets, mid = synth.large_state_workload(n_seq=n_seq, T=T)
+    D = values.shape[1]
+    NS = len(init["pi"])
+    ctx = H.Context(0)
+    model = H.Model(ctx, [init])
+    batch = H.Batch(values, offsets, mid, dim=D).make_plan(ctx, model)
+    stats = H.Stats(ctx, model)
+    dev = batch.values.device
+    S = batch.n_seq
+    ll = torch.empty(S, dtype=torch.float64, device=dev)
+    path = torch.empty(batch.total_T, dtype=torch.int32, device=dev)
+    score = torch.empty(S, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream()
+    sp = C.c_void_p(stream.cuda_stream)
+    flush_buf = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    opts = H.mstep_opts()
+    b = batch.c()
+    L = ctx.lib
+
+    def step():
+        H.check(L.hmm_estep_stats(ctx.h, model.h, C.byref(b), stats.h, C.c_void_p(ll.data_ptr()), sp))
+        H.check(L.hmm_mstep(ctx.h, model.h, stats.h, C.byref(b), C.byref(opts), sp))
+        H.check(L.hmm_viterbi(ctx.h, model.h, C.byref(b), None, C.c_void_p(path.data_ptr()),
+                              C.c_void_p(score.data_ptr()), sp))
+
+    def measure(tensor, steps, warmup):
+        ctx.set_option(_lib.OPT_TENSOR_RECURRENCE, 1 if tensor else 0)
+        model.set([init])
+        for _ in range(warmup):
+            step()
+        torch.cuda.synchronize()
+        ctx.profile(reset=True)
+        ctx.set_option(_lib.OPT_PROFILE, 1)
+        evs = []
+        with ClockSampler(0) as clk:
+            for _ in range(steps):
+                flush_buf.fill_(1)
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                step()
+                e1.record(stream)
+                evs.append((e0, e1))
+            torch.cuda.synchronize()
+        ctx.set_option(_lib.OPT_PROFILE, 0)
+        prof = ctx.profile(reset=True)
+        ms = float(np.mean([a.elapsed_time(b) for a, b in evs]))
+        # log-likelihoods of the first E-step from the initial parameters
+        model.set([init])
+        H.check(L.hmm_estep_stats(ctx.h, model.h, C.byref(b), stats.h, C.c_void_p(ll.data_ptr()), sp))
+        torch.cuda.synchronize()
+        return ms, prof, clk.summary(), ll.cpu().numpy().copy()
+
+    ms_tc, prof_tc, clk_tc, ll_tc = measure(True, args.steps, max(args.warmup, 3))
+    ms_32, prof_32, _, ll_32 = measure(False, max(1, min(args.steps, 2)), 1)
+    nst = max(prof_tc["estep"][1], 1)
+    rec_ms = prof_tc["estep"][0] / nst
+    # tensor work of one recursion launch: forward and backward GEMMs, 2 N^2 flop per (sequence, t) each
+    flops = 4.0 * NS * NS * float(offsets[-1])
+    pk = peaks()
+    peak = float(pk.get("bf16_tflops", 1900.0))   # FP16 dense rate = BF16 dense rate
+    achieved = flops / (rec_ms / 1e3) / 1e12
+    c_step = 2.0 * cells(offsets, NS)
+    rel = np.abs(ll_tc - ll_32) / np.maximum(1.0, np.abs(ll_32))
+    steps = args.steps
+
+    def per(prof, k, n):
+        return prof[k][0] / n
+    line = dict(metric=METRIC, value=c_step / (ms_tc / 1e3), unit=UNIT, n_gpus=1, steps=steps,
+                warmup=max(args.warmup, 3), ms_per_step=ms_tc, higher_is_better=True, scaling="weak",
+                vs_baseline=None, dtype="f16 operands, f32 accumulate (recursions); f32/f64 elsewhere",
+                data="synthetic",
+                config=dict(workload=f"precision: N={NS} states (Dirichlet(0.1) rows), {S} sequences x T={T}, "
+                                     f"diagonal Gaussian D={D}; one EM iteration + Viterbi",
+                            n_states=NS, n_seq_per_gpu=S, total_T=int(offsets[-1]), dim=D,
+                            l2="flushed before every timed step (256 MiB write, outside the events)"),
+                clocks=clk_tc,
+                roofline=dict(bound="tensor", achieved=achieved, peak=peak, unit="TFLOP/s", frac=achieved / peak,
+                              traffic=None, kernel="tc_fb_kernel (tcgen05 forward + backward recursions)",
+                              peak_note="measured bf16 dense GEMM peak (FP16 runs at the BF16 rate)"),
+                breakdown=dict(recursion_ms=rec_ms, emission_ms=per(prof_tc, "emission", steps),
+                               posterior_stats_xi_ms=per(prof_tc, "reduce", steps),
+                               mstep_ms=per(prof_tc, "mstep", steps), viterbi_ms=per(prof_tc, "viterbi", steps)),
+                fp32_path=dict(ms_per_step=ms_32,
+                               recursion_ms=prof_32["estep"][0] / max(prof_32["estep"][1], 1),
+                               speedup_recursion=(prof_32["estep"][0] / max(prof_32["estep"][1], 1)) / rec_ms,
+                               speedup_step=ms_32 / ms_tc),
+                tensor_vs_fp32=dict(loglik_max_rel=float(rel.max()), loglik_median_rel=float(np.median(rel))),
+                gpu_launches=int(sum(v[1] for v in prof_tc.values())))
+    print(json.dumps(line), flush=True)
+    return line
+
+
 def main():
     args = args_parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "precision":
+        run_precision(args)
     else:
         run_ours(args)
 

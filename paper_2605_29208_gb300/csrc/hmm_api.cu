@@ -440,10 +440,30 @@ void mv_statistics(hmm_ctx ctx, hmm_model model, const hmm_batch* b, hmm_plan pl
                    cudaStream_t st) {
   const int NP = model->NP, KS = model->KS, RS = NP * KS;
   const int64_t S = b->n_seq;
-  stats->mv_part.ensure((size_t)std::max<int64_t>(S, 1) * RS * 4);
+  if (NP <= 32) stats->mv_part.ensure((size_t)std::max<int64_t>(S, 1) * RS * 4);
   stats->mv_chunk.ensure((size_t)std::max(plan->n_chunks, 1) * RS * 8);
   stats->mv_rec.ensure((size_t)model->M * RS * 8);
   KTimer kt(ctx, HMM_KT_REDUCE, st);
+  if (NP > 32) {
+    // tiled raw moments per chunk, fixed-order model sums, then the shift
+    if (plan->n_chunks > 0) {
+      const int ftiles = (KS + MVM_TILE - 1) / MVM_TILE;
+      mv_moments_kernel<<<dim3((unsigned)((NP / MVM_TILE) * ftiles), (unsigned)plan->n_chunks), 256, 0, st>>>(
+          model->family.as<int>(), NP, model->N, model->D, KS, b->values, stats->gamma.as<float>(), b->offsets,
+          b->model_id, plan->seq_by_model.as<int32_t>(), plan->chunk_lo.as<int32_t>(), plan->chunk_hi.as<int32_t>(),
+          stats->mv_chunk.as<double>());
+      HMM_CUDA(cudaGetLastError());
+    }
+    reduce_chunks_l2<<<model->M, 128, 0, st>>>(stats->mv_chunk.as<double>(), plan->model_chunk_ptr.as<int32_t>(), RS,
+                                               stats->mv_rec.as<double>());
+    HMM_CUDA(cudaGetLastError());
+    const int n = model->M * NP;
+    mv_shift_kernel<<<(n + 127) / 128, 128, 0, st>>>(model->family.as<int>(), model->mvcoef.as<float>(), model->M,
+                                                     NP, model->N, model->D, model->KM, KS,
+                                                     stats->mv_rec.as<double>());
+    HMM_CUDA(cudaGetLastError());
+    return;
+  }
   if (S > 0) {
     mv_stats_kernel<<<(unsigned)S, 128, 0, st>>>(model->family.as<int>(), model->mvcoef.as<float>(), NP, model->N,
                                                  model->D, model->KM, KS, b->values, stats->gamma.as<float>(),

@@ -212,3 +212,124 @@ __global__ void mv_mstep_kernel(const int* __restrict__ family, double* __restri
 }
 
 }  // namespace hmm
+
+namespace hmm {
+
+// Large-N statistics of the multivariate families: raw weighted moments
+// R[j][z] = sum_t gamma_t(j) f_z(y_t) per 64-sequence chunk with
+// f = (1, y_d, y_d^2) (diagonal) or (1, y_d, y_d y_e) (full), as a
+// 64-state x 64-feature tiled outer-product sum over the chunk's rows
+// (float32 in registers, float64 every 256 rows); mv_shift_kernel turns the
+// reduced sums into the moments about the current mean that mv_mstep_kernel
+// reads.
+constexpr int MVM_TILE = 64;
+constexpr int MVM_KT = 16;
+
+__device__ __forceinline__ float mv_feature(int fam, int D, int z, const float* yr) {
+  if (z == 0) return 1.f;
+  if (z <= D) return yr[z - 1];
+  const int q = z - 1 - D;
+  if (fam == HMM_DIAG_GAUSS) return q < D ? yr[q] * yr[q] : 0.f;
+  return q < D * D ? yr[q / D] * yr[q % D] : 0.f;
+}
+
+__global__ void __launch_bounds__(256) mv_moments_kernel(const int* __restrict__ family, int NP, int N, int D, int KS,
+                                                         const float* __restrict__ y, const float* __restrict__ gamma,
+                                                         const int64_t* __restrict__ offsets,
+                                                         const int32_t* __restrict__ model_id,
+                                                         const int32_t* __restrict__ seq_by_model,
+                                                         const int32_t* __restrict__ chunk_lo,
+                                                         const int32_t* __restrict__ chunk_hi,
+                                                         double* __restrict__ out) {
+  __shared__ __align__(16) float Xs[MVM_KT][MVM_TILE];
+  __shared__ __align__(16) float Fs[MVM_KT][MVM_TILE];
+  const int ftiles = (KS + MVM_TILE - 1) / MVM_TILE;
+  const int ti = blockIdx.x / ftiles, tf = blockIdx.x % ftiles;
+  const int c = blockIdx.y;
+  const int tid = threadIdx.x, ty = tid / 16, tx = tid % 16;
+  const int lo = chunk_lo[c], hi = chunk_hi[c];
+  const int fam = family[model_id[seq_by_model[lo]]];
+  const int nf = mv_stat_count(fam, D);
+  float acc[4][4];
+  double dacc[4][4];
+#pragma unroll
+  for (int p = 0; p < 4; ++p)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc[p][q] = 0.f, dacc[p][q] = 0.0;
+  int since = 0;
+  for (int qs = lo; qs < hi; ++qs) {
+    const int s = seq_by_model[qs];
+    const int64_t b = offsets[s], e = offsets[s + 1];
+    for (int64_t t0 = b; t0 < e; t0 += MVM_KT) {
+      for (int z = tid; z < MVM_KT * MVM_TILE; z += 256) {
+        const int r = z / MVM_TILE, col = z % MVM_TILE;
+        const int64_t t = t0 + r;
+        float xv = 0.f, fv = 0.f;
+        if (t < e) {
+          const int j = ti * MVM_TILE + col, f = tf * MVM_TILE + col;
+          if (j < N) xv = gamma[t * N + j];
+          if (f < nf) fv = mv_feature(fam, D, f, y + t * D);
+        }
+        Xs[r][col] = xv;
+        Fs[r][col] = fv;
+      }
+      __syncthreads();
+#pragma unroll
+      for (int r = 0; r < MVM_KT; ++r) {
+        const float4 x = *reinterpret_cast<const float4*>(&Xs[r][ty * 4]);
+        const float4 f4 = *reinterpret_cast<const float4*>(&Fs[r][tx * 4]);
+        const float xa[4] = {x.x, x.y, x.z, x.w}, fa[4] = {f4.x, f4.y, f4.z, f4.w};
+#pragma unroll
+        for (int p = 0; p < 4; ++p)
+#pragma unroll
+          for (int q = 0; q < 4; ++q) acc[p][q] = fmaf(xa[p], fa[q], acc[p][q]);
+      }
+      __syncthreads();
+      since += MVM_KT;
+      if (since >= 256) {
+#pragma unroll
+        for (int p = 0; p < 4; ++p)
+#pragma unroll
+          for (int q = 0; q < 4; ++q) dacc[p][q] += acc[p][q], acc[p][q] = 0.f;
+        since = 0;
+      }
+    }
+  }
+  double* o = out + (size_t)c * NP * KS;
+#pragma unroll
+  for (int p = 0; p < 4; ++p)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int j = ti * MVM_TILE + ty * 4 + p, f = tf * MVM_TILE + tx * 4 + q;
+      if (j < NP && f < KS) o[(size_t)j * KS + f] = dacc[p][q] + (double)acc[p][q];
+    }
+}
+
+// Raw moments -> moments about the current (float32) mean, in place.
+__global__ void mv_shift_kernel(const int* __restrict__ family, const float* __restrict__ mvc, int M, int NP, int N,
+                                int D, int KM, int KS, double* __restrict__ rec) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= M * NP) return;
+  const int m = idx / NP, k = idx % NP;
+  if (k >= N) return;
+  const int fam = family[m];
+  double* R = rec + (size_t)idx * KS;
+  const float* c = mvc + (size_t)idx * KM;
+  const double W = R[0];
+  if (fam == HMM_DIAG_GAUSS) {
+    for (int d = 0; d < D; ++d) {
+      const double mu = c[d], m1 = R[1 + d];
+      R[1 + D + d] = R[1 + D + d] - 2.0 * mu * m1 + mu * mu * W;
+      R[1 + d] = m1 - mu * W;
+    }
+  } else {
+    for (int d = 0; d < D; ++d)
+      for (int e = 0; e < D; ++e) {
+        const double md = c[d], me = c[e];
+        R[1 + D + d * D + e] = R[1 + D + d * D + e] - md * R[1 + e] - me * R[1 + d] + md * me * W;
+      }
+    for (int d = 0; d < D; ++d) R[1 + d] -= (double)c[d] * W;
+  }
+}
+
+}  // namespace hmm

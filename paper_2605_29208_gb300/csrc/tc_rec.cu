@@ -13,11 +13,14 @@
 //   1. one thread issues 4 x CL MMAs (M = 128, N = 64, K = 16), K-block kb
 //      as soon as its data have arrived (mbarrier per K-block);
 //   2. every thread owns one sequence (one TMEM lane): it loads its 64
-//      accumulators, forms u = log2 b + log2 s, and publishes its partial
-//      row maximum to every CTA of the cluster (DSMEM stores);
-//   3. cluster barrier; E = floor(max over the cluster), v = 2^(u - E);
-//      the CTA writes its FP16 slice into its own K-block and pushes it to
-//      the other CTAs with bulk copies that complete their K-block barriers.
+//      accumulators, forms u = log2 b + log2 s, and sends its partial row
+//      maximum to every CTA of the cluster (st.async completing the
+//      receiver's row-maximum mbarrier);
+//   3. once the cluster's maxima are in, E = floor(max), v = 2^(u - E);
+//      each warp writes its 32 rows of the FP16 slice into the CTA's own
+//      K-block and pushes them to the other CTAs with 4 KB bulk copies that
+//      complete their K-block barriers (no CTA-wide or cluster-wide barrier
+//      inside the step).
 // The rows written to global memory (forward v_t, backward bt_t = A z_{t+1},
 // float64 offsets) have exactly the layout of the CUDA-core large-N kernel,
 // so the posterior, statistics and xi kernels are shared.
@@ -122,7 +125,7 @@ struct TcShape {
   static constexpr uint32_t KB_V = TC_M * 128;   // one K-block of V
   // at least 32 KB so that at most 7 CTAs (448 TMEM columns) share an SM
   static constexpr size_t smem_bytes() {
-    const size_t b = 1024 + V_BYTES + B_BYTES + (size_t)CL * TC_M * 4 + 64 * 4 + (CL + 1) * 8 + 16;
+    const size_t b = 1024 + V_BYTES + B_BYTES + (size_t)CL * TC_M * 4 + 2 * 64 * 4 + (CL + 2) * 8 + 16;
     return b < 32768 ? 32768 : b;
   }
 };
@@ -136,10 +139,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_fb_kernel(TcArgs a) {
   uint8_t* Vs = sm;
   uint8_t* Bs = Vs + S::V_BYTES;
   float* rmax = reinterpret_cast<float*>(Bs + S::B_BYTES);   // [CL][TC_M]
-  float* csc = rmax + CL * TC_M;                             // [TC_NC]
-  uint64_t* kbar = reinterpret_cast<uint64_t*>(csc + TC_NC); // [CL]
-  uint64_t* mbar = kbar + CL;
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 1);
+  float* csc = rmax + CL * TC_M;                             // [TC_NC] column scale exponents
+  float* cinv = csc + TC_NC;                                 // [TC_NC] 2^-csc
+  uint64_t* kbar = reinterpret_cast<uint64_t*>(cinv + TC_NC);// [CL] K-block data of the next MMA
+  uint64_t* mbar = kbar + CL;                                // MMA completion
+  uint64_t* rbar = mbar + 1;                                 // row maxima of the cluster
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(rbar + 1);
   __shared__ int s_tmax;
 
   const uint32_t rank = cluster_rank();
@@ -157,8 +162,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_fb_kernel(TcArgs a) {
   }
   if (tid == 0) {
     s_tmax = 0;
-    for (int b = 0; b < CL; ++b) mbar_init(&kbar[b], 1);
+    // own K-block: one arrival per warp; the others: the local expect_tx
+    for (int b = 0; b < CL; ++b) mbar_init(&kbar[b], b == (int)rank ? TC_THREADS / 32 : 1);
     mbar_init(mbar, 1);
+    mbar_init(rbar, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
@@ -176,6 +183,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_fb_kernel(TcArgs a) {
     float mx = 0.f;
     for (int k = 0; k < NP; ++k) mx = fmaxf(mx, row[k]);
     csc[tid] = mx > 0.f ? -floorf(log2f(mx)) : 0.f;
+    cinv[tid] = exp2f(-csc[tid]);
   }
   __syncthreads();
   for (int idx = tid; idx < TC_NC * NP; idx += TC_THREADS) {
@@ -192,7 +200,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_fb_kernel(TcArgs a) {
   cluster_sync();   // every CTA's barriers are initialised before any copy targets them
 
   const bool vec = (n0 + TC_NC <= N) && (N % 4 == 0);
-  float w[TC_NC];   // log2 b of the step, then u = log2 b + log2 s
+  float w[TC_NC];   // ln b of the step (loaded a step ahead), then u = log2 b + log2 s
   auto load_lb = [&](int k) {
     const bool act = k < len;
     const int64_t grow = base + (dir == 0 ? k : len - 1 - k);
@@ -201,17 +209,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_fb_kernel(TcArgs a) {
 #pragma unroll
       for (int c = 0; c < TC_NC; c += 4) {
         const float4 q = __ldg(reinterpret_cast<const float4*>(p + c));
-        w[c] = q.x * kLog2ef;
-        w[c + 1] = q.y * kLog2ef;
-        w[c + 2] = q.z * kLog2ef;
-        w[c + 3] = q.w * kLog2ef;
+        w[c] = q.x;
+        w[c + 1] = q.y;
+        w[c + 2] = q.z;
+        w[c + 3] = q.w;
       }
     } else {
 #pragma unroll
-      for (int c = 0; c < TC_NC; ++c) w[c] = (act && n0 + c < N) ? __ldg(p + c) * kLog2ef : -INFINITY;
+      for (int c = 0; c < TC_NC; ++c) w[c] = (act && n0 + c < N) ? __ldg(p + c) : -INFINITY;
     }
   };
-  load_lb(0);   // w holds log2 b
+  load_lb(0);
   double O = 0.0;
   const uint32_t idesc = tc_idesc(TC_M, TC_NC);
   const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16);
@@ -219,6 +227,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_fb_kernel(TcArgs a) {
   for (int k = 0; k < tmax; ++k) {
     const bool act = k < len;
     const int64_t grow = base + (dir == 0 ? k : len - 1 - k);
+    if (tid == 0) mbar_expect_tx(rbar, (uint32_t)(CL * TC_M * 4));
     if (k > 0) {
       if (tid == 0) {
         for (int kb = 0; kb < CL; ++kb) {
@@ -265,9 +274,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_fb_kernel(TcArgs a) {
           for (int z = 0; z < 4; ++z) {
             const int cc = 32 * h + c + z;
             const float sc = __uint_as_float(r[c + z]);
-            const float e = csc[cc];
-            sv[z] = sc * exp2f(-e);
-            w[cc] = w[cc] + log2f(sc) - e;   // w: log2 b -> u
+            sv[z] = sc * cinv[cc];
+            w[cc] = fmaf(w[cc], kLog2ef, lg2a(sc) - csc[cc]);   // w: ln b -> u
           }
           if (dir == 1 && act) *reinterpret_cast<float4*>(q + c) = make_float4(sv[0], sv[1], sv[2], sv[3]);
         }
@@ -275,7 +283,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_fb_kernel(TcArgs a) {
     } else {
 #pragma unroll
       for (int c = 0; c < TC_NC; ++c)
-        if (dir == 0) w[c] += a.mv.logpi2[(size_t)m * NP + n0 + c];
+        w[c] = w[c] * kLog2ef + (dir == 0 ? a.mv.logpi2[(size_t)m * NP + n0 + c] : 0.f);
       if (dir == 1 && act) {
         float* q = a.bv + grow * NP + n0;
 #pragma unroll
@@ -286,12 +294,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_fb_kernel(TcArgs a) {
     float mx = -INFINITY;
 #pragma unroll
     for (int c = 0; c < TC_NC; ++c) mx = fmaxf(mx, w[c]);
-    const uint32_t raddr = smem_u32(rmax + rank * TC_M + tid);
+    const uint32_t raddr = smem_u32(rmax + rank * TC_M + tid), rb = smem_u32(rbar);
 #pragma unroll
     for (int p = 0; p < CL; ++p)
-      asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(mapa(raddr, (uint32_t)p)), "f"(mx) : "memory");
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    cluster_sync();
+      asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.f32 [%0], %1, [%2];" ::"r"(
+                       mapa(raddr, (uint32_t)p)),
+                   "f"(mx), "r"(mapa(rb, (uint32_t)p))
+                   : "memory");
+    if (!mbar_wait(rbar, (uint32_t)(k & 1))) set_status(a.status, ST_TIMEOUT);
     float M = -INFINITY;
 #pragma unroll
     for (int p = 0; p < CL; ++p) M = fmaxf(M, rmax[p * TC_M + tid]);
@@ -305,7 +315,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_fb_kernel(TcArgs a) {
     for (int c = 0; c < TC_NC; c += 8) {
       float v[8];
 #pragma unroll
-      for (int q = 0; q < 8; ++q) v[q] = exp2f(w[c + q] - E);
+      for (int q = 0; q < 8; ++q) v[q] = ex2f(w[c + q] - E);
       if (dir == 0 && act) {
         float* g = a.fv + grow * NP + n0 + c;
         *reinterpret_cast<float4*>(g) = make_float4(v[0], v[1], v[2], v[3]);
@@ -316,23 +326,26 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_fb_kernel(TcArgs a) {
       for (int q = 0; q < 4; ++q) h[q] = __floats2half2_rn(v[2 * q], v[2 * q + 1]);
       *reinterpret_cast<uint4*>(vrow + sw128_off(tid, c)) = *reinterpret_cast<uint4*>(h);
     }
+    // this warp's 32 rows of the slice (4 KB, contiguous in the swizzled
+    // layout) go to the other CTAs; the local K-block counts one arrival per warp
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    __syncthreads();
-    if (k + 1 < tmax && tid == 0) {
-      const uint32_t srcv = smem_u32(vrow);
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncwarp();
+    if (k + 1 < tmax && (tid & 31) == 0) {
+      const uint32_t srcv = smem_u32(vrow + warp * 4096);
       for (int p = 0; p < CL; ++p) {
         if (p == (int)rank) continue;
         const uint32_t dst = mapa(srcv, (uint32_t)p);
         const uint32_t bar = mapa(smem_u32(&kbar[rank]), (uint32_t)p);
         asm volatile(
             "cp.async.bulk.shared::cluster.shared::cta.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
-            "r"(srcv), "r"(S::KB_V), "r"(bar)
+            "r"(srcv), "r"(4096), "r"(bar)
             : "memory");
       }
-      for (int kb = 0; kb < CL; ++kb) {
-        if (kb == (int)rank) mbar_arrive(&kbar[kb]);
-        else mbar_expect_tx(&kbar[kb], S::KB_V);
-      }
+      mbar_arrive(&kbar[rank]);
+      if (tid == 0)
+        for (int kb = 0; kb < CL; ++kb)
+          if (kb != (int)rank) mbar_expect_tx(&kbar[kb], S::KB_V);
     }
     if (k + 1 < tmax) load_lb(k + 1);
   }
