@@ -309,6 +309,84 @@ hmm_status hmm_fit(hmm_ctx ctx, hmm_model model, const hmm_batch* batch,
                    const hmm_fit_opts* opts, double* h_loglik_trace,
                    int32_t* iters_done, void* stream);
 
+/* ------------------------------------------------------------ serving
+ * A request server on one GPU: decode (Viterbi), posterior (forward-backward)
+ * and fit (Baum-Welch) requests, each carrying its own model and one
+ * observation sequence, are queued by hmm_serve_submit and run by a
+ * dispatcher with continuous batching: whenever a slot is free and the
+ * device-memory budget allows, the oldest pending request and the pending
+ * requests of the same kind, family, N, dim (and iteration count) are packed
+ * into one multi-model batch (one model per request) and launched on that
+ * slot's stream, while earlier batches still run on the other slots.  Models,
+ * EM state and scratch stay on the device for the whole request; only the
+ * inputs go up and the results come down.  The paper describes no serving
+ * system: the batching follows from its problem statement (independent
+ * sequences and models, Sec. 3), the entry points from the request kinds of
+ * Sec. 3.3-3.4 and Sec. 4. */
+typedef struct hmm_server_s* hmm_server;
+
+typedef enum {
+  HMM_REQ_DECODE = 0,      /* Viterbi path and score                         */
+  HMM_REQ_POSTERIOR = 1,   /* gamma rows and log-likelihood                  */
+  HMM_REQ_FIT = 2          /* n_iter Baum-Welch iterations from `params`     */
+} hmm_request_kind;
+
+typedef struct {
+  int32_t n_slots;         /* concurrent batches (streams), 0: 4               */
+  int32_t max_batch;       /* requests per batch, 0: 16                       */
+  int32_t max_queue;       /* pending requests before HMM_E_BUSY, 0: 4096      */
+  size_t mem_budget;       /* admission budget in bytes, 0: half of free memory */
+} hmm_serve_opts;
+
+typedef struct {
+  int32_t kind;            /* hmm_request_kind                                */
+  int32_t family;          /* hmm_family of the request's model              */
+  int32_t n_states;
+  int32_t dim;
+  const double* params;    /* host blob of one model (hmm_param_blob_size)    */
+  int64_t n_params;
+  const float* values;     /* host observations [T][dim]                      */
+  int64_t T;
+  int32_t n_iter;          /* HMM_REQ_FIT: iterations                         */
+} hmm_request;
+
+typedef struct {
+  int32_t status;          /* hmm_status of the request                       */
+  int32_t kind;
+  int64_t T;
+  double loglik;           /* POSTERIOR: log-likelihood; FIT: under the final
+                              parameters' predecessor (last trace entry)     */
+  double score;            /* DECODE: log probability of the best path        */
+  const int32_t* path;     /* DECODE: [T]                                     */
+  const float* gamma;      /* POSTERIOR: [T][n_states]                        */
+  const double* params;    /* FIT: fitted blob                                 */
+  const double* trace;     /* FIT: [n_iter] log-likelihood entering each iteration */
+  int32_t n_iter;
+  double latency_ms;       /* submit to completion                           */
+} hmm_result;
+
+/* Starts the server's dispatcher and slot threads on ctx's device (each slot
+ * owns a context, a stream and cached device buffers; ctx must outlive the
+ * server).  opts may be NULL. */
+hmm_status hmm_serve_create(hmm_ctx ctx, const hmm_serve_opts* opts, hmm_server* out);
+/* Copies the request's host inputs and queues it; *ticket identifies it.
+ * HMM_E_BUSY when max_queue requests are pending, HMM_E_ARG for an invalid
+ * request, HMM_E_NOMEM when its footprint exceeds the whole budget. */
+hmm_status hmm_serve_submit(hmm_server server, const hmm_request* req, uint64_t* ticket);
+/* HMM_E_NOTREADY while the request is pending or running; then fills *out
+ * (pointers owned by the server, valid until hmm_serve_release) and returns
+ * HMM_OK (out->status carries the request's own status). */
+hmm_status hmm_serve_poll(hmm_server server, uint64_t ticket, hmm_result* out);
+/* Blocks until the request completes (or timeout_ms passes: HMM_E_TIMEOUT). */
+hmm_status hmm_serve_wait(hmm_server server, uint64_t ticket, double timeout_ms, hmm_result* out);
+/* Frees a completed request's results. */
+hmm_status hmm_serve_release(hmm_server server, uint64_t ticket);
+/* h_out[8]: submitted, completed, p50 ms, p99 ms, mean ms, completed per
+ * second since the first submission, pending, running. */
+hmm_status hmm_serve_stats(hmm_server server, double* h_out);
+/* Finishes the running batches, drops pending requests, frees everything. */
+hmm_status hmm_serve_destroy(hmm_server server);
+
 #ifdef __cplusplus
 }
 #endif

@@ -327,3 +327,85 @@ def fit(ctx, model, batch, n_iter, tol=0.0, opts=None, stream=None):
     check(ctx.lib.hmm_fit(ctx.h, model.h, C.byref(b), C.byref(o), trace.ctypes.data_as(C.c_void_p),
                           C.byref(done), _stream(stream)))
     return trace[:done.value], done.value
+
+
+class Server:
+    """hmm_serve_*: a request server with continuous batching.  Requests
+    carry their own model dict and one host sequence; results come back as
+    numpy arrays."""
+
+    KINDS = {"decode": _lib.REQ_DECODE, "posterior": _lib.REQ_POSTERIOR, "fit": _lib.REQ_FIT}
+
+    def __init__(self, ctx: Context, n_slots=0, max_batch=0, max_queue=0, mem_budget=0):
+        self.lib = ctx.lib
+        self.ctx = ctx
+        o = _lib.hmm_serve_opts(n_slots, max_batch, max_queue, mem_budget)
+        h = C.c_void_p()
+        check(self.lib.hmm_serve_create(ctx.h, C.byref(o), C.byref(h)))
+        self.h = h
+        self._keep = {}
+
+    def submit(self, kind: str, model: dict, values, n_iter: int = 0) -> int:
+        fam = FAMILY[model["family"]]
+        N = len(model["pi"])
+        vals = np.ascontiguousarray(values, np.float32)
+        D = vals.shape[1] if vals.ndim == 2 else 1
+        blob = blob_from_model(model)
+        r = _lib.hmm_request(self.KINDS[kind], fam, N, D, blob.ctypes.data, blob.size, vals.ctypes.data,
+                             vals.shape[0], n_iter)
+        t = C.c_uint64()
+        check(self.lib.hmm_serve_submit(self.h, C.byref(r), C.byref(t)))
+        self._keep[t.value] = (kind, N, D, model["family"])
+        return t.value
+
+    def _convert(self, ticket, res):
+        kind, N, D, family = self._keep[ticket]
+        out = dict(status=res.status, latency_ms=res.latency_ms, loglik=res.loglik)
+        T = res.T
+        if kind == "decode":
+            out["path"] = np.ctypeslib.as_array(res.path, shape=(T,)).copy() if T else np.zeros(0, np.int32)
+            out["score"] = res.score
+        elif kind == "posterior":
+            out["gamma"] = (np.ctypeslib.as_array(res.gamma, shape=(T * N,)).reshape(T, N).copy()
+                            if T else np.zeros((0, N), np.float32))
+        else:
+            n = int(self.lib.hmm_param_blob_size(1, N, D, (C.c_int32 * 1)(FAMILY[family])))
+            out["params"] = model_from_blob(np.ctypeslib.as_array(res.params, shape=(n,)).copy(), family, N, D)[0]
+            out["trace"] = (np.ctypeslib.as_array(res.trace, shape=(res.n_iter,)).copy()
+                            if res.n_iter else np.zeros(0))
+        return out
+
+    def poll(self, ticket: int):
+        res = _lib.hmm_result()
+        st = self.lib.hmm_serve_poll(self.h, ticket, C.byref(res))
+        if st == 7:      # HMM_E_NOTREADY
+            return None
+        check(st)
+        return self._convert(ticket, res)
+
+    def wait(self, ticket: int, timeout_ms: float = 600000.0, release: bool = True):
+        res = _lib.hmm_result()
+        check(self.lib.hmm_serve_wait(self.h, ticket, timeout_ms, C.byref(res)))
+        out = self._convert(ticket, res)
+        if release:
+            check(self.lib.hmm_serve_release(self.h, ticket))
+            self._keep.pop(ticket, None)
+        return out
+
+    def stats(self) -> dict:
+        h = np.zeros(8, np.float64)
+        check(self.lib.hmm_serve_stats(self.h, h.ctypes.data_as(C.c_void_p)))
+        keys = ("submitted", "completed", "p50_ms", "p99_ms", "mean_ms", "completed_per_s", "pending", "running")
+        return dict(zip(keys, h.tolist()))
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.hmm_serve_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+

@@ -34,6 +34,26 @@ class hmm_fit_opts(C.Structure):
     _fields_ = [("max_iter", C.c_int32), ("tol", C.c_double), ("mstep", hmm_mstep_opts)]
 
 
+class hmm_serve_opts(C.Structure):
+    _fields_ = [("n_slots", C.c_int32), ("max_batch", C.c_int32), ("max_queue", C.c_int32),
+                ("mem_budget", C.c_size_t)]
+
+
+class hmm_request(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("family", C.c_int32), ("n_states", C.c_int32), ("dim", C.c_int32),
+                ("params", C.c_void_p), ("n_params", C.c_int64), ("values", C.c_void_p), ("T", C.c_int64),
+                ("n_iter", C.c_int32)]
+
+
+class hmm_result(C.Structure):
+    _fields_ = [("status", C.c_int32), ("kind", C.c_int32), ("T", C.c_int64), ("loglik", C.c_double),
+                ("score", C.c_double), ("path", C.POINTER(C.c_int32)), ("gamma", C.POINTER(C.c_float)),
+                ("params", C.POINTER(C.c_double)), ("trace", C.POINTER(C.c_double)), ("n_iter", C.c_int32),
+                ("latency_ms", C.c_double)]
+
+
+REQ_DECODE, REQ_POSTERIOR, REQ_FIT = 0, 1, 2
+
 # name -> (restype, argtypes)
 _SIGS = {
     "hmm_status_string": (C.c_char_p, [C.c_int]),
@@ -74,6 +94,13 @@ _SIGS = {
                             C.POINTER(hmm_mstep_opts), C.c_void_p]),
     "hmm_fit": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(hmm_batch), C.POINTER(hmm_fit_opts),
                           C.c_void_p, C.POINTER(C.c_int32), C.c_void_p]),
+    "hmm_serve_create": (C.c_int, [C.c_void_p, C.POINTER(hmm_serve_opts), C.POINTER(C.c_void_p)]),
+    "hmm_serve_submit": (C.c_int, [C.c_void_p, C.POINTER(hmm_request), C.POINTER(C.c_uint64)]),
+    "hmm_serve_poll": (C.c_int, [C.c_void_p, C.c_uint64, C.POINTER(hmm_result)]),
+    "hmm_serve_wait": (C.c_int, [C.c_void_p, C.c_uint64, C.c_double, C.POINTER(hmm_result)]),
+    "hmm_serve_release": (C.c_int, [C.c_void_p, C.c_uint64]),
+    "hmm_serve_stats": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "hmm_serve_destroy": (C.c_int, [C.c_void_p]),
 }
 
 # every symbol the header declares (checked by the not-gpu tests)

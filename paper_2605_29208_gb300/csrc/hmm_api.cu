@@ -223,9 +223,12 @@ void check_batch(hmm_model model, const hmm_batch* b) {
   HMM_REQUIRE(b->dim == model->D, "batch dim does not match the model");
 }
 
-// Builds a plan from host arrays.
-hmm_plan make_plan(hmm_ctx ctx, hmm_model model, const hmm_batch* b, const int64_t* ho,
-                   const int32_t* hm) {
+}  // namespace
+
+// Fills (or refills) a plan for the batch; device buffers only grow, so a
+// plan reused for batches of similar size allocates nothing.
+void hmm::fill_plan(hmm_plan p, hmm_ctx ctx, hmm_model model, const hmm_batch* b, const int64_t* ho,
+                    const int32_t* hm) {
   const int64_t S = b->n_seq;
   HMM_REQUIRE(S == 0 || (ho && hm), "host offsets/model_id needed for a plan");
   if (S > 0) {
@@ -239,9 +242,13 @@ hmm_plan make_plan(hmm_ctx ctx, hmm_model model, const hmm_batch* b, const int64
     HMM_REQUIRE(hm[s] >= 0 && hm[s] < model->M, "model_id out of range");
     maxT = std::max(maxT, ho[s + 1] - ho[s]);
   }
-  auto* p = new hmm_plan_s();
-  try {
+  {
     p->ctx = ctx;
+    p->n_tiles = 0;
+    p->n_groups = 0;
+    p->n_tc_tiles = 0;
+    p->estep_G = 0;
+    p->viterbi_G = 0;
     p->n_seq = S;
     p->total_T = b->total_T;
     p->M = model->M;
@@ -357,19 +364,10 @@ hmm_plan make_plan(hmm_ctx ctx, hmm_model model, const hmm_batch* b, const int64
     }
     p->uniform_family = uf < 0 ? -1 : uf;
     p->h_order = std::move(order);
-  } catch (...) {
-    p->order.release();
-    p->seq_by_model.release();
-    p->chunk_lo.release();
-    p->chunk_hi.release();
-    p->model_chunk_ptr.release();
-    delete p;
-    throw;
   }
-  return p;
 }
 
-void destroy_plan(hmm_plan p) {
+void hmm::destroy_plan(hmm_plan p) {
   if (!p) return;
   p->order.release();
   p->seq_by_model.release();
@@ -381,6 +379,20 @@ void destroy_plan(hmm_plan p) {
   p->lg_groups.release();
   p->tc_tiles.release();
   delete p;
+}
+
+namespace {
+
+// Builds a plan from host arrays.
+hmm_plan make_plan(hmm_ctx ctx, hmm_model model, const hmm_batch* b, const int64_t* ho, const int32_t* hm) {
+  auto* p = new hmm_plan_s();
+  try {
+    fill_plan(p, ctx, model, b, ho, hm);
+  } catch (...) {
+    destroy_plan(p);
+    throw;
+  }
+  return p;
 }
 
 // A plan for the batch: the caller's, or a temporary one built from host
@@ -744,6 +756,31 @@ void run_mstep(hmm_ctx ctx, hmm_model model, hmm_stats stats, const MStepOpts& o
 
 }  // namespace
 
+const double* hmm::fit_async(hmm_ctx ctx, hmm_model model, const hmm_batch* b, hmm_plan plan, hmm_stats stats,
+                             const hmm_mstep_opts* opts, int iters, cudaStream_t st) {
+  const MStepOpts mo = to_opts(opts);
+  const int M = model->M, RS = rec_size(model->NP);
+  ctx->trace.ensure((size_t)std::max(iters, 1) * M * 8 + 64);
+  int* it_dev = reinterpret_cast<int*>(ctx->trace.as<char>() + (size_t)std::max(iters, 1) * M * 8);
+  HMM_CUDA(cudaMemsetAsync(it_dev, 0, sizeof(int), st));
+  prepare_mstep(model, stats, b, plan);
+  for (int k = 0; k < iters; ++k) {
+    run_estep(ctx, model, b, plan, nullptr, nullptr, nullptr, true, stats, st);
+    trace_gather_kernel<<<(M + 255) / 256, 256, 0, st>>>(stats->rec.as<double>(), RS, M, ctx->trace.as<double>(),
+                                                        it_dev);
+    HMM_CUDA(cudaGetLastError());
+    run_mstep(ctx, model, stats, mo, b, plan, st);
+    bump_kernel<<<1, 1, 0, st>>>(it_dev);
+    HMM_CUDA(cudaGetLastError());
+  }
+  return ctx->trace.as<double>();
+}
+
+void hmm::estep_async(hmm_ctx ctx, hmm_model model, const hmm_batch* b, hmm_plan plan, hmm_stats stats,
+                      double* d_loglik, cudaStream_t st) {
+  run_estep(ctx, model, b, plan, nullptr, nullptr, d_loglik, true, stats, st);
+}
+
 // ================================================================ C ABI
 extern "C" {
 
@@ -959,7 +996,7 @@ hmm_status hmm_model_create(hmm_ctx ctx, int32_t n_models, int32_t n_states, int
       HMM_CUDA(cudaMemset(m->coef.p, 0, M * NP * KC * 4));
       lfact_kernel<<<(LF_YMAX + 255) / 256, 256>>>(m->lfact2.as<float>());
       HMM_CUDA(cudaGetLastError());
-      HMM_CUDA(cudaDeviceSynchronize());
+      HMM_CUDA(cudaStreamSynchronize(0));
     } catch (...) {
       for (auto* b : {&m->family, &m->pi, &m->A, &m->theta, &m->A32, &m->AT32, &m->logA2, &m->logAe, &m->pi32,
                       &m->logpi2, &m->logpie, &m->coef, &m->nbtab, &m->lfact2, &m->mvcoef})
@@ -1028,7 +1065,8 @@ hmm_status hmm_model_set_params(hmm_model model, const double* h_blob, int64_t n
                                                  model->KM, model->mvcoef.as<float>());
       HMM_CUDA(cudaGetLastError());
     }
-    HMM_CUDA(cudaDeviceSynchronize());
+    // the copies and derive kernels ran on the legacy default stream
+    HMM_CUDA(cudaStreamSynchronize(0));
   });
 }
 

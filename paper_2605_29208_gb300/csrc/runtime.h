@@ -153,3 +153,19 @@ struct hmm_plan_s {
   int viterbi_G = 0;
   std::vector<int32_t> h_order;
 };
+
+namespace hmm {
+// Internal entry points shared by the C ABI and the request server.
+// Fills (or refills) a plan for a batch from host offsets and model ids.
+void fill_plan(hmm_plan p, hmm_ctx ctx, hmm_model model, const hmm_batch* b, const int64_t* ho, const int32_t* hm);
+void destroy_plan(hmm_plan p);
+// `iters` Baum-Welch iterations enqueued on `st` with no host
+// synchronisation (stats and every scratch buffer must already be sized by
+// one earlier E-step on this batch); returns the context-owned device trace
+// [iters][M] of per-model log-likelihood sums.
+const double* fit_async(hmm_ctx ctx, hmm_model model, const hmm_batch* b, hmm_plan plan, hmm_stats stats,
+                        const hmm_mstep_opts* opts, int iters, cudaStream_t st);
+// Enqueues the E-step with statistics (used to size buffers before fit_async).
+void estep_async(hmm_ctx ctx, hmm_model model, const hmm_batch* b, hmm_plan plan, hmm_stats stats, double* d_loglik,
+                 cudaStream_t st);
+}  // namespace hmm
