@@ -46,7 +46,7 @@ def args_parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--family", choices=["gamma", "student_t"], default="gamma")
-    p.add_argument("--workload", choices=["scale", "batching", "precision"], default="scale",
+    p.add_argument("--workload", choices=["scale", "batching", "precision", "serving"], default="scale",
                    help="scale: N=16 x 4096 x 2000 (the bench line); batching: 100k ragged "
                         "sequences, N=8, 1024 mixed-family models")
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -54,6 +54,10 @@ def args_parse():
     p.add_argument("--estep-lanes", type=int, default=0)
     p.add_argument("--viterbi-lanes", type=int, default=0)
     p.add_argument("--quick", action="store_true", help="small case for profiling runs")
+    p.add_argument("--rate", type=float, default=2000.0, help="serving: Poisson arrival rate (requests/s)")
+    p.add_argument("--requests", type=int, default=1000, help="serving: number of requests")
+    p.add_argument("--t-max", type=int, default=100000, help="serving: longest sequence")
+    p.add_argument("--slots", type=int, default=32, help="serving: concurrent batches")
     return p.parse_args()
 
 
@@ -505,12 +509,76 @@ def run_precision(args):
     return line
 
 
+def run_serving(args):
+    """Request server under Poisson arrivals: decode / posterior / 10-iteration
+    fit requests, N in {4, 16, 64, 256}, T log-uniform in [100, t_max],
+    full-covariance Gaussian D = 8 or Gamma emissions, each request its own
+    model.  Reports p50 / p99 latency (submit to completion) beside the
+    throughput."""
+    import torch
+    import paper_2605_29208_gb300 as H
+    from paper_2605_29208_gb300 import synth
+    n_req = 100 if args.quick else args.requests
+    t_max = 5000 if args.quick else args.t_max
+    reqs = synth.serving_workload(n_req=n_req, rate=args.rate, t_max=t_max)
+    ctx = H.Context(0)
+    # warm the slots (model and buffer caches) with a short replay of the mix
+    srv = H.Server(ctx, n_slots=args.slots, max_batch=16)
+    warm = [srv.submit(r["kind"], r["model"], r["values"][:200], r["n_iter"]) for r in reqs[:64]]
+    for t, r in zip(warm, reqs[:64]):
+        x = srv.wait(t)
+        if x["status"] != 0:
+            print(f"warm-up request failed ({r['kind']}, {r['model']['family']}, N={len(r['model']['pi'])}): "
+                  f"{x.get('error')}", file=sys.stderr)
+    srv.close()
+    srv = H.Server(ctx, n_slots=args.slots, max_batch=16)
+    torch.cuda.synchronize()
+    with ClockSampler(0) as clk:
+        t0 = time.perf_counter()
+        tickets = []
+        for r in reqs:
+            while time.perf_counter() - t0 < r["arrival_s"]:
+                pass
+            tickets.append(srv.submit(r["kind"], r["model"], r["values"], r["n_iter"]))
+        results = [srv.wait(t, 3600e3) for t in tickets]
+        makespan = time.perf_counter() - t0
+    st = srv.stats()
+    srv.close()
+    lat = np.array([x["latency_ms"] for x in results])
+    cells = 0.0
+    for r in reqs:
+        N = len(r["model"]["pi"])
+        cells += N * N * len(r["values"]) * (r["n_iter"] if r["kind"] == "fit" else 1)
+    by_kind = {}
+    for r, x in zip(reqs, results):
+        by_kind.setdefault(r["kind"], []).append(x["latency_ms"])
+    line = dict(metric="serving latency p99 (submit to result), Poisson arrivals", value=float(np.percentile(lat, 99)),
+                unit="ms", higher_is_better=False, n_gpus=1, steps=n_req, warmup=64, ms_per_step=None,
+                scaling="weak", vs_baseline=None, dtype="f32 (f64 reductions)", data="synthetic",
+                config=dict(workload=f"serving: {n_req} requests at {args.rate:g}/s, decode/posterior/fit(10) = "
+                                     f"0.5/0.3/0.2, N in {{4,16,64,256}}, T log-uniform [100, {t_max}], "
+                                     f"full-cov Gaussian D=8 or Gamma, each request its own model",
+                            slots=args.slots, max_batch=16),
+                p50_ms=float(np.percentile(lat, 50)), p99_ms=float(np.percentile(lat, 99)),
+                mean_ms=float(lat.mean()), server_stats=st,
+                p50_by_kind={k: float(np.percentile(v, 50)) for k, v in by_kind.items()},
+                p99_by_kind={k: float(np.percentile(v, 99)) for k, v in by_kind.items()},
+                offered_rate=args.rate, completed_per_s=n_req / makespan, makespan_s=makespan,
+                cell_updates_per_s=cells / makespan, clocks=clk.summary(),
+                failed=int(sum(1 for x in results if x["status"] != 0)),
+                errors=sorted({x.get("error", "") for x in results if x["status"] != 0})[:5])
+    print(json.dumps(line), flush=True)
+    return line
+
+
 def main():
     args = args_parse()
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "precision":
         run_precision(args)
+    elif args.workload == "serving":
+        run_serving(args)
     else:
         run_ours(args)
 

@@ -363,6 +363,7 @@ typedef struct {
   const double* trace;     /* FIT: [n_iter] log-likelihood entering each iteration */
   int32_t n_iter;
   double latency_ms;       /* submit to completion                           */
+  const char* error;       /* message of a failed request, else ""            */
 } hmm_result;
 
 /* Starts the server's dispatcher and slot threads on ctx's device (each slot

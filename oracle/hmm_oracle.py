@@ -341,6 +341,18 @@ def bessel_ratio(kappa):
 # Weighted M-steps for one state (Sec. 4), w = gamma_t(j) over the
 # concatenated sequences of one model, y the matching observations.
 # --------------------------------------------------------------------------
+def _positive_step(x, step):
+    """Newton iterate x - step with the step halved until it is positive, at
+    most 64 times (reading: the paper's 'step halving' bound); NaN if that
+    fails, which makes the update undefined (see valid_update)."""
+    for _ in range(64):
+        new = x - step
+        if new > 0 and np.isfinite(new):
+            return new
+        step *= 0.5
+    return np.nan
+
+
 def _newton_done(old, new):
     return abs(new - old) <= NEWTON_TOL * max(1.0, abs(old))
 
@@ -372,11 +384,7 @@ def mstep_gamma(w, y, cur):
     for iters in range(1, NEWTON_MAXIT + 1):
         s = np.log(a) - digamma(a) - c
         ds = 1.0 / a - trigamma(a)
-        step = s / ds
-        new = a - step
-        while new <= 0:
-            step *= 0.5
-            new = a - step
+        new = _positive_step(a, s / ds)
         done = _newton_done(a, new)
         a = new
         if done:
@@ -404,9 +412,13 @@ def mstep_beta(w, y, cur):
         J = np.array([[trigamma(a) - tab, -tab], [-tab, trigamma(b) - tab]])
         step = np.linalg.solve(J, F)
         na, nb = a - step[0], b - step[1]
-        while na <= 0 or nb <= 0:
+        for _ in range(64):
+            if na > 0 and nb > 0:
+                break
             step *= 0.5
             na, nb = a - step[0], b - step[1]
+        if not (na > 0 and nb > 0):
+            na = nb = np.nan
         done = _newton_done(a, na) and _newton_done(b, nb)
         a, b = na, nb
         if done:
@@ -437,11 +449,7 @@ def mstep_weibull(w, y, cur):
         S0, S1, S2 = sums(k)
         f = 1.0 / k + mlog - S1 / S0
         df = -1.0 / (k * k) - (S2 * S0 - S1 * S1) / (S0 * S0)
-        step = f / df
-        new = k - step
-        while new <= 0:
-            step *= 0.5
-            new = k - step
+        new = _positive_step(k, f / df)
         done = _newton_done(k, new)
         k = new
         if done:
@@ -470,12 +478,7 @@ def mstep_negbin(w, y, cur):
             g = np.sum(w * (digamma(y + r) - digamma(r))) + Nj * np.log(r / (r + ybar))
             dg = (np.sum(w * (trigamma(y + r) - trigamma(r)))
                   + Nj * (1.0 / r - 1.0 / (r + ybar)))
-            step = g / dg
-            new = r - step
-            while new <= 0:
-                step *= 0.5
-                new = r - step
-            new = min(new, NEGBIN_RMAX)
+            new = min(_positive_step(r, g / dg), NEGBIN_RMAX)
             done = _newton_done(r, new)
             r = new
             if done:
@@ -498,12 +501,7 @@ def mstep_vonmises(w, y, cur):
     for iters in range(1, NEWTON_MAXIT + 1):
         A = bessel_ratio(k)
         dA = 1 - A * A - A / k
-        step = (A - R) / dA
-        new = k - step
-        while new <= 0:
-            step *= 0.5
-            new = k - step
-        new = min(new, KAPPA_MAX)
+        new = min(_positive_step(k, (A - R) / dA), KAPPA_MAX)
         done = _newton_done(k, new)
         k = new
         if done:
@@ -590,11 +588,40 @@ def mstep_emission(model: Model, W: np.ndarray, y: np.ndarray, nu_mode="ecm"):
             continue
         fn = MSTEP[model.family]
         kw = dict(nu_mode=nu_mode) if model.family == "student_t" else {}
-        res = fn(w, y, _state_params(model, j), **kw)
+        with np.errstate(all="ignore"):
+            res = fn(w, y, _state_params(model, j), **kw)
         iters[j] = res.pop("_iters", 0)
+        if not valid_update(model.family, res):   # reading: undefined update keeps theta_j
+            continue
         for k, v in res.items():
             new.params[k][j] = v
     return new, iters
+
+
+def valid_update(family, res) -> bool:
+    """Reading (extends the Sec. 4.4 collapse guard): an M-step result that is
+    not finite or leaves the family's parameter domain (a zero weighted
+    variance, a covariance that is not positive definite) is undefined on
+    the state's data, and the state keeps its parameters."""
+    vals = {k: np.asarray(v, dtype=np.float64) for k, v in res.items()}
+    if not all(np.all(np.isfinite(v)) for v in vals.values()):
+        return False
+    positive = {"gauss": ("sigma2",), "poisson": ("lam",), "gamma": ("alpha", "beta"),
+                "beta": ("a", "b"), "weibull": ("k", "lam"), "negbin": ("r",),
+                "student_t": ("sigma2", "nu"), "vonmises": (), "diag_gauss": ("var",)}
+    for k in positive.get(family, ()):
+        if not np.all(vals[k] > 0):
+            return False
+    if family == "vonmises" and not np.all(vals["kappa"] >= 0):
+        return False
+    if family == "negbin" and not (0 < vals["p"] < 1):
+        return False
+    if family == "full_gauss":
+        try:
+            np.linalg.cholesky(vals["cov"])
+        except np.linalg.LinAlgError:
+            return False
+    return True
 
 
 def mstep_transitions(model: Model, xi_sum, gamma1_sum, n_seq):

@@ -361,6 +361,9 @@ class Server:
     def _convert(self, ticket, res):
         kind, N, D, family = self._keep[ticket]
         out = dict(status=res.status, latency_ms=res.latency_ms, loglik=res.loglik)
+        if res.status != 0:
+            out["error"] = (res.error or b"").decode()
+            return out
         T = res.T
         if kind == "decode":
             out["path"] = np.ctypeslib.as_array(res.path, shape=(T,)).copy() if T else np.zeros(0, np.int32)

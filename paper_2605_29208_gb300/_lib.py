@@ -49,7 +49,7 @@ class hmm_result(C.Structure):
     _fields_ = [("status", C.c_int32), ("kind", C.c_int32), ("T", C.c_int64), ("loglik", C.c_double),
                 ("score", C.c_double), ("path", C.POINTER(C.c_int32)), ("gamma", C.POINTER(C.c_float)),
                 ("params", C.POINTER(C.c_double)), ("trace", C.POINTER(C.c_double)), ("n_iter", C.c_int32),
-                ("latency_ms", C.c_double)]
+                ("latency_ms", C.c_double), ("error", C.c_char_p)]
 
 
 REQ_DECODE, REQ_POSTERIOR, REQ_FIT = 0, 1, 2

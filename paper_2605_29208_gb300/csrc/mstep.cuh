@@ -206,18 +206,28 @@ __device__ inline bool newton_done(double old, double nw, double tol) {
   return fabs(nw - old) <= tol * fmax(1.0, fabs(old));
 }
 
+// Newton step x - step halved until the iterate stays positive, at most 64
+// times; NaN when that fails (x itself not positive, or a non-finite step),
+// which the M-step then treats as an undefined update.
+__device__ inline double positive_step(double x, double step) {
+  for (int h = 0; h < 64; ++h) {
+    const double nw = x - step;
+    if (nw > 0.0 && isfinite(nw)) return nw;
+    step *= 0.5;
+  }
+  return NAN;
+}
+
 // Gamma shape by Eq. 7-8 from the MOM seed; c = log ybar - mean log y.
 __device__ inline double gamma_shape(double ybar, double var, double c, const MStepOpts& o) {
+  // c > 0 unless every weighted observation is equal (no MLE then)
+  if (!(c > 0.0) || !(ybar > 0.0)) return NAN;
   double a = (var > 0.0) ? ybar * ybar / var : 0.5 / c;
   for (int it = 0; it < o.newton_maxit; ++it) {
     const double s = log(a) - digamma_d(a) - c;
     const double ds = 1.0 / a - trigamma_d(a);
-    double step = s / ds;
-    double nw = a - step;
-    while (nw <= 0.0) {
-      step *= 0.5;
-      nw = a - step;
-    }
+    const double nw = positive_step(a, s / ds);
+    if (!(nw > 0.0)) return NAN;
     const bool done = newton_done(a, nw, o.newton_tol);
     a = nw;
     if (done) break;
@@ -236,11 +246,16 @@ __device__ inline void beta_fit(double ybar, double var, double m1, double m2, c
     const double det = J00 * J11 - J01 * J01;
     double s0 = (J11 * F0 - J01 * F1) / det, s1 = (J00 * F1 - J01 * F0) / det;
     double na = a - s0, nb = b - s1;
-    while (na <= 0.0 || nb <= 0.0) {
+    for (int h = 0; h < 64 && !(na > 0.0 && nb > 0.0); ++h) {
       s0 *= 0.5;
       s1 *= 0.5;
       na = a - s0;
       nb = b - s1;
+    }
+    if (!(na > 0.0 && nb > 0.0 && isfinite(na) && isfinite(nb))) {
+      *pa = NAN;
+      *pb = NAN;
+      return;
     }
     const bool done = newton_done(a, na, o.newton_tol) && newton_done(b, nb, o.newton_tol);
     a = na;
@@ -257,12 +272,8 @@ __device__ inline double vonmises_kappa(double R, const MStepOpts& o) {
   for (int it = 0; it < o.newton_maxit; ++it) {
     const double A = bessel_ratio_d(k);
     const double dA = 1.0 - A * A - A / k;
-    double step = (A - R) / dA;
-    double nw = k - step;
-    while (nw <= 0.0) {
-      step *= 0.5;
-      nw = k - step;
-    }
+    double nw = positive_step(k, (A - R) / dA);
+    if (!(nw > 0.0)) return NAN;
     nw = fmin(nw, 1e6);
     const bool done = newton_done(k, nw, o.newton_tol);
     k = nw;
@@ -287,6 +298,21 @@ __device__ inline double student_nu(double W, double C, double nu0, const MStepO
   return nu;
 }
 
+// Domain check of a closed-form / Newton update (data-pass families are
+// checked when their passes finish).
+__device__ inline bool valid_update(int fam, const double* th) {
+  auto fin = [](double x) { return isfinite(x); };
+  switch (fam) {
+    case HMM_GAUSS: return fin(th[0]) && fin(th[1]) && th[1] > 0.0;
+    case HMM_POISSON: return fin(th[0]) && th[0] > 0.0;
+    case HMM_GAMMA: return fin(th[0]) && fin(th[1]) && th[0] > 0.0 && th[1] > 0.0;
+    case HMM_BETA: return fin(th[0]) && fin(th[1]) && th[0] > 0.0 && th[1] > 0.0;
+    case HMM_STUDENT_T: return fin(th[0]) && fin(th[1]) && fin(th[2]) && th[1] > 0.0 && th[2] > 0.0;
+    case HMM_VONMISES: return fin(th[0]) && fin(th[1]) && th[1] >= 0.0;
+    default: return true;
+  }
+}
+
 // One block per model, one thread per state: emission M-step of state k
 // (Sec. 4 with the collapse guard of Sec. 4.4), transition row k and pi_k,
 // then the derived tables of row k.  Families whose Newton step needs data
@@ -304,6 +330,8 @@ __global__ void mstep_kernel(ModelBufs mb, const double* __restrict__ rec, MStep
     const double W = S[0];
     const float* cf = mb.coef + ((size_t)m * NP + k) * KC;   // current shifts
     if (dps && (fam == HMM_WEIBULL || fam == HMM_NEGBIN)) dps[(size_t)m * NP + k].active = 0;
+    double old[4];
+    for (int z = 0; z < 4 && z < mb.P; ++z) old[z] = th[z];
     if (W >= o.collapse_eps) {
       switch (fam) {
         case HMM_GAUSS: {
@@ -379,6 +407,11 @@ __global__ void mstep_kernel(ModelBufs mb, const double* __restrict__ rec, MStep
         default:
           break;
       }
+      // an update that is undefined on this state's data (non-finite, or
+      // outside the family's domain, e.g. a zero weighted variance) keeps
+      // theta_j, as the collapse guard of Sec. 4.4 does for a vanishing weight
+      if (!valid_update(fam, th))
+        for (int z = 0; z < 4 && z < mb.P; ++z) th[z] = old[z];
     }
     if (o.update_transitions) {
       double* Arow = mb.A + ((size_t)m * NP + k) * NP;
@@ -566,17 +599,20 @@ __global__ void dp_update_kernel(ModelBufs mb, const double* __restrict__ rec, D
   if (fam == HMM_WEIBULL) {
     const double S0 = R[0], S1 = R[1], S2 = R[2];
     if (d.active == 2 || final) {   // scale from the converged (or last) shape
-      th[0] = d.x;
-      th[1] = exp(d.mlog + log(S0 / d.W) / d.x);
+      const double sc = exp(d.mlog + log(S0 / d.W) / d.x);
+      if (d.x > 0.0 && isfinite(d.x) && sc > 0.0 && isfinite(sc)) {
+        th[0] = d.x;
+        th[1] = sc;
+      }
       d.active = 0;
     } else {
       const double kk = d.x;
       const double f = 1.0 / kk - S1 / S0;
       const double df = -1.0 / (kk * kk) - (S2 * S0 - S1 * S1) / (S0 * S0);
-      double step = f / df, nw = kk - step;
-      while (nw <= 0.0) {
-        step *= 0.5;
-        nw = kk - step;
+      const double nw = positive_step(kk, f / df);
+      if (!(nw > 0.0)) {     // undefined on this state's data: keep theta_j
+        d.active = 0;
+        return;
       }
       d.iters++;
       const bool done = newton_done(kk, nw, tol) || d.iters >= o.newton_maxit;
@@ -587,10 +623,10 @@ __global__ void dp_update_kernel(ModelBufs mb, const double* __restrict__ rec, D
     const double r = d.x, W = d.W, ybar = d.ybar;
     const double g = R[0] + W * log(r / (r + ybar));
     const double dg = R[1] + W * (1.0 / r - 1.0 / (r + ybar));
-    double step = g / dg, nw = r - step;
-    while (nw <= 0.0) {
-      step *= 0.5;
-      nw = r - step;
+    double nw = positive_step(r, g / dg);
+    if (!(nw > 0.0)) {       // undefined on this state's data: keep theta_j
+      d.active = 0;
+      return;
     }
     nw = fmin(nw, 1e6);
     d.iters++;

@@ -75,6 +75,13 @@ __device__ inline void mv_derive_state(int fam, int D, const double* th, float* 
       Li[i * D + j] = -acc / L[i * D + i];
     }
   }
+  bool rep = true;   // the inverse factor must fit float32
+  for (int z = 0; z < D * D; ++z) rep = rep && fabs(Li[z]) < 1e30;
+  if (!rep) {
+    for (int z = 0; z < D * D; ++z) c[D + z] = 0.f;
+    c[D + D * D] = -INFINITY;
+    return;
+  }
   for (int z = 0; z < D * D; ++z) c[D + z] = (float)Li[z];
   c[D + D * D] = (float)(-0.5 * D * L2PI - logdet);
 }
@@ -195,20 +202,42 @@ __global__ void mv_mstep_kernel(const int* __restrict__ family, double* __restri
   double* th = theta + (size_t)idx * P;
   const double W = R[0];
   if (W < collapse_eps) return;                        // Sec. 4.4
-  for (int d = 0; d < D; ++d) th[d] = (double)c[d] + R[1 + d] / W;
+  double nt[32 + 32 * 32];
+  bool ok = true;
+  for (int d = 0; d < D; ++d) {
+    nt[d] = (double)c[d] + R[1 + d] / W;
+    ok = ok && isfinite(nt[d]);
+  }
   if (fam == HMM_DIAG_GAUSS) {                         // Eq. 21
     for (int d = 0; d < D; ++d) {
       const double m1 = R[1 + d] / W;
-      th[D + d] = fmax(R[1 + D + d] / W - m1 * m1, 1e-300);
+      nt[D + d] = R[1 + D + d] / W - m1 * m1;
+      ok = ok && isfinite(nt[D + d]) && nt[D + d] > 0.0;
     }
   } else {                                             // Eq. 23-24
     for (int i = 0; i < D; ++i)
       for (int j = 0; j < D; ++j) {
         const double mi = R[1 + i] / W, mj = R[1 + j] / W;
         const double cij = 0.5 * (R[1 + D + i * D + j] + R[1 + D + j * D + i]) / W - mi * mj;
-        th[D + i * D + j] = cij + (i == j ? tikhonov_eps : 0.0);
+        nt[D + i * D + j] = cij + (i == j ? tikhonov_eps : 0.0);
+      }
+    // positive definite (float64 Cholesky), else the update is undefined
+    double L[32 * 32];
+    for (int i = 0; i < D && ok; ++i)
+      for (int j = 0; j <= i && ok; ++j) {
+        double acc = nt[D + i * D + j];
+        for (int k2 = 0; k2 < j; ++k2) acc -= L[i * D + k2] * L[j * D + k2];
+        if (i == j) {
+          ok = isfinite(acc) && acc > 0.0;
+          if (ok) L[i * D + i] = sqrt(acc);
+        } else {
+          L[i * D + j] = acc / L[j * D + j];
+        }
       }
   }
+  // an undefined update keeps theta_j (the collapse guard of Sec. 4.4)
+  if (ok)
+    for (int z = 0; z < mv_coef_count(fam, D) - 1; ++z) th[z] = nt[z];
 }
 
 }  // namespace hmm

@@ -42,6 +42,7 @@ struct ServeReq {
   std::vector<float> values;
   // results
   hmm_status status = HMM_OK;
+  std::string error;
   double loglik = 0.0, score = 0.0;
   std::vector<int32_t> path;
   std::vector<float> gamma;
@@ -308,7 +309,10 @@ void slot_main(hmm_server s, Slot* sl) {
       std::lock_guard<std::mutex> lk(s->mu);
       const auto now = Clock::now();
       for (auto* r : group) {
-        if (bst != HMM_OK) r->status = bst;
+        if (bst != HMM_OK) {
+          r->status = bst;
+          r->error = msg;
+        }
         r->done = true;
         r->running = false;
         r->t_done = now;
@@ -484,6 +488,7 @@ static void fill_result(const ServeReq* r, hmm_result* out) {
   out->trace = r->trace.empty() ? nullptr : r->trace.data();
   out->n_iter = r->n_iter;
   out->latency_ms = std::chrono::duration<double, std::milli>(r->t_done - r->t_submit).count();
+  out->error = r->error.c_str();
 }
 
 hmm_status hmm_serve_poll(hmm_server s, uint64_t ticket, hmm_result* out) {

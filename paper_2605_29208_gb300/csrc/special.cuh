@@ -19,7 +19,10 @@
 
 namespace hmm {
 
+// Defined here for x > 0 only (NaN otherwise), so that the shift loops
+// below run at most 10 times.
 __host__ __device__ inline double digamma_d(double x) {
+  if (!(x > 0.0)) return NAN;
   double acc = 0.0;
   while (x < 10.0) {
     acc -= 1.0 / x;
@@ -34,6 +37,7 @@ __host__ __device__ inline double digamma_d(double x) {
 }
 
 __host__ __device__ inline double trigamma_d(double x) {
+  if (!(x > 0.0)) return NAN;
   double acc = 0.0;
   while (x < 10.0) {
     acc += 1.0 / (x * x);
@@ -49,6 +53,7 @@ __host__ __device__ inline double trigamma_d(double x) {
 // float32 versions for the per-observation Newton data passes
 // (shift to x >= 8, expansions to B_8).
 __device__ __forceinline__ float digamma_f(float x) {
+  if (!(x > 0.f)) return NAN;
   float acc = 0.f;
   while (x < 8.f) {
     acc -= 1.0f / x;
@@ -60,6 +65,7 @@ __device__ __forceinline__ float digamma_f(float x) {
 }
 
 __device__ __forceinline__ float trigamma_f(float x) {
+  if (!(x > 0.f)) return NAN;
   float acc = 0.f;
   while (x < 8.f) {
     acc += 1.0f / (x * x);

@@ -315,3 +315,54 @@ def small_models(family, N, n_models, seed, conc=1.0, D=1):
     rng = np.random.default_rng(seed)
     return [make_model(family, rng.dirichlet(np.ones(N)), dirichlet_rows(rng, N, conc),
                        **random_params(rng, family, N, D)) for _ in range(n_models)]
+
+
+def serving_workload(n_req=1000, rate=2000.0, t_min=100, t_max=100000, seed=MASTER_SEED + 5):
+    """Request stream for the server: Poisson arrivals at `rate` per second;
+    kind decode / posterior / fit (10 iterations) with probabilities 0.5 / 0.3
+    / 0.2; N uniform in {4, 16, 64, 256}; T log-uniform in [t_min, t_max];
+    emissions full-covariance Gaussian D = 8 (Wishart covariances) or Gamma,
+    half each; every request has its own model (fit requests start from a
+    perturbed copy).  Returns a list of dicts (arrival_s, kind, model,
+    values, n_iter) in arrival order."""
+    rng = np.random.default_rng(seed)
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, n_req))
+    kinds = rng.choice(["decode", "posterior", "fit"], size=n_req, p=[0.5, 0.3, 0.2])
+    Ns = rng.choice([4, 16, 64, 256], size=n_req)
+    Ts = np.round(np.exp(rng.uniform(np.log(t_min), np.log(t_max), n_req))).astype(np.int64)
+    fams = rng.choice(["full_gauss", "gamma"], size=n_req)
+    reqs = [None] * n_req
+    # hidden paths: all requests with the same N at once (time-major, vectorised)
+    for N in (4, 16, 64, 256):
+        idx = np.nonzero(Ns == N)[0]
+        if len(idx) == 0:
+            continue
+        models = []
+        for i in idx:
+            D = 8 if fams[i] == "full_gauss" else 1
+            models.append(make_model(fams[i], np.full(N, 1.0 / N), dirichlet_rows(rng, N, 1.0),
+                                     **random_params(rng, fams[i], N, D)))
+        lengths = Ts[idx]
+        cA = np.cumsum(np.stack([m["A"] for m in models]), axis=2)
+        S = len(idx)
+        offsets = np.zeros(S + 1, np.int64)
+        np.cumsum(lengths, out=offsets[1:])
+        states = np.empty(int(offsets[-1]), np.int64)
+        cur = rng.integers(0, N, S)
+        alive = np.arange(S)
+        for t in range(int(lengths.max())):
+            alive_now = alive[lengths[alive] > t]
+            if t > 0:
+                rows = cA[alive_now, cur[alive_now]]
+                u = rng.random(len(alive_now))[:, None]
+                cur[alive_now] = np.minimum((u * rows[:, -1:] >= rows).sum(1), N - 1)
+            states[offsets[alive_now] + t] = cur[alive_now]
+            alive = alive_now
+        for k, i in enumerate(idx):
+            q = states[offsets[k]:offsets[k + 1]]
+            y = sample_emissions(rng, models[k], q)
+            y = np.asarray(y, np.float32)
+            init = perturb(rng, models[k]) if kinds[i] == "fit" else models[k]
+            reqs[i] = dict(arrival_s=float(arrivals[i]), kind=str(kinds[i]), model=init, values=y,
+                           n_iter=10 if kinds[i] == "fit" else 0)
+    return reqs

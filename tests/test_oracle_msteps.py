@@ -297,3 +297,25 @@ def test_special_function_values():
     # asymptote 1 - 1/(2 kappa)
     assert abs(O.bessel_ratio(1e-3) - (5e-4 - 1e-9 / 16)) < 1e-15
     assert abs(O.bessel_ratio(1e4) - (1 - 1 / 2e4 - 1 / (8e8))) < 1e-11
+
+
+def test_undefined_update_keeps_parameters():
+    """Reading of the Sec. 4.4 guard: a state whose weighted data make the
+    update undefined (zero variance, zero rate) keeps its parameters, while
+    the other states update."""
+    y = np.array([0.0, 1.0, 2.0, 3.0, 4.0])
+    W = np.zeros((5, 2))
+    W[2, 0] = 1.0                      # state 0: one observation -> variance 0
+    W[:, 1] = 1.0                      # state 1: all observations
+    m = O.Model("gauss", np.array([0.5, 0.5]), np.full((2, 2), 0.5),
+                {"mu": np.array([7.0, 8.0]), "sigma2": np.array([3.0, 4.0])})
+    new, _ = O.mstep_emission(m, W, y)
+    assert new.params["mu"][0] == 7.0 and new.params["sigma2"][0] == 3.0
+    assert new.params["mu"][1] == 2.0 and abs(new.params["sigma2"][1] - 2.0) < 1e-12
+    yp = np.array([0.0, 0.0, 3.0])
+    Wp = np.array([[1.0, 0.0], [1.0, 0.0], [0.0, 1.0]])
+    mp = O.Model("poisson", np.array([0.5, 0.5]), np.full((2, 2), 0.5), {"lam": np.array([2.5, 1.0])})
+    newp, _ = O.mstep_emission(mp, Wp, yp)
+    assert newp.params["lam"][0] == 2.5 and newp.params["lam"][1] == 3.0
+    assert O.valid_update("full_gauss", {"mu": np.zeros(2), "cov": np.eye(2)})
+    assert not O.valid_update("full_gauss", {"mu": np.zeros(2), "cov": np.array([[1.0, 2.0], [2.0, 1.0]])})
