@@ -382,8 +382,9 @@ hmm_status hmm_serve_poll(hmm_server server, uint64_t ticket, hmm_result* out);
 hmm_status hmm_serve_wait(hmm_server server, uint64_t ticket, double timeout_ms, hmm_result* out);
 /* Frees a completed request's results. */
 hmm_status hmm_serve_release(hmm_server server, uint64_t ticket);
-/* h_out[8]: submitted, completed, p50 ms, p99 ms, mean ms, completed per
- * second since the first submission, pending, running. */
+/* h_out[10]: submitted, completed, p50 ms, p99 ms, mean ms, completed per
+ * second since the first submission, pending, running, batches run, mean
+ * slot occupancy (time the slots spent running batches / (slots x span)). */
 hmm_status hmm_serve_stats(hmm_server server, double* h_out);
 /* Finishes the running batches, drops pending requests, frees everything. */
 hmm_status hmm_serve_destroy(hmm_server server);

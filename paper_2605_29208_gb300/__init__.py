@@ -396,9 +396,10 @@ class Server:
         return out
 
     def stats(self) -> dict:
-        h = np.zeros(8, np.float64)
+        h = np.zeros(10, np.float64)
         check(self.lib.hmm_serve_stats(self.h, h.ctypes.data_as(C.c_void_p)))
-        keys = ("submitted", "completed", "p50_ms", "p99_ms", "mean_ms", "completed_per_s", "pending", "running")
+        keys = ("submitted", "completed", "p50_ms", "p99_ms", "mean_ms", "completed_per_s", "pending", "running",
+                "batches", "slot_occupancy")
         return dict(zip(keys, h.tolist()))
 
     def close(self):

@@ -16,6 +16,10 @@
 namespace hmm {
 
 static thread_local std::string g_last_error;
+cudaStream_t& alloc_stream() {
+  static thread_local cudaStream_t s = nullptr;
+  return s;
+}
 void set_error(const std::string& msg) { g_last_error = msg; }
 
 template <class F>

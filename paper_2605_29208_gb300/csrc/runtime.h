@@ -34,27 +34,49 @@ struct Error {
     if (!(cond)) throw ::hmm::Error{HMM_E_ARG, std::string(msg)};         \
   } while (0)
 
+// Stream for stream-ordered allocation on this thread (nullptr: plain
+// cudaMalloc / cudaFree).  The request server's slot threads set it to their
+// stream, so that growing a buffer never waits for the other slots' work
+// (cudaFree synchronises the whole device).
+cudaStream_t& alloc_stream();
+
 // A growable device buffer owned by the library.
 struct DevBuf {
   void* p = nullptr;
   size_t bytes = 0;
-  void ensure(size_t n) {
-    if (n <= bytes) return;
-    if (p) cudaFree(p);
+  cudaStream_t owner = nullptr;   // stream of a stream-ordered allocation
+  void free_now() {
+    if (!p) return;
+    if (owner) {
+      // stream-ordered memory is returned on the stream it was taken on
+      cudaFreeAsync(p, owner);
+    } else {
+      cudaFree(p);
+    }
     p = nullptr;
     bytes = 0;
-    cudaError_t e = cudaMalloc(&p, n);
+    owner = nullptr;
+  }
+  void ensure(size_t n) {
+    if (n <= bytes) return;
+    free_now();
+    cudaStream_t s = alloc_stream();
+    cudaError_t e;
+    if (s) {
+      e = cudaMallocAsync(&p, n, s);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(s);   // usable from any stream
+      owner = s;
+    } else {
+      e = cudaMalloc(&p, n);
+    }
     if (e != cudaSuccess) {
       p = nullptr;
+      owner = nullptr;
       throw Error{HMM_E_NOMEM, "cudaMalloc(" + std::to_string(n) + "): " + cudaGetErrorString(e)};
     }
     bytes = n;
   }
-  void release() {
-    if (p) cudaFree(p);
-    p = nullptr;
-    bytes = 0;
-  }
+  void release() { free_now(); }
   template <class T>
   T* as() const {
     return reinterpret_cast<T*>(p);

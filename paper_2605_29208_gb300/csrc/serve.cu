@@ -59,20 +59,17 @@ std::string model_key(const ServeReq* r) {
   return std::to_string(r->family) + "/" + std::to_string(r->N) + "/" + std::to_string(r->D);
 }
 
-// Pinned host staging that only grows.
-struct Pinned {
+// Host staging that only grows.  Pageable on purpose: cudaMallocHost /
+// cudaFreeHost synchronise the whole device, which would make one slot's
+// growth wait for every other slot's kernels; the copies from and to pageable
+// memory only block the calling slot thread.
+struct Staging {
+  std::vector<char> buf;
   void* p = nullptr;
-  size_t bytes = 0;
   void ensure(size_t n) {
-    if (n <= bytes) return;
-    if (p) cudaFreeHost(p);
-    p = nullptr;
-    bytes = 0;
-    HMM_CUDA(cudaMallocHost(&p, n));
-    bytes = n;
-  }
-  ~Pinned() {
-    if (p) cudaFreeHost(p);
+    if (n <= buf.size()) return;
+    buf.resize(std::max(n, 2 * buf.size()));
+    p = buf.data();
   }
   template <class T>
   T* as() {
@@ -92,7 +89,7 @@ struct Slot {
   std::map<std::string, hmm_stats> stats;
   hmm_plan plan = nullptr;
   DevBuf values, offsets, model_id, loglik, score, path, gamma;
-  Pinned h_in, h_out;
+  Staging h_in, h_out;
 };
 
 }  // namespace
@@ -112,7 +109,8 @@ struct hmm_server_s {
   bool stop = false;
   uint64_t next_ticket = 1;
   std::vector<double> lat_ms;
-  uint64_t submitted = 0, completed = 0;
+  uint64_t submitted = 0, completed = 0, batches = 0;
+  double busy_s = 0.0;          // summed slot time spent running batches
   int running = 0;
   Clock::time_point t_first, t_last;
   bool any = false;
@@ -286,6 +284,7 @@ void run_batch(hmm_server s, Slot* sl, std::vector<ServeReq*>& group) {
 
 void slot_main(hmm_server s, Slot* sl) {
   cudaSetDevice(s->device);
+  alloc_stream() = sl->stream;   // this slot's buffers grow without device-wide syncs
   for (;;) {
     std::vector<ServeReq*> group;
     {
@@ -296,6 +295,7 @@ void slot_main(hmm_server s, Slot* sl) {
     }
     hmm_status bst = HMM_OK;
     std::string msg;
+    const auto tb = Clock::now();
     try {
       run_batch(s, sl, group);
     } catch (const Error& e) {
@@ -320,6 +320,8 @@ void slot_main(hmm_server s, Slot* sl) {
         ++s->completed;
       }
       s->t_last = now;
+      s->busy_s += std::chrono::duration<double>(now - tb).count();
+      ++s->batches;
       s->used -= sl->bytes;
       sl->bytes = 0;
       sl->busy = false;
@@ -394,6 +396,13 @@ hmm_status hmm_serve_create(hmm_ctx ctx, const hmm_serve_opts* opts, hmm_server*
     }
     try {
       HMM_CUDA(cudaSetDevice(s->device));
+      {
+        // keep freed stream-ordered memory in this process's pool
+        cudaMemPool_t pool;
+        HMM_CUDA(cudaDeviceGetDefaultMemPool(&pool, s->device));
+        uint64_t thr = UINT64_MAX;
+        HMM_CUDA(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr));
+      }
       if (s->budget == 0) {
         size_t fr = 0, tot = 0;
         HMM_CUDA(cudaMemGetInfo(&fr, &tot));
@@ -574,6 +583,8 @@ hmm_status hmm_serve_stats(hmm_server s, double* h) {
   h[5] = span > 0 ? s->completed / span : 0.0;
   h[6] = (double)s->queue.size();
   h[7] = (double)s->running;
+  h[8] = (double)s->batches;
+  h[9] = span > 0 ? s->busy_s / (span * s->n_slots) : 0.0;
   return HMM_OK;
 }
 
@@ -592,13 +603,16 @@ hmm_status hmm_serve_destroy(hmm_server s) {
   cudaSetDevice(s->device);
   for (auto* sl : s->slots) {
     if (sl->stream) cudaStreamSynchronize(sl->stream);
+    alloc_stream() = sl->stream;
     for (auto& kv : sl->stats) hmm_stats_destroy(kv.second);
     for (auto& kv : sl->models) hmm_model_destroy(kv.second);
     if (sl->plan) destroy_plan(sl->plan);
     for (auto* b : {&sl->values, &sl->offsets, &sl->model_id, &sl->loglik, &sl->score, &sl->path, &sl->gamma})
       b->release();
-    if (sl->stream) cudaStreamDestroy(sl->stream);
+    if (sl->stream) cudaStreamSynchronize(sl->stream);
+    alloc_stream() = nullptr;
     if (sl->ctx) hmm_ctx_destroy(sl->ctx);
+    if (sl->stream) cudaStreamDestroy(sl->stream);
     delete sl;
   }
   for (auto& kv : s->reqs) delete kv.second;
