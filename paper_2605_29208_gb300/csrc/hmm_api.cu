@@ -426,6 +426,37 @@ void get_plan(hmm_ctx ctx, hmm_model model, const hmm_batch* b, cudaStream_t st,
   ref.owned = true;
 }
 
+// Multivariate emission table: the tiled kernel when the model set has one
+// multivariate family it covers, else the generic kernel.
+void launch_mv_emission(hmm_model model, const hmm_batch* b, hmm_plan plan, float* out, cudaStream_t st) {
+  int fam = model->h_family[0];
+  for (int f : model->h_family)
+    if (f != fam) fam = -1;
+  const int D = model->D;
+  if (fam == HMM_DIAG_GAUSS || (fam == HMM_FULL_GAUSS && D <= MV_TILED_FULL_D)) {
+    const dim3 grid((unsigned)plan->n_tiles, (unsigned)((model->N + 63) / 64));
+    const size_t smem = ((size_t)32 * (D + 1) + (size_t)64 * (model->KM | 1)) * 4;
+    if (fam == HMM_DIAG_GAUSS) {
+      auto kern = mv_emission_tiled_kernel<HMM_DIAG_GAUSS>;
+      HMM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      kern<<<grid, 256, smem, st>>>(model->mvcoef.as<float>(), model->NP, model->N, D, model->KM, b->values,
+                                    b->offsets, b->model_id, plan->tile_seq.as<int32_t>(),
+                                    plan->tile_row.as<int32_t>(), out);
+    } else {
+      auto kern = mv_emission_tiled_kernel<HMM_FULL_GAUSS>;
+      HMM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      kern<<<grid, 256, smem, st>>>(model->mvcoef.as<float>(), model->NP, model->N, D, model->KM, b->values,
+                                    b->offsets, b->model_id, plan->tile_seq.as<int32_t>(),
+                                    plan->tile_row.as<int32_t>(), out);
+    }
+  } else {
+    mv_emission_kernel<<<(unsigned)plan->n_tiles, 128, (size_t)32 * D * 4, st>>>(
+        model->family.as<int>(), model->mvcoef.as<float>(), model->NP, model->N, D, model->KM, b->values, b->offsets,
+        b->model_id, plan->tile_seq.as<int32_t>(), plan->tile_row.as<int32_t>(), out);
+  }
+  HMM_CUDA(cudaGetLastError());
+}
+
 // log b table of the batch in the context's buffer: multivariate families
 // (Sec. 4.5) one block per 32-row tile of a sequence, scalar families one
 // block per sequence.
@@ -440,12 +471,7 @@ const float* mv_table(hmm_ctx ctx, hmm_model model, const hmm_batch* b, hmm_plan
     }
   } else if (plan->n_tiles > 0) {
     KTimer kt(ctx, HMM_KT_EMISSION, st);
-    const size_t smem = (size_t)32 * model->D * 4;
-    mv_emission_kernel<<<(unsigned)plan->n_tiles, 128, smem, st>>>(
-        model->family.as<int>(), model->mvcoef.as<float>(), model->NP, model->N, model->D, model->KM, b->values,
-        b->offsets, b->model_id, plan->tile_seq.as<int32_t>(), plan->tile_row.as<int32_t>(),
-        ctx->mvlogb.as<float>());
-    HMM_CUDA(cudaGetLastError());
+    launch_mv_emission(model, b, plan, ctx->mvlogb.as<float>(), st);
   }
   return ctx->mvlogb.as<float>();
 }
@@ -1201,11 +1227,7 @@ hmm_status hmm_emission_logpdf(hmm_ctx ctx, hmm_model model, const hmm_batch* ba
       get_plan(ctx, model, batch, S(stream), pr);
       if (pr.p->n_tiles > 0) {
         KTimer kt(ctx, HMM_KT_EMISSION, S(stream));
-        mv_emission_kernel<<<(unsigned)pr.p->n_tiles, 128, (size_t)32 * model->D * 4, S(stream)>>>(
-            model->family.as<int>(), model->mvcoef.as<float>(), model->NP, model->N, model->D, model->KM,
-            batch->values, batch->offsets, batch->model_id, pr.p->tile_seq.as<int32_t>(),
-            pr.p->tile_row.as<int32_t>(), d_logb);
-        HMM_CUDA(cudaGetLastError());
+        launch_mv_emission(model, batch, pr.p, d_logb, S(stream));
       }
       if (pr.owned) HMM_CUDA(cudaStreamSynchronize(S(stream)));
       return;

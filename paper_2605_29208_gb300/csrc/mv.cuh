@@ -362,3 +362,93 @@ __global__ void mv_shift_kernel(const int* __restrict__ family, const float* __r
 }
 
 }  // namespace hmm
+
+namespace hmm {
+
+// Tiled form of mv_emission_kernel: a block computes one 32-row tile of a
+// sequence for 64 states, with the rows and the states' tables staged in
+// shared memory; a thread owns 2 rows x 4 states.  Diagonal Gaussian for any
+// D <= 32, full covariance for D <= MV_TILED_FULL_D (the triangular solve
+// keeps the D differences of a (row, state) pair in registers).
+constexpr int MV_TILED_FULL_D = 16;
+
+template <int FAM>
+__global__ void __launch_bounds__(256) mv_emission_tiled_kernel(const float* __restrict__ mvc, int NP, int N, int D,
+                                                                int KM, const float* __restrict__ y,
+                                                                const int64_t* __restrict__ offsets,
+                                                                const int32_t* __restrict__ model_id,
+                                                                const int32_t* __restrict__ tile_seq,
+                                                                const int32_t* __restrict__ tile_row,
+                                                                float* __restrict__ logb) {
+  extern __shared__ float msm[];
+  const int KMP = KM | 1;                  // odd stride: state rows on different banks
+  float* ys = msm;                         // [32][D + 1]
+  float* cs = ys + 32 * (D + 1);           // [64][KMP]
+  const int s = tile_seq[blockIdx.x];
+  const int64_t r0 = offsets[s] + tile_row[blockIdx.x];
+  const int nr = (int)min((int64_t)32, offsets[s + 1] - r0);
+  const int m = model_id[s];
+  const int k0 = blockIdx.y * 64;
+  const int nk = min(64, N - k0);
+  for (int z = threadIdx.x; z < nr * D; z += blockDim.x) ys[(z / D) * (D + 1) + z % D] = y[r0 * D + z];
+  for (int z = threadIdx.x; z < nk * KM; z += blockDim.x)
+    cs[(z / KM) * KMP + z % KM] = mvc[((size_t)m * NP + k0 + z / KM) * KM + z % KM];
+  __syncthreads();
+  const int ty = threadIdx.x / 16, tx = threadIdx.x % 16;
+  const int ra = ty * 2;
+  float acc[2][4];
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc[a][q] = 0.f;
+  if constexpr (FAM == HMM_DIAG_GAUSS) {
+    for (int d = 0; d < D; ++d) {
+      const float y0 = ys[ra * (D + 1) + d], y1 = ys[(ra + 1) * (D + 1) + d];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const float* c = cs + (tx * 4 + q) * KMP;
+        const float mu = c[d], h = c[D + d];
+        const float e0 = y0 - mu, e1 = y1 - mu;
+        acc[0][q] = fmaf(h * e0, e0, acc[0][q]);
+        acc[1][q] = fmaf(h * e1, e1, acc[1][q]);
+      }
+    }
+  } else {
+#pragma unroll
+    for (int a = 0; a < 2; ++a) {
+      const float* yr = ys + (ra + a) * (D + 1);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const float* c = cs + (tx * 4 + q) * KMP;
+        float e[MV_TILED_FULL_D];
+#pragma unroll
+        for (int j = 0; j < MV_TILED_FULL_D; ++j) e[j] = j < D ? yr[j] - c[j] : 0.f;
+        const float* Li = c + D;
+        float qq = 0.f;
+#pragma unroll
+        for (int i = 0; i < MV_TILED_FULL_D; ++i) {
+          if (i >= D) break;
+          float zi = 0.f;
+#pragma unroll
+          for (int j = 0; j <= i; ++j) zi = fmaf(Li[i * D + j], e[j], zi);
+          qq = fmaf(zi, zi, qq);
+        }
+        acc[a][q] = qq;
+      }
+    }
+  }
+#pragma unroll
+  for (int a = 0; a < 2; ++a) {
+    if (ra + a >= nr) continue;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int k = tx * 4 + q;
+      if (k >= nk) continue;
+      const float* c = cs + k * KMP;
+      const float cst = FAM == HMM_DIAG_GAUSS ? c[2 * D] : c[D + D * D];
+      logb[(r0 + ra + a) * N + k0 + k] = FAM == HMM_DIAG_GAUSS ? cst - acc[a][q] : cst - 0.5f * acc[a][q];
+    }
+  }
+}
+
+}  // namespace hmm
