@@ -304,7 +304,7 @@ void hmm::fill_plan(hmm_plan p, hmm_ctx ctx, hmm_model model, const hmm_batch* b
       HMM_CUDA(cudaMemcpy(p->chunk_hi.p, hi.data(), hi.size() * 4, cudaMemcpyHostToDevice));
     }
     HMM_CUDA(cudaMemcpy(p->model_chunk_ptr.p, mptr.data(), mptr.size() * 4, cudaMemcpyHostToDevice));
-    if (model->any_mv && S > 0) {
+    if ((model->any_mv || model->NP > 32) && S > 0) {
       std::vector<int32_t> ts, tr;
       for (int64_t q2 = 0; q2 < S; ++q2)
         for (int64_t r = 0; r < ho[q2 + 1] - ho[q2]; r += 32) {
@@ -317,6 +317,37 @@ void hmm::fill_plan(hmm_plan p, hmm_ctx ctx, hmm_model model, const hmm_batch* b
       if (!ts.empty()) {
         HMM_CUDA(cudaMemcpy(p->tile_seq.p, ts.data(), ts.size() * 4, cudaMemcpyHostToDevice));
         HMM_CUDA(cudaMemcpy(p->tile_row.p, tr.data(), tr.size() * 4, cudaMemcpyHostToDevice));
+      }
+    }
+    if (model->NP > 32 && S > 0) {
+      // K layout of the tensor-core xi: the chunks' rows (t < T - 1) one
+      // after another, each chunk padded to a multiple of 32
+      std::vector<int64_t> kseq(S, 0), kc0(lo.size());
+      std::vector<int32_t> kused(lo.size()), kpad(lo.size());
+      int64_t ktot = 0;
+      for (size_t c = 0; c < lo.size(); ++c) {
+        kc0[c] = ktot;
+        int64_t used = 0;
+        for (int32_t q2 = lo[c]; q2 < hi[c]; ++q2) {
+          const int32_t sq = bym[q2];
+          kseq[sq] = ktot + used;
+          used += std::max<int64_t>(ho[sq + 1] - ho[sq] - 1, 0);
+        }
+        HMM_REQUIRE(used < (1ll << 31) - 64, "chunk too long for the xi layout");
+        kused[c] = (int32_t)used;
+        kpad[c] = (int32_t)((used + 31) / 32 * 32);
+        ktot += kpad[c];
+      }
+      p->xi_ktot = std::max<int64_t>(ktot, 32);
+      p->xi_kseq.ensure((size_t)S * 8);
+      p->xi_kc0.ensure(std::max<size_t>(lo.size(), 1) * 8);
+      p->xi_kused.ensure(std::max<size_t>(lo.size(), 1) * 4);
+      p->xi_kpad.ensure(std::max<size_t>(lo.size(), 1) * 4);
+      HMM_CUDA(cudaMemcpy(p->xi_kseq.p, kseq.data(), (size_t)S * 8, cudaMemcpyHostToDevice));
+      if (!lo.empty()) {
+        HMM_CUDA(cudaMemcpy(p->xi_kc0.p, kc0.data(), lo.size() * 8, cudaMemcpyHostToDevice));
+        HMM_CUDA(cudaMemcpy(p->xi_kused.p, kused.data(), lo.size() * 4, cudaMemcpyHostToDevice));
+        HMM_CUDA(cudaMemcpy(p->xi_kpad.p, kpad.data(), lo.size() * 4, cudaMemcpyHostToDevice));
       }
     }
     if (model->NP > 32 && S > 0) {
@@ -382,6 +413,7 @@ void hmm::destroy_plan(hmm_plan p) {
   p->tile_row.release();
   p->lg_groups.release();
   p->tc_tiles.release();
+  for (auto* bb : {&p->xi_kseq, &p->xi_kc0, &p->xi_kused, &p->xi_kpad}) bb->release();
   delete p;
 }
 
@@ -577,8 +609,18 @@ void run_estep_large(hmm_ctx ctx, hmm_model model, const hmm_batch* b, hmm_plan 
   if (!want_stats) return;
   const bool table_stats = model->any_mv;
   HMM_CUDA(launch_large_stats(a, b->values, gamma, S, table_stats, ctx->partials.as<float>(), st));
-  HMM_CUDA(launch_large_xi(a, ctx->lg_rz.as<float>(), plan->seq_by_model.as<int32_t>(), plan->chunk_lo.as<int32_t>(),
-                           plan->chunk_hi.as<int32_t>(), plan->n_chunks, ctx->lg_xi.as<double>(), st));
+  if (ctx->tensor_rec && tc_xi_supported(NP)) {
+    ctx->xi_xt.ensure((size_t)NP * plan->xi_ktot * 4);
+    ctx->xi_yt.ensure((size_t)NP * plan->xi_ktot * 4);
+    HMM_CUDA(launch_tc_xi(a, ctx->lg_rz.as<float>(), plan->tile_seq.as<int32_t>(), plan->tile_row.as<int32_t>(),
+                          plan->n_tiles, plan->xi_kseq.as<int64_t>(), plan->xi_kc0.as<int64_t>(),
+                          plan->xi_kused.as<int32_t>(), plan->xi_kpad.as<int32_t>(), plan->n_chunks, plan->xi_ktot,
+                          ctx->xi_xt.as<float>(), ctx->xi_yt.as<float>(), ctx->lg_xi.as<double>(), ctx->status, st));
+  } else {
+    HMM_CUDA(launch_large_xi(a, ctx->lg_rz.as<float>(), plan->seq_by_model.as<int32_t>(),
+                             plan->chunk_lo.as<int32_t>(), plan->chunk_hi.as<int32_t>(), plan->n_chunks,
+                             ctx->lg_xi.as<double>(), st));
+  }
   HMM_CUDA(launch_large_reduce(ctx->partials.as<float>(), ll, ctx->lg_xi.as<double>(),
                                plan->seq_by_model.as<int32_t>(), plan->chunk_lo.as<int32_t>(),
                                plan->chunk_hi.as<int32_t>(), plan->n_chunks, NP, ctx->chunk_rec.as<double>(), st));
@@ -904,6 +946,8 @@ hmm_status hmm_ctx_destroy(hmm_ctx ctx) {
     ctx->lg_off.release();
     ctx->lg_rz.release();
     ctx->lg_xi.release();
+    ctx->xi_xt.release();
+    ctx->xi_yt.release();
     delete ctx;
   });
 }

@@ -43,6 +43,14 @@ bool tc_supported(int NP);
 int tc_tile_rows();
 cudaError_t launch_tc_fb(int NP, const LargeArgs& a, const int32_t* tiles, int n_tiles, int* status,
                          cudaStream_t st);
+// xi blocks on the tensor cores (TF32, K = time), padded N 128-1024: the
+// transposed operands XT / YT [NP][ktot] float32 in the chunk-ordered K layout
+// of the plan (kseq, kc0, kused, kpad), then the GEMM into xi_chunk
+bool tc_xi_supported(int NP);
+cudaError_t launch_tc_xi(const LargeArgs& a, const float* rz, const int32_t* tile_seq, const int32_t* tile_row,
+                         int n_tiles, const int64_t* kseq, const int64_t* kc0, const int32_t* kused,
+                         const int32_t* kpad, int n_chunks, int64_t ktot, float* XT, float* YT, double* xi_chunk,
+                         int* status, cudaStream_t st);
 // posterior rows: gamma [total_T][N], 1/Z_t [total_T], log-likelihoods
 cudaError_t launch_large_post(const LargeArgs& a, int NP, int N, int64_t n_seq, float* gamma, float* rz,
                               double* loglik, int* status, cudaStream_t st);

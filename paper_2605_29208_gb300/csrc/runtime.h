@@ -106,6 +106,7 @@ struct hmm_ctx_s {
   hmm::DevBuf lg_off;            // [2][total_T] float64 log2 offsets (forward, backward)
   hmm::DevBuf lg_rz;             // [total_T] 1 / Z_t
   hmm::DevBuf lg_xi;             // [n_chunks][NP][NP] float64 xi blocks
+  hmm::DevBuf xi_xt, xi_yt;      // [NP][xi_ktot] float32 operands of the tensor-core xi
   // options
   int profile = 0;
   int estep_lanes = 0;
@@ -172,6 +173,11 @@ struct hmm_plan_s {
   int n_groups = 0;
   hmm::DevBuf tc_tiles;          // [n_tc_tiles][tc_tile_rows()] tiles of the tensor-core recursions
   int n_tc_tiles = 0;
+  // chunk-ordered K layout of the tensor-core xi (padded N > 32): row t of
+  // sequence s sits at K index xi_kseq[s] + t; chunk c covers
+  // [xi_kc0[c], xi_kc0[c] + xi_kpad[c]) of which xi_kused[c] are rows
+  hmm::DevBuf xi_kseq, xi_kc0, xi_kused, xi_kpad;
+  int64_t xi_ktot = 0;
   int viterbi_G = 0;
   std::vector<int32_t> h_order;
 };

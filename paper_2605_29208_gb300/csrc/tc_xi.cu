@@ -1,0 +1,249 @@
+// xi on the tensor cores for large N (S6 of the path: sum_t xi_t as a GEMM
+// with K = time):  Xi_c(i, j) = sum over the rows t < T-1 of chunk c's
+// sequences of X_t(i) Y_t(j), with X_t = v_t / Z_t (forward row over Z_t) and
+// Y_t = z_{t+1} = bt_{t+1} 2^(log2 b(t+1) - E_{t+1}).
+//
+// 1. xi_prep_kernel writes X and Y transposed (states x K, float32, K
+//    contiguous) in a chunk-ordered K layout: the rows of a chunk's
+//    sequences are consecutive, each chunk's range padded to a multiple of 32
+//    with zeros; a 32 x 32 shared-memory transpose per block.
+// 2. xi_tc_kernel: one CTA per (128 i, up to 256 j, chunk) tile, K-blocks of
+//    32 (128 bytes) staged by cp.async into the 128-byte-swizzled K-major
+//    layout, 4 stages; one thread issues tcgen05.mma.kind::tf32 (M = 128,
+//    N = 256, K = 8) into TMEM; the epilogue writes the float64 block.
+// TF32 keeps float32's exponent range (1/Z_t can be large) with 10
+// significant bits, the same as the FP16 recursions.
+#include "launch.h"
+#include "tc_common.cuh"
+
+namespace hmm {
+namespace {
+
+using namespace tc;
+
+constexpr int XI_KB = 32;          // K elements per block (128 bytes of TF32)
+constexpr int XI_STAGES = 4;
+constexpr int XI_TM = 128;
+
+__global__ void __launch_bounds__(256) xi_prep_kernel(const float* __restrict__ fv, const float* __restrict__ bv,
+                                                      const double* __restrict__ ob, const float* __restrict__ rz,
+                                                      const float* __restrict__ logb, const int64_t* __restrict__ offsets,
+                                                      const int32_t* __restrict__ tile_seq,
+                                                      const int32_t* __restrict__ tile_row,
+                                                      const int64_t* __restrict__ kseq, int NP, int N, int64_t ktot,
+                                                      float* __restrict__ XT, float* __restrict__ YT) {
+  __shared__ float xs[32][33], ysh[32][33];
+  const int s = tile_seq[blockIdx.x];
+  const int64_t b = offsets[s], e = offsets[s + 1];
+  const int t0 = tile_row[blockIdx.x];
+  const int i0 = blockIdx.y * 32;
+  const int tx = threadIdx.x % 32, ty = threadIdx.x / 32;   // 32 x 8
+  // load: rows t0 + r (r = ty, ty + 8, ...), states i0 + tx
+  for (int r = ty; r < 32; r += 8) {
+    const int64_t t = b + t0 + r;
+    float xv = 0.f, yv = 0.f;
+    if (t + 1 < e) {
+      const int i = i0 + tx;
+      xv = fv[t * NP + i] * rz[t];
+      if (i < N) {
+        const float E = (float)(ob[t] - ob[t + 1]);
+        const float w = bv[(t + 1) * NP + i];
+        yv = w > 0.f ? exp2f(logb[(t + 1) * N + i] * 1.4426950408889634f + log2f(w) - E) : 0.f;
+      }
+    }
+    xs[r][tx] = xv;
+    ysh[r][tx] = yv;
+  }
+  __syncthreads();
+  // store transposed: state i0 + r, K index kseq[s] + t0 + tx
+  const int64_t k = kseq[s] + t0 + tx;
+  const bool valid = b + t0 + tx + 1 < e;
+  for (int r = ty; r < 32; r += 8) {
+    if (valid) {
+      XT[(size_t)(i0 + r) * ktot + k] = xs[tx][r];
+      YT[(size_t)(i0 + r) * ktot + k] = ysh[tx][r];
+    }
+  }
+}
+
+// zeros in the padding of each chunk's K range: [kc0 + used, kc0 + padded)
+__global__ void xi_pad_kernel(const int64_t* __restrict__ kc0, const int32_t* __restrict__ kused,
+                              const int32_t* __restrict__ kpad, int NP, int64_t ktot, float* XT, float* YT) {
+  const int c = blockIdx.x;
+  const int npad = kpad[c] - kused[c];
+  for (int z = threadIdx.x; z < npad * NP; z += blockDim.x) {
+    const int i = z / npad, q = z % npad;
+    const int64_t k = kc0[c] + kused[c] + q;
+    XT[(size_t)i * ktot + k] = 0.f;
+    YT[(size_t)i * ktot + k] = 0.f;
+  }
+}
+
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+}
+
+template <int TN>
+__global__ void __launch_bounds__(128, 1) xi_tc_kernel(const float* __restrict__ XT, const float* __restrict__ YT,
+                                                       int64_t ktot, const int64_t* __restrict__ kc0,
+                                                       const int32_t* __restrict__ kpad, int NP,
+                                                       double* __restrict__ xi_chunk, int* status) {
+  constexpr uint32_t A_BYTES = XI_TM * 128, B_BYTES = TN * 128, STAGE = A_BYTES + B_BYTES;
+  extern __shared__ uint8_t xr[];
+  uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(xr) + 1023) & ~uintptr_t(1023));
+  uint64_t* mb = reinterpret_cast<uint64_t*>(sm + XI_STAGES * STAGE);   // [XI_STAGES] MMA done per stage
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(mb + XI_STAGES);
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int tj_count = NP / TN;
+  const int ti = blockIdx.x / tj_count, tj = blockIdx.x % tj_count;
+  const int c = blockIdx.y;
+  const int64_t k0 = kc0[c];
+  const int nkb = kpad[c] / XI_KB;
+  if (tid == 0) {
+    for (int z = 0; z < XI_STAGES; ++z) mbar_init(&mb[z], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
+                 "r"(TN));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tslot;
+  const float* Ab = XT + (size_t)(ti * XI_TM) * ktot + k0;
+  const float* Bb = YT + (size_t)(tj * TN) * ktot + k0;
+  auto load_stage = [&](int kb, int st) {
+    const uint32_t sa = smem_u32(sm + st * STAGE), sb = sa + A_BYTES;
+    const int64_t ko = (int64_t)kb * XI_KB;
+    for (int z = tid; z < XI_TM * 8; z += 128) {
+      const int row = z >> 3, q = z & 7;
+      cp_async16(sa + sw128_chunk(row, q), Ab + (size_t)row * ktot + ko + q * 4);
+    }
+    for (int z = tid; z < TN * 8; z += 128) {
+      const int row = z >> 3, q = z & 7;
+      cp_async16(sb + sw128_chunk(row, q), Bb + (size_t)row * ktot + ko + q * 4);
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  };
+  const uint32_t idesc = tc_idesc_tf32(XI_TM, TN);
+  // prologue: stages 0 .. XI_STAGES-2
+  for (int z = 0; z < XI_STAGES - 1; ++z) {
+    if (z < nkb) load_stage(z, z);
+    else asm volatile("cp.async.commit_group;" ::: "memory");
+  }
+  for (int kb = 0; kb < nkb; ++kb) {
+    const int st = kb % XI_STAGES;
+    // refill the stage that the MMA of kb - 1 used once that MMA is done
+    const int nk = kb + XI_STAGES - 1;
+    if (nk < nkb) {
+      const int ns = nk % XI_STAGES;
+      if (kb >= 1) {
+        // the stage ns was last read by the MMAs of block nk - XI_STAGES = kb - 1
+        if (!mbar_wait(&mb[ns], (uint32_t)(((kb - 1) / XI_STAGES) & 1))) {
+          if (tid == 0) set_status(status, ST_TIMEOUT);
+        }
+      }
+      load_stage(nk, ns);
+    } else {
+      asm volatile("cp.async.commit_group;" ::: "memory");
+    }
+    asm volatile("cp.async.wait_group %0;" ::"n"(XI_STAGES - 1) : "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t sa = smem_u32(sm + st * STAGE), sb = sa + A_BYTES;
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk) {
+        const uint64_t ad = sw128_desc(sa + kk * 32), bd = sw128_desc(sb + kk * 32);
+        const uint32_t acc = (kb | kk) ? 1u : 0u;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+            "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+            : "memory");
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                       smem_u32(&mb[st]))
+                   : "memory");
+    }
+  }
+  // wait for the last block's MMAs (its commit covers every earlier MMA)
+  if (nkb > 0) {
+    const int st = (nkb - 1) % XI_STAGES;
+    if (!mbar_wait(&mb[st], (uint32_t)(((nkb - 1) / XI_STAGES) & 1)))
+      if (tid == 0) set_status(status, ST_TIMEOUT);
+  }
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
+  __syncwarp();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  // epilogue: lane = row i of the tile, 32 columns per load
+  double* out = xi_chunk + (size_t)c * NP * NP + (size_t)(ti * XI_TM + warp * 32 + (tid & 31)) * NP + tj * TN;
+  const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16);
+  for (int c0 = 0; c0 < TN; c0 += 32) {
+    uint32_t r[32];
+    if (nkb > 0) {
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+          "%14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+          : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+            "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+            "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]),
+            "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]),
+            "=r"(r[30]), "=r"(r[31])
+          : "r"(tl + c0));
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+    } else {
+#pragma unroll
+      for (int z = 0; z < 32; ++z) r[z] = 0u;
+    }
+#pragma unroll
+    for (int z = 0; z < 32; ++z) out[c0 + z] = (double)__uint_as_float(r[z]);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TN));
+}
+
+template <int TN>
+cudaError_t launch_xi_tn(const float* XT, const float* YT, int64_t ktot, const int64_t* kc0, const int32_t* kpad,
+                         int n_chunks, int NP, double* xi_chunk, int* status, cudaStream_t st) {
+  constexpr size_t smem = 1024 + (size_t)XI_STAGES * (XI_TM * 128 + TN * 128) + XI_STAGES * 8 + 16;
+  auto kern = xi_tc_kernel<TN>;
+  static bool done = false;
+  if (!done) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    done = true;
+  }
+  const dim3 grid((unsigned)((NP / XI_TM) * (NP / TN)), (unsigned)n_chunks);
+  kern<<<grid, 128, smem, st>>>(XT, YT, ktot, kc0, kpad, NP, xi_chunk, status);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+bool tc_xi_supported(int NP) { return NP >= 128 && NP <= 1024; }
+
+cudaError_t launch_tc_xi(const LargeArgs& a, const float* rz, const int32_t* tile_seq, const int32_t* tile_row,
+                         int n_tiles, const int64_t* kseq, const int64_t* kc0, const int32_t* kused,
+                         const int32_t* kpad, int n_chunks, int64_t ktot, float* XT, float* YT, double* xi_chunk,
+                         int* status, cudaStream_t st) {
+  const int NP = a.mv.NP, N = a.mv.N;
+  if (n_chunks == 0) return cudaSuccess;
+  if (n_tiles > 0) {
+    xi_prep_kernel<<<dim3((unsigned)n_tiles, (unsigned)(NP / 32)), 256, 0, st>>>(
+        a.fv, a.bv, a.ob, rz, a.logb, a.offsets, tile_seq, tile_row, kseq, NP, N, ktot, XT, YT);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  xi_pad_kernel<<<(unsigned)n_chunks, 256, 0, st>>>(kc0, kused, kpad, NP, ktot, XT, YT);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  if (NP >= 256) return launch_xi_tn<256>(XT, YT, ktot, kc0, kpad, n_chunks, NP, xi_chunk, status, st);
+  return launch_xi_tn<128>(XT, YT, ktot, kc0, kpad, n_chunks, NP, xi_chunk, status, st);
+}
+
+}  // namespace hmm

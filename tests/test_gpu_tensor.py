@@ -110,3 +110,37 @@ def test_tensor_matches_float32_path(H, ctx):
     ll0, ll1 = ll0.cpu().numpy(), ll1.cpu().numpy()
     assert np.all(np.abs(ll1 - ll0) <= TC_LL_RTOL * np.maximum(1.0, np.abs(ll0)))
     assert float((g1 - g0).abs().max()) <= TC_GAMMA_ATOL
+
+
+@pytest.mark.parametrize("N", [128, 300])
+def test_tensor_xi_statistics(H, ctx, N):
+    """E-step statistics with the tensor-core recursions and the TF32 xi GEMM
+    (K = time, chunk-ordered layout) against sums of the oracle's posteriors."""
+    models = synth.small_models("gauss", N, 2, seed=1300 + N)
+    lengths = [50, 3, 0, 200, 120, 1, 77, 40]
+    values, offsets, mid = synth.make_batch(1301, models, lengths, np.arange(len(lengths)) % 2)
+    model = H.Model(ctx, models)
+    batch = H.Batch(values, offsets, mid)
+    stats, _ = H.estep_stats(ctx, model, batch)
+    got = stats.get()
+    off = 0
+    for m, md in enumerate(models):
+        o = om(md)
+        g1, xi, ll, W = np.zeros(N), np.zeros((N, N)), 0.0, np.zeros(N)
+        idx = [s for s in range(len(lengths)) if mid[s] == m]
+        for s in idx:
+            y = np.asarray(values[offsets[s]:offsets[s + 1]], np.float64)
+            if len(y) == 0:
+                continue
+            fb = O.forward_backward(o, y)
+            ll += fb["logL"]
+            g1 += fb["gamma"][0]
+            xi += fb["xi_sum"]
+            W += fb["gamma"].sum(0)
+        rec = got[off:off + 2 + N + N * N + 3 * N]
+        off += 2 + N + N * N + 3 * N
+        assert rec[0] == len(idx)
+        assert abs(rec[1] - ll) <= TC_LL_RTOL * abs(ll)
+        np.testing.assert_allclose(rec[2:2 + N], g1, atol=TC_GAMMA_ATOL * len(idx))
+        np.testing.assert_allclose(rec[2 + N:2 + N + N * N].reshape(N, N), xi, rtol=5e-3, atol=5e-3)
+        np.testing.assert_allclose(rec[2 + N + N * N::3], W, rtol=2e-3, atol=2e-3)
