@@ -71,12 +71,16 @@ typedef enum {
  *   HMM_VONMISES    mu, kappa                           (Sec. 4.1-4.2, Eq. 12)
  *   HMM_DIAG_GAUSS  mu[D], var[D]                       (Sec. 4.5, Eq. 20-21)
  *   HMM_FULL_GAUSS  mu[D], cov[D][D]                    (Sec. 4.5, Eq. 22-24)
+ *   HMM_DISCRETE    p[K] symbol probabilities            (Sec. 4, "Discrete
+ *                   (categorical)"): the model's `dim` is the number of
+ *                   symbols K (2..1024); observations are the symbol indices
+ *                   0..K-1, one float per step (a batch's dim is 1)
  * Observations outside a family's support (y <= 0 for Gamma/Weibull,
  * y outside (0,1) for Beta, non-integer or negative counts) have density 0. */
 typedef enum {
   HMM_GAUSS = 0, HMM_POISSON = 1, HMM_GAMMA = 2, HMM_BETA = 3, HMM_WEIBULL = 4,
   HMM_NEGBIN = 5, HMM_STUDENT_T = 6, HMM_VONMISES = 7, HMM_DIAG_GAUSS = 8,
-  HMM_FULL_GAUSS = 9
+  HMM_FULL_GAUSS = 9, HMM_DISCRETE = 10
 } hmm_family;
 
 typedef struct hmm_ctx_s* hmm_ctx;       /* device + workspace            */

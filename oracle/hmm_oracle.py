@@ -55,7 +55,7 @@ NEGBIN_RMAX = 1e6            # reading: no finite MLE when var <= mean
 KAPPA_MAX = 1e6              # reading: R -> 1 gives kappa -> inf
 
 FAMILIES = ("gauss", "poisson", "gamma", "beta", "weibull", "negbin",
-            "student_t", "vonmises", "diag_gauss", "full_gauss")
+            "student_t", "vonmises", "diag_gauss", "full_gauss", "discrete")
 
 
 @dataclass
@@ -153,6 +153,13 @@ def emission_logpdf(model: Model, y: np.ndarray) -> np.ndarray:
             d = y[:, None, :] - mu[None]
             return np.sum(-0.5 * np.log(2 * np.pi * var)[None]
                           - d ** 2 / (2 * var[None]), axis=2)
+        if f == "discrete":     # Sec. 4, "Discrete (categorical)": b_j(k) = p_jk
+            pk = p["p"]                          # [N, K]
+            K = pk.shape[1]
+            ok = _is_count(y) & (y < K)
+            idx = np.where(ok, y, 0).astype(np.int64)
+            out = np.log(pk[:, idx]).T           # [T, N]
+            return np.where(ok[:, None], out, -np.inf)
         if f == "full_gauss":   # Sec. 4.5, Eq. 22 through the Cholesky factor
             mu, cov = p["mu"], p["cov"]          # [N, D], [N, D, D]
             T, D = y.shape
@@ -558,6 +565,14 @@ def mstep_diag_gauss(w, y, cur):
     return dict(mu=mu, var=var)
 
 
+def mstep_discrete(w, y, cur):
+    """Sec. 4, Discrete (categorical): p_jk = N_j^-1 sum_t gamma_t(j) 1[y_t = k]."""
+    K = np.asarray(cur["p"]).shape[0]
+    Nj = w.sum()
+    counts = np.array([np.sum(w[y == k]) for k in range(K)])
+    return dict(p=counts / Nj)
+
+
 def mstep_full_gauss(w, y, cur):
     """Sec. 4.5, Eq. 23-24: weighted mean and covariance + eps I."""
     Nj = w.sum()
@@ -570,7 +585,7 @@ def mstep_full_gauss(w, y, cur):
 MSTEP = dict(gauss=mstep_gauss, poisson=mstep_poisson, gamma=mstep_gamma,
              beta=mstep_beta, weibull=mstep_weibull, negbin=mstep_negbin,
              student_t=mstep_student_t, vonmises=mstep_vonmises,
-             diag_gauss=mstep_diag_gauss, full_gauss=mstep_full_gauss)
+             diag_gauss=mstep_diag_gauss, full_gauss=mstep_full_gauss, discrete=mstep_discrete)
 
 
 def _state_params(model: Model, j: int) -> dict:
@@ -615,6 +630,8 @@ def valid_update(family, res) -> bool:
     if family == "vonmises" and not np.all(vals["kappa"] >= 0):
         return False
     if family == "negbin" and not (0 < vals["p"] < 1):
+        return False
+    if family == "discrete" and not (np.all(vals["p"] >= 0) and abs(vals["p"].sum() - 1) < 1e-9):
         return False
     if family == "full_gauss":
         try:

@@ -39,7 +39,7 @@ PARAM_ORDER = {
     "gauss": ("mu", "sigma2"), "poisson": ("lam",), "gamma": ("alpha", "beta"),
     "beta": ("a", "b"), "weibull": ("k", "lam"), "negbin": ("r", "p"),
     "student_t": ("mu", "sigma2", "nu"), "vonmises": ("mu", "kappa"),
-    "diag_gauss": ("mu", "var"), "full_gauss": ("mu", "cov"),
+    "diag_gauss": ("mu", "var"), "full_gauss": ("mu", "cov"), "discrete": ("p",),
 }
 
 
@@ -64,11 +64,11 @@ def model_from_blob(blob: np.ndarray, family: str, N: int, D: int = 1) -> tuple[
     A = blob[q:q + N * N].reshape(N, N).copy(); q += N * N
     names = PARAM_ORDER[family]
     sizes = {"mu": D if family in ("diag_gauss", "full_gauss") else 1,
-             "var": D, "cov": D * D}
+             "var": D, "cov": D * D, "p": D}
     params = {n: [] for n in names}
     for j in range(N):
         for n in names:
-            k = sizes.get(n, 1) if family in ("diag_gauss", "full_gauss") else 1
+            k = sizes.get(n, 1) if family in ("diag_gauss", "full_gauss", "discrete") else 1
             v = blob[q:q + k]; q += k
             params[n].append(v.reshape(D, D) if n == "cov" else (v if k > 1 else v[0]))
     params = {n: np.array(v) for n, v in params.items()}
@@ -120,7 +120,10 @@ class Model:
         self.families = [m["family"] for m in models]
         self.N = len(models[0]["pi"])
         mu = models[0]["params"].get("mu")
-        self.D = (np.asarray(mu).shape[1] if self.families[0] in ("diag_gauss", "full_gauss") else 1)
+        if self.families[0] == "discrete":        # dim = number of symbols
+            self.D = int(np.asarray(models[0]["params"]["p"]).shape[1])
+        else:
+            self.D = (np.asarray(mu).shape[1] if self.families[0] in ("diag_gauss", "full_gauss") else 1)
         fam = np.array([FAMILY[f] for f in self.families], np.int32)
         h = C.c_void_p()
         check(self.lib.hmm_model_create(ctx.h, len(models), self.N, self.D,

@@ -15,7 +15,7 @@ OPT_PROFILE, OPT_ESTEP_LANES, OPT_VITERBI_LANES, OPT_PLAIN_ESTEP, OPT_TENSOR_REC
 KT_SLOTS = ("estep", "reduce", "mstep", "viterbi", "emission", "plain", "slot6", "slot7")
 
 FAMILY = {"gauss": 0, "poisson": 1, "gamma": 2, "beta": 3, "weibull": 4, "negbin": 5,
-          "student_t": 6, "vonmises": 7, "diag_gauss": 8, "full_gauss": 9}
+          "student_t": 6, "vonmises": 7, "diag_gauss": 8, "full_gauss": 9, "discrete": 10}
 
 
 class hmm_batch(C.Structure):

@@ -60,6 +60,7 @@ static int scalar_param_count(int fam) {
 }
 
 static int param_count(int fam, int D) {
+  if (fam == HMM_DISCRETE) return D;      // D = number of symbols
   if (fam == HMM_DIAG_GAUSS) return 2 * D;
   if (fam == HMM_FULL_GAUSS) return D + D * D;
   return scalar_param_count(fam);
@@ -494,7 +495,15 @@ void launch_mv_emission(hmm_model model, const hmm_batch* b, hmm_plan plan, floa
 // block per sequence.
 const float* mv_table(hmm_ctx ctx, hmm_model model, const hmm_batch* b, hmm_plan plan, cudaStream_t st) {
   ctx->mvlogb.ensure(std::max<int64_t>(b->total_T, 1) * model->N * 4);
-  if (!model->any_mv) {
+  if (model->any_discrete) {
+    if (b->n_seq > 0) {
+      KTimer kt(ctx, HMM_KT_EMISSION, st);
+      discrete_emission_kernel<<<(unsigned)b->n_seq, 128, 0, st>>>(model->dtab.as<float>(), model->NP, model->N,
+                                                                   model->K, b->values, b->offsets, b->model_id,
+                                                                   ctx->mvlogb.as<float>());
+      HMM_CUDA(cudaGetLastError());
+    }
+  } else if (!model->any_mv) {
     if (b->n_seq > 0) {
       KTimer kt(ctx, HMM_KT_EMISSION, st);
       emission_kernel<<<(unsigned)b->n_seq, 128, 0, st>>>(model->view(), b->values, b->offsets, b->model_id,
@@ -514,15 +523,17 @@ void mv_statistics(hmm_ctx ctx, hmm_model model, const hmm_batch* b, hmm_plan pl
                    cudaStream_t st) {
   const int NP = model->NP, KS = model->KS, RS = NP * KS;
   const int64_t S = b->n_seq;
-  if (NP <= 32) stats->mv_part.ensure((size_t)std::max<int64_t>(S, 1) * RS * 4);
+  if (NP <= 32 && !model->any_discrete) stats->mv_part.ensure((size_t)std::max<int64_t>(S, 1) * RS * 4);
   stats->mv_chunk.ensure((size_t)std::max(plan->n_chunks, 1) * RS * 8);
   stats->mv_rec.ensure((size_t)model->M * RS * 8);
   KTimer kt(ctx, HMM_KT_REDUCE, st);
-  if (NP > 32) {
-    // tiled raw moments per chunk, fixed-order model sums, then the shift
+  if (NP > 32 || model->any_discrete) {
+    // tiled raw moments per chunk (symbol counts for the discrete family),
+    // fixed-order model sums, then the shift to the current means
     if (plan->n_chunks > 0) {
       const int ftiles = (KS + MVM_TILE - 1) / MVM_TILE;
-      mv_moments_kernel<<<dim3((unsigned)((NP / MVM_TILE) * ftiles), (unsigned)plan->n_chunks), 256, 0, st>>>(
+      mv_moments_kernel<<<dim3((unsigned)(((NP + MVM_TILE - 1) / MVM_TILE) * ftiles), (unsigned)plan->n_chunks), 256, 0,
+                          st>>>(
           model->family.as<int>(), NP, model->N, model->D, KS, b->values, stats->gamma.as<float>(), b->offsets,
           b->model_id, plan->seq_by_model.as<int32_t>(), plan->chunk_lo.as<int32_t>(), plan->chunk_hi.as<int32_t>(),
           stats->mv_chunk.as<double>());
@@ -531,6 +542,7 @@ void mv_statistics(hmm_ctx ctx, hmm_model model, const hmm_batch* b, hmm_plan pl
     reduce_chunks_l2<<<model->M, 128, 0, st>>>(stats->mv_chunk.as<double>(), plan->model_chunk_ptr.as<int32_t>(), RS,
                                                stats->mv_rec.as<double>());
     HMM_CUDA(cudaGetLastError());
+    if (model->any_discrete) return;   // counts need no shift
     const int n = model->M * NP;
     mv_shift_kernel<<<(n + 127) / 128, 128, 0, st>>>(model->family.as<int>(), model->mvcoef.as<float>(), model->M,
                                                      NP, model->N, model->D, model->KM, KS,
@@ -577,7 +589,7 @@ void run_estep_large(hmm_ctx ctx, hmm_model model, const hmm_batch* b, hmm_plan 
       ctx->gamma.ensure(TT * N * 4);
       gamma = ctx->gamma.as<float>();
     }
-  } else if (want_stats && stats && (model->any_mv || model->any_negbin || model->any_weibull)) {
+  } else if (want_stats && stats && (model->table_family() || model->any_negbin || model->any_weibull)) {
     throw Error{HMM_E_ARG, "statistics of these families keep their own occupancies"};
   }
   if (want_stats) {
@@ -607,7 +619,7 @@ void run_estep_large(hmm_ctx ctx, hmm_model model, const hmm_batch* b, hmm_plan 
   KTimer kt(ctx, HMM_KT_REDUCE, st);
   HMM_CUDA(launch_large_post(a, NP, N, S, gamma, ctx->lg_rz.as<float>(), ll, ctx->status, st));
   if (!want_stats) return;
-  const bool table_stats = model->any_mv;
+  const bool table_stats = model->table_family();
   HMM_CUDA(launch_large_stats(a, b->values, gamma, S, table_stats, ctx->partials.as<float>(), st));
   if (ctx->tensor_rec && tc_xi_supported(NP)) {
     ctx->xi_xt.ensure((size_t)NP * plan->xi_ktot * 4);
@@ -627,7 +639,7 @@ void run_estep_large(hmm_ctx ctx, hmm_model model, const hmm_batch* b, hmm_plan 
   reduce_chunks_l2<<<model->M, 256, 0, st>>>(ctx->chunk_rec.as<double>(), plan->model_chunk_ptr.as<int32_t>(),
                                              rec_size(NP), stats->rec.as<double>());
   HMM_CUDA(cudaGetLastError());
-  if (model->any_mv) mv_statistics(ctx, model, b, plan, stats, st);
+  if (model->table_family()) mv_statistics(ctx, model, b, plan, stats, st);
   stats->valid = true;
 }
 
@@ -644,11 +656,11 @@ void run_estep(hmm_ctx ctx, hmm_model model, const hmm_batch* b, hmm_plan plan, 
     run_estep_large(ctx, model, b, plan, logb, gamma, ll, want_stats, stats, st);
     return;
   }
-  if (model->any_mv && ctx->plain_estep)
+  if (model->table_family() && ctx->plain_estep)
     throw Error{HMM_E_UNSUPPORTED, "the plain path covers the scalar families only"};
   const int64_t S = b->n_seq;
-  const bool mv_stats = want_stats && stats && model->any_mv;
-  if (model->any_mv && !logb) logb = mv_table(ctx, model, b, plan, st);
+  const bool mv_stats = want_stats && stats && model->table_family();
+  if (model->table_family() && !logb) logb = mv_table(ctx, model, b, plan, st);
   ctx->scratch.ensure(std::max<int64_t>(b->total_T, 1) * NP * 4 + 64);
   const int F = NP + NST;
   ctx->partials.ensure(std::max<int64_t>(S, 1) * 2 * NP * F * 4);
@@ -694,7 +706,7 @@ void run_estep(hmm_ctx ctx, hmm_model model, const hmm_batch* b, hmm_plan plan, 
   a.loglik = ll;
   a.work_counter = ctx->counters;
   a.status = ctx->status;
-  const bool dpass = want_stats && stats && (model->any_negbin || model->any_weibull || model->any_mv);
+  const bool dpass = want_stats && stats && (model->any_negbin || model->any_weibull || model->table_family());
   if (dpass && !gamma) {
     // the Weibull / negative-binomial M-steps re-read the occupancies, and
     // the multivariate moments are formed from them
@@ -753,7 +765,7 @@ void prepare_mstep(hmm_model model, hmm_stats stats, const hmm_batch* b, hmm_pla
 
 void run_mstep(hmm_ctx ctx, hmm_model model, hmm_stats stats, const MStepOpts& o, const hmm_batch* b,
                hmm_plan plan, cudaStream_t st) {
-  if (model->any_mv) HMM_REQUIRE(stats->mv_rec.p != nullptr, "multivariate statistics were never computed");
+  if (model->table_family()) HMM_REQUIRE(stats->mv_rec.p != nullptr, "table-family statistics were never computed");
   const bool dpass = model->any_negbin || model->any_weibull;
   if (dpass && model->NP > 32)
     throw Error{HMM_E_UNSUPPORTED, "Weibull / negative-binomial M-steps support padded N <= 32"};
@@ -768,6 +780,16 @@ void run_mstep(hmm_ctx ctx, hmm_model model, hmm_stats stats, const MStepOpts& o
     KTimer kt(ctx, HMM_KT_MSTEP, st);
     mstep_kernel<<<model->M, model->NP, 0, st>>>(model->bufs(), stats->rec.as<double>(), o, dps);
     HMM_CUDA(cudaGetLastError());
+    if (model->any_discrete) {   // Sec. 4 "Discrete": weighted symbol frequencies
+      const int n = model->M * model->NP;
+      discrete_mstep_kernel<<<(n + 127) / 128, 128, 0, st>>>(model->theta.as<double>(), stats->mv_rec.as<double>(),
+                                                             model->M, model->NP, model->N, model->P, model->K,
+                                                             o.collapse_eps);
+      HMM_CUDA(cudaGetLastError());
+      discrete_derive_kernel<<<(n + 127) / 128, 128, 0, st>>>(model->theta.as<double>(), model->M, model->NP,
+                                                              model->N, model->P, model->K, model->dtab.as<float>());
+      HMM_CUDA(cudaGetLastError());
+    }
     if (model->any_mv) {   // Sec. 4.5: means, (co)variances, then the new factors
       const int n = model->M * model->NP;
       mv_mstep_kernel<<<(n + 127) / 128, 128, 0, st>>>(model->family.as<int>(), model->theta.as<double>(),
@@ -875,8 +897,9 @@ const char* hmm_last_error(void) { return g_last_error.c_str(); }
 const char* hmm_version(void) { return "hmmgpu 0.1 (sm_103a)"; }
 
 int32_t hmm_family_param_count(int32_t family, int32_t dim) {
-  if (family < 0 || family > HMM_FULL_GAUSS) return -1;
+  if (family < 0 || family > HMM_DISCRETE) return -1;
   if (family >= HMM_DIAG_GAUSS && dim < 1) return -1;
+  if (family == HMM_DISCRETE && (dim < 1 || dim > 1024)) return -1;
   return param_count(family, dim);
 }
 
@@ -1022,21 +1045,32 @@ hmm_status hmm_model_create(hmm_ctx ctx, int32_t n_models, int32_t n_states, int
       m->N = n_states;
       m->NP = padded_states(n_states);
       m->D = dim;
+      m->dim_arg = dim;
       m->h_family.assign(h_family, h_family + n_models);
       int P = 1;
       for (int i = 0; i < n_models; ++i) {
         const int f = h_family[i];
-        HMM_REQUIRE(f >= 0 && f <= HMM_FULL_GAUSS, "unknown family");
+        HMM_REQUIRE(f >= 0 && f <= HMM_DISCRETE, "unknown family");
         const bool mv = f == HMM_DIAG_GAUSS || f == HMM_FULL_GAUSS;
-        HMM_REQUIRE(mv || dim == 1, "scalar families need dim == 1");
+        HMM_REQUIRE(mv || f == HMM_DISCRETE || dim == 1, "scalar families need dim == 1");
+        m->any_discrete |= f == HMM_DISCRETE;
         m->any_negbin |= f == HMM_NEGBIN;
         m->any_weibull |= f == HMM_WEIBULL;
         m->any_mv |= mv;
         P = std::max(P, param_count(f, dim));
       }
-      for (int i = 0; i < n_models; ++i)
+      for (int i = 0; i < n_models; ++i) {
         HMM_REQUIRE(!m->any_mv || h_family[i] == HMM_DIAG_GAUSS || h_family[i] == HMM_FULL_GAUSS,
                     "multivariate and scalar families cannot share a model set");
+        HMM_REQUIRE(!m->any_discrete || h_family[i] == HMM_DISCRETE,
+                    "the discrete family cannot share a model set with others");
+      }
+      if (m->any_discrete) {
+        HMM_REQUIRE(dim >= 1 && dim <= 1024, "the discrete family needs 1 <= dim (symbols) <= 1024");
+        m->K = dim;
+        m->KS = dim;
+        m->D = 1;                  // observations: one symbol index per step
+      }
       m->P = P;
       const size_t M = n_models, NP = m->NP;
       m->family.ensure(M * 4);
@@ -1052,6 +1086,7 @@ hmm_status hmm_model_create(hmm_ctx ctx, int32_t n_models, int32_t n_states, int
       m->logpie.ensure(M * NP * 4);
       m->coef.ensure(M * NP * KC * 4);
       if (m->any_negbin) m->nbtab.ensure(M * NP * NB_YMAX * 4);
+      if (m->any_discrete) m->dtab.ensure(M * NP * (size_t)m->K * 4);
       if (m->any_mv) {
         HMM_REQUIRE(dim <= 32, "multivariate families support dim <= 32");
         for (int i = 0; i < n_models; ++i)
@@ -1073,7 +1108,7 @@ hmm_status hmm_model_create(hmm_ctx ctx, int32_t n_models, int32_t n_states, int
       HMM_CUDA(cudaStreamSynchronize(0));
     } catch (...) {
       for (auto* b : {&m->family, &m->pi, &m->A, &m->theta, &m->A32, &m->AT32, &m->logA2, &m->logAe, &m->pi32,
-                      &m->logpi2, &m->logpie, &m->coef, &m->nbtab, &m->lfact2, &m->mvcoef})
+                      &m->logpi2, &m->logpie, &m->coef, &m->nbtab, &m->lfact2, &m->mvcoef, &m->dtab})
         b->release();
       delete m;
       throw;
@@ -1086,7 +1121,7 @@ hmm_status hmm_model_destroy(hmm_model m) {
   return guarded([&] {
     if (!m) return;
     for (auto* b : {&m->family, &m->pi, &m->A, &m->theta, &m->A32, &m->AT32, &m->logA2, &m->logAe, &m->pi32,
-                    &m->logpi2, &m->logpie, &m->coef, &m->nbtab, &m->lfact2, &m->mvcoef})
+                    &m->logpi2, &m->logpie, &m->coef, &m->nbtab, &m->lfact2, &m->mvcoef, &m->dtab})
       b->release();
     delete m;
   });
@@ -1096,12 +1131,12 @@ hmm_status hmm_model_set_params(hmm_model model, const double* h_blob, int64_t n
   return guarded([&] {
     HMM_REQUIRE(model && h_blob, "NULL argument");
     const int M = model->M, N = model->N, NP = model->NP, P = model->P, D = model->D;
-    const int64_t need = hmm_param_blob_size(M, N, D, model->h_family.data());
+    const int64_t need = hmm_param_blob_size(M, N, model->dim_arg, model->h_family.data());
     HMM_REQUIRE(n_values == need, "parameter blob has the wrong size");
     std::vector<double> pi((size_t)M * NP, 0.0), A((size_t)M * NP * NP, 0.0), th((size_t)M * NP * P, 0.0);
     const double* q = h_blob;
     for (int m = 0; m < M; ++m) {
-      const int pc = param_count(model->h_family[m], D);
+      const int pc = param_count(model->h_family[m], model->dim_arg);
       double psum = 0.0;
       for (int j = 0; j < N; ++j) {
         HMM_REQUIRE(q[j] >= 0.0 && std::isfinite(q[j]), "pi must be finite and >= 0");
@@ -1121,10 +1156,15 @@ hmm_status hmm_model_set_params(hmm_model model, const double* h_blob, int64_t n
         q += N;
       }
       for (int j = 0; j < N; ++j) {
+        double psum = 0.0;
         for (int z = 0; z < pc; ++z) {
           HMM_REQUIRE(std::isfinite(q[z]), "parameters must be finite");
           th[((size_t)m * NP + j) * P + z] = q[z];
+          psum += q[z];
+          if (model->h_family[m] == HMM_DISCRETE) HMM_REQUIRE(q[z] >= 0.0, "symbol probabilities must be >= 0");
         }
+        if (model->h_family[m] == HMM_DISCRETE)
+          HMM_REQUIRE(std::fabs(psum - 1.0) < 1e-6, "symbol probabilities must sum to 1");
         q += pc;
       }
     }
@@ -1139,6 +1179,11 @@ hmm_status hmm_model_set_params(hmm_model model, const double* h_blob, int64_t n
                                                  model->KM, model->mvcoef.as<float>());
       HMM_CUDA(cudaGetLastError());
     }
+    if (model->any_discrete) {
+      discrete_derive_kernel<<<(n + 127) / 128, 128>>>(model->theta.as<double>(), M, NP, N, P, model->K,
+                                                       model->dtab.as<float>());
+      HMM_CUDA(cudaGetLastError());
+    }
     // the copies and derive kernels ran on the legacy default stream
     HMM_CUDA(cudaStreamSynchronize(0));
   });
@@ -1148,7 +1193,7 @@ hmm_status hmm_model_get_params(hmm_model model, double* h_blob, int64_t n_value
   return guarded([&] {
     HMM_REQUIRE(model && h_blob, "NULL argument");
     const int M = model->M, N = model->N, NP = model->NP, P = model->P, D = model->D;
-    const int64_t need = hmm_param_blob_size(M, N, D, model->h_family.data());
+    const int64_t need = hmm_param_blob_size(M, N, model->dim_arg, model->h_family.data());
     HMM_REQUIRE(n_values == need, "parameter blob has the wrong size");
     HMM_CUDA(cudaDeviceSynchronize());
     std::vector<double> pi((size_t)M * NP), A((size_t)M * NP * NP), th((size_t)M * NP * P);
@@ -1157,7 +1202,7 @@ hmm_status hmm_model_get_params(hmm_model model, double* h_blob, int64_t n_value
     HMM_CUDA(cudaMemcpy(th.data(), model->theta.p, th.size() * 8, cudaMemcpyDeviceToHost));
     double* q = h_blob;
     for (int m = 0; m < M; ++m) {
-      const int pc = param_count(model->h_family[m], D);
+      const int pc = param_count(model->h_family[m], model->dim_arg);
       for (int j = 0; j < N; ++j) *q++ = pi[(size_t)m * NP + j];
       for (int i = 0; i < N; ++i)
         for (int j = 0; j < N; ++j) *q++ = A[((size_t)m * NP + i) * NP + j];
@@ -1266,6 +1311,14 @@ hmm_status hmm_emission_logpdf(hmm_ctx ctx, hmm_model model, const hmm_batch* ba
     HMM_REQUIRE(ctx && model && d_logb, "NULL argument");
     check_batch(model, batch);
     if (batch->n_seq == 0) return;
+    if (model->any_discrete) {
+      KTimer kt(ctx, HMM_KT_EMISSION, S(stream));
+      discrete_emission_kernel<<<(unsigned)batch->n_seq, 128, 0, S(stream)>>>(
+          model->dtab.as<float>(), model->NP, model->N, model->K, batch->values, batch->offsets, batch->model_id,
+          d_logb);
+      HMM_CUDA(cudaGetLastError());
+      return;
+    }
     if (model->any_mv) {
       PlanRef pr;
       get_plan(ctx, model, batch, S(stream), pr);
@@ -1334,7 +1387,7 @@ hmm_status hmm_viterbi(hmm_ctx ctx, hmm_model model, const hmm_batch* batch, con
       if (pr.owned) HMM_CUDA(cudaStreamSynchronize(S(stream)));
       return;
     }
-    if (model->any_mv && !d_logb) d_logb = mv_table(ctx, model, batch, pr.p, S(stream));
+    if (model->table_family() && !d_logb) d_logb = mv_table(ctx, model, batch, pr.p, S(stream));
     const int NP = model->NP;
     ctx->psi.ensure(std::max<int64_t>(batch->total_T, 1) * NP + 64);
     VitArgs a;
@@ -1392,6 +1445,7 @@ hmm_status hmm_stats_destroy(hmm_stats stats) {
 
 static int canon_fam_count(int fam, int D) {
   switch (fam) {
+    case HMM_DISCRETE: return D;   // D: the model's dim (number of symbols)
     case HMM_GAUSS: return 3;
     case HMM_POISSON: return 2;
     case HMM_GAMMA: return 4;
@@ -1411,7 +1465,7 @@ int64_t hmm_stats_size(hmm_stats stats) {
   const hmm_model m = stats->model;
   int64_t tot = 0;
   for (int i = 0; i < m->M; ++i)
-    tot += 2 + m->N + (int64_t)m->N * m->N + (int64_t)m->N * canon_fam_count(m->h_family[i], m->D);
+    tot += 2 + m->N + (int64_t)m->N * m->N + (int64_t)m->N * canon_fam_count(m->h_family[i], m->dim_arg);
   return tot;
 }
 
@@ -1431,12 +1485,14 @@ hmm_status hmm_stats_get(hmm_stats stats, double* h_out, int64_t n_values) {
     const int D = md->D, KM = md->KM, KS = md->KS;
     std::vector<double> mrec;
     std::vector<float> mvc;
-    if (md->any_mv) {
-      HMM_REQUIRE(stats->mv_rec.p != nullptr, "multivariate statistics were never computed");
+    if (md->table_family()) {
+      HMM_REQUIRE(stats->mv_rec.p != nullptr, "table-family statistics were never computed");
       mrec.resize((size_t)M * NP * KS);
-      mvc.resize((size_t)M * NP * KM);
       HMM_CUDA(cudaMemcpy(mrec.data(), stats->mv_rec.p, mrec.size() * 8, cudaMemcpyDeviceToHost));
-      HMM_CUDA(cudaMemcpy(mvc.data(), md->mvcoef.p, mvc.size() * 4, cudaMemcpyDeviceToHost));
+      if (md->any_mv) {
+        mvc.resize((size_t)M * NP * KM);
+        HMM_CUDA(cudaMemcpy(mvc.data(), md->mvcoef.p, mvc.size() * 4, cudaMemcpyDeviceToHost));
+      }
     }
     double* q = h_out;
     for (int m = 0; m < M; ++m) {
@@ -1497,6 +1553,11 @@ hmm_status hmm_stats_get(hmm_stats stats, double* h_out, int64_t n_values) {
             q[1] = St[1];
             q[2] = St[2];
             break;
+          case HMM_DISCRETE: {   // weighted symbol counts
+            const double* Rm = mrec.data() + ((size_t)m * NP + j) * KS;
+            for (int k = 0; k < md->K; ++k) q[k] = Rm[k];
+            break;
+          }
           case HMM_DIAG_GAUSS:
           case HMM_FULL_GAUSS: {
             // raw moments W, sum g y_d, then sum g y_d^2 or sum g y_d y_e from
@@ -1518,11 +1579,11 @@ hmm_status hmm_stats_get(hmm_stats stats, double* h_out, int64_t n_values) {
             break;
           }
           default:
-            for (int z = 0; z < canon_fam_count(fam, md->D); ++z) q[z] = 0.0;
+            for (int z = 0; z < canon_fam_count(fam, md->dim_arg); ++z) q[z] = 0.0;
             q[0] = W;
             break;
         }
-        q += canon_fam_count(fam, md->D);
+        q += canon_fam_count(fam, md->dim_arg);
       }
     }
   });

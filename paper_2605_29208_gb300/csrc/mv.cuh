@@ -255,6 +255,7 @@ constexpr int MVM_TILE = 64;
 constexpr int MVM_KT = 16;
 
 __device__ __forceinline__ float mv_feature(int fam, int D, int z, const float* yr) {
+  if (fam == HMM_DISCRETE) return yr[0] == (float)z ? 1.f : 0.f;   // symbol indicator 1[y = z]
   if (z == 0) return 1.f;
   if (z <= D) return yr[z - 1];
   const int q = z - 1 - D;
@@ -278,7 +279,7 @@ __global__ void __launch_bounds__(256) mv_moments_kernel(const int* __restrict__
   const int tid = threadIdx.x, ty = tid / 16, tx = tid % 16;
   const int lo = chunk_lo[c], hi = chunk_hi[c];
   const int fam = family[model_id[seq_by_model[lo]]];
-  const int nf = mv_stat_count(fam, D);
+  const int nf = fam == HMM_DISCRETE ? KS : mv_stat_count(fam, D);
   float acc[4][4];
   double dacc[4][4];
 #pragma unroll
@@ -452,3 +453,54 @@ __global__ void __launch_bounds__(256) mv_emission_tiled_kernel(const float* __r
 }
 
 }  // namespace hmm
+
+namespace hmm {
+
+// ---------------------------------------------------------------------------
+// Discrete (categorical) family (Sec. 4, "Discrete"): per state K symbol
+// probabilities; log b_j(y) = ln p_jy for an integer y in [0, K), else -inf.
+// ---------------------------------------------------------------------------
+__global__ void discrete_derive_kernel(const double* __restrict__ theta, int M, int NP, int N, int P, int K,
+                                       float* __restrict__ dtab) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= M * NP) return;
+  const int k = idx % NP;
+  float* t = dtab + (size_t)idx * K;
+  const double* th = theta + (size_t)idx * P;
+  for (int z = 0; z < K; ++z) t[z] = (k < N && th[z] > 0.0) ? (float)log(th[z]) : -INFINITY;
+}
+
+// log b table [total_T][N]: one block per sequence, threads over (t, state)
+__global__ void discrete_emission_kernel(const float* __restrict__ dtab, int NP, int N, int K,
+                                         const float* __restrict__ y, const int64_t* __restrict__ offsets,
+                                         const int32_t* __restrict__ model_id, float* __restrict__ logb) {
+  const int s = blockIdx.x;
+  const int64_t b = offsets[s], e = offsets[s + 1];
+  const int m = model_id[s];
+  const float* tab = dtab + (size_t)m * NP * K;
+  for (int64_t idx = threadIdx.x; idx < (e - b) * N; idx += blockDim.x) {
+    const int64_t t = b + idx / N;
+    const int j = (int)(idx % N);
+    const float v = y[t];
+    const bool ok = v >= 0.f && v < (float)K && floorf(v) == v;
+    logb[t * N + j] = ok ? tab[(size_t)j * K + (int)v] : -INFINITY;
+  }
+}
+
+// p_jk = count_jk / sum_k count_jk (Sec. 4, "Discrete"); a state whose
+// weight is below the collapse threshold keeps its probabilities (Sec. 4.4)
+__global__ void discrete_mstep_kernel(double* __restrict__ theta, const double* __restrict__ rec, int M, int NP, int N,
+                                      int P, int K, double collapse_eps) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= M * NP) return;
+  if (idx % NP >= N) return;
+  const double* R = rec + (size_t)idx * K;
+  double W = 0.0;
+  for (int z = 0; z < K; ++z) W += R[z];
+  if (!(W >= collapse_eps)) return;
+  double* th = theta + (size_t)idx * P;
+  for (int z = 0; z < K; ++z) th[z] = R[z] / W;
+}
+
+}  // namespace hmm
+

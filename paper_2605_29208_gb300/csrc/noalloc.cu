@@ -71,7 +71,7 @@ extern "C" hmm_status hmm_forward_backward_static(hmm_model model, const hmm_bat
                 "batch values are NULL");
     HMM_REQUIRE(batch->dim == model->D, "batch dim does not match the model");
     if (model->NP > 32) throw Error{HMM_E_UNSUPPORTED, "state counts above 32 are not supported"};
-    if (model->any_mv && !d_logb)
+    if (model->table_family() && !d_logb)
       throw Error{HMM_E_UNSUPPORTED, "multivariate families need an emission table (d_logb)"};
     const int NP = model->NP;
     const int64_t S = batch->n_seq;

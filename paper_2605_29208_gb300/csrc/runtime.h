@@ -128,7 +128,11 @@ struct hmm_model_s {
   hmm_ctx ctx = nullptr;
   int M = 0, N = 0, NP = 0, D = 1, P = 0;
   std::vector<int32_t> h_family;
-  bool any_negbin = false, any_weibull = false, any_mv = false;
+  bool any_negbin = false, any_weibull = false, any_mv = false, any_discrete = false;
+  int K = 0;                     // symbols of the discrete family
+  int dim_arg = 1;               // the `dim` the model was created with (K for discrete)
+  hmm::DevBuf dtab;              // [M][NP][K] float32 ln p_jk (discrete family)
+  bool table_family() const { return any_mv || any_discrete; }
   hmm::DevBuf family, pi, A, theta, A32, AT32, logA2, logAe, pi32, logpi2, logpie, coef, nbtab, lfact2;
   int KM = 0, KS = 0;            // multivariate coefficient / statistic slots per state
   hmm::DevBuf mvcoef;            // [M][NP][KM] float32 (multivariate families)

@@ -130,13 +130,15 @@ int padded(int n) {
 size_t footprint(const ServeReq* r) {
   const size_t NP = (size_t)padded(r->N), T = (size_t)std::max<int64_t>(r->T, 1);
   const size_t P = (size_t)std::max(1, hmm_family_param_count(r->family, r->D));
-  return T * (4 * (size_t)r->D + 16 * NP + 4 * (size_t)r->N + 2 * NP + 32) + NP * NP * 40 + NP * P * 16 + 4096;
+  const size_t od = r->family == HMM_DISCRETE ? 1 : (size_t)r->D;
+  return T * (4 * od + 16 * NP + 4 * (size_t)r->N + 2 * NP + 32) + NP * NP * 40 + NP * P * 16 + 4096;
 }
 
 void run_batch(hmm_server s, Slot* sl, std::vector<ServeReq*>& group) {
   const ServeReq* r0 = group[0];
   const int K = (int)group.size(), MB = s->max_batch;
   const int kind = r0->kind, N = r0->N, D = r0->D;
+  const int OD = r0->family == HMM_DISCRETE ? 1 : D;   // values per step
   HMM_CUDA(cudaSetDevice(s->device));
   // the slot's model for this family / N / dim (M = max_batch, unused models
   // carry a copy of the last request's parameters and no sequences)
@@ -167,10 +169,11 @@ void run_batch(hmm_server s, Slot* sl, std::vector<ServeReq*>& group) {
     off[k + 1] = off[k] + group[k]->T;
     mid[k] = k;
   }
-  const size_t vbytes = (size_t)TT * D * 4;
+  const size_t vbytes = (size_t)TT * OD * 4;
   sl->h_in.ensure(vbytes + (K + 1) * 8 + K * 4 + 64);
   float* hv = sl->h_in.as<float>();
-  for (int k = 0; k < K; ++k) std::memcpy(hv + (size_t)off[k] * D, group[k]->values.data(), group[k]->values.size() * 4);
+  for (int k = 0; k < K; ++k)
+    std::memcpy(hv + (size_t)off[k] * OD, group[k]->values.data(), group[k]->values.size() * 4);
   sl->values.ensure(std::max<size_t>(vbytes, 16));
   sl->offsets.ensure((K + 1) * 8);
   sl->model_id.ensure(K * 4);
@@ -188,7 +191,7 @@ void run_batch(hmm_server s, Slot* sl, std::vector<ServeReq*>& group) {
   b.model_id = sl->model_id.as<int32_t>();
   b.n_seq = K;
   b.total_T = TT;
-  b.dim = D;
+  b.dim = OD;
   b.plan = nullptr;
   if (!sl->plan) sl->plan = new hmm_plan_s();
   fill_plan(sl->plan, sl->ctx, model, &b, off.data(), mid.data());
@@ -437,7 +440,7 @@ hmm_status hmm_serve_submit(hmm_server s, const hmm_request* q, uint64_t* ticket
   try {
     HMM_REQUIRE(s && q && ticket, "NULL argument");
     HMM_REQUIRE(q->kind >= HMM_REQ_DECODE && q->kind <= HMM_REQ_FIT, "unknown request kind");
-    HMM_REQUIRE(q->family >= 0 && q->family <= HMM_FULL_GAUSS, "unknown family");
+    HMM_REQUIRE(q->family >= 0 && q->family <= HMM_DISCRETE, "unknown family");
     HMM_REQUIRE(q->n_states >= 1 && q->n_states <= 1024 && q->dim >= 1, "bad model sizes");
     HMM_REQUIRE(q->T >= 0 && (q->T == 0 || q->values), "bad observations");
     HMM_REQUIRE(q->kind != HMM_REQ_FIT || q->n_iter >= 0, "n_iter must be >= 0");
@@ -451,7 +454,8 @@ hmm_status hmm_serve_submit(hmm_server s, const hmm_request* q, uint64_t* ticket
     r->T = q->T;
     r->n_iter = q->kind == HMM_REQ_FIT ? q->n_iter : 0;
     r->params.assign(q->params, q->params + need);
-    r->values.assign(q->values, q->values + (size_t)q->T * q->dim);
+    // observations: dim values per step (one symbol index for the discrete family)
+    r->values.assign(q->values, q->values + (size_t)q->T * (q->family == HMM_DISCRETE ? 1 : q->dim));
     r->bytes = footprint(r);
     {
       std::lock_guard<std::mutex> lk(s->mu);

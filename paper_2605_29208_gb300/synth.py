@@ -16,7 +16,8 @@ Parameter names per family (rate parameterisation for the Gamma):
   gauss (mu, sigma2), poisson (lam), gamma (alpha, beta=rate),
   beta (a, b), weibull (k, lam), negbin (r, p), student_t (mu, sigma2, nu),
   vonmises (mu, kappa), diag_gauss (mu[N,D], var[N,D]),
-  full_gauss (mu[N,D], cov[N,D,D]).
+  full_gauss (mu[N,D], cov[N,D,D]), discrete (p[N,K]: symbol probabilities;
+  observations are the symbol indices 0..K-1 as floats).
 """
 from __future__ import annotations
 
@@ -35,6 +36,7 @@ PARAM_NAMES = {
     "vonmises": ("mu", "kappa"),
     "diag_gauss": ("mu", "var"),
     "full_gauss": ("mu", "cov"),
+    "discrete": ("p",),
 }
 
 
@@ -73,6 +75,8 @@ def random_params(rng, family, N, D=1):
         return dict(mu=rng.uniform(-np.pi, np.pi, N), kappa=rng.uniform(0.5, 20, N))
     if family == "diag_gauss":
         return dict(mu=rng.normal(0, 3, (N, D)), var=rng.uniform(0.2, 2, (N, D)))
+    if family == "discrete":      # D = number of symbols; rows Dirichlet(1)
+        return dict(p=rng.dirichlet(np.ones(D), size=N))
     if family == "full_gauss":
         cov = np.empty((N, D, D))
         for j in range(N):
@@ -87,6 +91,10 @@ def sample_emissions(rng, model, states):
     f, p = model["family"], model["params"]
     q = states
     n = len(q)
+    if f == "discrete":
+        cp = np.cumsum(p["p"], axis=1)[q]
+        u = rng.random(n)[:, None]
+        return np.minimum((u * cp[:, -1:] >= cp).sum(1), cp.shape[1] - 1).astype(np.float64)
     if f == "gauss":
         return p["mu"][q] + np.sqrt(p["sigma2"][q]) * rng.standard_normal(n)
     if f == "poisson":
@@ -238,6 +246,9 @@ def perturb(rng, model, frac=0.2):
             params[k] = v + rng.uniform(-0.3, 0.3, v.shape)
         elif model["family"] in ("gauss", "student_t", "diag_gauss", "full_gauss") and k == "mu":
             params[k] = v + rng.uniform(-0.3, 0.3, v.shape)
+        elif model["family"] == "discrete":
+            q = v * rng.uniform(1 - frac, 1 + frac, v.shape)
+            params[k] = q / q.sum(axis=1, keepdims=True)
         elif k == "p":
             params[k] = np.clip(v * rng.uniform(1 - frac, 1 + frac, v.shape), 0.02, 0.98)
         elif k == "cov":

@@ -319,3 +319,45 @@ def test_undefined_update_keeps_parameters():
     assert newp.params["lam"][0] == 2.5 and newp.params["lam"][1] == 3.0
     assert O.valid_update("full_gauss", {"mu": np.zeros(2), "cov": np.eye(2)})
     assert not O.valid_update("full_gauss", {"mu": np.zeros(2), "cov": np.array([[1.0, 2.0], [2.0, 1.0]])})
+
+
+def test_discrete_emission_and_mstep():
+    """Categorical family (Sec. 4, 'Discrete'): log b_j(k) = log p_jk, symbols
+    outside 0..K-1 (or not integers) have density 0; the M-step is the
+    weighted symbol frequency -- with hard 0/1 weights, each cluster's
+    empirical frequencies; with N = 1, the overall frequencies."""
+    p = np.array([[0.5, 0.25, 0.25], [0.1, 0.1, 0.8]])
+    m = O.Model("discrete", np.array([0.5, 0.5]), np.full((2, 2), 0.5), {"p": p.copy()})
+    y = np.array([0.0, 2.0, 1.0, 3.0, 0.5, -1.0])
+    lb = O.emission_logpdf(m, y)
+    np.testing.assert_allclose(lb[:3], np.log(p[:, [0, 2, 1]]).T)
+    assert np.all(np.isneginf(lb[3:]))
+    rng = np.random.default_rng(0)
+    ys = rng.integers(0, 3, 500).astype(float)
+    lab = rng.integers(0, 2, 500)
+    W = np.stack([(lab == 0), (lab == 1)], axis=1).astype(float)
+    new, _ = O.mstep_emission(m, W, ys)
+    for j in range(2):
+        freq = np.bincount(ys[lab == j].astype(int), minlength=3) / (lab == j).sum()
+        np.testing.assert_allclose(new.params["p"][j], freq, rtol=1e-12)
+    m1 = O.Model("discrete", np.array([1.0]), np.ones((1, 1)), {"p": np.array([[0.2, 0.3, 0.5]])})
+    new1, _ = O.mstep_emission(m1, np.ones((500, 1)), ys)
+    np.testing.assert_allclose(new1.params["p"][0], np.bincount(ys.astype(int), minlength=3) / 500, rtol=1e-12)
+
+
+def test_discrete_recursions_brute_force():
+    """Forward-backward and Viterbi with categorical emissions against the
+    enumeration of all N^T paths (N = 3, T = 6)."""
+    rng = np.random.default_rng(4)
+    N, K, T = 3, 4, 6
+    m = O.Model("discrete", rng.dirichlet(np.ones(N)), rng.dirichlet(np.ones(N), size=N),
+                {"p": rng.dirichlet(np.ones(K), size=N)})
+    y = rng.integers(0, K, T).astype(float)
+    logb = O.emission_logpdf(m, y)
+    bf = O.brute_force(np.log(m.pi), np.log(m.A), logb)
+    fb = O.forward_backward(m, y)
+    assert abs(fb["logL"] - bf["logL"]) < 1e-12
+    np.testing.assert_allclose(fb["gamma"], bf["gamma"], atol=1e-12)
+    q, sc = O.viterbi(m, y)
+    np.testing.assert_array_equal(q, bf["map_path"])
+    assert abs(sc - bf["map_score"]) < 1e-12
