@@ -292,6 +292,16 @@ __device__ void estep_item(WarpSmem<C>& sm, const EStepArgs& a, int item, int la
     gl[q] = 0.f;
   }
   bool started = false;    // the chain has produced its first vector
+  // The first step of a chain reads no previous vector, but the xi update
+  // multiplies that buffer by a zero weight: clear it, so that stale shared
+  // memory (NaN or inf) cannot turn 0 x buffer into NaN (a chain whose first
+  // step falls in phase 2, e.g. the forward chain of a length-1 sequence).
+#pragma unroll
+  for (int q = 0; q < R; ++q) {
+    sm.xbuf[0][chain][k0 + q] = 0.f;
+    sm.xbuf[1][chain][k0 + q] = 0.f;
+  }
+  __syncwarp();
   const float* ybase = a.y + base;
   const float* sbase = a.scratch + base * NP + k0;
   float* wbase = a.scratch + base * NP + k0;

@@ -75,6 +75,7 @@ struct KTimer {
   int slot;
   cudaStream_t st;
   cudaEvent_t e0 = nullptr;
+  int kernels = 1;             // kernels the region launches (set by the region)
   static cudaEvent_t take(hmm_ctx c) {
     if (!c->event_pool.empty()) {
       cudaEvent_t e = c->event_pool.back();
@@ -97,7 +98,7 @@ struct KTimer {
     cudaEvent_t e1 = take(ctx);
     if (!e1) return;
     cudaEventRecord(e1, st);
-    ctx->pending.push_back({slot, e0, e1});
+    ctx->pending.push_back({slot, e0, e1, kernels});
   }
 };
 
@@ -519,14 +520,14 @@ const float* mv_table(hmm_ctx ctx, hmm_model model, const hmm_batch* b, hmm_plan
 
 // Shifted weighted moments of the multivariate families from the
 // occupancies in stats->gamma, reduced in fixed order into stats->mv_rec.
-void mv_statistics(hmm_ctx ctx, hmm_model model, const hmm_batch* b, hmm_plan plan, hmm_stats stats,
-                   cudaStream_t st) {
+int mv_statistics(hmm_ctx ctx, hmm_model model, const hmm_batch* b, hmm_plan plan, hmm_stats stats,
+                  cudaStream_t st) {
   const int NP = model->NP, KS = model->KS, RS = NP * KS;
   const int64_t S = b->n_seq;
   if (NP <= 32 && !model->any_discrete) stats->mv_part.ensure((size_t)std::max<int64_t>(S, 1) * RS * 4);
   stats->mv_chunk.ensure((size_t)std::max(plan->n_chunks, 1) * RS * 8);
   stats->mv_rec.ensure((size_t)model->M * RS * 8);
-  KTimer kt(ctx, HMM_KT_REDUCE, st);
+  (void)ctx;   // timed inside the caller's reduction region
   if (NP > 32 || model->any_discrete) {
     // tiled raw moments per chunk (symbol counts for the discrete family),
     // fixed-order model sums, then the shift to the current means
@@ -542,13 +543,13 @@ void mv_statistics(hmm_ctx ctx, hmm_model model, const hmm_batch* b, hmm_plan pl
     reduce_chunks_l2<<<model->M, 128, 0, st>>>(stats->mv_chunk.as<double>(), plan->model_chunk_ptr.as<int32_t>(), RS,
                                                stats->mv_rec.as<double>());
     HMM_CUDA(cudaGetLastError());
-    if (model->any_discrete) return;   // counts need no shift
+    if (model->any_discrete) return (plan->n_chunks > 0) + 1;   // counts need no shift
     const int n = model->M * NP;
     mv_shift_kernel<<<(n + 127) / 128, 128, 0, st>>>(model->family.as<int>(), model->mvcoef.as<float>(), model->M,
                                                      NP, model->N, model->D, model->KM, KS,
                                                      stats->mv_rec.as<double>());
     HMM_CUDA(cudaGetLastError());
-    return;
+    return (plan->n_chunks > 0) + 2;
   }
   if (S > 0) {
     mv_stats_kernel<<<(unsigned)S, 128, 0, st>>>(model->family.as<int>(), model->mvcoef.as<float>(), NP, model->N,
@@ -565,6 +566,7 @@ void mv_statistics(hmm_ctx ctx, hmm_model model, const hmm_batch* b, hmm_plan pl
   reduce_chunks_l2<<<model->M, 128, 0, st>>>(stats->mv_chunk.as<double>(), plan->model_chunk_ptr.as<int32_t>(), RS,
                                              stats->mv_rec.as<double>());
   HMM_CUDA(cudaGetLastError());
+  return (S > 0) + (plan->n_chunks > 0) + 1;
 }
 
 // Large-N E-step (padded N > 32): emission table, forward and backward
@@ -619,9 +621,11 @@ void run_estep_large(hmm_ctx ctx, hmm_model model, const hmm_batch* b, hmm_plan 
   KTimer kt(ctx, HMM_KT_REDUCE, st);
   HMM_CUDA(launch_large_post(a, NP, N, S, gamma, ctx->lg_rz.as<float>(), ll, ctx->status, st));
   if (!want_stats) return;
+  kt.kernels = 4;   // post, statistics, xi reduction, model reduction (+ below)
   const bool table_stats = model->table_family();
   HMM_CUDA(launch_large_stats(a, b->values, gamma, S, table_stats, ctx->partials.as<float>(), st));
   if (ctx->tensor_rec && tc_xi_supported(NP)) {
+    kt.kernels += 2 + (plan->n_tiles > 0);   // prep (+ pad) + GEMM in place of the CUDA-core xi
     ctx->xi_xt.ensure((size_t)NP * plan->xi_ktot * 4);
     ctx->xi_yt.ensure((size_t)NP * plan->xi_ktot * 4);
     HMM_CUDA(launch_tc_xi(a, ctx->lg_rz.as<float>(), plan->tile_seq.as<int32_t>(), plan->tile_row.as<int32_t>(),
@@ -639,7 +643,8 @@ void run_estep_large(hmm_ctx ctx, hmm_model model, const hmm_batch* b, hmm_plan 
   reduce_chunks_l2<<<model->M, 256, 0, st>>>(ctx->chunk_rec.as<double>(), plan->model_chunk_ptr.as<int32_t>(),
                                              rec_size(NP), stats->rec.as<double>());
   HMM_CUDA(cudaGetLastError());
-  if (model->table_family()) mv_statistics(ctx, model, b, plan, stats, st);
+  kt.kernels += 1;   // the xi kernel of either form
+  if (model->table_family()) kt.kernels += mv_statistics(ctx, model, b, plan, stats, st);
   stats->valid = true;
 }
 
@@ -686,6 +691,7 @@ void run_estep(hmm_ctx ctx, hmm_model model, const hmm_batch* b, hmm_plan plan, 
     pa.loglik = ll;
     {
       KTimer kt(ctx, HMM_KT_PLAIN, st);
+      kt.kernels = 2;
       HMM_CUDA(launch_plain(NP, pa, st));
     }
   }
@@ -724,6 +730,7 @@ void run_estep(hmm_ctx ctx, hmm_model model, const hmm_batch* b, hmm_plan plan, 
   }
   if (want_stats) {
     KTimer kt(ctx, HMM_KT_REDUCE, st);
+    kt.kernels = (plan->n_chunks > 0) + 1;
     const int RS = rec_size(NP);
     ctx->chunk_rec.ensure((size_t)std::max(plan->n_chunks, 1) * RS * 8);
     if (plan->n_chunks > 0) {
@@ -735,7 +742,7 @@ void run_estep(hmm_ctx ctx, hmm_model model, const hmm_batch* b, hmm_plan plan, 
     reduce_chunks_l2<<<model->M, 256, 0, st>>>(ctx->chunk_rec.as<double>(), plan->model_chunk_ptr.as<int32_t>(),
                                                RS, stats->rec.as<double>());
     HMM_CUDA(cudaGetLastError());
-    if (mv_stats) mv_statistics(ctx, model, b, plan, stats, st);
+    if (mv_stats) kt.kernels += mv_statistics(ctx, model, b, plan, stats, st);
     stats->valid = true;
   }
 }
@@ -778,6 +785,7 @@ void run_mstep(hmm_ctx ctx, hmm_model model, hmm_stats stats, const MStepOpts& o
   }
   {
     KTimer kt(ctx, HMM_KT_MSTEP, st);
+    kt.kernels = 1 + 2 * (int)model->any_discrete + 2 * (int)model->any_mv;
     mstep_kernel<<<model->M, model->NP, 0, st>>>(model->bufs(), stats->rec.as<double>(), o, dps);
     HMM_CUDA(cudaGetLastError());
     if (model->any_discrete) {   // Sec. 4 "Discrete": weighted symbol frequencies
@@ -815,6 +823,7 @@ void run_mstep(hmm_ctx ctx, hmm_model model, hmm_stats stats, const MStepOpts& o
   const unsigned blocks = (unsigned)((S * 32 + 255) / 256);
   const int nthr = model->M * NP;
   KTimer kt(ctx, HMM_KT_MSTEP, st);
+  kt.kernels = 2 + (passes + 1) * ((int)model->any_negbin + 3 + (plan->n_chunks > 0));
   prepare_mstep(model, stats, b, plan);
   // active-state counters, one per pass (the update of pass p fills p + 1);
   // passes with no active state return at once
@@ -1014,7 +1023,7 @@ hmm_status hmm_ctx_profile_read(hmm_ctx ctx, double* h_ms, int64_t* h_launches, 
       HMM_CUDA(cudaEventElapsedTime(&ms, r.e0, r.e1));
       if (r.slot >= 0 && r.slot < HMM_KT_SLOTS) {
         ctx->kt_ms[r.slot] += ms;
-        ctx->kt_n[r.slot] += 1;
+        ctx->kt_n[r.slot] += r.kernels;
       }
       ctx->event_pool.push_back(r.e0);
       ctx->event_pool.push_back(r.e1);

@@ -117,6 +117,7 @@ struct hmm_ctx_s {
   struct Rec {
     int slot;
     cudaEvent_t e0, e1;
+    int kernels;                 // kernels launched between e0 and e1
   };
   std::vector<Rec> pending;
   std::vector<cudaEvent_t> event_pool;

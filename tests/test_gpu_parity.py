@@ -330,3 +330,22 @@ def test_autotune_keeps_results(H, ctx):
     for s in range(0, 300, 17):
         fb = O.forward_backward(oms[mid[s]], values[offsets[s]:offsets[s + 1]])
         check_ll(np.array([ll1[s]]), np.array([fb["logL"]]), s)
+
+
+def test_length_one_sequences_after_other_work(H, ctx):
+    """A chain whose first step is in phase 2 (the forward chain of a length-1
+    sequence) must not read a stale previous-vector buffer into xi: after a
+    large launch has left arbitrary shared memory behind, the statistics of
+    length-1 sequences are finite and their transition sums are zero."""
+    models = synth.small_models("gamma", 16, 1, seed=5)
+    v0, o0, m0 = synth.make_batch(5, models, [3000] * 64, np.zeros(64, np.int32))
+    model = H.Model(ctx, models)
+    H.forward_backward(ctx, model, H.Batch(v0, o0, m0))
+    values, offsets, mid = synth.make_batch(6, models, [1] * 40, np.zeros(40, np.int32))
+    stats, ll = H.estep_stats(ctx, model, H.Batch(values, offsets, mid))
+    rec = stats.get()
+    assert np.all(np.isfinite(rec))
+    N = 16
+    assert np.all(rec[2 + N:2 + N + N * N] == 0.0)
+    fb = [O.forward_backward(om(models[0]), values[offsets[s]:offsets[s + 1]])["logL"] for s in range(40)]
+    check_ll(ll.cpu().numpy(), np.array(fb))
