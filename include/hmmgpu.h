@@ -143,7 +143,7 @@ typedef enum {
   HMM_OPT_PLAIN_ESTEP = 4,    /* 1: run E-steps with the plain float32 log-space
                                  kernels (straight log-sum-exp of Sec. 3.2, N^2
                                  exponentials per step) -- the GPU baseline     */
-  HMM_OPT_TENSOR_RECURRENCE = 5 /* 1: padded N in {64, ..., 512} run the forward
+  HMM_OPT_TENSOR_RECURRENCE = 5, /* 1: padded N in {64, ..., 512} run the forward
                                  and backward recursions (Eq. 2 in the shifted
                                  exp-space form) as tcgen05 GEMMs with FP16
                                  operands and FP32 accumulation; the shift and
@@ -151,6 +151,12 @@ typedef enum {
                                  float32 CUDA-core recursions.  The FP16 path's
                                  error against float64 is larger than the float32
                                  path's (about 1e-3 absolute on gamma).          */
+  HMM_OPT_TIME_PARALLEL = 6     /* forward-backward without statistics at padded
+                                 N <= 32: 0 (default) runs the time-parallel form
+                                 (chunk transfer matrices, boundary vectors,
+                                 chunks recomputed in parallel) when the batch
+                                 has fewer sequences than SMs and a sequence of
+                                 at least 2048 steps; 1 always; -1 never.        */
 } hmm_option;
 
 /* Kernel timing slots of hmm_ctx_profile_read. */

@@ -27,6 +27,8 @@ constexpr int NST = 6;
 constexpr int NB_YMAX = 512;
 // log2(y!) table for integer y < LF_YMAX (Poisson), float64 -> float32.
 constexpr int LF_YMAX = 1024;
+// Rows per block of the emission-table kernels (grid: sequence x slab).
+constexpr long long EMIS_SLAB = 4096;
 
 // Device status word bits (sticky, read by hmm_ctx_status).
 enum : int {

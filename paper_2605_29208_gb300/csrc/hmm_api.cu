@@ -128,10 +128,14 @@ __global__ void trace_gather_kernel(const double* __restrict__ rec, int RS, int 
 __global__ void bump_kernel(int* it) { *it += 1; }
 
 // Single-state emission log-densities of a whole batch (natural log).
+// Blocks (sequence, slab of EMIS_SLAB rows).
+inline unsigned slabs_of(int64_t max_T) { return (unsigned)std::max<int64_t>(1, (max_T + EMIS_SLAB - 1) / EMIS_SLAB); }
 __global__ void emission_kernel(ModelView mv, const float* __restrict__ y, const int64_t* __restrict__ offsets,
                                 const int32_t* __restrict__ model_id, float* __restrict__ logb) {
   const int s = blockIdx.x;
-  const int64_t b = offsets[s], e = offsets[s + 1];
+  const int64_t b = offsets[s] + (int64_t)blockIdx.y * EMIS_SLAB;
+  const int64_t e = min(offsets[s + 1], b + (int64_t)EMIS_SLAB);
+  if (b >= e) return;
   const int m = model_id[s];
   const int fam = mv.family[m];
   const int N = mv.N, NP = mv.NP;
@@ -251,6 +255,7 @@ void hmm::fill_plan(hmm_plan p, hmm_ctx ctx, hmm_model model, const hmm_batch* b
   {
     p->ctx = ctx;
     p->n_tiles = 0;
+    p->n_tp_chunks = 0;
     p->n_groups = 0;
     p->n_tc_tiles = 0;
     p->estep_G = 0;
@@ -394,6 +399,36 @@ void hmm::fill_plan(hmm_plan p, hmm_ctx ctx, hmm_model model, const hmm_batch* b
         HMM_CUDA(cudaMemcpy(p->tc_tiles.p, tiles.data(), tiles.size() * 4, cudaMemcpyHostToDevice));
       }
     }
+    if (model->NP <= 32 && S > 0) {
+      // time-parallel chunks of L steps: the boundary walk costs ~T/L
+      // sequential chunk steps and the chunks ~L sequential steps each, so L
+      // ~ sqrt(T) (a power of two in [64, 4096]) balances the two
+      int L = 64;
+      while (L < 4096 && (double)L * L < 4.0 * (double)maxT) L *= 2;
+      p->tp_L = L;
+      const int TP_L = L;
+      std::vector<int32_t> cs, ct, s0(S), sn(S);
+      for (int64_t q2 = 0; q2 < S; ++q2) {
+        const int64_t Tq = ho[q2 + 1] - ho[q2];
+        s0[q2] = (int32_t)cs.size();
+        for (int64_t t = 0; t < Tq; t += TP_L) {
+          cs.push_back((int32_t)q2);
+          ct.push_back((int32_t)t);
+        }
+        sn[q2] = (int32_t)cs.size() - s0[q2];
+      }
+      p->n_tp_chunks = (int)cs.size();
+      p->tp_chunk_seq.ensure(std::max<size_t>(cs.size(), 1) * 4);
+      p->tp_chunk_t0.ensure(std::max<size_t>(ct.size(), 1) * 4);
+      p->tp_seq_chunk0.ensure((size_t)S * 4);
+      p->tp_seq_nchunk.ensure((size_t)S * 4);
+      if (!cs.empty()) {
+        HMM_CUDA(cudaMemcpy(p->tp_chunk_seq.p, cs.data(), cs.size() * 4, cudaMemcpyHostToDevice));
+        HMM_CUDA(cudaMemcpy(p->tp_chunk_t0.p, ct.data(), ct.size() * 4, cudaMemcpyHostToDevice));
+      }
+      HMM_CUDA(cudaMemcpy(p->tp_seq_chunk0.p, s0.data(), (size_t)S * 4, cudaMemcpyHostToDevice));
+      HMM_CUDA(cudaMemcpy(p->tp_seq_nchunk.p, sn.data(), (size_t)S * 4, cudaMemcpyHostToDevice));
+    }
     int uf = -2;
     for (int64_t q2 = 0; q2 < S; ++q2) {
       const int f = model->h_family[hm[q2]];
@@ -415,7 +450,9 @@ void hmm::destroy_plan(hmm_plan p) {
   p->tile_row.release();
   p->lg_groups.release();
   p->tc_tiles.release();
-  for (auto* bb : {&p->xi_kseq, &p->xi_kc0, &p->xi_kused, &p->xi_kpad}) bb->release();
+  for (auto* bb : {&p->xi_kseq, &p->xi_kc0, &p->xi_kused, &p->xi_kpad, &p->tp_chunk_seq, &p->tp_chunk_t0,
+                   &p->tp_seq_chunk0, &p->tp_seq_nchunk})
+    bb->release();
   delete p;
 }
 
@@ -499,16 +536,16 @@ const float* mv_table(hmm_ctx ctx, hmm_model model, const hmm_batch* b, hmm_plan
   if (model->any_discrete) {
     if (b->n_seq > 0) {
       KTimer kt(ctx, HMM_KT_EMISSION, st);
-      discrete_emission_kernel<<<(unsigned)b->n_seq, 128, 0, st>>>(model->dtab.as<float>(), model->NP, model->N,
-                                                                   model->K, b->values, b->offsets, b->model_id,
-                                                                   ctx->mvlogb.as<float>());
+      discrete_emission_kernel<<<dim3((unsigned)b->n_seq, slabs_of(plan->max_T)), 128, 0, st>>>(
+          model->dtab.as<float>(), model->NP, model->N, model->K, b->values, b->offsets, b->model_id,
+          ctx->mvlogb.as<float>());
       HMM_CUDA(cudaGetLastError());
     }
   } else if (!model->any_mv) {
     if (b->n_seq > 0) {
       KTimer kt(ctx, HMM_KT_EMISSION, st);
-      emission_kernel<<<(unsigned)b->n_seq, 128, 0, st>>>(model->view(), b->values, b->offsets, b->model_id,
-                                                         ctx->mvlogb.as<float>());
+      emission_kernel<<<dim3((unsigned)b->n_seq, slabs_of(plan->max_T)), 128, 0, st>>>(
+          model->view(), b->values, b->offsets, b->model_id, ctx->mvlogb.as<float>());
       HMM_CUDA(cudaGetLastError());
     }
   } else if (plan->n_tiles > 0) {
@@ -619,7 +656,7 @@ void run_estep_large(hmm_ctx ctx, hmm_model model, const hmm_batch* b, hmm_plan 
       HMM_CUDA(launch_large_fb(NP, a, st));
   }
   KTimer kt(ctx, HMM_KT_REDUCE, st);
-  HMM_CUDA(launch_large_post(a, NP, N, S, gamma, ctx->lg_rz.as<float>(), ll, ctx->status, st));
+  HMM_CUDA(launch_large_post(a, NP, N, S, plan->max_T, gamma, ctx->lg_rz.as<float>(), ll, ctx->status, st));
   if (!want_stats) return;
   kt.kernels = 4;   // post, statistics, xi reduction, model reduction (+ below)
   const bool table_stats = model->table_family();
@@ -648,6 +685,68 @@ void run_estep_large(hmm_ctx ctx, hmm_model model, const hmm_batch* b, hmm_plan 
   stats->valid = true;
 }
 
+// Time-parallel forward-backward (no statistics) at padded N <= 32: the
+// chunked transfer / boundary / recompute kernels write the rows of the
+// large-N path and its posterior kernel finishes (gamma, log-likelihoods).
+bool use_time_parallel(hmm_ctx ctx, hmm_model model, hmm_plan plan, bool want_stats) {
+  if (want_stats || model->NP > 32 || ctx->time_parallel < 0 || ctx->plain_estep) return false;
+  if (plan->n_tp_chunks == 0) return false;
+  if (ctx->time_parallel > 0) return true;
+  return plan->n_seq <= ctx->n_sm && plan->max_T >= 2048;
+}
+
+void run_fb_time_parallel(hmm_ctx ctx, hmm_model model, const hmm_batch* b, hmm_plan plan, const float* logb,
+                          float* gamma, double* ll, cudaStream_t st) {
+  const int NP = model->NP, N = model->N;
+  const int64_t S = b->n_seq, TT = std::max<int64_t>(b->total_T, 1);
+  if (!logb) logb = mv_table(ctx, model, b, plan, st);
+  ctx->scratch.ensure(TT * NP * 4 + 64);
+  ctx->lg_bv.ensure(TT * NP * 4);
+  ctx->lg_off.ensure(TT * 2 * 8);
+  ctx->lg_rz.ensure(TT * 4);
+  const size_t nc = (size_t)std::max(plan->n_tp_chunks, 1);
+  ctx->tp_Q.ensure(nc * 2 * NP * NP * 4);
+  ctx->tp_qexp.ensure(nc * 2 * NP * 8);
+  ctx->tp_bvec.ensure(nc * 2 * NP * 4);
+  ctx->tp_boff.ensure(nc * 2 * 8);
+  if (!gamma) {
+    ctx->gamma.ensure(TT * N * 4);
+    gamma = ctx->gamma.as<float>();
+  }
+  if (S == 0) return;
+  TpArgs t{};
+  t.L = plan->tp_L;
+  t.logb = logb;
+  t.offsets = b->offsets;
+  t.model_id = b->model_id;
+  t.mv = model->view();
+  t.chunk_seq = plan->tp_chunk_seq.as<int32_t>();
+  t.chunk_t0 = plan->tp_chunk_t0.as<int32_t>();
+  t.seq_chunk0 = plan->tp_seq_chunk0.as<int32_t>();
+  t.seq_nchunk = plan->tp_seq_nchunk.as<int32_t>();
+  t.Q = ctx->tp_Q.as<float>();
+  t.qexp = ctx->tp_qexp.as<long long>();
+  t.bvec = ctx->tp_bvec.as<float>();
+  t.boff = ctx->tp_boff.as<long long>();
+  t.fv = ctx->scratch.as<float>();
+  t.bv = ctx->lg_bv.as<float>();
+  t.oa = ctx->lg_off.as<double>();
+  t.ob = ctx->lg_off.as<double>() + TT;
+  {
+    KTimer kt(ctx, HMM_KT_ESTEP, st);
+    kt.kernels = 3;
+    HMM_CUDA(launch_tp_fb(NP, t, plan->n_tp_chunks, (int)S, st));
+  }
+  LargeArgs a{};
+  a.offsets = b->offsets;
+  a.fv = t.fv;
+  a.bv = t.bv;
+  a.oa = t.oa;
+  a.ob = t.ob;
+  KTimer kt(ctx, HMM_KT_REDUCE, st);
+  HMM_CUDA(launch_large_post(a, NP, N, S, plan->max_T, gamma, ctx->lg_rz.as<float>(), ll, ctx->status, st));
+}
+
 // The fused E-step over a batch.  gamma (optional) receives [total_T][N].
 void run_estep(hmm_ctx ctx, hmm_model model, const hmm_batch* b, hmm_plan plan, const float* logb,
                float* gamma, double* loglik, bool want_stats, hmm_stats stats, cudaStream_t st) {
@@ -659,6 +758,15 @@ void run_estep(hmm_ctx ctx, hmm_model model, const hmm_batch* b, hmm_plan plan, 
       ll = ctx->loglik.as<double>();
     }
     run_estep_large(ctx, model, b, plan, logb, gamma, ll, want_stats, stats, st);
+    return;
+  }
+  if (use_time_parallel(ctx, model, plan, want_stats)) {
+    double* ll = loglik;
+    if (!ll) {
+      ctx->loglik.ensure(std::max<int64_t>(b->n_seq, 1) * 8);
+      ll = ctx->loglik.as<double>();
+    }
+    run_fb_time_parallel(ctx, model, b, plan, logb, gamma, ll, st);
     return;
   }
   if (model->table_family() && ctx->plain_estep)
@@ -980,6 +1088,7 @@ hmm_status hmm_ctx_destroy(hmm_ctx ctx) {
     ctx->lg_xi.release();
     ctx->xi_xt.release();
     ctx->xi_yt.release();
+    for (auto* bb : {&ctx->tp_Q, &ctx->tp_qexp, &ctx->tp_bvec, &ctx->tp_boff}) bb->release();
     delete ctx;
   });
 }
@@ -1008,6 +1117,7 @@ hmm_status hmm_ctx_set_option(hmm_ctx ctx, int32_t key, int64_t value) {
       case HMM_OPT_VITERBI_LANES: ctx->viterbi_lanes = (int)value; break;
       case HMM_OPT_PLAIN_ESTEP: ctx->plain_estep = value != 0; break;
       case HMM_OPT_TENSOR_RECURRENCE: ctx->tensor_rec = value != 0; break;
+      case HMM_OPT_TIME_PARALLEL: ctx->time_parallel = (int)value; break;
       default: throw Error{HMM_E_ARG, "unknown option"};
     }
   });
@@ -1320,27 +1430,29 @@ hmm_status hmm_emission_logpdf(hmm_ctx ctx, hmm_model model, const hmm_batch* ba
     HMM_REQUIRE(ctx && model && d_logb, "NULL argument");
     check_batch(model, batch);
     if (batch->n_seq == 0) return;
+    PlanRef prr;
+    get_plan(ctx, model, batch, S(stream), prr);
+    const unsigned slabs = slabs_of(prr.p->max_T);
     if (model->any_discrete) {
       KTimer kt(ctx, HMM_KT_EMISSION, S(stream));
-      discrete_emission_kernel<<<(unsigned)batch->n_seq, 128, 0, S(stream)>>>(
+      discrete_emission_kernel<<<dim3((unsigned)batch->n_seq, slabs), 128, 0, S(stream)>>>(
           model->dtab.as<float>(), model->NP, model->N, model->K, batch->values, batch->offsets, batch->model_id,
           d_logb);
       HMM_CUDA(cudaGetLastError());
+      if (prr.owned) HMM_CUDA(cudaStreamSynchronize(S(stream)));
       return;
     }
     if (model->any_mv) {
-      PlanRef pr;
-      get_plan(ctx, model, batch, S(stream), pr);
-      if (pr.p->n_tiles > 0) {
+      if (prr.p->n_tiles > 0) {
         KTimer kt(ctx, HMM_KT_EMISSION, S(stream));
-        launch_mv_emission(model, batch, pr.p, d_logb, S(stream));
+        launch_mv_emission(model, batch, prr.p, d_logb, S(stream));
       }
-      if (pr.owned) HMM_CUDA(cudaStreamSynchronize(S(stream)));
+      if (prr.owned) HMM_CUDA(cudaStreamSynchronize(S(stream)));
       return;
     }
     KTimer kt(ctx, HMM_KT_EMISSION, S(stream));
-    emission_kernel<<<(unsigned)batch->n_seq, 128, 0, S(stream)>>>(model->view(), batch->values, batch->offsets,
-                                                                   batch->model_id, d_logb);
+    emission_kernel<<<dim3((unsigned)batch->n_seq, slabs), 128, 0, S(stream)>>>(model->view(), batch->values,
+                                                                             batch->offsets, batch->model_id, d_logb);
     HMM_CUDA(cudaGetLastError());
   });
 }

@@ -7,6 +7,8 @@ namespace hmm {
 namespace {
 
 // One warp per row: Z_t, gamma_t, 1/Z_t and (at t = 0) the log-likelihood.
+// Block (sequence, slab): the slab's POST_SLAB rows of the sequence.
+constexpr int64_t POST_SLAB = 2048;
 __global__ void large_post_kernel(const float* __restrict__ fv, const float* __restrict__ bv,
                                   const double* __restrict__ oa, const double* __restrict__ ob,
                                   const int64_t* __restrict__ offsets, int NP, int N, float* __restrict__ gamma,
@@ -15,10 +17,12 @@ __global__ void large_post_kernel(const float* __restrict__ fv, const float* __r
   const int64_t b = offsets[s], e = offsets[s + 1];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   if (e == b) {
-    if (threadIdx.x == 0 && loglik) loglik[s] = 0.0;
+    if (threadIdx.x == 0 && blockIdx.y == 0 && loglik) loglik[s] = 0.0;
     return;
   }
-  for (int64_t t = b + warp; t < e; t += nw) {
+  // rows of this block: slab blockIdx.y of POST_SLAB rows
+  const int64_t r0 = b + (int64_t)blockIdx.y * POST_SLAB, r1 = min(e, r0 + POST_SLAB);
+  for (int64_t t = r0 + warp; t < r1; t += nw) {
     float z = 0.f;
     for (int j = lane; j < NP; j += 32) z = fmaf(fv[t * NP + j], bv[t * NP + j], z);
     z = warp_sum_f(z);
@@ -241,10 +245,11 @@ cudaError_t launch_large_fb(int NP, const LargeArgs& a, cudaStream_t st) {
   return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_large_post(const LargeArgs& a, int NP, int N, int64_t n_seq, float* gamma, float* rz,
-                              double* loglik, int* status, cudaStream_t st) {
+cudaError_t launch_large_post(const LargeArgs& a, int NP, int N, int64_t n_seq, int64_t max_T, float* gamma,
+                              float* rz, double* loglik, int* status, cudaStream_t st) {
   if (n_seq == 0) return cudaSuccess;
-  large_post_kernel<<<(unsigned)n_seq, 256, 0, st>>>(a.fv, a.bv, a.oa, a.ob, a.offsets, NP, N, gamma, rz, loglik,
+  const unsigned slabs = (unsigned)std::max<int64_t>(1, (max_T + POST_SLAB - 1) / POST_SLAB);
+  large_post_kernel<<<dim3((unsigned)n_seq, slabs), 256, 0, st>>>(a.fv, a.bv, a.oa, a.ob, a.offsets, NP, N, gamma, rz, loglik,
                                                      status);
   return cudaGetLastError();
 }

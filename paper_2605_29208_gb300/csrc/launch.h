@@ -18,7 +18,7 @@ int default_viterbi_G(int NP, int64_t n_seq, int n_sm);
 
 // Sequences per work item of each kernel.
 inline int estep_seqs_per_item(int G) { return 16 / G; }
-inline int viterbi_seqs_per_item(int G) { return 32 / G; }
+inline int viterbi_seqs_per_item(int G) { return 16 / G; }   // two chains per sequence
 
 constexpr int kWarpsPerBlock = 4;
 
@@ -51,9 +51,32 @@ cudaError_t launch_tc_xi(const LargeArgs& a, const float* rz, const int32_t* til
                          int n_tiles, const int64_t* kseq, const int64_t* kc0, const int32_t* kused,
                          const int32_t* kpad, int n_chunks, int64_t ktot, float* XT, float* YT, double* xi_chunk,
                          int* status, cudaStream_t st);
+// time-parallel forward-backward rows for small N (padded N <= 32): chunks of
+// L steps, transfer matrices, boundary vectors, recomputed rows in the
+// large-N row format (fv, bv, oa, ob)
+struct TpArgs {
+  int L;                        // chunk length (steps)
+  const float* logb;            // [total_T][N] natural log
+  const int64_t* offsets;
+  const int32_t* model_id;
+  ModelView mv;
+  const int32_t* chunk_seq;     // [n_chunks] sequence of each chunk
+  const int32_t* chunk_t0;      // [n_chunks] first step of each chunk
+  const int32_t* seq_chunk0;    // [n_seq] first chunk of each sequence
+  const int32_t* seq_nchunk;    // [n_seq] its chunk count
+  float* Q;                     // [n_chunks][2][NP][NP] transfer matrices (rows scaled)
+  long long* qexp;              // [n_chunks][2][NP] log2 row scales (integers)
+  float* bvec;                  // [n_chunks][2][NP] boundary vectors
+  long long* boff;              // [n_chunks][2] their log2 offsets (integers)
+  float* fv;
+  float* bv;
+  double* oa;
+  double* ob;
+};
+cudaError_t launch_tp_fb(int NP, const TpArgs& a, int n_chunks, int n_seq, cudaStream_t st);
 // posterior rows: gamma [total_T][N], 1/Z_t [total_T], log-likelihoods
-cudaError_t launch_large_post(const LargeArgs& a, int NP, int N, int64_t n_seq, float* gamma, float* rz,
-                              double* loglik, int* status, cudaStream_t st);
+cudaError_t launch_large_post(const LargeArgs& a, int NP, int N, int64_t n_seq, int64_t max_T, float* gamma,
+                              float* rz, double* loglik, int* status, cudaStream_t st);
 // per-sequence statistic partials [n_seq][NP][NST] (slot NST-1: gamma_1)
 cudaError_t launch_large_stats(const LargeArgs& a, const float* y, const float* gamma, int64_t n_seq, bool table,
                                float* part, cudaStream_t st);

@@ -470,12 +470,15 @@ __global__ void discrete_derive_kernel(const double* __restrict__ theta, int M, 
   for (int z = 0; z < K; ++z) t[z] = (k < N && th[z] > 0.0) ? (float)log(th[z]) : -INFINITY;
 }
 
-// log b table [total_T][N]: one block per sequence, threads over (t, state)
+// log b table [total_T][N]: blocks (sequence, slab of EMIS_SLAB rows),
+// threads over (t, state)
 __global__ void discrete_emission_kernel(const float* __restrict__ dtab, int NP, int N, int K,
                                          const float* __restrict__ y, const int64_t* __restrict__ offsets,
                                          const int32_t* __restrict__ model_id, float* __restrict__ logb) {
   const int s = blockIdx.x;
-  const int64_t b = offsets[s], e = offsets[s + 1];
+  const int64_t b = offsets[s] + (int64_t)blockIdx.y * EMIS_SLAB;
+  const int64_t e = min(offsets[s + 1], b + (int64_t)EMIS_SLAB);
+  if (b >= e) return;
   const int m = model_id[s];
   const float* tab = dtab + (size_t)m * NP * K;
   for (int64_t idx = threadIdx.x; idx < (e - b) * N; idx += blockDim.x) {

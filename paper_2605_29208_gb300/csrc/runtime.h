@@ -113,6 +113,8 @@ struct hmm_ctx_s {
   int viterbi_lanes = 0;
   int plain_estep = 0;
   int tensor_rec = 0;            // HMM_OPT_TENSOR_RECURRENCE
+  int time_parallel = 0;         // HMM_OPT_TIME_PARALLEL
+  hmm::DevBuf tp_Q, tp_qexp, tp_bvec, tp_boff;   // time-parallel chunk data
   // kernel timing
   struct Rec {
     int slot;
@@ -183,6 +185,11 @@ struct hmm_plan_s {
   // [xi_kc0[c], xi_kc0[c] + xi_kpad[c]) of which xi_kused[c] are rows
   hmm::DevBuf xi_kseq, xi_kc0, xi_kused, xi_kpad;
   int64_t xi_ktot = 0;
+  // time-parallel chunks (padded N <= 32): chunk -> (sequence, first step),
+  // sequence -> (first chunk, chunk count)
+  hmm::DevBuf tp_chunk_seq, tp_chunk_t0, tp_seq_chunk0, tp_seq_nchunk;
+  int n_tp_chunks = 0;
+  int tp_L = 128;                // chunk length of the time-parallel path
   int viterbi_G = 0;
   std::vector<int32_t> h_order;
 };

@@ -64,7 +64,7 @@ int default_viterbi_G(int NP, int64_t n_seq, int n_sm) {
   int G = NP >= 4 ? NP / 4 : 1;
   if (!viterbi_small_supported(NP, G)) G = 1;
   while (G < 16 && G < NP && viterbi_small_supported(NP, 2 * G)) {
-    const double warps = (double)n_seq / (32 / G);
+    const double warps = (double)n_seq / viterbi_seqs_per_item(G);
     if (warps >= 2.0 * n_sm) break;
     G *= 2;
   }
