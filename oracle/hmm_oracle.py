@@ -23,6 +23,10 @@ Citations name the paper's section and equation numbers:
             Eq. 15-16 (CM-step 1), Eq. 17-19 (CM-step 2 for nu).
   Sec. 4.4  state-collapse guard (N_j < 1e-8 keeps the parameters).
   Sec. 4.5  diagonal Gaussian (Eq. 20-21), full covariance (Eq. 22-24).
+  Sec. 4    closed forms of the further scalar families: log-normal,
+            exponential, Rayleigh, uniform, discrete; Sec. 4.2 chi-squared
+            (Gamma with beta = 1/2, one parameter) and Pareto (min, then a
+            closed-form shape).
 
 Where the paper is silent the readings used are listed in the module
 constants and functions below (transition/initial M-step, tie breaks,
@@ -55,7 +59,8 @@ NEGBIN_RMAX = 1e6            # reading: no finite MLE when var <= mean
 KAPPA_MAX = 1e6              # reading: R -> 1 gives kappa -> inf
 
 FAMILIES = ("gauss", "poisson", "gamma", "beta", "weibull", "negbin",
-            "student_t", "vonmises", "diag_gauss", "full_gauss", "discrete")
+            "student_t", "vonmises", "diag_gauss", "full_gauss", "discrete",
+            "lognormal", "exponential", "rayleigh", "uniform", "chisq", "pareto")
 
 
 @dataclass
@@ -160,6 +165,39 @@ def emission_logpdf(model: Model, y: np.ndarray) -> np.ndarray:
             idx = np.where(ok, y, 0).astype(np.int64)
             out = np.log(pk[:, idx]).T           # [T, N]
             return np.where(ok[:, None], out, -np.inf)
+        if f == "lognormal":    # Sec. 4 "Log-normal": a Gaussian on log y, y > 0
+            mu, s2 = p["mu"], p["sigma2"]
+            yy = y[:, None]
+            ly = np.log(np.where(yy > 0, yy, 1.0))
+            out = -ly - 0.5 * np.log(2 * np.pi * s2) - (ly - mu) ** 2 / (2 * s2)
+            return np.where(yy > 0, out, -np.inf)
+        if f == "exponential":  # Sec. 4 "Exponential": rate lambda, y >= 0
+            lam = p["lam"]
+            yy = y[:, None]
+            out = np.log(lam) - lam * yy
+            return np.where(yy >= 0, out, -np.inf)
+        if f == "rayleigh":     # Sec. 4 "Rayleigh": y / s2 exp(-y^2 / (2 s2)), y >= 0
+            s2 = p["sigma2"]
+            yy = y[:, None]
+            out = np.log(yy) - np.log(s2) - yy ** 2 / (2 * s2)
+            return np.where(yy >= 0, out, -np.inf)
+        if f == "uniform":      # Sec. 4 "Uniform": 1 / (b - a) on the closed interval [a, b]
+            a, b = p["a"], p["b"]
+            yy = y[:, None]
+            out = -np.log(b - a) + 0 * yy
+            return np.where((yy >= a) & (yy <= b), out, -np.inf)
+        if f == "chisq":        # Sec. 4.2 "Chi-squared": Gamma(nu / 2, rate 1/2), y > 0
+            nu = p["nu"]
+            yy = y[:, None]
+            ly = np.log(np.where(yy > 0, yy, 1.0))
+            out = (nu / 2 - 1) * ly - yy / 2 - nu / 2 * np.log(2.0) - sp.gammaln(nu / 2)
+            return np.where(yy > 0, out, -np.inf)
+        if f == "pareto":       # Sec. 4.2 "Pareto": alpha xm^alpha / y^(alpha+1), y >= xm
+            xm, al = p["xm"], p["alpha"]
+            yy = y[:, None]
+            ly = np.log(np.where(yy > 0, yy, 1.0))
+            out = np.log(al) + al * np.log(xm) - (al + 1) * ly
+            return np.where(yy >= xm, out, -np.inf)
         if f == "full_gauss":   # Sec. 4.5, Eq. 22 through the Cholesky factor
             mu, cov = p["mu"], p["cov"]          # [N, D], [N, D, D]
             T, D = y.shape
@@ -582,10 +620,88 @@ def mstep_full_gauss(w, y, cur):
     return dict(mu=mu, cov=cov)
 
 
+def _safe_log(y):
+    """log y where y > 0, else 0 (rows outside the support carry weight 0)."""
+    return np.log(np.where(y > 0, y, 1.0))
+
+
+def mstep_lognormal(w, y, cur):
+    """Sec. 4 "Log-normal": the Gaussian M-step applied to log y."""
+    Nj = w.sum()
+    ly = _safe_log(y)
+    mu = np.sum(w * ly) / Nj
+    return dict(mu=mu, sigma2=np.sum(w * (ly - mu) ** 2) / Nj)
+
+
+def mstep_exponential(w, y, cur):
+    """Sec. 4 "Exponential": lambda = 1 / ybar_j."""
+    return dict(lam=w.sum() / np.sum(w * y))
+
+
+def mstep_rayleigh(w, y, cur):
+    """Sec. 4 "Rayleigh": sigma^2 = (2 N_j)^-1 sum_t gamma_t(j) y_t^2."""
+    return dict(sigma2=np.sum(w * y * y) / (2 * w.sum()))
+
+
+def support_rows(family, y, cur):
+    """Reading of the min / max in the Uniform and Pareto M-steps (Sec. 4,
+    Sec. 4.2): taken over the rows the state can emit under its current
+    parameters, {t : b_j(y_t) > 0}.  These are the rows with gamma_t(j) > 0
+    whenever pi and A are strictly positive, and the maximiser of Eq. 6 must
+    keep every such row inside the new support; the test is exact in any
+    precision (a comparison of y with the current bounds)."""
+    if family == "uniform":
+        return (y >= cur["a"]) & (y <= cur["b"])
+    if family == "pareto":
+        return y >= cur["xm"]
+    raise ValueError(family)
+
+
+def mstep_uniform(w, y, cur):
+    """Sec. 4 "Uniform": a = min_t y_t, b = max_t y_t over the state's rows."""
+    sel = support_rows("uniform", y, cur)
+    if not sel.any():
+        return dict(a=np.nan, b=np.nan)
+    return dict(a=np.min(y[sel]), b=np.max(y[sel]))
+
+
+def mstep_chisq(w, y, cur):
+    """Sec. 4.2 "Chi-squared": the Gamma M-step with alpha = nu/2 and rate
+    beta = 1/2 fixed, optimised over nu alone.  The weighted score in
+    x = nu/2 is N_j (mean_w log y - log 2 - digamma(x)); digamma increases
+    from -inf to +inf on (0, inf), so the root is unique; it is bracketed
+    and found by Brent's method (a library root finder)."""
+    from scipy.optimize import brentq
+    Nj = w.sum()
+    c = np.sum(w * _safe_log(y)) / Nj - np.log(2.0)
+    lo, hi = 1e-12, 1.0
+    while sp.digamma(hi) < c:
+        hi *= 2.0
+        if hi > 1e300:
+            return dict(nu=np.nan)
+    if sp.digamma(lo) > c:
+        return dict(nu=np.nan)
+    x = brentq(lambda v: sp.digamma(v) - c, lo, hi, xtol=1e-15, rtol=4 * np.finfo(float).eps, maxiter=500)
+    return dict(nu=2.0 * x)
+
+
+def mstep_pareto(w, y, cur):
+    """Sec. 4.2 "Pareto": xm = min_t y_t over the state's rows (the
+    constrained MLE), then alpha = N_j / sum_t gamma_t(j) log(y_t / xm)."""
+    sel = support_rows("pareto", y, cur)
+    if not sel.any():
+        return dict(xm=np.nan, alpha=np.nan)
+    xm = np.min(y[sel])
+    Nj = w.sum()
+    return dict(xm=xm, alpha=Nj / (np.sum(w * _safe_log(y)) - Nj * np.log(xm)))
+
+
 MSTEP = dict(gauss=mstep_gauss, poisson=mstep_poisson, gamma=mstep_gamma,
              beta=mstep_beta, weibull=mstep_weibull, negbin=mstep_negbin,
              student_t=mstep_student_t, vonmises=mstep_vonmises,
-             diag_gauss=mstep_diag_gauss, full_gauss=mstep_full_gauss, discrete=mstep_discrete)
+             diag_gauss=mstep_diag_gauss, full_gauss=mstep_full_gauss, discrete=mstep_discrete,
+             lognormal=mstep_lognormal, exponential=mstep_exponential, rayleigh=mstep_rayleigh,
+             uniform=mstep_uniform, chisq=mstep_chisq, pareto=mstep_pareto)
 
 
 def _state_params(model: Model, j: int) -> dict:
@@ -623,7 +739,9 @@ def valid_update(family, res) -> bool:
         return False
     positive = {"gauss": ("sigma2",), "poisson": ("lam",), "gamma": ("alpha", "beta"),
                 "beta": ("a", "b"), "weibull": ("k", "lam"), "negbin": ("r",),
-                "student_t": ("sigma2", "nu"), "vonmises": (), "diag_gauss": ("var",)}
+                "student_t": ("sigma2", "nu"), "vonmises": (), "diag_gauss": ("var",),
+                "lognormal": ("sigma2",), "exponential": ("lam",), "rayleigh": ("sigma2",),
+                "chisq": ("nu",), "pareto": ("xm", "alpha")}
     for k in positive.get(family, ()):
         if not np.all(vals[k] > 0):
             return False
@@ -632,6 +750,8 @@ def valid_update(family, res) -> bool:
     if family == "negbin" and not (0 < vals["p"] < 1):
         return False
     if family == "discrete" and not (np.all(vals["p"] >= 0) and abs(vals["p"].sum() - 1) < 1e-9):
+        return False
+    if family == "uniform" and not vals["a"] < vals["b"]:
         return False
     if family == "full_gauss":
         try:

@@ -37,6 +37,12 @@ PARAM_NAMES = {
     "diag_gauss": ("mu", "var"),
     "full_gauss": ("mu", "cov"),
     "discrete": ("p",),
+    "lognormal": ("mu", "sigma2"),
+    "exponential": ("lam",),
+    "rayleigh": ("sigma2",),
+    "uniform": ("a", "b"),
+    "chisq": ("nu",),
+    "pareto": ("xm", "alpha"),
 }
 
 
@@ -77,6 +83,19 @@ def random_params(rng, family, N, D=1):
         return dict(mu=rng.normal(0, 3, (N, D)), var=rng.uniform(0.2, 2, (N, D)))
     if family == "discrete":      # D = number of symbols; rows Dirichlet(1)
         return dict(p=rng.dirichlet(np.ones(D), size=N))
+    if family == "lognormal":     # mu, sigma2 of log y
+        return dict(mu=rng.normal(0, 1, N), sigma2=rng.uniform(0.1, 1, N))
+    if family == "exponential":
+        return dict(lam=rng.uniform(0.2, 5, N))
+    if family == "rayleigh":
+        return dict(sigma2=rng.uniform(0.2, 4, N))
+    if family == "uniform":       # overlapping intervals
+        a = rng.uniform(-5, 0, N)
+        return dict(a=a, b=a + rng.uniform(1, 6, N))
+    if family == "chisq":
+        return dict(nu=rng.uniform(1, 10, N))
+    if family == "pareto":
+        return dict(xm=rng.uniform(0.5, 3, N), alpha=rng.uniform(1.5, 6, N))
     if family == "full_gauss":
         cov = np.empty((N, D, D))
         for j in range(N):
@@ -114,6 +133,29 @@ def sample_emissions(rng, model, states):
         return rng.vonmises(p["mu"][q], p["kappa"][q])
     if f == "diag_gauss":
         return p["mu"][q] + np.sqrt(p["var"][q]) * rng.standard_normal((n, p["mu"].shape[1]))
+    if f == "lognormal":
+        return np.exp(p["mu"][q] + np.sqrt(p["sigma2"][q]) * rng.standard_normal(n))
+    if f == "exponential":
+        return rng.exponential(1.0 / p["lam"][q])
+    if f == "rayleigh":
+        return rng.rayleigh(np.sqrt(p["sigma2"][q]))
+    if f == "uniform":
+        # drawn on the float32 grid inside [a, b] so the rounded value stays in the support
+        a, b = p["a"][q], p["b"][q]
+        y = np.asarray(a + (b - a) * rng.random(n), np.float32).astype(np.float64)
+        lo = np.asarray(a, np.float32).astype(np.float64)
+        lo = np.where(lo < a, np.nextafter(lo.astype(np.float32), np.float32(np.inf)).astype(np.float64), lo)
+        hi = np.asarray(b, np.float32).astype(np.float64)
+        hi = np.where(hi > b, np.nextafter(hi.astype(np.float32), np.float32(-np.inf)).astype(np.float64), hi)
+        return np.clip(y, lo, hi)
+    if f == "chisq":
+        return rng.chisquare(p["nu"][q])
+    if f == "pareto":
+        # inverse CDF, rounded up onto the float32 grid so y >= xm holds after rounding
+        y = p["xm"][q] * (1.0 - rng.random(n)) ** (-1.0 / p["alpha"][q])
+        y32 = np.asarray(y, np.float32)
+        y32 = np.where(y32.astype(np.float64) < p["xm"][q], np.nextafter(y32, np.float32(np.inf)), y32)
+        return y32.astype(np.float64)
     if f == "full_gauss":
         D = p["mu"].shape[1]
         z = rng.standard_normal((n, D))
@@ -143,6 +185,8 @@ def simulate_many(rng, pi, A, lengths):
     cA = np.cumsum(A, axis=1)
     N = len(pi)
     Q = np.empty((S, Tmax), dtype=np.int64)
+    if Tmax == 0:
+        return [Q[s, :0] for s in range(S)]
     u = rng.random((Tmax, S))
     Q[:, 0] = np.minimum((u[0][:, None] * cpi[-1] >= cpi[None, :]).sum(1), N - 1)
     for t in range(1, Tmax):
@@ -249,6 +293,12 @@ def perturb(rng, model, frac=0.2):
         elif model["family"] == "discrete":
             q = v * rng.uniform(1 - frac, 1 + frac, v.shape)
             params[k] = q / q.sum(axis=1, keepdims=True)
+        elif model["family"] == "uniform":
+            # widened, so that every observation stays inside its state's support
+            w = (model["params"]["b"] - model["params"]["a"]) * rng.uniform(0, frac, v.shape)
+            params[k] = v - w if k == "a" else v + w
+        elif model["family"] == "pareto" and k == "xm":
+            params[k] = v * rng.uniform(1 - frac, 1, v.shape)   # lowered: the support only grows
         elif k == "p":
             params[k] = np.clip(v * rng.uniform(1 - frac, 1 + frac, v.shape), 0.02, 0.98)
         elif k == "cov":
