@@ -45,7 +45,9 @@ def args_parse():
     p.add_argument("--steps", type=int, default=300)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    p.add_argument("--family", choices=["gamma", "student_t"], default="gamma")
+    p.add_argument("--family", default="gamma",
+                   choices=["gamma", "student_t", "gauss", "poisson", "vonmises", "lognormal", "exponential",
+                            "rayleigh", "uniform", "chisq", "pareto"])
     p.add_argument("--workload", choices=["scale", "batching", "precision", "serving", "discrete"], default="scale",
                    help="scale: N=16 x 4096 x 2000 (the bench line); batching: 100k ragged "
                         "sequences, N=8, 1024 mixed-family models")

@@ -75,12 +75,24 @@ typedef enum {
  *                   (categorical)"): the model's `dim` is the number of
  *                   symbols K (2..1024); observations are the symbol indices
  *                   0..K-1, one float per step (a batch's dim is 1)
- * Observations outside a family's support (y <= 0 for Gamma/Weibull,
- * y outside (0,1) for Beta, non-integer or negative counts) have density 0. */
+ *   HMM_LOGNORMAL   mu, sigma2 of log y                 (Sec. 4 "Log-normal")
+ *   HMM_EXPONENTIAL lambda (rate)                       (Sec. 4 "Exponential")
+ *   HMM_RAYLEIGH    sigma2                              (Sec. 4 "Rayleigh")
+ *   HMM_UNIFORM     a, b (a < b; closed interval)       (Sec. 4 "Uniform")
+ *   HMM_CHISQ       nu (degrees of freedom)             (Sec. 4.2 "Chi-squared")
+ *   HMM_PARETO      xm, alpha (scale, shape)            (Sec. 4.2 "Pareto")
+ * Observations outside a family's support (y <= 0 for Gamma/Weibull/
+ * log-normal/chi-squared, y < 0 for exponential/Rayleigh, y outside (0,1)
+ * for Beta, outside [a, b] for uniform, y < xm for Pareto, non-integer or
+ * negative counts) have density 0.  The last six families (and the
+ * discrete one) evaluate their densities into a log b table; a model set
+ * holds families of one group only: the first eight scalar families, the
+ * two multivariate ones, the discrete one, or the last six. */
 typedef enum {
   HMM_GAUSS = 0, HMM_POISSON = 1, HMM_GAMMA = 2, HMM_BETA = 3, HMM_WEIBULL = 4,
   HMM_NEGBIN = 5, HMM_STUDENT_T = 6, HMM_VONMISES = 7, HMM_DIAG_GAUSS = 8,
-  HMM_FULL_GAUSS = 9, HMM_DISCRETE = 10
+  HMM_FULL_GAUSS = 9, HMM_DISCRETE = 10, HMM_LOGNORMAL = 11, HMM_EXPONENTIAL = 12,
+  HMM_RAYLEIGH = 13, HMM_UNIFORM = 14, HMM_CHISQ = 15, HMM_PARETO = 16
 } hmm_family;
 
 typedef struct hmm_ctx_s* hmm_ctx;       /* device + workspace            */
@@ -281,7 +293,13 @@ hmm_status hmm_stats_destroy(hmm_stats stats);
  *   VONMISES  W, W cos y, W sin y
  *   DIAG_GAUSS W, Wy_d (D), Wy_d^2 (D)
  *   FULL_GAUSS W, Wy_d (D), Wy_d y_e (D*D)
- * where W = sum_t gamma_t(j) (x) and x the named function of y_t. */
+ *   DISCRETE  W 1[y = k] (K)
+ *   LOGNORMAL W, W log y, W (log y)^2     EXPONENTIAL W, Wy
+ *   RAYLEIGH  W, Wy^2                     CHISQ       W, W log y
+ *   UNIFORM   W, min y, max y             PARETO      W, W log y, min y
+ * where W = sum_t gamma_t(j) (x) and x the named function of y_t; the
+ * uniform / Pareto min and max run over the rows of the model's sequences
+ * that lie in the state's current support (b_j(y_t) > 0). */
 int64_t hmm_stats_size(hmm_stats stats);
 hmm_status hmm_stats_get(hmm_stats stats, double* h_out, int64_t n_values);
 

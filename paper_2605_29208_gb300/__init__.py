@@ -40,6 +40,8 @@ PARAM_ORDER = {
     "beta": ("a", "b"), "weibull": ("k", "lam"), "negbin": ("r", "p"),
     "student_t": ("mu", "sigma2", "nu"), "vonmises": ("mu", "kappa"),
     "diag_gauss": ("mu", "var"), "full_gauss": ("mu", "cov"), "discrete": ("p",),
+    "lognormal": ("mu", "sigma2"), "exponential": ("lam",), "rayleigh": ("sigma2",),
+    "uniform": ("a", "b"), "chisq": ("nu",), "pareto": ("xm", "alpha"),
 }
 
 

@@ -16,7 +16,8 @@ OPT_TIME_PARALLEL = 6
 KT_SLOTS = ("estep", "reduce", "mstep", "viterbi", "emission", "plain", "slot6", "slot7")
 
 FAMILY = {"gauss": 0, "poisson": 1, "gamma": 2, "beta": 3, "weibull": 4, "negbin": 5,
-          "student_t": 6, "vonmises": 7, "diag_gauss": 8, "full_gauss": 9, "discrete": 10}
+          "student_t": 6, "vonmises": 7, "diag_gauss": 8, "full_gauss": 9, "discrete": 10,
+          "lognormal": 11, "exponential": 12, "rayleigh": 13, "uniform": 14, "chisq": 15, "pareto": 16}
 
 
 class hmm_batch(C.Structure):

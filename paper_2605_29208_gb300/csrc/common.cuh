@@ -159,6 +159,25 @@ __device__ __forceinline__ Feat feat_of(int fam, float y, const float* __restric
       f.ok = (y == y);
       sincosf(y, &f.b, &f.a);  // a = cos y, b = sin y
       break;
+    case HMM_LOGNORMAL:
+    case HMM_CHISQ:
+      f.ok = y > 0.f;
+      f.a = log2f(y);
+      break;
+    case HMM_EXPONENTIAL:
+      f.ok = y >= 0.f;
+      break;
+    case HMM_RAYLEIGH:
+      f.ok = y >= 0.f;
+      f.a = log2f(y);          // -inf at y = 0: density 0 there
+      break;
+    case HMM_UNIFORM:          // the support is per state (emis_log2)
+      f.ok = (y == y);
+      break;
+    case HMM_PARETO:
+      f.ok = y > 0.f;
+      f.a = log2f(y);
+      break;
     default:
       break;
   }
@@ -196,9 +215,49 @@ __device__ __forceinline__ float emis_log2(int fam, const Feat& f, const float* 
     }
     case HMM_VONMISES:           // kappa cos(y - mu) log2e + const
       return fmaf(c[0], f.a, fmaf(c[1], f.b, c[2]));
+    case HMM_LOGNORMAL: {        // -log2 y + c2 - ((log2 y - mu log2e) c1)^2
+      const float z = (f.a - c[0]) * c[1];
+      return fmaf(-z, z, c[2]) - f.a;
+    }
+    case HMM_EXPONENTIAL:        // log2 lam - lam log2e y
+      return fmaf(c[0], f.y, c[1]);
+    case HMM_RAYLEIGH:           // log2 y - log2 s2 - log2e y^2 / (2 s2)
+      return f.a + fmaf(c[0], f.y * f.y, c[1]);
+    case HMM_UNIFORM:            // -log2(b - a) on [c0, c1] (bounds rounded inwards to float)
+      return (f.y >= c[0] && f.y <= c[1]) ? c[2] : -INFINITY;
+    case HMM_CHISQ:              // (nu/2 - 1) log2 y - log2e y / 2 + const
+      return fmaf(c[0], f.a, fmaf(c[1], f.y, c[2]));
+    case HMM_PARETO:             // log2 alpha + alpha log2 xm - (alpha + 1) log2 y for y >= xm
+      return f.y >= c[2] ? fmaf(c[0], f.a, c[1]) : -INFINITY;
     default:
       return 0.f;
   }
 }
+
+// The families of the last group (log-normal .. Pareto): density tables,
+// statistics from the occupancies (table_stat_count features per row).
+__host__ __device__ inline bool is_ext_family(int fam) { return fam >= HMM_LOGNORMAL && fam <= HMM_PARETO; }
+__host__ __device__ inline int ext_stat_count(int fam) {
+  switch (fam) {
+    case HMM_LOGNORMAL: return 3;   // 1, log y, (log y)^2
+    case HMM_UNIFORM: return 1;     // 1 (the support min / max come from their own kernel)
+    default: return 2;              // 1, and y (exponential), y^2 (Rayleigh), log y (chi-squared, Pareto)
+  }
+}
+
+// per-row statistic features: slot 0 is the weight
+__device__ __forceinline__ float ext_feature(int fam, int z, float y) {
+  if (z == 0) return 1.f;
+  const float l = y > 0.f ? logf(y) : 0.f;   // rows outside the support carry gamma = 0
+  switch (fam) {
+    case HMM_LOGNORMAL: return z == 1 ? l : (z == 2 ? l * l : 0.f);
+    case HMM_EXPONENTIAL: return z == 1 ? y : 0.f;
+    case HMM_RAYLEIGH: return z == 1 ? y * y : 0.f;
+    case HMM_CHISQ:
+    case HMM_PARETO: return z == 1 ? l : 0.f;
+    default: return 0.f;
+  }
+}
+
 
 }  // namespace hmm

@@ -10,6 +10,7 @@
 #include "launch.h"
 #include "mstep.cuh"
 #include "mv.cuh"
+#include "ext.cuh"
 #include "plain.cuh"
 #include "runtime.h"
 
@@ -55,6 +56,12 @@ static int scalar_param_count(int fam) {
     case HMM_NEGBIN: return 2;
     case HMM_STUDENT_T: return 3;
     case HMM_VONMISES: return 2;
+    case HMM_LOGNORMAL: return 2;
+    case HMM_EXPONENTIAL: return 1;
+    case HMM_RAYLEIGH: return 1;
+    case HMM_UNIFORM: return 2;
+    case HMM_CHISQ: return 1;
+    case HMM_PARETO: return 2;
     default: return -1;
   }
 }
@@ -561,11 +568,12 @@ int mv_statistics(hmm_ctx ctx, hmm_model model, const hmm_batch* b, hmm_plan pla
                   cudaStream_t st) {
   const int NP = model->NP, KS = model->KS, RS = NP * KS;
   const int64_t S = b->n_seq;
-  if (NP <= 32 && !model->any_discrete) stats->mv_part.ensure((size_t)std::max<int64_t>(S, 1) * RS * 4);
+  const bool raw = model->any_discrete || model->any_ext;   // feature sums, no shift
+  if (NP <= 32 && !raw) stats->mv_part.ensure((size_t)std::max<int64_t>(S, 1) * RS * 4);
   stats->mv_chunk.ensure((size_t)std::max(plan->n_chunks, 1) * RS * 8);
   stats->mv_rec.ensure((size_t)model->M * RS * 8);
   (void)ctx;   // timed inside the caller's reduction region
-  if (NP > 32 || model->any_discrete) {
+  if (NP > 32 || raw) {
     // tiled raw moments per chunk (symbol counts for the discrete family),
     // fixed-order model sums, then the shift to the current means
     if (plan->n_chunks > 0) {
@@ -581,6 +589,24 @@ int mv_statistics(hmm_ctx ctx, hmm_model model, const hmm_batch* b, hmm_plan pla
                                                stats->mv_rec.as<double>());
     HMM_CUDA(cudaGetLastError());
     if (model->any_discrete) return (plan->n_chunks > 0) + 1;   // counts need no shift
+    if (model->any_ext) {
+      int nk = (plan->n_chunks > 0) + 1;
+      if (model->any_support) {   // support min / max of the uniform and Pareto states
+        const int n = model->M * NP;
+        stats->ext_mm.ensure((size_t)n * 2 * 4);
+        ext_support_init_kernel<<<(n + 127) / 128, 128, 0, st>>>(stats->ext_mm.as<int>(), n);
+        HMM_CUDA(cudaGetLastError());
+        nk += 1;
+        if (S > 0) {
+          ext_support_kernel<<<dim3((unsigned)S, slabs_of(plan->max_T)), 128, (size_t)model->N * 2 * 4, st>>>(
+              model->family.as<int>(), model->coef.as<float>(), NP, model->N, b->values, b->offsets, b->model_id,
+              stats->ext_mm.as<int>());
+          HMM_CUDA(cudaGetLastError());
+          nk += 1;
+        }
+      }
+      return nk;
+    }
     const int n = model->M * NP;
     mv_shift_kernel<<<(n + 127) / 128, 128, 0, st>>>(model->family.as<int>(), model->mvcoef.as<float>(), model->M,
                                                      NP, model->N, model->D, model->KM, KS,
@@ -893,7 +919,15 @@ void run_mstep(hmm_ctx ctx, hmm_model model, hmm_stats stats, const MStepOpts& o
   }
   {
     KTimer kt(ctx, HMM_KT_MSTEP, st);
-    kt.kernels = 1 + 2 * (int)model->any_discrete + 2 * (int)model->any_mv;
+    kt.kernels = 1 + 2 * (int)model->any_discrete + 2 * (int)model->any_mv + (int)model->any_ext;
+    if (model->any_ext) {   // Sec. 4 / 4.2 closed forms and the chi-squared Newton; derived below
+      const int n = model->M * model->NP;
+      if (model->any_support) HMM_REQUIRE(stats->ext_mm.p != nullptr, "support statistics were never computed");
+      ext_mstep_kernel<<<(n + 127) / 128, 128, 0, st>>>(model->family.as<int>(), model->theta.as<double>(),
+                                                        stats->mv_rec.as<double>(), stats->ext_mm.as<int>(),
+                                                        model->M, model->NP, model->N, model->P, model->KS, o);
+      HMM_CUDA(cudaGetLastError());
+    }
     mstep_kernel<<<model->M, model->NP, 0, st>>>(model->bufs(), stats->rec.as<double>(), o, dps);
     HMM_CUDA(cudaGetLastError());
     if (model->any_discrete) {   // Sec. 4 "Discrete": weighted symbol frequencies
@@ -1014,7 +1048,7 @@ const char* hmm_last_error(void) { return g_last_error.c_str(); }
 const char* hmm_version(void) { return "hmmgpu 0.1 (sm_103a)"; }
 
 int32_t hmm_family_param_count(int32_t family, int32_t dim) {
-  if (family < 0 || family > HMM_DISCRETE) return -1;
+  if (family < 0 || family > HMM_PARETO) return -1;
   if (family >= HMM_DIAG_GAUSS && dim < 1) return -1;
   if (family == HMM_DISCRETE && (dim < 1 || dim > 1024)) return -1;
   return param_count(family, dim);
@@ -1169,13 +1203,15 @@ hmm_status hmm_model_create(hmm_ctx ctx, int32_t n_models, int32_t n_states, int
       int P = 1;
       for (int i = 0; i < n_models; ++i) {
         const int f = h_family[i];
-        HMM_REQUIRE(f >= 0 && f <= HMM_DISCRETE, "unknown family");
+        HMM_REQUIRE(f >= 0 && f <= HMM_PARETO, "unknown family");
         const bool mv = f == HMM_DIAG_GAUSS || f == HMM_FULL_GAUSS;
         HMM_REQUIRE(mv || f == HMM_DISCRETE || dim == 1, "scalar families need dim == 1");
         m->any_discrete |= f == HMM_DISCRETE;
         m->any_negbin |= f == HMM_NEGBIN;
         m->any_weibull |= f == HMM_WEIBULL;
         m->any_mv |= mv;
+        m->any_ext |= is_ext_family(f);
+        m->any_support |= ext_has_support_stats(f);
         P = std::max(P, param_count(f, dim));
       }
       for (int i = 0; i < n_models; ++i) {
@@ -1183,7 +1219,11 @@ hmm_status hmm_model_create(hmm_ctx ctx, int32_t n_models, int32_t n_states, int
                     "multivariate and scalar families cannot share a model set");
         HMM_REQUIRE(!m->any_discrete || h_family[i] == HMM_DISCRETE,
                     "the discrete family cannot share a model set with others");
+        HMM_REQUIRE(!m->any_ext || is_ext_family(h_family[i]),
+                    "log-normal .. Pareto share a model set only with each other");
       }
+      if (m->any_ext)
+        for (int i = 0; i < n_models; ++i) m->KS = std::max(m->KS, ext_stat_count(h_family[i]));
       if (m->any_discrete) {
         HMM_REQUIRE(dim >= 1 && dim <= 1024, "the discrete family needs 1 <= dim (symbols) <= 1024");
         m->K = dim;
@@ -1284,6 +1324,15 @@ hmm_status hmm_model_set_params(hmm_model model, const double* h_blob, int64_t n
         }
         if (model->h_family[m] == HMM_DISCRETE)
           HMM_REQUIRE(std::fabs(psum - 1.0) < 1e-6, "symbol probabilities must sum to 1");
+        switch (model->h_family[m]) {
+          case HMM_LOGNORMAL: HMM_REQUIRE(q[1] > 0.0, "log-normal sigma2 must be > 0"); break;
+          case HMM_EXPONENTIAL: HMM_REQUIRE(q[0] > 0.0, "exponential rate must be > 0"); break;
+          case HMM_RAYLEIGH: HMM_REQUIRE(q[0] > 0.0, "Rayleigh sigma2 must be > 0"); break;
+          case HMM_UNIFORM: HMM_REQUIRE(q[0] < q[1], "uniform bounds need a < b"); break;
+          case HMM_CHISQ: HMM_REQUIRE(q[0] > 0.0, "chi-squared nu must be > 0"); break;
+          case HMM_PARETO: HMM_REQUIRE(q[0] > 0.0 && q[1] > 0.0, "Pareto xm and alpha must be > 0"); break;
+          default: break;
+        }
         q += pc;
       }
     }
@@ -1558,10 +1607,19 @@ hmm_status hmm_stats_destroy(hmm_stats stats) {
   return guarded([&] {
     if (!stats) return;
     for (auto* bb : {&stats->rec, &stats->gamma, &stats->dps, &stats->dp_part, &stats->dp_chunk, &stats->dp_rec,
-                     &stats->nb_d, &stats->dp_count, &stats->mv_part, &stats->mv_chunk, &stats->mv_rec})
+                     &stats->nb_d, &stats->dp_count, &stats->mv_part, &stats->mv_chunk, &stats->mv_rec,
+                     &stats->ext_mm})
       bb->release();
     delete stats;
   });
+}
+
+// inverse of the device's ordered float keys (support min / max)
+static double ext_unkey_host(int k) {
+  const uint32_t u = (uint32_t)(k >= 0 ? k : k ^ 0x7fffffff);
+  float f;
+  std::memcpy(&f, &u, 4);
+  return (double)f;
 }
 
 static int canon_fam_count(int fam, int D) {
@@ -1577,6 +1635,12 @@ static int canon_fam_count(int fam, int D) {
     case HMM_VONMISES: return 3;
     case HMM_DIAG_GAUSS: return 1 + 2 * D;
     case HMM_FULL_GAUSS: return 1 + D + D * D;
+    case HMM_LOGNORMAL: return 3;
+    case HMM_EXPONENTIAL: return 2;
+    case HMM_RAYLEIGH: return 2;
+    case HMM_UNIFORM: return 3;
+    case HMM_CHISQ: return 2;
+    case HMM_PARETO: return 3;
   }
   return 0;
 }
@@ -1606,10 +1670,16 @@ hmm_status hmm_stats_get(hmm_stats stats, double* h_out, int64_t n_values) {
     const int D = md->D, KM = md->KM, KS = md->KS;
     std::vector<double> mrec;
     std::vector<float> mvc;
+    std::vector<int> emm;
     if (md->table_family()) {
       HMM_REQUIRE(stats->mv_rec.p != nullptr, "table-family statistics were never computed");
       mrec.resize((size_t)M * NP * KS);
       HMM_CUDA(cudaMemcpy(mrec.data(), stats->mv_rec.p, mrec.size() * 8, cudaMemcpyDeviceToHost));
+      if (md->any_support) {
+        HMM_REQUIRE(stats->ext_mm.p != nullptr, "support statistics were never computed");
+        emm.resize((size_t)M * NP * 2);
+        HMM_CUDA(cudaMemcpy(emm.data(), stats->ext_mm.p, emm.size() * 4, cudaMemcpyDeviceToHost));
+      }
       if (md->any_mv) {
         mvc.resize((size_t)M * NP * KM);
         HMM_CUDA(cudaMemcpy(mvc.data(), md->mvcoef.p, mvc.size() * 4, cudaMemcpyDeviceToHost));
@@ -1677,6 +1747,22 @@ hmm_status hmm_stats_get(hmm_stats stats, double* h_out, int64_t n_values) {
           case HMM_DISCRETE: {   // weighted symbol counts
             const double* Rm = mrec.data() + ((size_t)m * NP + j) * KS;
             for (int k = 0; k < md->K; ++k) q[k] = Rm[k];
+            break;
+          }
+          case HMM_LOGNORMAL:
+          case HMM_EXPONENTIAL:
+          case HMM_RAYLEIGH:
+          case HMM_CHISQ:
+          case HMM_UNIFORM:
+          case HMM_PARETO: {   // feature sums, then the support min / max
+            const double* Rm = mrec.data() + ((size_t)m * NP + j) * KS;
+            const int nf = ext_stat_count(fam);
+            for (int k = 0; k < nf; ++k) q[k] = Rm[k];
+            if (fam == HMM_UNIFORM || fam == HMM_PARETO) {
+              const int* g = emm.data() + ((size_t)m * NP + j) * 2;
+              q[nf] = ext_unkey_host(g[0]);
+              if (fam == HMM_UNIFORM) q[nf + 1] = ext_unkey_host(g[1]);
+            }
             break;
           }
           case HMM_DIAG_GAUSS:

@@ -143,6 +143,47 @@ __device__ inline void derive_coef(int fam, const double* th, float* c, float* n
       c[2] = (float)(-(log(2.0 * 3.14159265358979323846) + log_i0_d(k)) * L2E);
       break;
     }
+    case HMM_LOGNORMAL: {
+      const double mu = th[0], s2 = th[1];
+      c[0] = (float)(mu * L2E);
+      c[1] = (float)sqrt(kLn2 / (2.0 * s2));
+      c[2] = (float)(-0.5 * log2(2.0 * 3.14159265358979323846 * s2));
+      break;
+    }
+    case HMM_EXPONENTIAL: {
+      const double lam = th[0];
+      c[0] = (float)(-lam * L2E);
+      c[1] = (float)log2(lam);
+      break;
+    }
+    case HMM_RAYLEIGH: {
+      const double s2 = th[0];
+      c[0] = (float)(-L2E / (2.0 * s2));
+      c[1] = (float)(-log2(s2));
+      break;
+    }
+    case HMM_UNIFORM: {
+      // bounds rounded inwards: for a float y, y >= a iff y >= ru(a), y <= b iff y <= rd(b)
+      const double a = th[0], b = th[1];
+      c[0] = __double2float_ru(a);
+      c[1] = __double2float_rd(b);
+      c[2] = (float)(-log2(b - a));
+      break;
+    }
+    case HMM_CHISQ: {
+      const double h = 0.5 * th[0];
+      c[0] = (float)(h - 1.0);
+      c[1] = (float)(-0.5 * L2E);
+      c[2] = (float)((-h * kLn2 - lgamma(h)) * L2E);
+      break;
+    }
+    case HMM_PARETO: {
+      const double xm = th[0], al = th[1];
+      c[0] = (float)(-(al + 1.0));
+      c[1] = (float)(log2(al) + al * log2(xm));
+      c[2] = __double2float_ru(xm);
+      break;
+    }
     default:
       break;
   }
@@ -152,7 +193,10 @@ __device__ inline void derive_coef(int fam, const double* th, float* c, float* n
 __device__ inline int additive_slot(int fam) {
   switch (fam) {
     case HMM_POISSON:
-    case HMM_NEGBIN: return 1;
+    case HMM_NEGBIN:
+    case HMM_EXPONENTIAL:
+    case HMM_RAYLEIGH:
+    case HMM_PARETO: return 1;
     case HMM_WEIBULL:
     case HMM_STUDENT_T: return 3;
     default: return 2;
@@ -309,6 +353,12 @@ __device__ inline bool valid_update(int fam, const double* th) {
     case HMM_BETA: return fin(th[0]) && fin(th[1]) && th[0] > 0.0 && th[1] > 0.0;
     case HMM_STUDENT_T: return fin(th[0]) && fin(th[1]) && fin(th[2]) && th[1] > 0.0 && th[2] > 0.0;
     case HMM_VONMISES: return fin(th[0]) && fin(th[1]) && th[1] >= 0.0;
+    case HMM_LOGNORMAL: return fin(th[0]) && fin(th[1]) && th[1] > 0.0;
+    case HMM_EXPONENTIAL:
+    case HMM_RAYLEIGH:
+    case HMM_CHISQ: return fin(th[0]) && th[0] > 0.0;
+    case HMM_UNIFORM: return fin(th[0]) && fin(th[1]) && th[0] < th[1];
+    case HMM_PARETO: return fin(th[0]) && fin(th[1]) && th[0] > 0.0 && th[1] > 0.0;
     default: return true;
   }
 }

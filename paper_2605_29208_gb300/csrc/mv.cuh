@@ -256,6 +256,7 @@ constexpr int MVM_KT = 16;
 
 __device__ __forceinline__ float mv_feature(int fam, int D, int z, const float* yr) {
   if (fam == HMM_DISCRETE) return yr[0] == (float)z ? 1.f : 0.f;   // symbol indicator 1[y = z]
+  if (is_ext_family(fam)) return ext_feature(fam, z, yr[0]);
   if (z == 0) return 1.f;
   if (z <= D) return yr[z - 1];
   const int q = z - 1 - D;
@@ -279,7 +280,7 @@ __global__ void __launch_bounds__(256) mv_moments_kernel(const int* __restrict__
   const int tid = threadIdx.x, ty = tid / 16, tx = tid % 16;
   const int lo = chunk_lo[c], hi = chunk_hi[c];
   const int fam = family[model_id[seq_by_model[lo]]];
-  const int nf = fam == HMM_DISCRETE ? KS : mv_stat_count(fam, D);
+  const int nf = fam == HMM_DISCRETE ? KS : (is_ext_family(fam) ? ext_stat_count(fam) : mv_stat_count(fam, D));
   float acc[4][4];
   double dacc[4][4];
 #pragma unroll

@@ -135,7 +135,11 @@ struct hmm_model_s {
   int K = 0;                     // symbols of the discrete family
   int dim_arg = 1;               // the `dim` the model was created with (K for discrete)
   hmm::DevBuf dtab;              // [M][NP][K] float32 ln p_jk (discrete family)
-  bool table_family() const { return any_mv || any_discrete; }
+  // the last family group (log-normal .. Pareto): densities through the
+  // table, statistics from the occupancies; uniform / Pareto also need the
+  // support min / max
+  bool any_ext = false, any_support = false;
+  bool table_family() const { return any_mv || any_discrete || any_ext; }
   hmm::DevBuf family, pi, A, theta, A32, AT32, logA2, logAe, pi32, logpi2, logpie, coef, nbtab, lfact2;
   int KM = 0, KS = 0;            // multivariate coefficient / statistic slots per state
   hmm::DevBuf mvcoef;            // [M][NP][KM] float32 (multivariate families)
@@ -160,6 +164,7 @@ struct hmm_stats_s {
   hmm::DevBuf mv_part;           // [S][NP][KS] float32 multivariate moments
   hmm::DevBuf mv_chunk;          // [n_chunks][NP*KS] float64
   hmm::DevBuf mv_rec;            // [M][NP*KS] float64
+  hmm::DevBuf ext_mm;            // [M][NP][2] int32 ordered keys of the support min / max
 };
 
 struct hmm_plan_s {

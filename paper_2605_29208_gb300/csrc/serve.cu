@@ -440,7 +440,7 @@ hmm_status hmm_serve_submit(hmm_server s, const hmm_request* q, uint64_t* ticket
   try {
     HMM_REQUIRE(s && q && ticket, "NULL argument");
     HMM_REQUIRE(q->kind >= HMM_REQ_DECODE && q->kind <= HMM_REQ_FIT, "unknown request kind");
-    HMM_REQUIRE(q->family >= 0 && q->family <= HMM_DISCRETE, "unknown family");
+    HMM_REQUIRE(q->family >= 0 && q->family <= HMM_PARETO, "unknown family");
     HMM_REQUIRE(q->n_states >= 1 && q->n_states <= 1024 && q->dim >= 1, "bad model sizes");
     HMM_REQUIRE(q->T >= 0 && (q->T == 0 || q->values), "bad observations");
     HMM_REQUIRE(q->kind != HMM_REQ_FIT || q->n_iter >= 0, "n_iter must be >= 0");

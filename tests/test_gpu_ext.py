@@ -1,0 +1,192 @@
+"""Parity of the further scalar families (Sec. 4 log-normal, exponential,
+Rayleigh, uniform; Sec. 4.2 chi-squared, Pareto) on the CUDA path with the
+FP64 oracle: log-density table, forward-backward, the E-step statistics
+(feature sums and the support min / max), the M-step, a short fit and
+Viterbi, at small and large N, with the tolerances of the other families
+(logL 1e-5 relative, gamma 1e-4 absolute, parameters 1e-4 relative).  The
+support min / max are exact."""
+import numpy as np
+import pytest
+
+from oracle import hmm_oracle as O
+from paper_2605_29208_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+LL_RTOL = 1e-5
+GAMMA_ATOL = 1e-4
+PARAM_RTOL = 1e-4
+LENGTHS = [1, 2, 0, 37, 130, 9, 64, 65, 300]
+FAMS = ["lognormal", "exponential", "rayleigh", "uniform", "chisq", "pareto"]
+CASES = [(f, N) for f in FAMS for N in (3, 16, 64)]
+
+
+@pytest.fixture(scope="module")
+def H():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import paper_2605_29208_gb300 as H
+    from paper_2605_29208_gb300 import build
+    build.build()
+    return H
+
+
+@pytest.fixture(scope="module")
+def ctx(H):
+    return H.Context(0)
+
+
+def om(d):
+    return O.Model(d["family"], d["pi"].copy(), d["A"].copy(),
+                   {k: np.array(v, copy=True) for k, v in d["params"].items()})
+
+
+def setup(H, ctx, f, N, lengths=LENGTHS, n_models=2, seed=0):
+    models = synth.small_models(f, N, n_models, seed=2500 + seed + N + FAMS.index(f))
+    mid = np.arange(len(lengths)) % n_models
+    values, offsets, mid = synth.make_batch(2600 + seed + N, models, lengths, mid)
+    return models, values, offsets, mid, H.Model(ctx, models), H.Batch(values, offsets, mid)
+
+
+@pytest.mark.parametrize("f,N", CASES)
+def test_ext_forward_backward(H, ctx, f, N):
+    models, values, offsets, mid, model, batch = setup(H, ctx, f, N)
+    lb = H.emission_logpdf(ctx, model, batch).cpu().numpy()
+    ll, gamma, _ = H.forward_backward(ctx, model, batch)
+    ll, gamma = ll.cpu().numpy(), gamma.cpu().numpy()
+    for s in range(len(LENGTHS)):
+        y = values[offsets[s]:offsets[s + 1]]
+        if len(y) == 0:
+            assert ll[s] == 0.0
+            continue
+        o = om(models[mid[s]])
+        np.testing.assert_allclose(lb[offsets[s]:offsets[s + 1]], O.emission_logpdf(o, y), rtol=1e-6, atol=1e-5)
+        fb = O.forward_backward(o, y)
+        assert abs(ll[s] - fb["logL"]) <= LL_RTOL * max(1.0, abs(fb["logL"])), (s, ll[s], fb["logL"])
+        np.testing.assert_allclose(gamma[offsets[s]:offsets[s + 1]], fb["gamma"], atol=GAMMA_ATOL, rtol=0)
+
+
+def family_sums(f, o, y, g):
+    """The canonical per-state sums of one sequence (see the C header)."""
+    N = g.shape[1]
+    ly = np.log(np.where(y > 0, y, 1.0))
+    W = g.sum(0)
+    if f == "lognormal":
+        return np.stack([W, g.T @ ly, g.T @ (ly * ly)], 1)
+    if f == "exponential":
+        return np.stack([W, g.T @ y], 1)
+    if f == "rayleigh":
+        return np.stack([W, g.T @ (y * y)], 1)
+    if f == "chisq":
+        return np.stack([W, g.T @ ly], 1)
+    if f == "pareto":
+        return np.stack([W, g.T @ ly, np.zeros(N)], 1)
+    return np.stack([W, np.zeros(N), np.zeros(N)], 1)
+
+
+def support_extremes(f, o, Y):
+    N = o.n_states
+    lo, hi = np.full(N, np.inf), np.full(N, -np.inf)
+    for j in range(N):
+        cur = {k: v[j] for k, v in o.params.items()}
+        sel = O.support_rows(f, Y, cur)
+        if sel.any():
+            lo[j], hi[j] = Y[sel].min(), Y[sel].max()
+    return lo, hi
+
+
+@pytest.mark.parametrize("f,N", CASES)
+def test_ext_estep_statistics(H, ctx, f, N):
+    models, values, offsets, mid, model, batch = setup(H, ctx, f, N, n_models=3, seed=1)
+    stats, _ = H.estep_stats(ctx, model, batch)
+    got = stats.get()
+    off = 0
+    for m, md in enumerate(models):
+        o = om(md)
+        idx = [s for s in range(len(LENGTHS)) if mid[s] == m]
+        g1, xi, ll = np.zeros(N), np.zeros((N, N)), 0.0
+        fam = None
+        Y = []
+        for s in idx:
+            y = values[offsets[s]:offsets[s + 1]]
+            Y.append(y)
+            if len(y) == 0:
+                continue
+            fb = O.forward_backward(o, y)
+            ll += fb["logL"]
+            g1 += fb["gamma"][0]
+            xi += fb["xi_sum"]
+            fs = family_sums(f, o, y, fb["gamma"])
+            fam = fs if fam is None else fam + fs
+        nf = 3 if f in ("lognormal", "uniform", "pareto") else 2
+        if fam is None:
+            fam = np.zeros((N, nf))
+        if f in ("uniform", "pareto"):
+            lo, hi = support_extremes(f, o, np.concatenate(Y))
+            if f == "uniform":
+                fam[:, 1], fam[:, 2] = lo, hi
+            else:
+                fam[:, 2] = lo
+        ref = np.concatenate([[len(idx), ll], g1, xi.ravel(), fam.ravel()])
+        rec = got[off:off + len(ref)]
+        off += len(ref)
+        head = 2 + N + N * N
+        np.testing.assert_allclose(rec[:head], ref[:head], rtol=2e-5, atol=2e-4)
+        r3, f3 = rec[head:].reshape(N, nf), ref[head:].reshape(N, nf)
+        exact = {"uniform": [1, 2], "pareto": [2]}.get(f, [])
+        for c in range(nf):
+            if c in exact:
+                np.testing.assert_array_equal(r3[:, c], f3[:, c])
+            else:
+                np.testing.assert_allclose(r3[:, c], f3[:, c], rtol=2e-5, atol=2e-4)
+
+
+@pytest.mark.parametrize("f,N", CASES)
+def test_ext_mstep_and_fit(H, ctx, f, N):
+    truth = synth.small_models(f, N, 1, seed=2700 + N + FAMS.index(f))
+    lengths = [400, 250, 1, 333, 128]
+    values, offsets, mid = synth.make_batch(2701, truth, lengths, np.zeros(len(lengths), np.int32))
+    rng = np.random.default_rng(11)
+    init = [synth.perturb(rng, t) for t in truth]
+    model = H.Model(ctx, init)
+    batch = H.Batch(values, offsets, mid)
+    stats, _ = H.estep_stats(ctx, model, batch)
+    H.mstep(ctx, model, stats, batch=batch)
+    ref, _ = O.em_iteration([om(m) for m in init], values, offsets, mid)
+    for g, r in zip(model.get(), ref):
+        np.testing.assert_allclose(g["A"], r.A, rtol=PARAM_RTOL, atol=1e-6)
+        for k, v in r.params.items():
+            np.testing.assert_allclose(g["params"][k], v, rtol=PARAM_RTOL, atol=1e-6, err_msg=k)
+    model2 = H.Model(ctx, init)
+    trace, done = H.fit(ctx, model2, batch, n_iter=4)
+    ref_models, ref_trace = O.fit([om(m) for m in init], values, offsets, mid, 4)
+    np.testing.assert_allclose(trace[:, 0], ref_trace.sum(axis=1), rtol=LL_RTOL)
+    for k, v in ref_models[0].params.items():
+        np.testing.assert_allclose(model2.get()[0]["params"][k], v, rtol=5 * PARAM_RTOL, atol=1e-6, err_msg=k)
+
+
+@pytest.mark.parametrize("f,N", CASES)
+def test_ext_viterbi(H, ctx, f, N):
+    models, values, offsets, mid, model, batch = setup(H, ctx, f, N, seed=2)
+    path, score = H.viterbi(ctx, model, batch)
+    path, score = path.cpu().numpy(), score.cpu().numpy()
+    for s in range(len(LENGTHS)):
+        y = values[offsets[s]:offsets[s + 1]]
+        if len(y) == 0:
+            continue
+        o = om(models[mid[s]])
+        q, sc, gap, fgap = O.viterbi_gaps(np.log(o.pi), np.log(o.A), O.emission_logpdf(o, y))
+        assert abs(score[s] - sc) <= 1e-5 * max(1.0, abs(sc))
+        diff = np.nonzero(path[offsets[s]:offsets[s + 1]] != q)[0]
+        if len(diff):
+            t = diff[-1]
+            assert (fgap if t == len(y) - 1 else gap[t + 1, q[t + 1]]) < 1e-3
+
+
+def test_ext_set_params_rejects_bad_domains(H, ctx):
+    from paper_2605_29208_gb300 import HmmError
+    m = synth.small_models("uniform", 3, 1, seed=1)[0]
+    m["params"]["b"] = m["params"]["a"] - 1.0
+    with pytest.raises(HmmError):
+        H.Model(ctx, [m])
