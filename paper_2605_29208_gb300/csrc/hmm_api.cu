@@ -146,6 +146,22 @@ __global__ void emission_kernel(ModelView mv, const float* __restrict__ y, const
   const int m = model_id[s];
   const int fam = mv.family[m];
   const int N = mv.N, NP = mv.NP;
+  if (N <= (int)blockDim.x) {
+    // a fixed (row, state) slot per thread: blockDim / N rows per pass, the
+    // state's coefficients in registers, stores coalesced along the row
+    const int rpp = blockDim.x / N, rr = threadIdx.x / N, k = threadIdx.x % N;
+    if (rr >= rpp) return;
+    float c[KC];
+#pragma unroll
+    for (int z = 0; z < KC; ++z) c[z] = mv.coef[((size_t)m * NP + k) * KC + z];
+    const float* nbt = mv.nbtab ? mv.nbtab + ((size_t)m * NP + k) * NB_YMAX : nullptr;
+    for (int64_t t = b + rr; t < e; t += rpp) {
+      const Feat f = feat_of(fam, y[t], mv.lfact2);
+      const float l2 = f.ok ? emis_log2(fam, f, c, nbt) : -INFINITY;
+      logb[t * N + k] = l2 * kLn2f;
+    }
+    return;
+  }
   for (int64_t idx = threadIdx.x; idx < (e - b) * N; idx += blockDim.x) {
     const int64_t t = b + idx / N;
     const int k = (int)(idx % N);
@@ -569,11 +585,34 @@ int mv_statistics(hmm_ctx ctx, hmm_model model, const hmm_batch* b, hmm_plan pla
   const int NP = model->NP, KS = model->KS, RS = NP * KS;
   const int64_t S = b->n_seq;
   const bool raw = model->any_discrete || model->any_ext;   // feature sums, no shift
-  if (NP <= 32 && !raw) stats->mv_part.ensure((size_t)std::max<int64_t>(S, 1) * RS * 4);
+  // few raw features at small N: per-sequence sums (feat_stats_kernel)
+  const bool raw_small = raw && NP <= 32 && KS <= FEAT_SMALL_MAX;
+  if (NP <= 32 && (!raw || raw_small)) stats->mv_part.ensure((size_t)std::max<int64_t>(S, 1) * RS * 4);
   stats->mv_chunk.ensure((size_t)std::max(plan->n_chunks, 1) * RS * 8);
   stats->mv_rec.ensure((size_t)model->M * RS * 8);
   (void)ctx;   // timed inside the caller's reduction region
-  if (NP > 32 || raw) {
+  int nk = 0;
+  if (raw_small) {
+    if (S > 0) {
+      feat_stats_kernel<<<(unsigned)S, 256, 0, st>>>(model->family.as<int>(), NP, model->N, KS, b->values,
+                                                    stats->gamma.as<float>(), b->offsets, b->model_id,
+                                                    stats->mv_part.as<float>());
+      HMM_CUDA(cudaGetLastError());
+      ++nk;
+    }
+    if (plan->n_chunks > 0) {
+      reduce_records_l1<<<plan->n_chunks, 128, 0, st>>>(stats->mv_part.as<float>(), RS,
+                                                      plan->seq_by_model.as<int32_t>(), plan->chunk_lo.as<int32_t>(),
+                                                      plan->chunk_hi.as<int32_t>(), stats->mv_chunk.as<double>());
+      HMM_CUDA(cudaGetLastError());
+      ++nk;
+    }
+    reduce_chunks_l2<<<model->M, 128, 0, st>>>(stats->mv_chunk.as<double>(), plan->model_chunk_ptr.as<int32_t>(), RS,
+                                               stats->mv_rec.as<double>());
+    HMM_CUDA(cudaGetLastError());
+    ++nk;
+  }
+  if (!raw_small && (NP > 32 || raw)) {
     // tiled raw moments per chunk (symbol counts for the discrete family),
     // fixed-order model sums, then the shift to the current means
     if (plan->n_chunks > 0) {
@@ -588,10 +627,10 @@ int mv_statistics(hmm_ctx ctx, hmm_model model, const hmm_batch* b, hmm_plan pla
     reduce_chunks_l2<<<model->M, 128, 0, st>>>(stats->mv_chunk.as<double>(), plan->model_chunk_ptr.as<int32_t>(), RS,
                                                stats->mv_rec.as<double>());
     HMM_CUDA(cudaGetLastError());
-    if (model->any_discrete) return (plan->n_chunks > 0) + 1;   // counts need no shift
-    if (model->any_ext) {
-      int nk = (plan->n_chunks > 0) + 1;
-      if (model->any_support) {   // support min / max of the uniform and Pareto states
+    nk = (plan->n_chunks > 0) + 1;
+  }
+  if (raw) {   // counts and feature sums need no shift
+    if (model->any_support) {   // support min / max of the uniform and Pareto states
         const int n = model->M * NP;
         stats->ext_mm.ensure((size_t)n * 2 * 4);
         ext_support_init_kernel<<<(n + 127) / 128, 128, 0, st>>>(stats->ext_mm.as<int>(), n);
@@ -604,9 +643,10 @@ int mv_statistics(hmm_ctx ctx, hmm_model model, const hmm_batch* b, hmm_plan pla
           HMM_CUDA(cudaGetLastError());
           nk += 1;
         }
-      }
-      return nk;
     }
+    return nk;
+  }
+  if (NP > 32) {
     const int n = model->M * NP;
     mv_shift_kernel<<<(n + 127) / 128, 128, 0, st>>>(model->family.as<int>(), model->mvcoef.as<float>(), model->M,
                                                      NP, model->N, model->D, model->KM, KS,

@@ -336,6 +336,62 @@ __global__ void __launch_bounds__(256) mv_moments_kernel(const int* __restrict__
     }
 }
 
+// Raw feature sums per sequence for padded N <= 32 and few features
+// (discrete with K <= FEAT_SMALL_MAX symbols, the log-normal .. Pareto
+// group): part[s][k][z] = sum_t gamma_t(k) f_z(y_t).  One block of 256
+// threads per sequence; a warp covers 32 / NP rows per pass with one lane
+// per (row, state), so each pass reads whole occupancy rows; a thread keeps
+// one float32 sum per feature (flushed every 64 passes), and the partials of
+// a state are added in a fixed (warp, row-in-warp) order, so the result does
+// not depend on scheduling.  The per-sequence records are then reduced like
+// the multivariate moments (chunks, then models).
+constexpr int FEAT_SMALL_MAX = 8;
+
+__global__ void __launch_bounds__(256) feat_stats_kernel(const int* __restrict__ family, int NP, int N, int KS,
+                                                         const float* __restrict__ y,
+                                                         const float* __restrict__ gamma,
+                                                         const int64_t* __restrict__ offsets,
+                                                         const int32_t* __restrict__ model_id,
+                                                         float* __restrict__ part) {
+  __shared__ float red[FEAT_SMALL_MAX][256];
+  const int s = blockIdx.x;
+  const int64_t b = offsets[s], e = offsets[s + 1];
+  const int fam = family[model_id[s]];
+  const int nf = fam == HMM_DISCRETE ? KS : ext_stat_count(fam);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int RW = 32 / NP;                       // rows per warp and pass
+  const int k = lane % NP, rs = lane / NP;
+  float acc[FEAT_SMALL_MAX], in[FEAT_SMALL_MAX];
+#pragma unroll
+  for (int z = 0; z < FEAT_SMALL_MAX; ++z) acc[z] = in[z] = 0.f;
+  int cnt = 0;
+  for (int64_t t = b + (int64_t)w * RW + rs; t < e; t += (int64_t)nw * RW) {
+    if (k < N) {
+      const float g = gamma[t * N + k];
+#pragma unroll
+      for (int z = 0; z < FEAT_SMALL_MAX; ++z)
+        if (z < nf) in[z] = fmaf(g, mv_feature(fam, 1, z, y + t), in[z]);
+    }
+    if (++cnt == 64) {
+#pragma unroll
+      for (int z = 0; z < FEAT_SMALL_MAX; ++z) acc[z] += in[z], in[z] = 0.f;
+      cnt = 0;
+    }
+  }
+#pragma unroll
+  for (int z = 0; z < FEAT_SMALL_MAX; ++z) red[z][threadIdx.x] = acc[z] + in[z];
+  __syncthreads();
+  // state k's partials sit at threads w * 32 + r * NP + k
+  for (int f = threadIdx.x; f < NP * KS; f += blockDim.x) {
+    const int kk = f / KS, z = f % KS;
+    float v = 0.f;
+    if (kk < N && z < nf)
+      for (int ww = 0; ww < nw; ++ww)
+        for (int r = 0; r < RW; ++r) v += red[z][ww * 32 + r * NP + kk];
+    part[(size_t)s * NP * KS + f] = v;
+  }
+}
+
 // Raw moments -> moments about the current (float32) mean, in place.
 __global__ void mv_shift_kernel(const int* __restrict__ family, const float* __restrict__ mvc, int M, int NP, int N,
                                 int D, int KM, int KS, double* __restrict__ rec) {
@@ -482,6 +538,17 @@ __global__ void discrete_emission_kernel(const float* __restrict__ dtab, int NP,
   if (b >= e) return;
   const int m = model_id[s];
   const float* tab = dtab + (size_t)m * NP * K;
+  if (N <= (int)blockDim.x) {   // a fixed (row, state) slot per thread, as in emission_kernel
+    const int rpp = blockDim.x / N, rr = threadIdx.x / N, j = threadIdx.x % N;
+    if (rr >= rpp) return;
+    const float* tj = tab + (size_t)j * K;
+    for (int64_t t = b + rr; t < e; t += rpp) {
+      const float v = y[t];
+      const bool ok = v >= 0.f && v < (float)K && floorf(v) == v;
+      logb[t * N + j] = ok ? tj[(int)v] : -INFINITY;
+    }
+    return;
+  }
   for (int64_t idx = threadIdx.x; idx < (e - b) * N; idx += blockDim.x) {
     const int64_t t = b + idx / N;
     const int j = (int)(idx % N);
