@@ -144,6 +144,22 @@ int32_t hmm_family_param_count(int32_t family, int32_t dim);
 /* Total size in float64 values of the parameter blob of n_models models. */
 int64_t hmm_param_blob_size(int32_t n_models, int32_t n_states, int32_t dim,
                             const int32_t* h_family);
+/* Model-selection criteria of one fitted model (the paper names AIC, BIC and
+ * AICc for model comparison, Sec. 5 and the multivariate example, without
+ * formulas; these are the textbook forms).  Host-only arithmetic, no device
+ * work.  k = the number of free parameters: (N - 1) initial probabilities,
+ * N (N - 1) transition probabilities and N times the free emission
+ * parameters of the family (the count of hmm_family_param_count, except
+ * discrete K - 1 and full covariance D + D (D + 1) / 2);
+ *   h_out[0] = k, h_out[1] = AIC = 2 k - 2 logL,
+ *   h_out[2] = BIC = k ln(n_obs) - 2 logL,
+ *   h_out[3] = AICc = AIC + 2 k (k + 1) / (n_obs - k - 1)  (+inf when
+ *              n_obs <= k + 1).
+ * loglik: the model's total log-likelihood (natural log); n_obs: its number
+ * of observations (time steps).  HMM_E_ARG for an unknown family, n_states
+ * < 1, n_obs < 1 or a NULL h_out. */
+hmm_status hmm_information_criteria(int32_t family, int32_t n_states, int32_t dim, double loglik,
+                                    int64_t n_obs, double* h_out);
 
 /* ------------------------------------------------------------ context */
 /* Context options (hmm_ctx_set_option). */

@@ -837,6 +837,37 @@ def fit(models, values, offsets, model_id, n_iter, nu_mode="ecm"):
     return models, np.array(trace)
 
 
+def free_parameter_count(model: Model) -> int:
+    """Free parameters of an HMM, counted from its parameter arrays: the
+    N - 1 free initial probabilities, N (N - 1) free transition
+    probabilities, and every emission parameter entry except those fixed by
+    a constraint (a probability row sums to 1; a covariance matrix is
+    symmetric)."""
+    N = model.n_states
+    k = (N - 1) + N * (N - 1)
+    for name, v in model.params.items():
+        v = np.asarray(v)
+        if model.family == "discrete" and name == "p":          # rows on the simplex
+            k += v.shape[0] * (v.shape[1] - 1)
+        elif model.family == "full_gauss" and name == "cov":    # symmetric D x D
+            D = v.shape[1]
+            k += v.shape[0] * D * (D + 1) // 2
+        else:
+            k += v.size
+    return k
+
+
+def information_criteria(model: Model, logL: float, n_obs: int) -> dict:
+    """AIC, BIC and AICc (named by the paper for model comparison, no formula
+    printed): the textbook definitions 2k - 2 logL, k ln n - 2 logL and
+    AIC + 2k(k+1)/(n-k-1) (infinite when n <= k + 1)."""
+    k = free_parameter_count(model)
+    aic = 2 * k - 2 * logL
+    bic = k * math.log(n_obs) - 2 * logL
+    aicc = aic + 2 * k * (k + 1) / (n_obs - k - 1) if n_obs - k - 1 > 0 else math.inf
+    return dict(k=k, aic=aic, bic=bic, aicc=aicc)
+
+
 def batch_loglik(models, values, offsets, model_id):
     seqs = split_batch(values, offsets)
     return np.array([forward_backward(models[model_id[s]], seqs[s])["logL"]

@@ -16,7 +16,7 @@ from . import _lib
 from ._lib import FAMILY, HmmError, check
 
 __all__ = ["Context", "Model", "Batch", "FAMILY", "HmmError", "blob_from_model",
-           "model_from_blob"]
+           "model_from_blob", "information_criteria"]
 
 
 def _torch():
@@ -219,6 +219,17 @@ class Batch:
 
 
 # ------------------------------------------------------------------ calls
+def information_criteria(family: str, n_states: int, loglik: float, n_obs: int, dim: int = 1) -> dict:
+    """hmm_information_criteria: free-parameter count k, AIC, BIC and AICc of
+    one fitted model (host arithmetic in the library, no device work)."""
+    from . import _lib
+    lib = _lib.load()
+    out = np.zeros(4, np.float64)
+    check(lib.hmm_information_criteria(FAMILY[family], int(n_states), int(dim), float(loglik), int(n_obs),
+                                       out.ctypes.data_as(C.c_void_p)))
+    return dict(k=int(out[0]), aic=float(out[1]), bic=float(out[2]), aicc=float(out[3]))
+
+
 def emission_logpdf(ctx, model, batch, out=None, stream=None):
     torch = _torch()
     if out is None:

@@ -63,6 +63,7 @@ _SIGS = {
     "hmm_version": (C.c_char_p, []),
     "hmm_family_param_count": (C.c_int32, [C.c_int32, C.c_int32]),
     "hmm_param_blob_size": (C.c_int64, [C.c_int32, C.c_int32, C.c_int32, C.c_void_p]),
+    "hmm_information_criteria": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, C.c_double, C.c_int64, C.c_void_p]),
     "hmm_ctx_create": (C.c_int, [C.c_int, C.c_size_t, C.POINTER(C.c_void_p)]),
     "hmm_ctx_destroy": (C.c_int, [C.c_void_p]),
     "hmm_ctx_status": (C.c_int, [C.c_void_p, C.c_void_p]),

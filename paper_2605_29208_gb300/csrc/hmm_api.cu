@@ -1094,6 +1094,26 @@ int32_t hmm_family_param_count(int32_t family, int32_t dim) {
   return param_count(family, dim);
 }
 
+hmm_status hmm_information_criteria(int32_t family, int32_t n_states, int32_t dim, double loglik, int64_t n_obs,
+                                    double* h_out) {
+  return guarded([&] {
+    HMM_REQUIRE(h_out != nullptr, "NULL argument");
+    HMM_REQUIRE(n_states >= 1 && n_obs >= 1, "n_states and n_obs must be >= 1");
+    const int pc = hmm_family_param_count(family, dim);
+    HMM_REQUIRE(pc >= 0, "unknown family or dimension");
+    int64_t e = pc;                                          // free emission parameters per state
+    if (family == HMM_DISCRETE) e = dim - 1;                 // the K probabilities sum to 1
+    if (family == HMM_FULL_GAUSS) e = dim + (int64_t)dim * (dim + 1) / 2;   // symmetric covariance
+    const double N = n_states, n = (double)n_obs;
+    const double k = (N - 1.0) + N * (N - 1.0) + N * (double)e;
+    const double aic = 2.0 * k - 2.0 * loglik;
+    h_out[0] = k;
+    h_out[1] = aic;
+    h_out[2] = k * std::log(n) - 2.0 * loglik;
+    h_out[3] = (n - k - 1.0 > 0.0) ? aic + 2.0 * k * (k + 1.0) / (n - k - 1.0) : INFINITY;
+  });
+}
+
 int64_t hmm_param_blob_size(int32_t n_models, int32_t n_states, int32_t dim, const int32_t* h_family) {
   if (n_models <= 0 || n_states <= 0 || !h_family) return -1;
   int64_t tot = 0;
