@@ -74,3 +74,14 @@ def test_library_rejects_bad_arguments():
         H.information_criteria("gauss", 0, 0.0, 10)
     with pytest.raises(HmmError):
         H.information_criteria("gauss", 2, 0.0, 0)
+
+
+def test_restart_batch_layout():
+    """The restart batch repeats the sequences once per model, in order."""
+    from paper_2605_29208_gb300.restarts import _replicate
+    values = np.arange(7, dtype=np.float64)
+    offsets = np.array([0, 3, 3, 7])
+    vals, offs, mid = _replicate(values, offsets, 3)
+    np.testing.assert_array_equal(vals, np.tile(values, 3))
+    np.testing.assert_array_equal(offs, [0, 3, 3, 7, 10, 10, 14, 17, 17, 21])
+    np.testing.assert_array_equal(mid, [0, 0, 0, 1, 1, 1, 2, 2, 2])
