@@ -16,8 +16,8 @@ step outside the events, GPU clocks sampled with nvidia-smi during the timed
 steps.  The dominant kernel (the fused E-step) is timed separately by the
 library's event hooks on its own stream for the roofline entry.
 
---impl reference times the CPU checker (oracle/) on a bounded sample of the
-same workload, for the driver's ratio.
+--impl reference times the FP64 CPU oracle (oracle/) on a bounded sample of
+the same workload, as the reference arm of a comparison.
 """
 from __future__ import annotations
 
@@ -160,7 +160,7 @@ class ClockSampler:
     def __init__(self, index):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+        self.path = os.path.join(ROOT, "bench_logs", f"clocks_rank{index}.csv")
 
     def __enter__(self):
         try:

@@ -57,7 +57,7 @@ typedef enum {
   HMM_E_TIMEOUT = 5,      /* a bounded device wait expired                           */
   HMM_E_BUSY = 6,         /* server queue full                                       */
   HMM_E_NOTREADY = 7,     /* server request still pending                            */
-  HMM_E_UNSUPPORTED = 8   /* valid request outside what this build implements        */
+  HMM_E_UNSUPPORTED = 8   /* valid request outside what this library implements      */
 } hmm_status;
 
 /* Emission families (paper Sec. 4).  Parameters per state, in blob order:

@@ -994,7 +994,7 @@ void run_mstep(hmm_ctx ctx, hmm_model model, hmm_stats stats, const MStepOpts& o
     }
   }
   if (!dpass || b->n_seq == 0) return;
-  // Newton steps that re-read the data (SURVEY S8): a fixed number of passes
+  // Newton steps that re-read the data: a fixed number of passes
   // (converged states skip their work), then the Weibull scale pass
   const int NP = model->NP, RS = NP * 3;
   const int64_t S = b->n_seq;

@@ -480,7 +480,7 @@ __global__ void mstep_kernel(ModelBufs mb, const double* __restrict__ rec, MStep
 
 // ---------------------------------------------------------------------------
 // Data passes for the Newton steps that need the observations again
-// (SURVEY S8): Weibull shape (Eq. 11) and negative-binomial r.
+// (Weibull shape, Eq. 11, and negative-binomial r).
 // One warp per sequence, one lane per state, float32 sums over the sequence,
 // then the same fixed-order float64 chunk reductions as the E-step.
 // Per state three sums:
