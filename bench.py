@@ -125,11 +125,30 @@ def cpu_baseline(init, values, offsets, mid, target_s=12.0):
                        f"numpy float64 single thread, {dt:.1f} s")
 
 
+def arm_config(args, NS, S, offsets, n_models, ws, c_step):
+    """The workload's `config` entry (both arms print the same one)."""
+    return dict(workload=(f"{args.family} HMM, N={NS} states, {S} sequences x "
+                          f"T={int(offsets[1] - offsets[0])}, one EM iteration + Viterbi"
+                          if args.workload == "scale" else
+                          f"batching: {S} ragged sequences (sum T = {int(offsets[-1])}), "
+                          f"N={NS}, {n_models} mixed-family models, one EM iteration + Viterbi"),
+                family=args.family if args.workload == "scale" else "mixed",
+                n_states=NS, n_seq_per_gpu=S, total_T=int(offsets[-1]),
+                seq_len=int(offsets[1] - offsets[0]) if args.workload == "scale" else "ragged",
+                global_batch=S * ws,
+                parallelism=f"dp{ws}" if ws > 1 else "single GPU",
+                cell_updates_per_step=c_step,
+                l2="flushed before every timed step (256 MiB write, outside the events)")
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
         return
     truth, init, values, offsets, mid = workload(args, 0)
+    inits = init if isinstance(init, list) else [init]
+    NS = len(inits[0]["pi"])
+    S = len(offsets) - 1
     n_sample = 8 if not args.quick else 4
     for _ in range(args.warmup):
         oracle_step_sample(init, values, offsets, mid, 2)
@@ -143,10 +162,10 @@ def run_reference(args):
     line = dict(impl="reference", metric=METRIC, value=value, unit=UNIT, n_gpus=args.gpus,
                 steps=args.steps, warmup=args.warmup, ms_per_step=ms, higher_is_better=True,
                 scaling="weak", vs_baseline=None, dtype="f64", data="synthetic",
-                config=dict(workload=f"{args.family} N={N_STATES} sample of {n_sample} x T={T_LEN}",
-                            n_seq_sample=n_sample, seq_len=T_LEN, n_states=N_STATES),
+                config=arm_config(args, NS, S, offsets, len(inits), ws, 2.0 * cells(offsets, NS)),
                 cpu_baseline=dict(value=value, unit=UNIT, cores=1, kind="oracle",
-                                  sample=f"{n_sample} sequences of the workload per step"),
+                                  sample=f"{n_sample} sequences of the workload per step (numpy float64, "
+                                         f"one thread), rate scaled to cell updates per second"),
                 e2e=dict(value=value, unit=UNIT, h2d_bytes_per_step=0, d2h_bytes_per_step=0))
     print(json.dumps(line), flush=True)
 
@@ -374,18 +393,7 @@ def run_ours(args):
         line = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=ws, steps=args.steps,
                     warmup=max(args.warmup, 3), ms_per_step=ms, higher_is_better=True,
                     scaling="weak", vs_baseline=None, dtype="f32", data="synthetic",
-                    config=dict(workload=(f"{args.family} HMM, N={NS} states, {S} sequences x "
-                                          f"T={int(offsets[1] - offsets[0])}, one EM iteration + Viterbi"
-                                          if args.workload == "scale" else
-                                          f"batching: {S} ragged sequences (sum T = {int(offsets[-1])}), "
-                                          f"N={NS}, {len(models)} mixed-family models, one EM iteration + Viterbi"),
-                                family=args.family if args.workload == "scale" else "mixed",
-                                n_states=NS, n_seq_per_gpu=S, total_T=int(offsets[-1]),
-                                seq_len=int(offsets[1] - offsets[0]) if args.workload == "scale" else "ragged",
-                                global_batch=S * ws,
-                                parallelism=f"dp{ws}" if ws > 1 else "single GPU",
-                                cell_updates_per_step=c_step,
-                                l2="flushed before every timed step (256 MiB write, outside the events)"),
+                    config=arm_config(args, NS, S, offsets, len(models), ws, c_step),
                     clocks=clocks, e2e=dict(value=ws * c_step / (e2e_ms / 1e3), unit=UNIT,
                                             ms_per_step=e2e_ms, h2d_bytes_per_step=h2d,
                                             d2h_bytes_per_step=d2h),
