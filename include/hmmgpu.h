@@ -183,8 +183,9 @@ typedef enum {
                                  N <= 32: 0 (default) runs the time-parallel form
                                  (chunk transfer matrices, boundary vectors,
                                  chunks recomputed in parallel) when the batch
-                                 has fewer sequences than SMs and a sequence of
-                                 at least 2048 steps; 1 always; -1 never.        */
+                                 has at most as many sequences as the GPU has
+                                 SMs and a sequence of at least 2048 steps;
+                                 1 always; -1 never.                             */
 } hmm_option;
 
 /* Kernel timing slots of hmm_ctx_profile_read. */
