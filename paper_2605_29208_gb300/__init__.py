@@ -5,6 +5,23 @@ This module is argument marshalling only: every step of the computation
 runs in the CUDA kernels of ``libhmmgpu.so``.  PyTorch supplies device
 memory and streams.  There is no CPU fallback: importing the wrappers on a
 machine without the built library, or calling them without a GPU, raises.
+
+Typical use (models are dicts: family, pi [N], A [N, N], params {name:
+array}; a batch is the packed ragged layout: values, offsets [S + 1],
+model_id [S])::
+
+    import paper_2605_29208_gb300 as H
+    ctx = H.Context(0)
+    model = H.Model(ctx, [start_model])             # one or many models
+    batch = H.Batch(values, offsets, model_id).make_plan(ctx, model)
+    trace, n_done = H.fit(ctx, model, batch, n_iter=20)    # Baum-Welch
+    loglik, gamma, _ = H.forward_backward(ctx, model, batch)
+    path, score = H.viterbi(ctx, model, batch)
+    fitted = model.get()
+
+Starting models: ``initialize.kmeanspp_init``; restarts and state-count
+selection in one batch: ``restarts.fit_restarts`` / ``restarts.select_states``;
+a request server with continuous batching: ``Server``.
 """
 from __future__ import annotations
 
