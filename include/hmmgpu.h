@@ -145,7 +145,7 @@ int32_t hmm_family_param_count(int32_t family, int32_t dim);
 int64_t hmm_param_blob_size(int32_t n_models, int32_t n_states, int32_t dim,
                             const int32_t* h_family);
 /* Model-selection criteria of one fitted model (the paper names AIC, BIC and
- * AICc for model comparison, Sec. 5 and the multivariate example, without
+ * AICc for model comparison, Sec. 5.6 and the multivariate example, without
  * formulas; these are the textbook forms).  Host-only arithmetic, no device
  * work.  k = the number of free parameters: (N - 1) initial probabilities,
  * N (N - 1) transition probabilities and N times the free emission

@@ -1,5 +1,6 @@
 """Random restarts and model selection in one batch (the paper's
-k-means++ initialisation, Sec. 5, and its AIC / BIC / AICc comparison).
+k-means++ initialisation, Sec. 4.5, and its AIC / BIC / AICc comparison,
+Sec. 5.6).
 
 Every restart (and every candidate state count) is its own model of one
 multi-model batch: the observations are repeated once per model with that

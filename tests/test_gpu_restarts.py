@@ -1,5 +1,5 @@
 """Random restarts in one multi-model batch and state-count selection by
-BIC (paper Sec. 5: k-means++ starts; AIC / BIC / AICc comparison): every
+BIC (paper Sec. 4.5: k-means++ starts; Sec. 5.6: AIC / BIC / AICc): every
 restart in the shared batch against the FP64 oracle fitting that restart
 alone, and BIC picking the generating state count on well-separated data."""
 import numpy as np
