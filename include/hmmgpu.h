@@ -75,10 +75,10 @@ typedef enum {
  *                   (categorical)"): the model's `dim` is the number of
  *                   symbols K (2..1024); observations are the symbol indices
  *                   0..K-1, one float per step (a batch's dim is 1)
- *   HMM_LOGNORMAL   mu, sigma2 of log y                 (Sec. 4 "Log-normal")
- *   HMM_EXPONENTIAL lambda (rate)                       (Sec. 4 "Exponential")
- *   HMM_RAYLEIGH    sigma2                              (Sec. 4 "Rayleigh")
- *   HMM_UNIFORM     a, b (a < b; closed interval)       (Sec. 4 "Uniform")
+ *   HMM_LOGNORMAL   mu, sigma2 of log y                 (Sec. 4.1 "Log-normal")
+ *   HMM_EXPONENTIAL lambda (rate)                       (Sec. 4.1 "Exponential")
+ *   HMM_RAYLEIGH    sigma2                              (Sec. 4.1 "Rayleigh")
+ *   HMM_UNIFORM     a, b (a < b; closed interval)       (Sec. 4.1 "Uniform")
  *   HMM_CHISQ       nu (degrees of freedom)             (Sec. 4.2 "Chi-squared")
  *   HMM_PARETO      xm, alpha (scale, shape)            (Sec. 4.2 "Pareto")
  * Observations outside a family's support (y <= 0 for Gamma/Weibull/

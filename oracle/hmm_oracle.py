@@ -165,23 +165,23 @@ def emission_logpdf(model: Model, y: np.ndarray) -> np.ndarray:
             idx = np.where(ok, y, 0).astype(np.int64)
             out = np.log(pk[:, idx]).T           # [T, N]
             return np.where(ok[:, None], out, -np.inf)
-        if f == "lognormal":    # Sec. 4 "Log-normal": a Gaussian on log y, y > 0
+        if f == "lognormal":    # Sec. 4.1 "Log-normal": a Gaussian on log y, y > 0
             mu, s2 = p["mu"], p["sigma2"]
             yy = y[:, None]
             ly = np.log(np.where(yy > 0, yy, 1.0))
             out = -ly - 0.5 * np.log(2 * np.pi * s2) - (ly - mu) ** 2 / (2 * s2)
             return np.where(yy > 0, out, -np.inf)
-        if f == "exponential":  # Sec. 4 "Exponential": rate lambda, y >= 0
+        if f == "exponential":  # Sec. 4.1 "Exponential": rate lambda, y >= 0
             lam = p["lam"]
             yy = y[:, None]
             out = np.log(lam) - lam * yy
             return np.where(yy >= 0, out, -np.inf)
-        if f == "rayleigh":     # Sec. 4 "Rayleigh": y / s2 exp(-y^2 / (2 s2)), y >= 0
+        if f == "rayleigh":     # Sec. 4.1 "Rayleigh": y / s2 exp(-y^2 / (2 s2)), y >= 0
             s2 = p["sigma2"]
             yy = y[:, None]
             out = np.log(yy) - np.log(s2) - yy ** 2 / (2 * s2)
             return np.where(yy >= 0, out, -np.inf)
-        if f == "uniform":      # Sec. 4 "Uniform": 1 / (b - a) on the closed interval [a, b]
+        if f == "uniform":      # Sec. 4.1 "Uniform": 1 / (b - a) on the closed interval [a, b]
             a, b = p["a"], p["b"]
             yy = y[:, None]
             out = -np.log(b - a) + 0 * yy
@@ -626,7 +626,7 @@ def _safe_log(y):
 
 
 def mstep_lognormal(w, y, cur):
-    """Sec. 4 "Log-normal": the Gaussian M-step applied to log y."""
+    """Sec. 4.1 "Log-normal": the Gaussian M-step applied to log y."""
     Nj = w.sum()
     ly = _safe_log(y)
     mu = np.sum(w * ly) / Nj
@@ -634,12 +634,12 @@ def mstep_lognormal(w, y, cur):
 
 
 def mstep_exponential(w, y, cur):
-    """Sec. 4 "Exponential": lambda = 1 / ybar_j."""
+    """Sec. 4.1 "Exponential": lambda = 1 / ybar_j."""
     return dict(lam=w.sum() / np.sum(w * y))
 
 
 def mstep_rayleigh(w, y, cur):
-    """Sec. 4 "Rayleigh": sigma^2 = (2 N_j)^-1 sum_t gamma_t(j) y_t^2."""
+    """Sec. 4.1 "Rayleigh": sigma^2 = (2 N_j)^-1 sum_t gamma_t(j) y_t^2."""
     return dict(sigma2=np.sum(w * y * y) / (2 * w.sum()))
 
 
@@ -658,7 +658,7 @@ def support_rows(family, y, cur):
 
 
 def mstep_uniform(w, y, cur):
-    """Sec. 4 "Uniform": a = min_t y_t, b = max_t y_t over the state's rows."""
+    """Sec. 4.1 "Uniform": a = min_t y_t, b = max_t y_t over the state's rows."""
     sel = support_rows("uniform", y, cur)
     if not sel.any():
         return dict(a=np.nan, b=np.nan)

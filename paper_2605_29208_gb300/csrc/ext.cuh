@@ -1,4 +1,4 @@
-// Further scalar families of paper Sec. 4 and Sec. 4.2: log-normal,
+// Further scalar families of paper Sec. 4.1 and Sec. 4.2: log-normal,
 // exponential, Rayleigh, uniform, chi-squared and Pareto.
 //
 // Their densities go into the log b table (emission_kernel with the

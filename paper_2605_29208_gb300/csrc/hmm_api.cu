@@ -970,7 +970,7 @@ void run_mstep(hmm_ctx ctx, hmm_model model, hmm_stats stats, const MStepOpts& o
     }
     mstep_kernel<<<model->M, model->NP, 0, st>>>(model->bufs(), stats->rec.as<double>(), o, dps);
     HMM_CUDA(cudaGetLastError());
-    if (model->any_discrete) {   // Sec. 4 "Discrete": weighted symbol frequencies
+    if (model->any_discrete) {   // Sec. 4.1 "Discrete": weighted symbol frequencies
       const int n = model->M * model->NP;
       discrete_mstep_kernel<<<(n + 127) / 128, 128, 0, st>>>(model->theta.as<double>(), stats->mv_rec.as<double>(),
                                                              model->M, model->NP, model->N, model->P, model->K,

@@ -1,4 +1,4 @@
-"""Parity of the further scalar families (Sec. 4 log-normal, exponential,
+"""Parity of the further scalar families (Sec. 4.1 log-normal, exponential,
 Rayleigh, uniform; Sec. 4.2 chi-squared, Pareto) on the CUDA path with the
 FP64 oracle: log-density table, forward-backward, the E-step statistics
 (feature sums and the support min / max), the M-step, a short fit and

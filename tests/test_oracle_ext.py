@@ -1,4 +1,4 @@
-"""Pins of the oracle's further scalar families (Sec. 4 log-normal,
+"""Pins of the oracle's further scalar families (Sec. 4.1 log-normal,
 exponential, Rayleigh, uniform; Sec. 4.2 chi-squared and Pareto) against
 things other than the oracle itself:
 
