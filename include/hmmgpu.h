@@ -279,7 +279,13 @@ hmm_status hmm_forward_backward(hmm_ctx ctx, hmm_model model, const hmm_batch* b
  * shared by every call in the process and kept between calls: calls whose
  * GPU work overlaps race on it, so order them on one stream.  The first call
  * on a device looks up the array's address; make it before any stream
- * capture. */
+ * capture.  Sizes, pointers and the family are checked on the host
+ * (HMM_E_ARG / HMM_E_UNSUPPORTED); the contents of the device arrays are
+ * checked on the device (offsets[0] = 0, non-decreasing, offsets[n_seq] =
+ * total_T, model ids in [0, n_models)): a malformed batch processes no
+ * sequence, writes NaN to every d_loglik entry and leaves HMM_E_ARG in the
+ * context's sticky status (hmm_ctx_status).  The caller's current device is
+ * restored before the call returns. */
 hmm_status hmm_forward_backward_static(hmm_model model, const hmm_batch* batch,
                                        const float* d_logb, float* d_gamma,
                                        double* d_loglik, void* stream);

@@ -365,6 +365,81 @@ def viterbi_fp32(logpi32, logA32, logb32):
     return q, score
 
 
+def _shift32(v, off):
+    """Subtract the float32 maximum when it is finite; the shift goes to the
+    float64 offset."""
+    m = v.max()
+    if np.isfinite(m):
+        return (v - m).astype(np.float32), off + float(m)
+    return v, off
+
+
+def viterbi_fp32_mitm(logpi32, logA32, logb32):
+    """Viterbi decoded from both ends in float32 (the reading of Sec. 3.3,
+    Eq. 3-4, used by the device for small state counts), with a fixed
+    operation order so that decoded paths can be compared bit for bit.
+
+    With h = floor(T/2):
+      forward, t = 0..h: delta_0(j) = logpi(j) + logb_0(j); for t >= 1
+          c(i, j) = delta_{t-1}(i) + logA(i, j), psi_t(j) = lowest i
+          attaining max_i c(i, j), delta_t(j) = c(psi_t(j), j) + logb_t(j);
+      backward, t = T-1..h: beta_{T-1}(i) = 0; for t < T-1
+          v(j) = beta_{t+1}(j) + logb_{t+1}(j),
+          c(i, j) = v(j) + logA(i, j), phi_t(i) = lowest j attaining
+          max_j c(i, j), beta_t(i) = c(i, phi_t(i));
+      after every step of either chain its maximum, when finite, is
+      subtracted and added to that chain's float64 offset;
+      meeting point: q_h = lowest j attaining max_j delta_h(j) + beta_h(j);
+      q_{t-1} = psi_t(q_t) for t = h..1, q_{t+1} = phi_t(q_t) for t = h..T-2.
+    Every operation on the scores is a float32 addition, subtraction or
+    comparison.  The score is max_j (delta_h(j) + beta_h(j)) plus both
+    offsets.  Returns (path int32 [T], score float64)."""
+    f32 = np.float32
+    logpi32 = np.asarray(logpi32, dtype=f32)
+    logA32 = np.asarray(logA32, dtype=f32)
+    logb32 = np.asarray(logb32, dtype=f32)
+    T, N = logb32.shape
+    if T == 0:
+        return np.zeros(0, np.int32), 0.0
+    h = T // 2
+    cols = np.arange(N)
+    psi = np.zeros((T, N), dtype=np.int32)
+    d, doff = _shift32((logpi32 + logb32[0]).astype(f32), 0.0)
+    for t in range(1, h + 1):
+        cand = (d[:, None] + logA32).astype(f32)        # [i, j]
+        psi[t] = np.argmax(cand, axis=0)                 # lowest i at ties
+        d, doff = _shift32((cand[psi[t], cols] + logb32[t]).astype(f32), doff)
+    phi = np.zeros((T, N), dtype=np.int32)
+    b, boff = _shift32(np.zeros(N, dtype=f32), 0.0)
+    for t in range(T - 2, h - 1, -1):
+        v = (b + logb32[t + 1]).astype(f32)
+        cand = (v[None, :] + logA32).astype(f32)        # [i, j]
+        phi[t] = np.argmax(cand, axis=1)                 # lowest j at ties
+        b, boff = _shift32(cand[cols, phi[t]].astype(f32), boff)
+    c = (d + b).astype(f32)
+    q = np.empty(T, dtype=np.int32)
+    q[h] = int(np.argmax(c))
+    for t in range(h, 0, -1):
+        q[t - 1] = psi[t, q[t]]
+    for t in range(h, T - 1):
+        q[t + 1] = phi[t, q[t]]
+    return q, doff + boff + float(c[q[h]])
+
+
+def path_logprob(logpi, logA, logb, path):
+    """log P(q, y) of one state path (the product whose maximum Eq. 3
+    takes): log pi_{q_1} + sum_t log a_{q_{t-1} q_t} + sum_t log b_{q_t}(y_t),
+    in float64."""
+    path = np.asarray(path, dtype=np.int64)
+    T = len(path)
+    if T == 0:
+        return 0.0
+    lp = float(logpi[path[0]])
+    lp += float(np.sum(logA[path[:-1], path[1:]]))
+    lp += float(np.sum(logb[np.arange(T), path]))
+    return lp
+
+
 # --------------------------------------------------------------------------
 # Special functions used by the M-steps (library routines)
 # --------------------------------------------------------------------------

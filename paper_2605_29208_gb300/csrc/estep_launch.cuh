@@ -11,14 +11,10 @@ cudaError_t estep_launch_fam(const EStepArgs& a, int n_sm, cudaStream_t st) {
   constexpr int WPB = kWarpsPerBlock;
   const size_t smem = sizeof(WarpSmem<SmallCfg<NP, G>>) * WPB;
   auto kern = estep_small_kernel<NP, G, WPB, MODE, FAMK>;
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
+  cudaError_t e = ensure_max_dyn_smem(reinterpret_cast<const void*>(kern), smem);
+  if (e != cudaSuccess) return e;
   int per_sm = 0;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, WPB * 32, smem);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, WPB * 32, smem);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) per_sm = 1;
   const int want = (a.n_items + WPB - 1) / WPB;

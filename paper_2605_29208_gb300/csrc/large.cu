@@ -197,24 +197,12 @@ __global__ void large_reduce_l1(const float* __restrict__ part, const double* __
 
 
 
-// Opt-in shared memory above 48 KB, once per kernel (`done` is a static of
-// the caller's template instance, so every kernel has its own flag).
-template <class K>
-cudaError_t prepare(K kern, size_t smem, bool& done) {
-  if (!done) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    done = true;
-  }
-  return cudaSuccess;
-}
 
 template <int NP>
 cudaError_t launch_fb_np(const LargeArgs& a, cudaStream_t st) {
   const size_t smem = LgShape<NP>::smem_bytes();
   auto kern = large_fb_kernel<NP>;
-  static bool done = false;
-  cudaError_t e = prepare(kern, smem, done);
+  cudaError_t e = ensure_max_dyn_smem(reinterpret_cast<const void*>(kern), smem);
   if (e != cudaSuccess) return e;
   kern<<<dim3((unsigned)a.n_groups, 2), LG_NT, smem, st>>>(a);
   return cudaGetLastError();
@@ -224,8 +212,7 @@ template <int NP>
 cudaError_t launch_vit_np(const LargeArgs& a, cudaStream_t st) {
   const size_t smem = LgVitShape<NP>::smem_bytes();
   auto kern = large_viterbi_kernel<NP>;
-  static bool done = false;
-  cudaError_t e = prepare(kern, smem, done);
+  cudaError_t e = ensure_max_dyn_smem(reinterpret_cast<const void*>(kern), smem);
   if (e != cudaSuccess) return e;
   kern<<<(unsigned)a.n_groups, LG_NT, smem, st>>>(a);
   return cudaGetLastError();

@@ -4,11 +4,31 @@
 
 #include <cuda_runtime.h>
 
+#include <mutex>
+#include <set>
+#include <utility>
+
 #include "estep_small.cuh"
 #include "large.cuh"
 #include "viterbi_small.cuh"
 
 namespace hmm {
+
+// Raises a kernel's dynamic shared-memory limit on the current device.  The
+// attribute is a per-device property of the kernel, so it is set once per
+// (kernel, device) pair; thread-safe.
+inline cudaError_t ensure_max_dyn_smem(const void* kernel, size_t bytes) {
+  static std::mutex mu;
+  static std::set<std::pair<const void*, int>> done;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lk(mu);
+  if (done.count({kernel, dev})) return cudaSuccess;
+  e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess) done.insert({kernel, dev});
+  return e;
+}
 
 // Chain shapes compiled for the small-N kernels: (padded N, lanes per chain).
 bool estep_small_supported(int NP, int G);

@@ -299,11 +299,9 @@ template <int NP>
 cudaError_t launch_tc_np(const TcArgs& a, cudaStream_t st) {
   using S = TcShape<NP>;
   auto kern = tc_fb_kernel<NP>;
-  static bool done = false;
-  if (!done) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::smem_bytes());
+  {
+    cudaError_t e = ensure_max_dyn_smem(reinterpret_cast<const void*>(kern), S::smem_bytes());
     if (e != cudaSuccess) return e;
-    done = true;
   }
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(S::CL, (unsigned)a.n_tiles, 2);

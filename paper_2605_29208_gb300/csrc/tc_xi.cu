@@ -212,11 +212,9 @@ cudaError_t launch_xi_tn(const float* XT, const float* YT, int64_t ktot, const i
                          int n_chunks, int NP, double* xi_chunk, int* status, cudaStream_t st) {
   constexpr size_t smem = 1024 + (size_t)XI_STAGES * (XI_TM * 128 + TN * 128) + XI_STAGES * 8 + 16;
   auto kern = xi_tc_kernel<TN>;
-  static bool done = false;
-  if (!done) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  {
+    cudaError_t e = ensure_max_dyn_smem(reinterpret_cast<const void*>(kern), smem);
     if (e != cudaSuccess) return e;
-    done = true;
   }
   const dim3 grid((unsigned)((NP / XI_TM) * (NP / TN)), (unsigned)n_chunks);
   kern<<<grid, 128, smem, st>>>(XT, YT, ktot, kc0, kpad, NP, xi_chunk, status);

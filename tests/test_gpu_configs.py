@@ -7,6 +7,7 @@ import pytest
 
 from oracle import hmm_oracle as O
 from paper_2605_29208_gb300 import initialize, synth
+from parity import assert_params_close, check_fit_iterations, check_viterbi_fp64
 
 pytestmark = pytest.mark.gpu
 
@@ -28,16 +29,11 @@ def test_tiny_gauss_fit_and_decode(H):
     ctx = H.Context(0)
     model = H.Model(ctx, [init])
     batch = H.Batch(values, offsets, mid)
-    trace, done = H.fit(ctx, model, batch, n_iter=20)
-    assert done == 20
-    om = O.Model("gauss", init["pi"].copy(), init["A"].copy(), {k: v.copy() for k, v in init["params"].items()})
-    ref_models, ref_trace = O.fit([om], values, offsets, mid, 20)
+    trace, (ref_models, ref_trace) = check_fit_iterations(H, ctx, model, batch, values, offsets, mid, 20)
     np.testing.assert_allclose(trace[:, 0], ref_trace.sum(axis=1), rtol=1e-5)
     got = model.get()[0]
     ref = ref_models[0]
-    np.testing.assert_allclose(got["A"], ref.A, rtol=1e-3, atol=1e-6)
-    for k, v in ref.params.items():
-        np.testing.assert_allclose(got["params"][k], v, rtol=1e-3, err_msg=k)
+    assert_params_close([got], [ref], rtol=1e-4)
     # the fit lands near the generating parameters
     np.testing.assert_allclose(np.sort(got["params"]["mu"]), [-1, 1], atol=0.25)
     # EM never decreases the likelihood
@@ -45,11 +41,4 @@ def test_tiny_gauss_fit_and_decode(H):
     path, score = H.viterbi(ctx, model, batch)
     path = path.cpu().numpy()
     score = float(score.cpu().numpy()[0])
-    lpi, lA = np.log(ref.pi), np.log(ref.A)
-    q, sc, gap, fgap = O.viterbi_gaps(lpi, lA, O.emission_logpdf(ref, values))
-    assert abs(score - sc) <= 1e-4 * abs(sc)
-    diff = np.nonzero(path != q)[0]
-    if len(diff):
-        t = diff[-1]
-        margin = fgap if t == len(values) - 1 else gap[t + 1, q[t + 1]]
-        assert margin < 1e-3
+    check_viterbi_fp64(path, score, ref, values, where="tiny")

@@ -10,6 +10,7 @@ import pytest
 
 from oracle import hmm_oracle as O
 from paper_2605_29208_gb300 import synth
+from parity import assert_params_close, check_fit_iterations, check_viterbi_fp64, check_viterbi_table_batch
 
 pytestmark = pytest.mark.gpu
 
@@ -159,11 +160,9 @@ def test_ext_mstep_and_fit(H, ctx, f, N):
         for k, v in r.params.items():
             np.testing.assert_allclose(g["params"][k], v, rtol=PARAM_RTOL, atol=1e-6, err_msg=k)
     model2 = H.Model(ctx, init)
-    trace, done = H.fit(ctx, model2, batch, n_iter=4)
-    ref_models, ref_trace = O.fit([om(m) for m in init], values, offsets, mid, 4)
+    trace, (ref_models, ref_trace) = check_fit_iterations(H, ctx, model2, batch, values, offsets, mid, 4, atol=1e-6)
     np.testing.assert_allclose(trace[:, 0], ref_trace.sum(axis=1), rtol=LL_RTOL)
-    for k, v in ref_models[0].params.items():
-        np.testing.assert_allclose(model2.get()[0]["params"][k], v, rtol=5 * PARAM_RTOL, atol=1e-6, err_msg=k)
+    assert_params_close(model2.get(), ref_models, rtol=PARAM_RTOL, atol=1e-6)
 
 
 @pytest.mark.parametrize("f,N", CASES)
@@ -176,12 +175,9 @@ def test_ext_viterbi(H, ctx, f, N):
         if len(y) == 0:
             continue
         o = om(models[mid[s]])
-        q, sc, gap, fgap = O.viterbi_gaps(np.log(o.pi), np.log(o.A), O.emission_logpdf(o, y))
-        assert abs(score[s] - sc) <= 1e-5 * max(1.0, abs(sc))
-        diff = np.nonzero(path[offsets[s]:offsets[s + 1]] != q)[0]
-        if len(diff):
-            t = diff[-1]
-            assert (fgap if t == len(y) - 1 else gap[t + 1, q[t + 1]]) < 1e-3
+        check_viterbi_fp64(path[offsets[s]:offsets[s + 1]], score[s], o, y, where=s)
+    # the decode is a function of the float32 table: bit-exact with the float32-mode oracle
+    check_viterbi_table_batch(H, ctx, model, batch, models, values, offsets, mid, path, score)
 
 
 def test_ext_set_params_rejects_bad_domains(H, ctx):

@@ -8,6 +8,7 @@ import pytest
 
 from oracle import hmm_oracle as O
 from paper_2605_29208_gb300 import synth
+from parity import check_viterbi_fp64
 
 pytestmark = pytest.mark.gpu
 
@@ -75,12 +76,7 @@ def test_scale_full_size(H):
     path, score = path.cpu().numpy(), score.cpu().numpy()
     for s in (0, 3000):
         y = values[offsets[s]:offsets[s + 1]]
-        q, sc, gap, fgap = O.viterbi_gaps(np.log(o.pi), np.log(o.A), O.emission_logpdf(o, y))
-        assert abs(score[s] - sc) <= 1e-5 * abs(sc)
-        diff = np.nonzero(path[offsets[s]:offsets[s + 1]] != q)[0]
-        if len(diff):
-            t = diff[-1]
-            assert (fgap if t == len(y) - 1 else gap[t + 1, q[t + 1]]) < 1e-3
+        check_viterbi_fp64(path[offsets[s]:offsets[s + 1]], score[s], o, y, where=("scale", s))
     stats = stats_invariants(H, ctx, model, batch, [init], offsets, mid, 16)
     H.mstep(ctx, model, stats, batch=batch)
     got = model.get()[0]

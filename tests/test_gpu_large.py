@@ -8,6 +8,7 @@ import pytest
 
 from oracle import hmm_oracle as O
 from paper_2605_29208_gb300 import synth
+from parity import check_fit_iterations, check_viterbi_fp32, check_viterbi_fp64, check_viterbi_table_batch
 
 pytestmark = pytest.mark.gpu
 
@@ -167,11 +168,9 @@ def test_large_fit(H, ctx):
     init = [synth.perturb(rng, t) for t in truth]
     model = H.Model(ctx, init)
     batch = H.Batch(values, offsets, mid)
-    trace, done = H.fit(ctx, model, batch, n_iter=3)
-    assert done == 3
-    ref_models, ref_trace = O.fit([om(m) for m in init], values, offsets, mid, 3)
+    trace, (ref_models, ref_trace) = check_fit_iterations(H, ctx, model, batch, values, offsets, mid, 3)
     np.testing.assert_allclose(trace[:, 0], ref_trace.sum(axis=1), rtol=LL_RTOL)
-    assert_params_close(model.get(), ref_models, 5 * PARAM_RTOL)
+    assert_params_close(model.get(), ref_models, PARAM_RTOL)
 
 
 @pytest.mark.parametrize("N", [64, 100, 256, 600])
@@ -193,9 +192,8 @@ def test_large_viterbi_bit_exact_table(H, ctx, N):
     lpi = np.log(m["pi"]).astype(np.float32)
     lA = np.log(m["A"]).astype(np.float32)
     for s in range(len(lengths)):
-        q, sc = O.viterbi_fp32(lpi, lA, logb[offsets[s]:offsets[s + 1]])
-        np.testing.assert_array_equal(path[offsets[s]:offsets[s + 1]], q)
-        assert abs(score[s] - sc) <= 1e-5 * max(1.0, abs(sc))
+        check_viterbi_fp32(path[offsets[s]:offsets[s + 1]], score[s], lpi, lA, logb[offsets[s]:offsets[s + 1]], N,
+                           where=s)
 
 
 @pytest.mark.parametrize("family,N", [("gauss", 70), ("poisson", 128)])
@@ -214,14 +212,8 @@ def test_large_viterbi_vs_fp64(H, ctx, family, N):
             assert score[s] == 0.0
             continue
         o = om(models[mid[s]])
-        q, sc, gap, fgap = O.viterbi_gaps(np.log(o.pi), np.log(o.A), O.emission_logpdf(o, y))
-        g = path[offsets[s]:offsets[s + 1]]
-        assert abs(score[s] - sc) <= 1e-5 * max(1.0, abs(sc))
-        diff = np.nonzero(g != q)[0]
-        if len(diff):
-            t = diff[-1]
-            margin = fgap if t == len(y) - 1 else gap[t + 1, q[t + 1]]
-            assert margin < 1e-3, (s, t, margin)
+        check_viterbi_fp64(path[offsets[s]:offsets[s + 1]], score[s], o, y, where=(family, N, s))
+    check_viterbi_table_batch(H, ctx, model, batch, models, values, offsets, mid, path, score)
 
 
 def test_large_weibull_mstep_unsupported(H, ctx):

@@ -7,6 +7,7 @@ import pytest
 
 from oracle import hmm_oracle as O
 from paper_2605_29208_gb300 import synth
+from parity import check_fit_iterations, check_viterbi_fp64, check_viterbi_table_batch
 
 pytestmark = pytest.mark.gpu
 
@@ -152,11 +153,10 @@ def test_mv_fit(H, ctx, family, N, D):
     init = [synth.perturb(rng, t) for t in truth]
     model = H.Model(ctx, init)
     batch = H.Batch(values, offsets, mid, dim=D)
-    trace, done = H.fit(ctx, model, batch, n_iter=5)
-    assert done == 5
-    ref_models, ref_trace = O.fit([om(m) for m in init], values.astype(np.float64), offsets, mid, 5)
+    trace, (ref_models, ref_trace) = check_fit_iterations(H, ctx, model, batch, values.astype(np.float64), offsets,
+                                                          mid, 5)
     np.testing.assert_allclose(trace[:, 0], ref_trace.sum(axis=1), rtol=LL_RTOL)
-    assert_params_close(model.get(), ref_models, 5 * PARAM_RTOL)
+    assert_params_close(model.get(), ref_models, PARAM_RTOL)
     assert np.all(np.diff(trace[:, 0]) >= -1e-6 * np.abs(trace[:, 0]).max())
 
 
@@ -176,14 +176,8 @@ def test_mv_viterbi_vs_fp64(H, ctx, family, N, D):
         if len(y) == 0:
             continue
         o = om(models[mid[s]])
-        q, sc, gap, fgap = O.viterbi_gaps(np.log(o.pi), np.log(o.A), O.emission_logpdf(o, y))
-        g = path[offsets[s]:offsets[s + 1]]
-        assert abs(score[s] - sc) <= 1e-5 * max(1.0, abs(sc))
-        diff = np.nonzero(g != q)[0]
-        if len(diff):
-            t = diff[-1]
-            margin = fgap if t == len(y) - 1 else gap[t + 1, q[t + 1]]
-            assert margin < 1e-3, (s, t, margin)
+        check_viterbi_fp64(path[offsets[s]:offsets[s + 1]], score[s], o, y, where=(family, N, D, s))
+    check_viterbi_table_batch(H, ctx, model, batch, models, values, offsets, mid, path, score)
 
 
 def test_mv_not_positive_definite(H, ctx):

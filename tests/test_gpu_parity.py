@@ -8,6 +8,7 @@ import pytest
 
 from oracle import hmm_oracle as O
 from paper_2605_29208_gb300 import synth
+from parity import check_fit_iterations, check_viterbi_fp32, check_viterbi_fp64
 
 pytestmark = pytest.mark.gpu
 
@@ -209,11 +210,10 @@ def test_fit_parity(H, ctx, family):
     init = [synth.perturb(rng, t) for t in truth]
     model = H.Model(ctx, init)
     batch = H.Batch(values, offsets, mid)
-    trace, done = H.fit(ctx, model, batch, n_iter=5)
-    assert done == 5
-    ref_models, ref_trace = O.fit([om(m) for m in init], values, offsets, mid, 5)
+    trace, (ref_models, ref_trace) = check_fit_iterations(H, ctx, model, batch, values, offsets, mid, 5)
+    # the compounded five iterations from the same start
     np.testing.assert_allclose(trace[:, 0], ref_trace.sum(axis=1), rtol=LL_RTOL)
-    assert_params_close(model.get(), ref_models, rtol=5 * PARAM_RTOL)
+    assert_params_close(model.get(), ref_models, rtol=PARAM_RTOL)
     # EM monotonicity on the device trace
     assert np.all(np.diff(trace[:, 0]) >= -1e-6 * np.abs(trace[:, 0]).max())
 
@@ -238,9 +238,8 @@ def test_viterbi_bit_exact_table(H, ctx, N):
     lpi = np.log(m["pi"]).astype(np.float32)
     lA = np.log(m["A"]).astype(np.float32)
     for s in range(len(lengths)):
-        q, sc = O.viterbi_fp32(lpi, lA, logb[offsets[s]:offsets[s + 1]])
-        np.testing.assert_array_equal(path[offsets[s]:offsets[s + 1]], q)
-        assert abs(score[s] - sc) <= 1e-5 * max(1.0, abs(sc))
+        check_viterbi_fp32(path[offsets[s]:offsets[s + 1]], score[s], lpi, lA, logb[offsets[s]:offsets[s + 1]], N,
+                           where=s)
 
 
 @pytest.mark.parametrize("family", SCALAR)
@@ -255,16 +254,7 @@ def test_viterbi_vs_fp64(H, ctx, family):
     score = score.cpu().numpy()
     for s in range(len(offsets) - 1):
         y = values[offsets[s]:offsets[s + 1]]
-        o = om(models[mid[s]])
-        lpi, lA = np.log(o.pi), np.log(o.A)
-        q, sc, gap, fgap = O.viterbi_gaps(lpi, lA, O.emission_logpdf(o, y))
-        g = path[offsets[s]:offsets[s + 1]]
-        assert abs(score[s] - sc) <= 1e-5 * max(1.0, abs(sc))
-        diff = np.nonzero(g != q)[0]
-        if len(diff):
-            t = diff[-1]          # first divergence in traceback order
-            margin = fgap if t == len(y) - 1 else gap[t + 1, q[t + 1]]
-            assert margin < 1e-3, (s, t, margin)
+        check_viterbi_fp64(path[offsets[s]:offsets[s + 1]], score[s], om(models[mid[s]]), y, where=(family, s))
 
 
 @pytest.mark.parametrize("family", SCALAR)

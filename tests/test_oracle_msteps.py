@@ -361,3 +361,34 @@ def test_discrete_recursions_brute_force():
     q, sc = O.viterbi(m, y)
     np.testing.assert_array_equal(q, bf["map_path"])
     assert abs(sc - bf["map_score"]) < 1e-12
+
+
+@pytest.mark.parametrize("N", [2, 3])
+def test_transition_and_initial_update_vs_brute_force(N):
+    """The transition / initial M-step of one Baum-Welch iteration against
+    expected counts by enumeration of every state path: a_ij = sum over
+    sequences of E[#(i -> j)] / sum over sequences of sum_{t < T} P(q_t = i),
+    pi_j = mean over sequences of P(q_1 = j).  The batch mixes lengths 1..6
+    so that a length-1 sequence adds to pi but not to A."""
+    rng = np.random.default_rng(40 + N)
+    pi = rng.dirichlet(np.ones(N))
+    A = rng.dirichlet(np.ones(N), size=N)
+    m = M("gauss", N, mu=list(np.linspace(-1, 1, N)), sigma2=list(rng.uniform(0.5, 2, N)))
+    m.pi, m.A = pi, A
+    lengths = [6, 1, 4, 5, 2]
+    seqs = [rng.normal(0, 1.5, T) for T in lengths]
+    values = np.concatenate(seqs)
+    offsets = np.concatenate([[0], np.cumsum(lengths)]).astype(np.int64)
+    mid = np.zeros(len(lengths), np.int32)
+    new, _ = O.em_iteration([m], values, offsets, mid)
+    xi = np.zeros((N, N))
+    den = np.zeros(N)
+    g1 = np.zeros(N)
+    for y in seqs:
+        logb = O.emission_logpdf(m, y)
+        bf = O.brute_force(np.log(pi), np.log(A), logb)
+        xi += bf["xi_sum"]
+        den += bf["gamma"][:-1].sum(axis=0)
+        g1 += bf["gamma"][0]
+    np.testing.assert_allclose(new[0].A, xi / den[:, None], rtol=1e-11, atol=1e-13)
+    np.testing.assert_allclose(new[0].pi, g1 / len(seqs), rtol=1e-11, atol=1e-13)
