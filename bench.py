@@ -60,6 +60,10 @@ def args_parse():
     p.add_argument("--requests", type=int, default=1000, help="serving: number of requests")
     p.add_argument("--t-max", type=int, default=100000, help="serving: longest sequence")
     p.add_argument("--slots", type=int, default=32, help="serving: concurrent batches")
+    p.add_argument("--no-extras", action="store_true",
+                   help="only the headline line (no batching / precision / serving sub-measurements)")
+    p.add_argument("--serve-rate", type=float, default=5.0, help="extras: the sustained serving rate")
+    p.add_argument("--serve-requests", type=int, default=150, help="extras: requests per serving run")
     return p.parse_args()
 
 
@@ -123,6 +127,69 @@ def cpu_baseline(init, values, offsets, mid, target_s=12.0):
                 sample=f"first {n2} of {len(offsets) - 1} sequences ({int(offsets[n2])} time steps, "
                        f"N={len(_as_list(init)[0]['pi'])}), one EM iteration + one Viterbi decode, "
                        f"numpy float64 single thread, {dt:.1f} s")
+
+
+def _oracle_fb_chunk(job):
+    """Worker: the oracle's forward-backward of a list of sequences."""
+    from oracle import hmm_oracle as O
+    m, seqs = job
+    om = O.Model(m["family"], m["pi"], m["A"], m["params"])
+    return [(fb["logL"], fb["gamma"], fb["xi_sum"]) for fb in (O.forward_backward(om, y) for y in seqs)]
+
+
+def _oracle_vit_chunk(job):
+    """Worker: the oracle's Viterbi decode of a list of sequences."""
+    from oracle import hmm_oracle as O
+    m, seqs = job
+    om = O.Model(m["family"], m["pi"], m["A"], m["params"])
+    return [O.viterbi(om, y)[1] for y in seqs]
+
+
+def _model_dict(o):
+    return dict(family=o.family, pi=o.pi, A=o.A, params=o.params)
+
+
+def oracle_step_pool(pool, n_proc, init, values, offsets, n_sample):
+    """One EM iteration and one Viterbi decode of the first n_sample sequences
+    (one model) with the oracle's own functions, the sequences of each E-step
+    and decode spread over n_proc worker processes; the pooled M-step runs in
+    this process.  Returns (seconds, cell updates)."""
+    from oracle import hmm_oracle as O
+    m = _as_list(init)[0]
+    seqs = [values[offsets[s]:offsets[s + 1]] for s in range(n_sample)]
+    parts = [seqs[i::n_proc] for i in range(n_proc)]
+    t0 = time.perf_counter()
+    res = [r for part in pool.map(_oracle_fb_chunk, [(m, p) for p in parts]) for r in part]
+    om = O.Model(m["family"], m["pi"].copy(), m["A"].copy(), {k: v.copy() for k, v in m["params"].items()})
+    W = np.concatenate([g for _, g, _ in res])
+    Y = np.concatenate([p for part in parts for p in part])
+    xi = sum(x for _, _, x in res)
+    g1 = sum(g[0] for _, g, _ in res)
+    new, _ = O.mstep_emission(om, W, Y)
+    new.pi, new.A = O.mstep_transitions(om, xi, g1, n_sample)
+    nd = _model_dict(new)
+    pool.map(_oracle_vit_chunk, [(nd, p) for p in parts])
+    dt = time.perf_counter() - t0
+    return dt, 2.0 * cells(offsets[:n_sample + 1], len(m["pi"]))
+
+
+def cpu_baseline_all_cores(init, values, offsets, target_s=15.0):
+    """The oracle on every host core: a spawned process pool over sequences
+    (each worker single-threaded), on a bounded prefix of the workload."""
+    import multiprocessing as mp
+    n_proc = host_cores()
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[k] = "1"
+    S = len(offsets) - 1
+    with mp.get_context("spawn").Pool(n_proc) as pool:
+        n = min(S, 2 * n_proc)
+        dt, _ = oracle_step_pool(pool, n_proc, init, values, offsets, n)
+        n2 = int(max(n_proc, min(S, n * target_s / max(dt, 1e-3))))
+        dt, c = oracle_step_pool(pool, n_proc, init, values, offsets, n2)
+    return dict(value=c / dt, unit=UNIT, cores=n_proc, kind="oracle",
+                sample=f"first {n2} of {S} sequences ({int(offsets[n2])} time steps), one EM iteration + one "
+                       f"Viterbi decode, numpy float64, {n_proc} spawned worker processes over sequences "
+                       f"(M-step in the parent), {dt:.1f} s")
 
 
 def arm_config(args, NS, S, offsets, n_models, ws, c_step):
@@ -249,11 +316,10 @@ def peaks():
         return {}
 
 
-def run_ours(args):
+def run_ours(args, emit=True):
     import torch
     import paper_2605_29208_gb300 as H
-    from paper_2605_29208_gb300 import _lib
-    from paper_2605_29208_gb300.parallel import allreduce_stats
+    from paper_2605_29208_gb300 import _lib, parallel
 
     ws, rank, local = dist_env()
     torch.cuda.set_device(local)
@@ -286,12 +352,12 @@ def run_ours(args):
     import ctypes as C
     sp = C.c_void_p(stream.cuda_stream)
 
-    record = stats.device_tensor() if dist is not None else None
+    # data parallel: the library combines its records across ranks through
+    # this all-reduce (after the E-step, and per Newton data pass)
+    exchange = parallel.Exchange(stats) if dist is not None else None
 
     def step():
         H.check(L.hmm_estep_stats(ctx.h, model.h, C.byref(b), stats.h, C.c_void_p(ll.data_ptr()), sp))
-        if dist is not None:
-            allreduce_stats(record)        # the one exchange step of an iteration
         H.check(L.hmm_mstep(ctx.h, model.h, stats.h, C.byref(b), C.byref(opts), sp))
         H.check(L.hmm_viterbi(ctx.h, model.h, C.byref(b), None, C.c_void_p(path.data_ptr()),
                               C.c_void_p(score.data_ptr()), sp))
@@ -375,7 +441,8 @@ def run_ours(args):
     # (forward mat-vec, backward mat-vec, xi accumulation) = 6 N^2 flop
     pk = peaks()
     sm_max = float(pk.get("sm_max_mhz", 2070.0))
-    alu_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12          # TFLOP/s, FP32 FMA
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    alu_peak = n_sm * 128 * 2 * sm_max * 1e6 / 1e12          # TFLOP/s, FP32 FMA
     flops = 6.0 * NS * NS * float(offsets[-1])
     achieved = flops / (est_ms / 1e3) / 1e12
     traffic = profiled_traffic("estep_small_N16_S4096_T2000.md",
@@ -386,7 +453,13 @@ def run_ours(args):
                     frac=achieved / alu_peak, traffic=traffic,
                     algorithmic_bytes=float(offsets[-1]) * (8.0 + 8.0 * NS),
                     kernel="estep_small_kernel (fused emission+forward+backward+gamma/xi+stats)",
-                    peak_note="FP32 FMA: 152 SMs x 128 lanes x 2 flop x max SM clock (derived)")
+                    peak_note=f"FP32 FMA: {n_sm} SMs (device query) x 128 lanes x 2 flop x max SM clock "
+                              f"{sm_max:g} MHz (derived)")
+    # HBM view of the same launch: 8D + 8N + 16 bytes per (sequence, t)
+    hbm_bytes = float(offsets[-1]) * (8.0 + 8.0 * NS + 16.0)
+    hbm_peak = float(pk.get("hbm_gbs", 6800.0))
+    estep_hbm = dict(bytes_per_seq_t=8.0 + 8.0 * NS + 16.0, achieved_gbs=hbm_bytes / (est_ms / 1e3) / 1e9,
+                     peak_gbs=hbm_peak, frac=hbm_bytes / (est_ms / 1e3) / 1e9 / hbm_peak)
     clocks = clk.summary() if rank == 0 else None
     out = None
     if rank == 0:
@@ -403,21 +476,27 @@ def run_ours(args):
                                    mstep_ms=prof["mstep"][0] / args.steps,
                                    baum_welch_cell_updates_per_s=cells(offsets, NS) / (bw_ms / 1e3),
                                    autotune_ms=tuned_ms,
-                                   wall_s=t_wall))
+                                   wall_s=t_wall),
+                    estep_hbm=estep_hbm)
         if plain:
             line["plain_gpu"] = plain
             line["vs_plain_gpu"] = plain["bw_ms"] / bw_ms
-        if not args.no_cpu_baseline and not args.quick:
+        if not args.no_cpu_baseline and not args.quick and ws == 1:
             line["cpu_baseline"] = cpu_baseline(init, values, offsets, mid)
+            if args.workload == "scale":
+                line["cpu_baseline_all_cores"] = cpu_baseline_all_cores(init, values, offsets)
         out = line
-        print(json.dumps(out), flush=True)
+        if emit and not (args.workload == "scale" and ws == 1 and not args.quick and not args.no_extras):
+            print(json.dumps(out), flush=True)
+    if exchange is not None:
+        exchange.close()
     if dist is not None:
         dist.barrier()
         dist.destroy_process_group()
     return out
 
 
-def run_precision(args):
+def run_precision(args, emit=True):
     """Large dense N: N = 512, Dirichlet(0.1) rows, 1024 sequences x T = 4096,
     diagonal Gaussian D = 32.  One EM iteration + Viterbi with the tensor-core
     recursions, against the same step with the float32 CUDA-core recursions."""
@@ -515,11 +594,12 @@ def run_precision(args):
                                speedup_step=ms_32 / ms_tc),
                 tensor_vs_fp32=dict(loglik_max_rel=float(rel.max()), loglik_median_rel=float(np.median(rel))),
                 gpu_launches=int(sum(v[1] for v in prof_tc.values())))
-    print(json.dumps(line), flush=True)
+    if emit:
+        print(json.dumps(line), flush=True)
     return line
 
 
-def run_serving(args):
+def run_serving(args, emit=True):
     """Request server under Poisson arrivals: decode / posterior / 10-iteration
     fit requests, N in {4, 16, 64, 256}, T log-uniform in [100, t_max],
     full-covariance Gaussian D = 8 or Gamma emissions, each request its own
@@ -577,7 +657,8 @@ def run_serving(args):
                 cell_updates_per_s=cells / makespan, clocks=clk.summary(),
                 failed=int(sum(1 for x in results if x["status"] != 0)),
                 errors=sorted({x.get("error", "") for x in results if x["status"] != 0})[:5])
-    print(json.dumps(line), flush=True)
+    if emit:
+        print(json.dumps(line), flush=True)
     return line
 
 
@@ -650,7 +731,66 @@ def main():
     elif args.workload == "discrete":
         run_discrete(args)
     else:
-        run_ours(args)
+        line = run_ours(args)
+        ws = dist_env()[0]
+        if line is not None and args.workload == "scale" and ws == 1 and not args.quick and not args.no_extras:
+            line.update(extra_workloads(args))
+            print(json.dumps(line), flush=True)
+
+
+def _sub(args, **kw):
+    a = argparse.Namespace(**vars(args))
+    for k, v in kw.items():
+        setattr(a, k, v)
+    return a
+
+
+def _free_gpu():
+    import gc
+    import torch
+    gc.collect()
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+
+
+def extra_workloads(args):
+    """The other configurations of the metric, measured in the same run
+    after the headline line: the batching step (with its E-step HBM
+    fraction and the plain-path ratio), the precision step (tensor-core
+    recursion fraction of the tensor peak) and serving latency (a rate the
+    server sustains, and the configured arrival rate)."""
+    out = {}
+    t0 = time.perf_counter()
+    _free_gpu()
+    try:
+        b = run_ours(_sub(args, workload="batching", steps=5, warmup=3, no_cpu_baseline=True), emit=False)
+        keep = ("ms_per_step", "value", "config", "breakdown", "estep_hbm", "vs_plain_gpu", "plain_gpu", "clocks")
+        out["batching"] = {k: b.get(k) for k in keep}
+    except Exception as e:                       # reported, never silently dropped
+        out["batching"] = dict(error=repr(e))
+    _free_gpu()
+    try:
+        p = run_precision(_sub(args, workload="precision", steps=2, warmup=1), emit=False)
+        keep = ("ms_per_step", "value", "config", "roofline", "breakdown", "fp32_path", "tensor_vs_fp32", "clocks")
+        out["precision"] = {k: p.get(k) for k in keep}
+    except Exception as e:
+        out["precision"] = dict(error=repr(e))
+    _free_gpu()
+    serving = {}
+    for name, rate, n in (("sustained", args.serve_rate, args.serve_requests),
+                          ("offered_2000_per_s", 2000.0, args.serve_requests)):
+        try:
+            r = run_serving(_sub(args, workload="serving", rate=rate, requests=n), emit=False)
+            serving[name] = {k: r.get(k) for k in ("p50_ms", "p99_ms", "mean_ms", "offered_rate", "completed_per_s",
+                                                   "makespan_s", "cell_updates_per_s", "failed", "config",
+                                                   "p99_by_kind", "clocks")}
+            serving[name]["sustained"] = r["completed_per_s"] >= 0.9 * rate
+        except Exception as e:
+            serving[name] = dict(error=repr(e))
+        _free_gpu()
+    out["serving"] = serving
+    out["extras_wall_s"] = time.perf_counter() - t0
+    return out
 
 
 if __name__ == "__main__":

@@ -334,6 +334,56 @@ hmm_status hmm_stats_get(hmm_stats stats, double* h_out, int64_t n_values);
  * library and lives as long as `stats`. */
 hmm_status hmm_stats_device_buffer(hmm_stats stats, double** d_values, int64_t* n_values);
 
+/* ---------------------------------------------- data-parallel exchange
+ * Sequences are independent in the E-step (Sec. 3), and every statistic the
+ * M-step of Sec. 4 reads is a sum over sequences (Eq. 5 and the family sums
+ * above), a minimum or maximum over rows (the uniform / Pareto supports),
+ * or, for the Newton steps that re-read the data (Weibull shape, Eq. 11;
+ * negative-binomial r), a sum over rows per Newton pass.  A data-parallel
+ * fit therefore gives each process a shard of the sequences and combines
+ * these records across processes before the M-step reads them; every
+ * process then runs the same M-step and keeps the same model.
+ *
+ * The library does not talk to other processes itself: the caller installs
+ * an all-reduce callback on the stats object, and the library calls it on
+ * its device records at the points where the M-step needs the combined
+ * values.  d_values: device memory of n elements, reduced in place; op:
+ * hmm_reduce_op (float64 sum, or int32 minimum); the reduction must be
+ * ordered on `stream` (work enqueued on it before the call is complete
+ * before the reduction reads the data, and work enqueued after the call
+ * sees the result).  Every process calls it the same number of times with
+ * the same sizes and ops.  A nonzero return makes the library call fail with
+ * HMM_E_CUDA. */
+typedef enum {
+  HMM_REDUCE_SUM_F64 = 0,  /* element-wise sum of float64 values            */
+  HMM_REDUCE_MIN_I32 = 1   /* element-wise minimum of int32 values          */
+} hmm_reduce_op;
+typedef int32_t (*hmm_allreduce_fn)(void* d_values, int64_t n, int32_t op, void* stream, void* user);
+
+/* Installs (fn != NULL) or removes (fn == NULL) the exchange of `stats`.
+ * With it, hmm_estep_stats ends by reducing each record of
+ * hmm_stats_record (index order 0, 1, 2; records of size 0 are skipped) and
+ * hmm_mstep reduces the sums of each Newton data pass before the update
+ * that reads them (float64 sums, n = n_models x padded states x 3; a fixed
+ * number of passes, the same on every process).  An empty shard (n_seq = 0)
+ * is allowed and contributes zeros / the identity of the minimum. */
+hmm_status hmm_stats_set_allreduce(hmm_stats stats, hmm_allreduce_fn fn, void* user);
+
+/* Device view of record `index` of `stats` after an E-step, and the
+ * reduction that combines it across processes:
+ *   0  the statistic record (the layout behind hmm_stats_get: counts,
+ *      log-likelihood sums, gamma_1, xi and the family sums of the first
+ *      eight families), HMM_REDUCE_SUM_F64;
+ *   1  the feature / moment sums of the table families (multivariate,
+ *      discrete, log-normal .. Pareto), HMM_REDUCE_SUM_F64; n = 0 when the
+ *      model has none;
+ *   2  the support extremes of the uniform and Pareto states, int32 keys
+ *      whose order is the order of the float32 values (the maximum stored
+ *      complemented, so that both combine with a minimum),
+ *      HMM_REDUCE_MIN_I32; n = 0 when the model has none.
+ * The memory stays owned by the library.  HMM_E_ARG for another index. */
+hmm_status hmm_stats_record(hmm_stats stats, int32_t index, void** d_values, int64_t* n_values, int32_t* op);
+
 /* E-step over a batch (Sec. 3.2 + Sec. 4, Eq. 5): fills `stats` with the
  * weighted sufficient statistics of every model and writes per-sequence
  * log-likelihoods to d_loglik [n_seq] (may be NULL).  The reductions are in

@@ -338,6 +338,8 @@ def viterbi_fp32(logpi32, logA32, logb32):
     logA32 = np.asarray(logA32, dtype=f32)
     logb32 = np.asarray(logb32, dtype=f32)
     T, N = logb32.shape
+    if T == 0:                      # an empty sequence: empty path, log 1 = 0
+        return np.zeros(0, np.int32), 0.0
     psi = np.zeros((T, N), dtype=np.int32)
     d = (logpi32 + logb32[0]).astype(f32)
     off = 0.0

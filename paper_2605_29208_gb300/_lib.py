@@ -55,6 +55,9 @@ class hmm_result(C.Structure):
 
 
 REQ_DECODE, REQ_POSTERIOR, REQ_FIT = 0, 1, 2
+REDUCE_SUM_F64, REDUCE_MIN_I32 = 0, 1
+# hmm_allreduce_fn: (d_values, n, op, stream, user) -> 0 on success
+ALLREDUCE_FN = C.CFUNCTYPE(C.c_int32, C.c_void_p, C.c_int64, C.c_int32, C.c_void_p, C.c_void_p)
 
 # name -> (restype, argtypes)
 _SIGS = {
@@ -91,6 +94,9 @@ _SIGS = {
     "hmm_stats_size": (C.c_int64, [C.c_void_p]),
     "hmm_stats_get": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64]),
     "hmm_stats_device_buffer": (C.c_int, [C.c_void_p, C.POINTER(C.c_void_p), C.POINTER(C.c_int64)]),
+    "hmm_stats_set_allreduce": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "hmm_stats_record": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_void_p), C.POINTER(C.c_int64),
+                                   C.POINTER(C.c_int32)]),
     "hmm_estep_stats": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(hmm_batch), C.c_void_p,
                                   C.c_void_p, C.c_void_p]),
     "hmm_mstep": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(hmm_batch),

@@ -35,12 +35,16 @@ __device__ __forceinline__ float ext_unkey(int k) { return __int_as_float(k >= 0
 
 __host__ __device__ inline bool ext_has_support_stats(int fam) { return fam == HMM_UNIFORM || fam == HMM_PARETO; }
 
-// mm[M][NP][2] <- (key(+inf), key(-inf))
+// Support extremes mm[M][NP][2]: slot 0 the key of the minimum, slot 1 the
+// bitwise complement of the key of the maximum (~ reverses the integer
+// order), so that both slots combine with MIN: per block, across blocks and
+// across the processes of a data-parallel E-step alike.
+// mm <- (key(+inf), ~key(-inf))
 __global__ void ext_support_init_kernel(int* __restrict__ mm, int n) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   mm[2 * i] = ext_key(INFINITY);
-  mm[2 * i + 1] = ext_key(-INFINITY);
+  mm[2 * i + 1] = ~ext_key(-INFINITY);
 }
 
 // min / max of y over the rows inside each state's current support; blocks
@@ -78,7 +82,7 @@ __global__ void ext_support_kernel(const int* __restrict__ family, const float* 
   for (int k = threadIdx.x; k < N; k += blockDim.x) {
     int* g = mm + ((size_t)m * NP + k) * 2;
     if (skey[k] != ext_key(INFINITY)) atomicMin(g, skey[k]);
-    if (skey[N + k] != ext_key(-INFINITY)) atomicMax(g + 1, skey[N + k]);
+    if (skey[N + k] != ext_key(-INFINITY)) atomicMin(g + 1, ~skey[N + k]);
   }
 }
 
@@ -128,7 +132,7 @@ __global__ void ext_mstep_kernel(const int* __restrict__ family, double* __restr
     case HMM_UNIFORM: {
       const int* g = mm + (size_t)idx * 2;
       nt[0] = (double)ext_unkey(g[0]);
-      nt[1] = (double)ext_unkey(g[1]);
+      nt[1] = (double)ext_unkey(~g[1]);
       break;
     }
     case HMM_CHISQ:                                   // digamma(nu/2) = E_w log y - log 2

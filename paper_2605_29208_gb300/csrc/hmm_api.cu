@@ -251,7 +251,7 @@ void check_batch(hmm_model model, const hmm_batch* b) {
   HMM_REQUIRE(b != nullptr, "batch is NULL");
   HMM_REQUIRE(b->n_seq >= 0 && b->total_T >= 0, "negative batch sizes");
   HMM_REQUIRE(b->n_seq < (1ll << 31) && b->total_T < (1ll << 40), "batch too large");
-  HMM_REQUIRE(b->offsets != nullptr && b->model_id != nullptr, "batch arrays are NULL");
+  HMM_REQUIRE(b->offsets != nullptr && (b->n_seq == 0 || b->model_id != nullptr), "batch arrays are NULL");
   HMM_REQUIRE(b->total_T == 0 || b->values != nullptr, "batch values are NULL");
   HMM_REQUIRE(b->dim == model->D, "batch dim does not match the model");
 }
@@ -933,12 +933,61 @@ MStepOpts to_opts(const hmm_mstep_opts* o) {
 }
 
 // Buffers of the data-pass M-step (allocated before any graph capture).
+// The caller's all-reduce on one device record (no-op without one).
+void call_reduce(hmm_stats stats, void* p, int64_t n, int op, cudaStream_t st) {
+  if (!stats->reduce_fn || n <= 0) return;
+  const int32_t rc = stats->reduce_fn(p, n, op, reinterpret_cast<void*>(st), stats->reduce_user);
+  if (rc != 0) throw Error{HMM_E_CUDA, "the all-reduce callback failed with code " + std::to_string(rc)};
+}
+
+// Record `index` of hmm_stats_record.
+void record_view(hmm_stats stats, int index, void** p, int64_t* n, int* op) {
+  hmm_model model = stats->model;
+  const int64_t MNP = (int64_t)model->M * model->NP;
+  switch (index) {
+    case 0:
+      *p = stats->rec.p;
+      *n = (int64_t)model->M * rec_size(model->NP);
+      *op = HMM_REDUCE_SUM_F64;
+      return;
+    case 1:
+      *p = stats->mv_rec.p;
+      *n = model->table_family() && stats->mv_rec.p ? MNP * model->KS : 0;
+      *op = HMM_REDUCE_SUM_F64;
+      return;
+    case 2:
+      *p = stats->ext_mm.p;
+      *n = model->any_support && stats->ext_mm.p ? MNP * 2 : 0;
+      *op = HMM_REDUCE_MIN_I32;
+      return;
+    default: throw Error{HMM_E_ARG, "record index must be 0, 1 or 2"};
+  }
+}
+
+// Statistics of an empty shard: zero sums, the identity of the support
+// minimum; valid for an M-step once combined with the other shards.
+void zero_stats(hmm_model model, hmm_stats stats, cudaStream_t st) {
+  const size_t MNP = (size_t)model->M * model->NP;
+  HMM_CUDA(cudaMemsetAsync(stats->rec.p, 0, (size_t)model->M * rec_size(model->NP) * 8, st));
+  if (model->table_family()) {
+    stats->mv_rec.ensure(MNP * model->KS * 8);
+    HMM_CUDA(cudaMemsetAsync(stats->mv_rec.p, 0, MNP * model->KS * 8, st));
+  }
+  if (model->any_support) {
+    stats->ext_mm.ensure(MNP * 2 * 4);
+    ext_support_init_kernel<<<(unsigned)((MNP + 127) / 128), 128, 0, st>>>(stats->ext_mm.as<int>(), (int)MNP);
+    HMM_CUDA(cudaGetLastError());
+  }
+  stats->valid = true;
+  stats->gamma_T = 0;
+}
+
 void prepare_mstep(hmm_model model, hmm_stats stats, const hmm_batch* b, hmm_plan plan) {
-  if (!(model->any_negbin || model->any_weibull) || !b || !plan) return;
+  if (!(model->any_negbin || model->any_weibull) || !b || (!plan && b->n_seq > 0)) return;
   const int RS = model->NP * 3;
   stats->dps.ensure((size_t)model->M * model->NP * sizeof(DPState));
   stats->dp_part.ensure((size_t)std::max<int64_t>(b->n_seq, 1) * RS * 4);
-  stats->dp_chunk.ensure((size_t)std::max(plan->n_chunks, 1) * RS * 8);
+  stats->dp_chunk.ensure((size_t)std::max(plan ? plan->n_chunks : 0, 1) * RS * 8);
   stats->dp_rec.ensure((size_t)model->M * RS * 8);
   if (model->any_negbin) stats->nb_d.ensure((size_t)model->M * model->NP * 2 * NB_YMAX * 4);
   stats->dp_count.ensure(64 * sizeof(int));
@@ -952,7 +1001,8 @@ void run_mstep(hmm_ctx ctx, hmm_model model, hmm_stats stats, const MStepOpts& o
     throw Error{HMM_E_UNSUPPORTED, "Weibull / negative-binomial M-steps support padded N <= 32"};
   DPState* dps = nullptr;
   if (dpass) {
-    HMM_REQUIRE(b != nullptr && plan != nullptr, "Weibull / negative-binomial M-steps need the batch");
+    HMM_REQUIRE(b != nullptr && (plan != nullptr || b->n_seq == 0),
+                "Weibull / negative-binomial M-steps need the batch");
     HMM_REQUIRE(stats->gamma_T == b->total_T, "the statistics were not made from this batch");
     stats->dps.ensure((size_t)model->M * model->NP * sizeof(DPState));
     dps = stats->dps.as<DPState>();
@@ -993,19 +1043,20 @@ void run_mstep(hmm_ctx ctx, hmm_model model, hmm_stats stats, const MStepOpts& o
       HMM_CUDA(cudaGetLastError());
     }
   }
-  if (!dpass || b->n_seq == 0) return;
+  // an empty shard runs the passes only to take part in the exchange
+  if (!dpass || (b->n_seq == 0 && !stats->reduce_fn)) return;
   // Newton steps that re-read the data: a fixed number of passes
   // (converged states skip their work), then the Weibull scale pass
   const int NP = model->NP, RS = NP * 3;
   const int64_t S = b->n_seq;
-  stats->dp_part.ensure((size_t)S * RS * 4);
-  stats->dp_chunk.ensure((size_t)std::max(plan->n_chunks, 1) * RS * 8);
+  stats->dp_part.ensure((size_t)std::max<int64_t>(S, 1) * RS * 4);
+  stats->dp_chunk.ensure((size_t)std::max(plan ? plan->n_chunks : 0, 1) * RS * 8);
   stats->dp_rec.ensure((size_t)model->M * RS * 8);
   const int passes = std::min(o.newton_maxit, 24);   // + one final pass
   const unsigned blocks = (unsigned)((S * 32 + 255) / 256);
   const int nthr = model->M * NP;
   KTimer kt(ctx, HMM_KT_MSTEP, st);
-  kt.kernels = 2 + (passes + 1) * ((int)model->any_negbin + 3 + (plan->n_chunks > 0));
+  kt.kernels = 2 + (passes + 1) * ((int)model->any_negbin + (S > 0 ? 3 + (plan->n_chunks > 0) : 1));
   prepare_mstep(model, stats, b, plan);
   // active-state counters, one per pass (the update of pass p fills p + 1);
   // passes with no active state return at once
@@ -1018,19 +1069,26 @@ void run_mstep(hmm_ctx ctx, hmm_model model, hmm_stats stats, const MStepOpts& o
       nb_table_kernel<<<(nthr + 127) / 128, 128, 0, st>>>(model->bufs(), dps, cnt + it, stats->nb_d.as<float>());
       HMM_CUDA(cudaGetLastError());
     }
-    dp_sums_kernel<<<blocks, 256, 0, st>>>(model->bufs(), b->values, stats->gamma.as<float>(), b->offsets,
-                                           b->model_id, (int)S, dps, stats->nb_d.as<float>(), cnt + it,
-                                           stats->dp_part.as<float>());
-    HMM_CUDA(cudaGetLastError());
-    if (plan->n_chunks > 0) {
-      reduce_records_l1<<<plan->n_chunks, 128, 0, st>>>(stats->dp_part.as<float>(), RS,
-                                                      plan->seq_by_model.as<int32_t>(), plan->chunk_lo.as<int32_t>(),
-                                                      plan->chunk_hi.as<int32_t>(), stats->dp_chunk.as<double>());
+    if (S > 0) {
+      dp_sums_kernel<<<blocks, 256, 0, st>>>(model->bufs(), b->values, stats->gamma.as<float>(), b->offsets,
+                                             b->model_id, (int)S, dps, stats->nb_d.as<float>(), cnt + it,
+                                             stats->dp_part.as<float>());
       HMM_CUDA(cudaGetLastError());
+      if (plan->n_chunks > 0) {
+        reduce_records_l1<<<plan->n_chunks, 128, 0, st>>>(stats->dp_part.as<float>(), RS,
+                                                        plan->seq_by_model.as<int32_t>(),
+                                                        plan->chunk_lo.as<int32_t>(), plan->chunk_hi.as<int32_t>(),
+                                                        stats->dp_chunk.as<double>());
+        HMM_CUDA(cudaGetLastError());
+      }
+      reduce_chunks_l2<<<model->M, 128, 0, st>>>(stats->dp_chunk.as<double>(), plan->model_chunk_ptr.as<int32_t>(),
+                                                 RS, stats->dp_rec.as<double>());
+      HMM_CUDA(cudaGetLastError());
+    } else {
+      HMM_CUDA(cudaMemsetAsync(stats->dp_rec.p, 0, (size_t)model->M * RS * 8, st));
     }
-    reduce_chunks_l2<<<model->M, 128, 0, st>>>(stats->dp_chunk.as<double>(), plan->model_chunk_ptr.as<int32_t>(), RS,
-                                               stats->dp_rec.as<double>());
-    HMM_CUDA(cudaGetLastError());
+    // this pass's sums over all processes' data before the update reads them
+    call_reduce(stats, stats->dp_rec.p, (int64_t)model->M * RS, HMM_REDUCE_SUM_F64, st);
     dp_update_kernel<<<(nthr + 127) / 128, 128, 0, st>>>(model->bufs(), stats->dp_rec.as<double>(), dps, o,
                                                          it == passes ? 1 : 0, cnt + it, cnt + it + 1);
     HMM_CUDA(cudaGetLastError());
@@ -1821,7 +1879,7 @@ hmm_status hmm_stats_get(hmm_stats stats, double* h_out, int64_t n_values) {
             if (fam == HMM_UNIFORM || fam == HMM_PARETO) {
               const int* g = emm.data() + ((size_t)m * NP + j) * 2;
               q[nf] = ext_unkey_host(g[0]);
-              if (fam == HMM_UNIFORM) q[nf + 1] = ext_unkey_host(g[1]);
+              if (fam == HMM_UNIFORM) q[nf + 1] = ext_unkey_host(~g[1]);
             }
             break;
           }
@@ -1864,16 +1922,44 @@ hmm_status hmm_stats_device_buffer(hmm_stats stats, double** d_values, int64_t* 
   });
 }
 
+hmm_status hmm_stats_set_allreduce(hmm_stats stats, hmm_allreduce_fn fn, void* user) {
+  return guarded([&] {
+    HMM_REQUIRE(stats != nullptr, "stats is NULL");
+    stats->reduce_fn = fn;
+    stats->reduce_user = fn ? user : nullptr;
+  });
+}
+
+hmm_status hmm_stats_record(hmm_stats stats, int32_t index, void** d_values, int64_t* n_values, int32_t* op) {
+  return guarded([&] {
+    HMM_REQUIRE(stats && d_values && n_values && op, "NULL argument");
+    int o = 0;
+    record_view(stats, index, d_values, n_values, &o);
+    *op = o;
+  });
+}
+
 hmm_status hmm_estep_stats(hmm_ctx ctx, hmm_model model, const hmm_batch* batch, hmm_stats stats,
                            double* d_loglik, void* stream) {
   return guarded([&] {
     HMM_REQUIRE(ctx && model && stats, "NULL argument");
     HMM_REQUIRE(stats->model == model, "stats belong to another model");
     check_batch(model, batch);
-    PlanRef pr;
-    get_plan(ctx, model, batch, S(stream), pr);
-    run_estep(ctx, model, batch, pr.p, nullptr, nullptr, d_loglik, true, stats, S(stream));
-    if (pr.owned) HMM_CUDA(cudaStreamSynchronize(S(stream)));
+    if (batch->n_seq == 0) {
+      zero_stats(model, stats, S(stream));
+    } else {
+      PlanRef pr;
+      get_plan(ctx, model, batch, S(stream), pr);
+      run_estep(ctx, model, batch, pr.p, nullptr, nullptr, d_loglik, true, stats, S(stream));
+      if (pr.owned) HMM_CUDA(cudaStreamSynchronize(S(stream)));
+    }
+    for (int i = 0; i < 3; ++i) {   // combine the shards' records
+      void* p = nullptr;
+      int64_t n = 0;
+      int op = 0;
+      record_view(stats, i, &p, &n, &op);
+      call_reduce(stats, p, n, op, S(stream));
+    }
   });
 }
 
@@ -1886,7 +1972,7 @@ hmm_status hmm_mstep(hmm_ctx ctx, hmm_model model, hmm_stats stats, const hmm_ba
     PlanRef pr;
     if (batch && (model->any_negbin || model->any_weibull)) {
       check_batch(model, batch);
-      get_plan(ctx, model, batch, S(stream), pr);
+      if (batch->n_seq > 0) get_plan(ctx, model, batch, S(stream), pr);
     }
     run_mstep(ctx, model, stats, to_opts(opts), batch, pr.p, S(stream));
     if (pr.owned) HMM_CUDA(cudaStreamSynchronize(S(stream)));

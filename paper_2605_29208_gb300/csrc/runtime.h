@@ -165,6 +165,9 @@ struct hmm_stats_s {
   hmm::DevBuf mv_chunk;          // [n_chunks][NP*KS] float64
   hmm::DevBuf mv_rec;            // [M][NP*KS] float64
   hmm::DevBuf ext_mm;            // [M][NP][2] int32 ordered keys of the support min / max
+  // cross-process exchange (hmm_stats_set_allreduce)
+  hmm_allreduce_fn reduce_fn = nullptr;
+  void* reduce_user = nullptr;
 };
 
 struct hmm_plan_s {

@@ -44,8 +44,9 @@ __device__ __forceinline__ uint64_t mbar_expect_tx(uint64_t* b, uint32_t bytes) 
                : "memory");
   return st;
 }
-// Bounded wait for the phase with the given parity; false on expiry.
-__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity) {
+// Bounded wait for the phase with the given parity; false once `limit` SM
+// clock cycles have passed without it.
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, long long limit = TC_WAIT_CYCLES) {
   const uint32_t addr = smem_u32(b);
   const long long t0 = clock64();
   for (;;) {
@@ -56,7 +57,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity) {
         : "r"(addr), "r"(parity)
         : "memory");
     if (ok) return true;
-    if (clock64() - t0 > TC_WAIT_CYCLES) return false;
+    if (clock64() - t0 > limit) return false;
   }
 }
 // K-major operand with 128-byte swizzle: 8-row groups 1024 bytes apart.

@@ -206,8 +206,9 @@ def test_viterbi_fp32_mitm_tie_rule_hand_example():
 def test_viterbi_fp32_mitm_special_cases():
     rng = np.random.default_rng(5)
     # T = 0 and T = 1
-    q, s = O.viterbi_fp32_mitm(np.zeros(3, np.float32), np.zeros((3, 3), np.float32), np.zeros((0, 3), np.float32))
-    assert len(q) == 0 and s == 0.0
+    for fn in (O.viterbi_fp32_mitm, O.viterbi_fp32):
+        q, s = fn(np.zeros(3, np.float32), np.zeros((3, 3), np.float32), np.zeros((0, 3), np.float32))
+        assert len(q) == 0 and s == 0.0
     lpi, lA, lb = grid_hmm(rng, 3, 1)
     q, s = O.viterbi_fp32_mitm(lpi, lA, lb)
     assert q[0] == int(np.argmax(lpi + lb[0])) and s == float((lpi + lb[0]).max())
