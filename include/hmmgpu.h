@@ -207,6 +207,18 @@ hmm_status hmm_ctx_destroy(hmm_ctx ctx);
  * kernel since the last call); synchronises `stream`, then clears it. */
 hmm_status hmm_ctx_status(hmm_ctx ctx, void* stream);
 
+/* Failure-detection self-test of the bounded device waits (the paper has no
+ * counterpart; it checks the library's own error path).  Every mbarrier wait
+ * of the tensor-core kernels gives up after a cycle limit and records
+ * HMM_E_TIMEOUT in the context's sticky status instead of hanging the GPU.
+ * This call launches one thread that waits, with that same bounded wait, on
+ * an mbarrier phase nothing ever completes, with a limit of limit_cycles SM
+ * clock cycles (1 .. the library's own limit, about 4e9), then returns;
+ * hmm_ctx_status afterwards reports HMM_E_TIMEOUT and the context stays
+ * usable.  h_waited (may be NULL; then the call does not synchronise)
+ * receives the cycles the wait took.  HMM_E_ARG for a limit out of range. */
+hmm_status hmm_ctx_wait_selftest(hmm_ctx ctx, int64_t limit_cycles, int64_t* h_waited, void* stream);
+
 /* Sets a context option (hmm_option); unknown keys give HMM_E_ARG. */
 hmm_status hmm_ctx_set_option(hmm_ctx ctx, int32_t key, int64_t value);
 /* Accumulated device milliseconds and launch counts per timing slot

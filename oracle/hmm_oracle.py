@@ -60,7 +60,8 @@ KAPPA_MAX = 1e6              # reading: R -> 1 gives kappa -> inf
 
 FAMILIES = ("gauss", "poisson", "gamma", "beta", "weibull", "negbin",
             "student_t", "vonmises", "diag_gauss", "full_gauss", "discrete",
-            "lognormal", "exponential", "rayleigh", "uniform", "chisq", "pareto")
+            "lognormal", "exponential", "rayleigh", "uniform", "chisq", "pareto",
+            "indep")
 
 
 @dataclass
@@ -71,6 +72,9 @@ class Model:
     pi: np.ndarray            # [N]
     A: np.ndarray             # [N, N] row-stochastic
     params: dict = field(default_factory=dict)
+    # family "indep" (Sec. 4.5, independent components): the scalar family
+    # of each observation dimension; parameters are named "d<k>.<name>"
+    components: tuple = ()
 
     @property
     def n_states(self) -> int:
@@ -79,7 +83,15 @@ class Model:
     def copy(self) -> "Model":
         return Model(self.family, self.pi.copy(), self.A.copy(),
                      {k: np.array(v, dtype=np.float64, copy=True)
-                      for k, v in self.params.items()})
+                      for k, v in self.params.items()}, tuple(self.components))
+
+
+def component_model(model: Model, d: int) -> Model:
+    """The scalar model of dimension d of an independent-components model
+    (same pi and A; the parameters of component d)."""
+    pre = f"d{d}."
+    return Model(model.components[d], model.pi, model.A,
+                 {k[len(pre):]: v for k, v in model.params.items() if k.startswith(pre)})
 
 
 # --------------------------------------------------------------------------
@@ -110,6 +122,9 @@ def emission_logpdf(model: Model, y: np.ndarray) -> np.ndarray:
     """
     f, p = model.family, model.params
     y = np.asarray(y, dtype=np.float64)
+    if f == "indep":            # Sec. 4.5: b_j(y) = prod_d phi_d(y_d)
+        y = y.reshape(len(y), -1)
+        return sum(emission_logpdf(component_model(model, d), y[:, d]) for d in range(len(model.components)))
     with np.errstate(divide="ignore", invalid="ignore"):
         if f == "gauss":        # Sec. 4.1, N(mu, sigma^2)
             mu, s2 = p["mu"], p["sigma2"]
@@ -790,6 +805,26 @@ def mstep_emission(model: Model, W: np.ndarray, y: np.ndarray, nu_mode="ecm"):
     W: [T_total, N] occupancies, y: observations of the same rows."""
     new = model.copy()
     iters = np.zeros(model.n_states, dtype=np.int64)
+    if model.family == "indep":
+        # Sec. 4.5: each component's scalar M-step with the same weights;
+        # rows of zero weight (outside some component's support) add nothing
+        y = np.asarray(y, dtype=np.float64).reshape(len(W), -1)
+        for j in range(model.n_states):
+            w = W[:, j]
+            if w.sum() < COLLAPSE_EPS:          # Sec. 4.4: keep theta_j
+                continue
+            rows = w > 0
+            for d, fam in enumerate(model.components):
+                cm = component_model(model, d)
+                kw = dict(nu_mode=nu_mode) if fam == "student_t" else {}
+                with np.errstate(all="ignore"):
+                    res = MSTEP[fam](w[rows], y[rows, d], _state_params(cm, j), **kw)
+                iters[j] += res.pop("_iters", 0)
+                if not valid_update(fam, res):   # undefined update keeps the component
+                    continue
+                for k, v in res.items():
+                    new.params[f"d{d}.{k}"][j] = v
+        return new, iters
     for j in range(model.n_states):
         w = W[:, j]
         if w.sum() < COLLAPSE_EPS:              # Sec. 4.4: keep theta_j

@@ -71,6 +71,7 @@ _SIGS = {
     "hmm_ctx_destroy": (C.c_int, [C.c_void_p]),
     "hmm_ctx_status": (C.c_int, [C.c_void_p, C.c_void_p]),
     "hmm_ctx_set_option": (C.c_int, [C.c_void_p, C.c_int32, C.c_int64]),
+    "hmm_ctx_wait_selftest": (C.c_int, [C.c_void_p, C.c_int64, C.POINTER(C.c_int64), C.c_void_p]),
     "hmm_ctx_profile_read": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_int32]),
     "hmm_model_create": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_int32, C.c_void_p,
                                    C.POINTER(C.c_void_p)]),
