@@ -92,7 +92,8 @@ typedef enum {
   HMM_GAUSS = 0, HMM_POISSON = 1, HMM_GAMMA = 2, HMM_BETA = 3, HMM_WEIBULL = 4,
   HMM_NEGBIN = 5, HMM_STUDENT_T = 6, HMM_VONMISES = 7, HMM_DIAG_GAUSS = 8,
   HMM_FULL_GAUSS = 9, HMM_DISCRETE = 10, HMM_LOGNORMAL = 11, HMM_EXPONENTIAL = 12,
-  HMM_RAYLEIGH = 13, HMM_UNIFORM = 14, HMM_CHISQ = 15, HMM_PARETO = 16
+  HMM_RAYLEIGH = 13, HMM_UNIFORM = 14, HMM_CHISQ = 15, HMM_PARETO = 16,
+  HMM_INDEP = 17          /* independent components: see hmm_model_create_indep */
 } hmm_family;
 
 typedef struct hmm_ctx_s* hmm_ctx;       /* device + workspace            */
@@ -234,6 +235,27 @@ hmm_status hmm_ctx_profile_read(hmm_ctx ctx, double* h_ms, int64_t* h_launches,
  * dim >= 1, scalar families dim == 1.  State counts up to 1024. */
 hmm_status hmm_model_create(hmm_ctx ctx, int32_t n_models, int32_t n_states,
                             int32_t dim, const int32_t* h_family, hmm_model* out);
+/* Independent-components models (paper Sec. 4.5, "Independent
+ * components"): every state of model m emits y_t in R^dim with density
+ * b_j(y_t) = prod_d phi_{m,d,j}(y_td), where component d of model m is the
+ * scalar family h_comp[m * dim + d] with its own parameters per state, and
+ * the M-step runs each component's scalar update with the same occupancy
+ * weights gamma_t(j).  Component families: HMM_GAUSS, HMM_POISSON,
+ * HMM_GAMMA, HMM_BETA, HMM_STUDENT_T, HMM_VONMISES, HMM_LOGNORMAL,
+ * HMM_EXPONENTIAL, HMM_RAYLEIGH, HMM_CHISQ (others: HMM_E_UNSUPPORTED);
+ * 1 <= dim <= 32; state counts up to 1024.  Batches have dim = `dim`
+ * (values [total_T][dim]).  Parameter blob per model: pi[N], A[N][N], then
+ * per state j the parameters of component 0, component 1, ... in the order
+ * of hmm_family (hmm_model_blob_size gives the total).  Statistics
+ * (hmm_stats_get) per state j of an independent-components model: W, then
+ * per component its sums (weights gamma_t(j)): GAUSS Wy, Wy^2; POISSON Wy;
+ * GAMMA Wy, W log y, Wy^2; BETA Wy, Wy^2, W log y, W log(1-y); STUDENT_T
+ * Wu, Wuy, Wuy^2, W(log u - u); VONMISES W cos y, W sin y; LOGNORMAL
+ * W log y, W (log y)^2; EXPONENTIAL Wy; RAYLEIGH Wy^2; CHISQ W log y. */
+hmm_status hmm_model_create_indep(hmm_ctx ctx, int32_t n_models, int32_t n_states, int32_t dim,
+                                  const int32_t* h_comp, hmm_model* out);
+/* Number of float64 values of `model`'s parameter blob (any family). */
+int64_t hmm_model_blob_size(hmm_model model);
 hmm_status hmm_model_destroy(hmm_model model);
 /* Copies the float64 parameter blob (layout above, n_values entries) to the
  * device and refreshes the derived single-precision tables. */

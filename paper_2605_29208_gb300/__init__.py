@@ -62,25 +62,37 @@ PARAM_ORDER = {
 }
 
 
+def _state_names(model: dict) -> list[str]:
+    """Parameter names of one state in blob order (independent components:
+    "d<k>.<name>" for every component k in order)."""
+    if model["family"] == "indep":
+        return [f"d{d}.{n}" for d, f in enumerate(model["components"]) for n in PARAM_ORDER[f]]
+    return list(PARAM_ORDER[model["family"]])
+
+
 def blob_from_model(model: dict) -> np.ndarray:
     """Flattens a model dict {family, pi, A, params} into the C-ABI blob
     (pi, A, then per state its family parameters)."""
     N = len(model["pi"])
     parts = [np.asarray(model["pi"], np.float64).ravel(), np.asarray(model["A"], np.float64).ravel()]
-    fam = model["family"]
     per_state = []
     for j in range(N):
-        for name in PARAM_ORDER[fam]:
+        for name in _state_names(model):
             per_state.append(np.asarray(model["params"][name][j], np.float64).ravel())
     parts.extend(per_state)
     return np.concatenate(parts)
 
 
-def model_from_blob(blob: np.ndarray, family: str, N: int, D: int = 1) -> tuple[dict, int]:
+def model_from_blob(blob: np.ndarray, family: str, N: int, D: int = 1, components=None) -> tuple[dict, int]:
     """Inverse of blob_from_model; returns (model, values consumed)."""
     q = 0
     pi = blob[q:q + N].copy(); q += N
     A = blob[q:q + N * N].reshape(N, N).copy(); q += N * N
+    if family == "indep":
+        names = _state_names(dict(family="indep", components=components))
+        vals = blob[q:q + N * len(names)].reshape(N, len(names)); q += N * len(names)
+        return dict(family="indep", components=list(components), pi=pi, A=A,
+                    params={n: vals[:, i].copy() for i, n in enumerate(names)}), q
     names = PARAM_ORDER[family]
     sizes = {"mu": D if family in ("diag_gauss", "full_gauss") else 1,
              "var": D, "cov": D * D, "p": D}
@@ -137,16 +149,24 @@ class Model:
     def __init__(self, ctx: Context, models: list[dict]):
         self.ctx, self.lib = ctx, ctx.lib
         self.families = [m["family"] for m in models]
+        self.components = [list(m.get("components", ())) for m in models]
         self.N = len(models[0]["pi"])
         mu = models[0]["params"].get("mu")
         if self.families[0] == "discrete":        # dim = number of symbols
             self.D = int(np.asarray(models[0]["params"]["p"]).shape[1])
+        elif self.families[0] == "indep":         # dim = number of components
+            self.D = len(self.components[0])
         else:
             self.D = (np.asarray(mu).shape[1] if self.families[0] in ("diag_gauss", "full_gauss") else 1)
         fam = np.array([FAMILY[f] for f in self.families], np.int32)
         h = C.c_void_p()
-        check(self.lib.hmm_model_create(ctx.h, len(models), self.N, self.D,
-                                        fam.ctypes.data_as(C.c_void_p), C.byref(h)))
+        if self.families[0] == "indep":
+            comp = np.array([[FAMILY[f] for f in c] for c in self.components], np.int32)
+            check(self.lib.hmm_model_create_indep(ctx.h, len(models), self.N, self.D,
+                                                  comp.ctypes.data_as(C.c_void_p), C.byref(h)))
+        else:
+            check(self.lib.hmm_model_create(ctx.h, len(models), self.N, self.D,
+                                            fam.ctypes.data_as(C.c_void_p), C.byref(h)))
         self.h = h
         self._fam = fam
         self.set(models)
@@ -156,8 +176,7 @@ class Model:
         return len(self.families)
 
     def blob_size(self):
-        return self.lib.hmm_param_blob_size(self.n_models, self.N, self.D,
-                                            self._fam.ctypes.data_as(C.c_void_p))
+        return self.lib.hmm_model_blob_size(self.h)
 
     def set(self, models: list[dict]):
         blob = np.concatenate([blob_from_model(m) for m in models])
@@ -168,8 +187,8 @@ class Model:
         blob = np.empty(n, np.float64)
         check(self.lib.hmm_model_get_params(self.h, blob.ctypes.data_as(C.c_void_p), n))
         out, q = [], 0
-        for f in self.families:
-            m, used = model_from_blob(blob[q:], f, self.N, self.D)
+        for f, comp in zip(self.families, self.components):
+            m, used = model_from_blob(blob[q:], f, self.N, self.D, comp)
             out.append(m)
             q += used
         return out

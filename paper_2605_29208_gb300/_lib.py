@@ -17,7 +17,8 @@ KT_SLOTS = ("estep", "reduce", "mstep", "viterbi", "emission", "plain", "slot6",
 
 FAMILY = {"gauss": 0, "poisson": 1, "gamma": 2, "beta": 3, "weibull": 4, "negbin": 5,
           "student_t": 6, "vonmises": 7, "diag_gauss": 8, "full_gauss": 9, "discrete": 10,
-          "lognormal": 11, "exponential": 12, "rayleigh": 13, "uniform": 14, "chisq": 15, "pareto": 16}
+          "lognormal": 11, "exponential": 12, "rayleigh": 13, "uniform": 14, "chisq": 15, "pareto": 16,
+          "indep": 17}
 
 
 class hmm_batch(C.Structure):
@@ -75,6 +76,9 @@ _SIGS = {
     "hmm_ctx_profile_read": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_int32]),
     "hmm_model_create": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_int32, C.c_void_p,
                                    C.POINTER(C.c_void_p)]),
+    "hmm_model_create_indep": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_int32, C.c_void_p,
+                                         C.POINTER(C.c_void_p)]),
+    "hmm_model_blob_size": (C.c_int64, [C.c_void_p]),
     "hmm_model_destroy": (C.c_int, [C.c_void_p]),
     "hmm_model_set_params": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64]),
     "hmm_model_get_params": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64]),

@@ -11,6 +11,7 @@
 #include "mstep.cuh"
 #include "mv.cuh"
 #include "ext.cuh"
+#include "indep.cuh"
 #include "plain.cuh"
 #include "runtime.h"
 
@@ -74,6 +75,34 @@ static int param_count(int fam, int D) {
 }
 
 static cudaStream_t S(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+// Parameters per state of model m (any family, independent components too).
+static int model_param_count(hmm_model model, int m) {
+  if (model->h_family[m] != HMM_INDEP) return param_count(model->h_family[m], model->dim_arg);
+  int pc = 0;
+  for (int d = 0; d < model->D; ++d) pc += indep_param_count(model->h_icomp[(size_t)m * model->D + d]);
+  return pc;
+}
+
+static int64_t model_blob_size(hmm_model model) {
+  int64_t tot = 0;
+  const int64_t N = model->N;
+  for (int m = 0; m < model->M; ++m) tot += N + N * N + N * model_param_count(model, m);
+  return tot;
+}
+
+// Domain of one scalar family's parameters q (hmm_model_set_params).
+static void check_scalar_params(int fam, const double* q) {
+  switch (fam) {
+    case HMM_LOGNORMAL: HMM_REQUIRE(q[1] > 0.0, "log-normal sigma2 must be > 0"); break;
+    case HMM_EXPONENTIAL: HMM_REQUIRE(q[0] > 0.0, "exponential rate must be > 0"); break;
+    case HMM_RAYLEIGH: HMM_REQUIRE(q[0] > 0.0, "Rayleigh sigma2 must be > 0"); break;
+    case HMM_UNIFORM: HMM_REQUIRE(q[0] < q[1], "uniform bounds need a < b"); break;
+    case HMM_CHISQ: HMM_REQUIRE(q[0] > 0.0, "chi-squared nu must be > 0"); break;
+    case HMM_PARETO: HMM_REQUIRE(q[0] > 0.0 && q[1] > 0.0, "Pareto xm and alpha must be > 0"); break;
+    default: break;
+  }
+}
 
 // Records a pair of CUDA events around the launches made in its scope when
 // the context's profiling option is on (not inside a graph capture).
@@ -554,9 +583,20 @@ void launch_mv_emission(hmm_model model, const hmm_batch* b, hmm_plan plan, floa
 // log b table of the batch in the context's buffer: multivariate families
 // (Sec. 4.5) one block per 32-row tile of a sequence, scalar families one
 // block per sequence.
+void launch_indep_emission(hmm_model model, const hmm_batch* b, hmm_plan plan, float* out, cudaStream_t st) {
+  if (b->n_seq == 0) return;
+  indep_emission_kernel<<<dim3((unsigned)b->n_seq, slabs_of(plan->max_T)), 128, 0, st>>>(
+      model->icomp.as<int>(), model->icoef.as<float>(), model->NP, model->N, model->D, model->lfact2.as<float>(),
+      b->values, b->offsets, b->model_id, out);
+  HMM_CUDA(cudaGetLastError());
+}
+
 const float* mv_table(hmm_ctx ctx, hmm_model model, const hmm_batch* b, hmm_plan plan, cudaStream_t st) {
   ctx->mvlogb.ensure(std::max<int64_t>(b->total_T, 1) * model->N * 4);
-  if (model->any_discrete) {
+  if (model->any_indep) {
+    KTimer kt(ctx, HMM_KT_EMISSION, st);
+    launch_indep_emission(model, b, plan, ctx->mvlogb.as<float>(), st);
+  } else if (model->any_discrete) {
     if (b->n_seq > 0) {
       KTimer kt(ctx, HMM_KT_EMISSION, st);
       discrete_emission_kernel<<<dim3((unsigned)b->n_seq, slabs_of(plan->max_T)), 128, 0, st>>>(
@@ -584,6 +624,31 @@ int mv_statistics(hmm_ctx ctx, hmm_model model, const hmm_batch* b, hmm_plan pla
                   cudaStream_t st) {
   const int NP = model->NP, KS = model->KS, RS = NP * KS;
   const int64_t S = b->n_seq;
+  if (model->any_indep) {   // per-component weighted sums, fixed-order reductions
+    stats->mv_part.ensure((size_t)std::max<int64_t>(S, 1) * RS * 4);
+    stats->mv_chunk.ensure((size_t)std::max(plan->n_chunks, 1) * RS * 8);
+    stats->mv_rec.ensure((size_t)model->M * RS * 8);
+    int nk = 1;
+    if (S > 0) {
+      indep_stats_kernel<<<(unsigned)S, 256, 0, st>>>(model->icomp.as<int>(), model->ishift.as<float>(),
+                                                      model->theta.as<double>(), NP, model->N, model->D, model->P, KS,
+                                                      b->values, stats->gamma.as<float>(), b->offsets, b->model_id,
+                                                      stats->mv_part.as<float>());
+      HMM_CUDA(cudaGetLastError());
+      ++nk;
+    }
+    if (plan->n_chunks > 0) {
+      reduce_records_l1<<<plan->n_chunks, 128, 0, st>>>(stats->mv_part.as<float>(), RS,
+                                                      plan->seq_by_model.as<int32_t>(), plan->chunk_lo.as<int32_t>(),
+                                                      plan->chunk_hi.as<int32_t>(), stats->mv_chunk.as<double>());
+      HMM_CUDA(cudaGetLastError());
+      ++nk;
+    }
+    reduce_chunks_l2<<<model->M, 128, 0, st>>>(stats->mv_chunk.as<double>(), plan->model_chunk_ptr.as<int32_t>(), RS,
+                                               stats->mv_rec.as<double>());
+    HMM_CUDA(cudaGetLastError());
+    return nk;
+  }
   const bool raw = model->any_discrete || model->any_ext;   // feature sums, no shift
   // few raw features at small N: per-sequence sums (feat_stats_kernel)
   const bool raw_small = raw && NP <= 32 && KS <= FEAT_SMALL_MAX;
@@ -1009,7 +1074,16 @@ void run_mstep(hmm_ctx ctx, hmm_model model, hmm_stats stats, const MStepOpts& o
   }
   {
     KTimer kt(ctx, HMM_KT_MSTEP, st);
-    kt.kernels = 1 + 2 * (int)model->any_discrete + 2 * (int)model->any_mv + (int)model->any_ext;
+    kt.kernels = 1 + 2 * (int)model->any_discrete + 2 * (int)model->any_mv + (int)model->any_ext +
+                 2 * (int)model->any_indep;
+    if (model->any_indep) {   // Sec. 4.5: every component's scalar update with the state's weights
+      const int n = model->M * model->NP * model->D;
+      indep_mstep_kernel<<<(n + 127) / 128, 128, 0, st>>>(model->icomp.as<int>(), model->ishift.as<float>(),
+                                                          model->theta.as<double>(), stats->mv_rec.as<double>(),
+                                                          model->M, model->NP, model->N, model->P, model->D,
+                                                          model->KS, o);
+      HMM_CUDA(cudaGetLastError());
+    }
     if (model->any_ext) {   // Sec. 4 / 4.2 closed forms and the chi-squared Newton; derived below
       const int n = model->M * model->NP;
       if (model->any_support) HMM_REQUIRE(stats->ext_mm.p != nullptr, "support statistics were never computed");
@@ -1020,6 +1094,13 @@ void run_mstep(hmm_ctx ctx, hmm_model model, hmm_stats stats, const MStepOpts& o
     }
     mstep_kernel<<<model->M, model->NP, 0, st>>>(model->bufs(), stats->rec.as<double>(), o, dps);
     HMM_CUDA(cudaGetLastError());
+    if (model->any_indep) {
+      const int n = model->M * model->NP * model->D;
+      indep_derive_kernel<<<(n + 127) / 128, 128, 0, st>>>(model->icomp.as<int>(), model->theta.as<double>(),
+                                                           model->M, model->NP, model->N, model->P, model->D,
+                                                           model->icoef.as<float>(), model->ishift.as<float>());
+      HMM_CUDA(cudaGetLastError());
+    }
     if (model->any_discrete) {   // Sec. 4.1 "Discrete": weighted symbol frequencies
       const int n = model->M * model->NP;
       discrete_mstep_kernel<<<(n + 127) / 128, 128, 0, st>>>(model->theta.as<double>(), stats->mv_rec.as<double>(),
@@ -1303,9 +1384,12 @@ hmm_status hmm_ctx_profile_read(hmm_ctx ctx, double* h_ms, int64_t* h_launches, 
   });
 }
 
-hmm_status hmm_model_create(hmm_ctx ctx, int32_t n_models, int32_t n_states, int32_t dim,
-                            const int32_t* h_family, hmm_model* out) {
-  return guarded([&] {
+namespace {
+// Model creation of hmm_model_create (h_comp == NULL) and
+// hmm_model_create_indep (h_family all HMM_INDEP, h_comp [n_models][dim]).
+void create_model(hmm_ctx ctx, int32_t n_models, int32_t n_states, int32_t dim, const int32_t* h_family,
+                  const int32_t* h_comp, hmm_model* out) {
+  {
     HMM_REQUIRE(ctx && out && h_family, "NULL argument");
     *out = nullptr;
     HMM_REQUIRE(n_models >= 1 && n_states >= 1 && n_states <= 1024 && dim >= 1, "bad model sizes");
@@ -1319,8 +1403,29 @@ hmm_status hmm_model_create(hmm_ctx ctx, int32_t n_models, int32_t n_states, int
       m->dim_arg = dim;
       m->h_family.assign(h_family, h_family + n_models);
       int P = 1;
+      if (h_comp) {   // independent components (Sec. 4.5)
+        HMM_REQUIRE(dim <= INDEP_MAX_D, "independent components support dim <= 32");
+        m->any_indep = true;
+        m->h_icomp.assign(h_comp, h_comp + (size_t)n_models * dim);
+        m->KS = 1;
+        for (int i = 0; i < n_models; ++i) {
+          int pc = 0, ks = 1;
+          for (int d = 0; d < dim; ++d) {
+            const int f = h_comp[(size_t)i * dim + d];
+            if (!indep_component_ok(f))
+              throw Error{HMM_E_UNSUPPORTED, "component family " + std::to_string(f) +
+                                                 " is not supported in independent components"};
+            pc += indep_param_count(f);
+            ks += indep_stat_count(f);
+          }
+          P = std::max(P, pc);
+          m->KS = std::max(m->KS, ks);
+        }
+      }
       for (int i = 0; i < n_models; ++i) {
         const int f = h_family[i];
+        HMM_REQUIRE((h_comp != nullptr) == (f == HMM_INDEP), "HMM_INDEP models are made by hmm_model_create_indep");
+        if (f == HMM_INDEP) continue;
         HMM_REQUIRE(f >= 0 && f <= HMM_PARETO, "unknown family");
         const bool mv = f == HMM_DIAG_GAUSS || f == HMM_FULL_GAUSS;
         HMM_REQUIRE(mv || f == HMM_DISCRETE || dim == 1, "scalar families need dim == 1");
@@ -1374,6 +1479,14 @@ hmm_status hmm_model_create(hmm_ctx ctx, int32_t n_models, int32_t n_states, int
         m->mvcoef.ensure(M * NP * m->KM * 4);
         HMM_CUDA(cudaMemset(m->mvcoef.p, 0, M * NP * m->KM * 4));
       }
+      if (m->any_indep) {
+        m->icomp.ensure(M * dim * 4);
+        m->icoef.ensure(M * NP * dim * KC * 4);
+        m->ishift.ensure(M * NP * dim * 4);
+        HMM_CUDA(cudaMemcpy(m->icomp.p, h_comp, M * dim * 4, cudaMemcpyHostToDevice));
+        HMM_CUDA(cudaMemset(m->icoef.p, 0, M * NP * dim * KC * 4));
+        HMM_CUDA(cudaMemset(m->ishift.p, 0, M * NP * dim * 4));
+      }
       m->lfact2.ensure(LF_YMAX * 4);
       HMM_CUDA(cudaMemcpy(m->family.p, h_family, M * 4, cudaMemcpyHostToDevice));
       HMM_CUDA(cudaMemset(m->pi.p, 0, M * NP * 8));
@@ -1385,20 +1498,39 @@ hmm_status hmm_model_create(hmm_ctx ctx, int32_t n_models, int32_t n_states, int
       HMM_CUDA(cudaStreamSynchronize(0));
     } catch (...) {
       for (auto* b : {&m->family, &m->pi, &m->A, &m->theta, &m->A32, &m->AT32, &m->logA2, &m->logAe, &m->pi32,
-                      &m->logpi2, &m->logpie, &m->coef, &m->nbtab, &m->lfact2, &m->mvcoef, &m->dtab})
+                      &m->logpi2, &m->logpie, &m->coef, &m->nbtab, &m->lfact2, &m->mvcoef, &m->dtab, &m->icomp,
+                      &m->icoef, &m->ishift})
         b->release();
       delete m;
       throw;
     }
     *out = m;
+  }
+}
+}  // namespace
+
+hmm_status hmm_model_create(hmm_ctx ctx, int32_t n_models, int32_t n_states, int32_t dim,
+                            const int32_t* h_family, hmm_model* out) {
+  return guarded([&] { create_model(ctx, n_models, n_states, dim, h_family, nullptr, out); });
+}
+
+hmm_status hmm_model_create_indep(hmm_ctx ctx, int32_t n_models, int32_t n_states, int32_t dim,
+                                  const int32_t* h_comp, hmm_model* out) {
+  return guarded([&] {
+    HMM_REQUIRE(h_comp != nullptr && n_models >= 1 && n_models <= (1 << 24), "NULL argument or bad model count");
+    std::vector<int32_t> fam((size_t)n_models, HMM_INDEP);
+    create_model(ctx, n_models, n_states, dim, fam.data(), h_comp, out);
   });
 }
+
+int64_t hmm_model_blob_size(hmm_model model) { return model ? model_blob_size(model) : -1; }
 
 hmm_status hmm_model_destroy(hmm_model m) {
   return guarded([&] {
     if (!m) return;
     for (auto* b : {&m->family, &m->pi, &m->A, &m->theta, &m->A32, &m->AT32, &m->logA2, &m->logAe, &m->pi32,
-                    &m->logpi2, &m->logpie, &m->coef, &m->nbtab, &m->lfact2, &m->mvcoef, &m->dtab})
+                    &m->logpi2, &m->logpie, &m->coef, &m->nbtab, &m->lfact2, &m->mvcoef, &m->dtab, &m->icomp,
+                    &m->icoef, &m->ishift})
       b->release();
     delete m;
   });
@@ -1408,12 +1540,12 @@ hmm_status hmm_model_set_params(hmm_model model, const double* h_blob, int64_t n
   return guarded([&] {
     HMM_REQUIRE(model && h_blob, "NULL argument");
     const int M = model->M, N = model->N, NP = model->NP, P = model->P, D = model->D;
-    const int64_t need = hmm_param_blob_size(M, N, model->dim_arg, model->h_family.data());
+    const int64_t need = model_blob_size(model);
     HMM_REQUIRE(n_values == need, "parameter blob has the wrong size");
     std::vector<double> pi((size_t)M * NP, 0.0), A((size_t)M * NP * NP, 0.0), th((size_t)M * NP * P, 0.0);
     const double* q = h_blob;
     for (int m = 0; m < M; ++m) {
-      const int pc = param_count(model->h_family[m], model->dim_arg);
+      const int pc = model_param_count(model, m);
       double psum = 0.0;
       for (int j = 0; j < N; ++j) {
         HMM_REQUIRE(q[j] >= 0.0 && std::isfinite(q[j]), "pi must be finite and >= 0");
@@ -1442,14 +1574,15 @@ hmm_status hmm_model_set_params(hmm_model model, const double* h_blob, int64_t n
         }
         if (model->h_family[m] == HMM_DISCRETE)
           HMM_REQUIRE(std::fabs(psum - 1.0) < 1e-6, "symbol probabilities must sum to 1");
-        switch (model->h_family[m]) {
-          case HMM_LOGNORMAL: HMM_REQUIRE(q[1] > 0.0, "log-normal sigma2 must be > 0"); break;
-          case HMM_EXPONENTIAL: HMM_REQUIRE(q[0] > 0.0, "exponential rate must be > 0"); break;
-          case HMM_RAYLEIGH: HMM_REQUIRE(q[0] > 0.0, "Rayleigh sigma2 must be > 0"); break;
-          case HMM_UNIFORM: HMM_REQUIRE(q[0] < q[1], "uniform bounds need a < b"); break;
-          case HMM_CHISQ: HMM_REQUIRE(q[0] > 0.0, "chi-squared nu must be > 0"); break;
-          case HMM_PARETO: HMM_REQUIRE(q[0] > 0.0 && q[1] > 0.0, "Pareto xm and alpha must be > 0"); break;
-          default: break;
+        if (model->h_family[m] == HMM_INDEP) {
+          const double* qc = q;
+          for (int d = 0; d < D; ++d) {
+            const int f = model->h_icomp[(size_t)m * D + d];
+            check_scalar_params(f, qc);
+            qc += indep_param_count(f);
+          }
+        } else {
+          check_scalar_params(model->h_family[m], q);
         }
         q += pc;
       }
@@ -1470,6 +1603,12 @@ hmm_status hmm_model_set_params(hmm_model model, const double* h_blob, int64_t n
                                                        model->dtab.as<float>());
       HMM_CUDA(cudaGetLastError());
     }
+    if (model->any_indep) {
+      const int ni = n * D;
+      indep_derive_kernel<<<(ni + 127) / 128, 128>>>(model->icomp.as<int>(), model->theta.as<double>(), M, NP, N, P,
+                                                     D, model->icoef.as<float>(), model->ishift.as<float>());
+      HMM_CUDA(cudaGetLastError());
+    }
     // the copies and derive kernels ran on the legacy default stream
     HMM_CUDA(cudaStreamSynchronize(0));
   });
@@ -1478,8 +1617,8 @@ hmm_status hmm_model_set_params(hmm_model model, const double* h_blob, int64_t n
 hmm_status hmm_model_get_params(hmm_model model, double* h_blob, int64_t n_values) {
   return guarded([&] {
     HMM_REQUIRE(model && h_blob, "NULL argument");
-    const int M = model->M, N = model->N, NP = model->NP, P = model->P, D = model->D;
-    const int64_t need = hmm_param_blob_size(M, N, model->dim_arg, model->h_family.data());
+    const int M = model->M, N = model->N, NP = model->NP, P = model->P;
+    const int64_t need = model_blob_size(model);
     HMM_REQUIRE(n_values == need, "parameter blob has the wrong size");
     HMM_CUDA(cudaDeviceSynchronize());
     std::vector<double> pi((size_t)M * NP), A((size_t)M * NP * NP), th((size_t)M * NP * P);
@@ -1488,7 +1627,7 @@ hmm_status hmm_model_get_params(hmm_model model, double* h_blob, int64_t n_value
     HMM_CUDA(cudaMemcpy(th.data(), model->theta.p, th.size() * 8, cudaMemcpyDeviceToHost));
     double* q = h_blob;
     for (int m = 0; m < M; ++m) {
-      const int pc = param_count(model->h_family[m], model->dim_arg);
+      const int pc = model_param_count(model, m);
       for (int j = 0; j < N; ++j) *q++ = pi[(size_t)m * NP + j];
       for (int i = 0; i < N; ++i)
         for (int j = 0; j < N; ++j) *q++ = A[((size_t)m * NP + i) * NP + j];
@@ -1600,6 +1739,12 @@ hmm_status hmm_emission_logpdf(hmm_ctx ctx, hmm_model model, const hmm_batch* ba
     PlanRef prr;
     get_plan(ctx, model, batch, S(stream), prr);
     const unsigned slabs = slabs_of(prr.p->max_T);
+    if (model->any_indep) {
+      KTimer kt(ctx, HMM_KT_EMISSION, S(stream));
+      launch_indep_emission(model, batch, prr.p, d_logb, S(stream));
+      if (prr.owned) HMM_CUDA(cudaStreamSynchronize(S(stream)));
+      return;
+    }
     if (model->any_discrete) {
       KTimer kt(ctx, HMM_KT_EMISSION, S(stream));
       discrete_emission_kernel<<<dim3((unsigned)batch->n_seq, slabs), 128, 0, S(stream)>>>(
@@ -1763,12 +1908,19 @@ static int canon_fam_count(int fam, int D) {
   return 0;
 }
 
+// Canonical statistics per state of model i (hmm_stats_get).
+static int canon_count(hmm_model md, int i) {
+  if (md->h_family[i] != HMM_INDEP) return canon_fam_count(md->h_family[i], md->dim_arg);
+  int n = 1;
+  for (int d = 0; d < md->D; ++d) n += indep_stat_count(md->h_icomp[(size_t)i * md->D + d]);
+  return n;
+}
+
 int64_t hmm_stats_size(hmm_stats stats) {
   if (!stats) return -1;
   const hmm_model m = stats->model;
   int64_t tot = 0;
-  for (int i = 0; i < m->M; ++i)
-    tot += 2 + m->N + (int64_t)m->N * m->N + (int64_t)m->N * canon_fam_count(m->h_family[i], m->dim_arg);
+  for (int i = 0; i < m->M; ++i) tot += 2 + m->N + (int64_t)m->N * m->N + (int64_t)m->N * canon_count(m, i);
   return tot;
 }
 
@@ -1803,6 +1955,11 @@ hmm_status hmm_stats_get(hmm_stats stats, double* h_out, int64_t n_values) {
         HMM_CUDA(cudaMemcpy(mvc.data(), md->mvcoef.p, mvc.size() * 4, cudaMemcpyDeviceToHost));
       }
     }
+    std::vector<float> ish;
+    if (md->any_indep) {
+      ish.resize((size_t)M * NP * D);
+      HMM_CUDA(cudaMemcpy(ish.data(), md->ishift.p, ish.size() * 4, cudaMemcpyDeviceToHost));
+    }
     double* q = h_out;
     for (int m = 0; m < M; ++m) {
       const double* R = rec.data() + (size_t)m * RS;
@@ -1817,6 +1974,29 @@ hmm_status hmm_stats_get(hmm_stats stats, double* h_out, int64_t n_values) {
         const double* St = R + rec_st(NP) + j * (NST - 1);
         const double c0 = coef[((size_t)m * NP + j) * KC];
         const double W = St[0];
+        if (fam == HMM_INDEP) {   // W, then each component's sums, shifts undone
+          const double* Rm = mrec.data() + ((size_t)m * NP + j) * KS;
+          q[0] = Rm[0];
+          int o = 1;
+          for (int d = 0; d < D; ++d) {
+            const int f = md->h_icomp[(size_t)m * D + d];
+            const double c = ish[((size_t)m * NP + j) * D + d];
+            const double* Sd = Rm + o;
+            double* qd = q + o;
+            const int n = indep_stat_count(f);
+            for (int z = 0; z < n; ++z) qd[z] = Sd[z];
+            if (f == HMM_GAUSS || f == HMM_LOGNORMAL) {
+              qd[0] = Sd[0] + c * Rm[0];
+              qd[1] = Sd[1] + 2.0 * c * Sd[0] + c * c * Rm[0];
+            } else if (f == HMM_STUDENT_T) {
+              qd[1] = Sd[1] + c * Sd[0];
+              qd[2] = Sd[2] + 2.0 * c * Sd[1] + c * c * Sd[0];
+            }
+            o += n;
+          }
+          q += canon_count(md, m);
+          continue;
+        }
         switch (fam) {
           case HMM_GAUSS:   // shifted by c0: sum w d, sum w d^2 -> raw moments
             q[0] = W;

@@ -139,7 +139,13 @@ struct hmm_model_s {
   // table, statistics from the occupancies; uniform / Pareto also need the
   // support min / max
   bool any_ext = false, any_support = false;
-  bool table_family() const { return any_mv || any_discrete || any_ext; }
+  // independent components (HMM_INDEP): the component family of each
+  // dimension per model, density coefficients [M][NP][D][KC] and shifts
+  // [M][NP][D] per component
+  bool any_indep = false;
+  std::vector<int32_t> h_icomp;  // [M][D]
+  hmm::DevBuf icomp, icoef, ishift;
+  bool table_family() const { return any_mv || any_discrete || any_ext || any_indep; }
   hmm::DevBuf family, pi, A, theta, A32, AT32, logA2, logAe, pi32, logpi2, logpie, coef, nbtab, lfact2;
   int KM = 0, KS = 0;            // multivariate coefficient / statistic slots per state
   hmm::DevBuf mvcoef;            // [M][NP][KM] float32 (multivariate families)

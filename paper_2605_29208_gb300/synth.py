@@ -105,11 +105,39 @@ def random_params(rng, family, N, D=1):
     raise ValueError(family)
 
 
+def component_model(model, d):
+    """Component d of an independent-components model dict, as a scalar
+    model dict (same pi and A)."""
+    pre = f"d{d}."
+    return make_model(model["components"][d], model["pi"], model["A"],
+                      **{k[len(pre):]: v for k, v in model["params"].items() if k.startswith(pre)})
+
+
+def indep_model(rng, components, N, conc=1.0):
+    """An independent-components model (Sec. 4.5): one scalar family per
+    observation dimension, parameters drawn as for that family."""
+    params = {}
+    for d, f in enumerate(components):
+        for k, v in random_params(rng, f, N).items():
+            params[f"d{d}.{k}"] = v
+    m = make_model("indep", rng.dirichlet(np.ones(N)), dirichlet_rows(rng, N, conc), **params)
+    m["components"] = list(components)
+    return m
+
+
+def indep_models(components, N, n_models, seed, conc=1.0):
+    rng = np.random.default_rng(seed)
+    return [indep_model(rng, components, N, conc) for _ in range(n_models)]
+
+
 def sample_emissions(rng, model, states):
     """Draw y_t from the emission of state q_t (vectorised over t)."""
     f, p = model["family"], model["params"]
     q = states
     n = len(q)
+    if f == "indep":
+        return np.stack([sample_emissions(rng, component_model(model, d), q)
+                         for d in range(len(model["components"]))], axis=1)
     if f == "discrete":
         cp = np.cumsum(p["p"], axis=1)[q]
         u = rng.random(n)[:, None]
@@ -284,6 +312,14 @@ def perturb(rng, model, frac=0.2):
     """EM start: parameters scaled by U[1-frac, 1+frac], A <- A/2 + 1/(2N),
     pi uniform."""
     N = len(model["pi"])
+    if model["family"] == "indep":
+        params = {}
+        for d in range(len(model["components"])):
+            for k, v in perturb(rng, component_model(model, d), frac)["params"].items():
+                params[f"d{d}.{k}"] = v
+        m = make_model("indep", np.full(N, 1.0 / N), 0.5 * model["A"] + 0.5 / N, **params)
+        m["components"] = list(model["components"])
+        return m
     params = {}
     for k, v in model["params"].items():
         if model["family"] in ("vonmises",) and k == "mu":

@@ -27,7 +27,7 @@ NEAR_TIES = []
 
 def om(d):
     return O.Model(d["family"], np.array(d["pi"], copy=True), np.array(d["A"], copy=True),
-                   {k: np.array(v, copy=True) for k, v in d["params"].items()})
+                   {k: np.array(v, copy=True) for k, v in d["params"].items()}, tuple(d.get("components", ())))
 
 
 def _logs(o):
