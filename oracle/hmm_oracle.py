@@ -873,19 +873,40 @@ def valid_update(family, res) -> bool:
     return True
 
 
-def mstep_transitions(model: Model, xi_sum, gamma1_sum, n_seq):
+def mstep_transitions(model: Model, xi_sum, gamma1_sum, n_seq, alpha_A=1.0, alpha_pi=1.0):
     """Reading (the paper names Baum-Welch but prints no transition update):
     a_ij = sum xi(i,j) / sum_j' xi(i,j') (the denominator equals
     sum_{t<T} gamma_t(i)); a row whose denominator is below 1e-8 is kept
     (the Sec. 4.4 rule applied to rows); pi_j = mean over the model's
-    sequences of gamma_1(j)."""
+    sequences of gamma_1(j).
+
+    MAP Baum-Welch (the paper names a MAP trainer, Sec. 5.6, without a
+    definition; reading): symmetric Dirichlet priors Dir(alpha_A) on every
+    row of A and Dir(alpha_pi) on pi, flat priors on the emission
+    parameters; the M-step takes the posterior mode, i.e. adds the
+    pseudo-counts alpha - 1 (alpha <= 1 adds none):
+    a_ij = (n_ij + alpha_A - 1) / (sum_j' n_ij' + N (alpha_A - 1)),
+    pi_j = (sum_s gamma_1(j) + alpha_pi - 1) / (S + N (alpha_pi - 1))."""
+    N = model.n_states
+    cA = max(alpha_A - 1.0, 0.0)
+    cp = max(alpha_pi - 1.0, 0.0)
     A = model.A.copy()
-    den = xi_sum.sum(axis=1)
-    for i in range(model.n_states):
+    num = xi_sum + cA
+    den = num.sum(axis=1)
+    for i in range(N):
         if den[i] >= COLLAPSE_EPS:
-            A[i] = xi_sum[i] / den[i]
-    pi = gamma1_sum / n_seq
+            A[i] = num[i] / den[i]
+    pi = (gamma1_sum + cp) / (n_seq + N * cp)
     return pi, A
+
+
+def log_dirichlet_prior(model: Model, alpha_A=1.0, alpha_pi=1.0) -> float:
+    """log of the (unnormalised) Dirichlet prior density of the MAP reading
+    at the model's pi and A: sum (alpha - 1) log p."""
+    cA = max(alpha_A - 1.0, 0.0)
+    cp = max(alpha_pi - 1.0, 0.0)
+    with np.errstate(divide="ignore"):
+        return float(cA * np.sum(np.log(model.A)) + cp * np.sum(np.log(model.pi)))
 
 
 # --------------------------------------------------------------------------
@@ -916,9 +937,10 @@ def estep(models, values, offsets, model_id):
     return out
 
 
-def em_iteration(models, values, offsets, model_id, nu_mode="ecm"):
+def em_iteration(models, values, offsets, model_id, nu_mode="ecm", alpha_A=1.0, alpha_pi=1.0):
     """E-step with the current models, then the M-step of Sec. 4 for the
-    emissions and the transition/initial reading.  Returns
+    emissions and the transition/initial reading (with alpha_A / alpha_pi
+    > 1: the MAP reading of mstep_transitions).  Returns
     (new_models, logL per sequence [S] under the OLD models)."""
     S = len(offsets) - 1
     logL = np.zeros(S)
@@ -933,9 +955,67 @@ def em_iteration(models, values, offsets, model_id, nu_mode="ecm"):
         Y = np.concatenate(res["Y"], axis=0)
         new, _ = mstep_emission(model, W, Y, nu_mode=nu_mode)
         new.pi, new.A = mstep_transitions(model, res["xi_sum"],
-                                          res["gamma1_sum"], res["n_seq"])
+                                          res["gamma1_sum"], res["n_seq"], alpha_A, alpha_pi)
         new_models.append(new)
     return new_models, logL
+
+
+# --------------------------------------------------------------------------
+# Viterbi training (the paper names a Viterbi trainer, Sec. 5.6, without a
+# definition; reading: segmental k-means / hard EM).  The E-step decodes
+# each sequence's Viterbi path q* (Eq. 3-4) and replaces the posteriors by
+# the path's indicators, gamma_t(j) = 1[q*_t = j] and
+# xi_t(i,j) = 1[q*_t = i, q*_{t+1} = j]; the M-step is the Baum-Welch one on
+# these weights.  The objective sum_s max_q log P(q, y_s) does not decrease:
+# the M-step maximises log P(q*, y) over the parameters for the fixed paths,
+# and decoding again can only raise the maximum over q.
+# --------------------------------------------------------------------------
+def viterbi_estep(models, values, offsets, model_id):
+    """Per model: the hard occupancies of every row of its data, transition
+    counts, first-state counts, the number of sequences, and per sequence
+    the Viterbi path and its score."""
+    seqs = split_batch(values, offsets)
+    out = []
+    for m, model in enumerate(models):
+        idx = [s for s in range(len(seqs)) if model_id[s] == m]
+        N = model.n_states
+        res = dict(seq=idx, score=[], path=[], W=[], Y=[], xi_sum=np.zeros((N, N)),
+                   gamma1_sum=np.zeros(N), n_seq=len(idx))
+        for s in idx:
+            y = seqs[s]
+            if len(y) == 0:
+                res["score"].append(0.0)
+                res["path"].append(np.zeros(0, np.int32))
+                continue
+            q, sc = viterbi(model, y)
+            W = np.zeros((len(y), N))
+            W[np.arange(len(y)), q] = 1.0
+            np.add.at(res["xi_sum"], (q[:-1], q[1:]), 1.0)
+            res["gamma1_sum"][q[0]] += 1.0
+            res["score"].append(sc)
+            res["path"].append(q)
+            res["W"].append(W)
+            res["Y"].append(y)
+        out.append(res)
+    return out
+
+
+def viterbi_train_iteration(models, values, offsets, model_id, nu_mode="ecm"):
+    """One Viterbi-training iteration; returns (new_models, the Viterbi
+    score of every sequence [S] under the OLD models)."""
+    S = len(offsets) - 1
+    score = np.zeros(S)
+    new_models = []
+    for model, res in zip(models, viterbi_estep(models, values, offsets, model_id)):
+        for s, sc in zip(res["seq"], res["score"]):
+            score[s] = sc
+        if not res["W"]:
+            new_models.append(model.copy())
+            continue
+        new, _ = mstep_emission(model, np.concatenate(res["W"]), np.concatenate(res["Y"]), nu_mode=nu_mode)
+        new.pi, new.A = mstep_transitions(model, res["xi_sum"], res["gamma1_sum"], res["n_seq"])
+        new_models.append(new)
+    return new_models, score
 
 
 def fit(models, values, offsets, model_id, n_iter, nu_mode="ecm"):
