@@ -124,12 +124,21 @@ typedef struct {
   int32_t nu_mode;       /* [0]     Student-t nu equation: 0 = ECM equation with
                                     the E[log U] constant, 1 = Eq. 18 as printed */
   int32_t update_transitions; /* [1 when the struct is NULL] 0 keeps pi and A    */
+  double dirichlet_A;    /* [0]     MAP Baum-Welch (the MAP trainer the paper
+                                    names, Sec. 5.6; reading): symmetric
+                                    Dirichlet concentration of every row of A;
+                                    the update adds dirichlet_A - 1 pseudo-counts
+                                    to each row's transitions (values <= 1: none) */
+  double dirichlet_pi;   /* [0]     the same for pi                              */
 } hmm_mstep_opts;
 
 typedef struct {
   int32_t max_iter;      /* number of Baum-Welch iterations                      */
   double tol;            /* stop when |dlogL| <= tol * |logL| (0: run max_iter)  */
   hmm_mstep_opts mstep;
+  int32_t trainer;       /* [0] Baum-Welch; 1 Viterbi training (hmm_estep_viterbi
+                            as the E-step; the trace then holds the sums of the
+                            best paths' log-probabilities)                     */
 } hmm_fit_opts;
 
 /* ---------------------------------------------------------------- basics */
@@ -424,6 +433,20 @@ hmm_status hmm_stats_record(hmm_stats stats, int32_t index, void** d_values, int
  * a fixed order (bitwise reproducible). */
 hmm_status hmm_estep_stats(hmm_ctx ctx, hmm_model model, const hmm_batch* batch,
                            hmm_stats stats, double* d_loglik, void* stream);
+
+/* Viterbi-training E-step (the Viterbi trainer the paper names, Sec. 5.6;
+ * reading: hard EM / segmental k-means).  Decodes every sequence's Viterbi
+ * path q* (Eq. 3-4, as hmm_viterbi) and fills `stats` with the statistics of
+ * the paths: occupancies gamma_t(j) = 1[q*_t = j], transition counts
+ * n_ij = #{t : q*_t = i, q*_{t+1} = j} (in place of the expected ones) and
+ * first states, so that hmm_mstep then runs the Baum-Welch M-step on these
+ * hard weights.  The statistic record's log-likelihood entry holds the sum
+ * of the paths' log-probabilities max_q log P(q, y), the objective that
+ * Viterbi training does not decrease.  d_score [n_seq] (may be NULL)
+ * receives them per sequence.  The installed all-reduce (if any) runs as
+ * after hmm_estep_stats. */
+hmm_status hmm_estep_viterbi(hmm_ctx ctx, hmm_model model, const hmm_batch* batch, hmm_stats stats,
+                             double* d_score, void* stream);
 
 /* M-step (Sec. 4, Eq. 6 with the closed forms, Newton-Raphson and ECM
  * steps of Sec. 4.1-4.5, the Sec. 4.4 collapse guard, and the transition /

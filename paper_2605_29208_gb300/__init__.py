@@ -358,6 +358,8 @@ def mstep_opts(nu_mode=0, update_transitions=1, **kw):
     o.newton_tol = kw.get("newton_tol", 0.0)
     o.nu_mode = nu_mode
     o.update_transitions = update_transitions
+    o.dirichlet_A = kw.get("dirichlet_A", 0.0)
+    o.dirichlet_pi = kw.get("dirichlet_pi", 0.0)
     return o
 
 
@@ -368,10 +370,24 @@ def mstep(ctx, model, stats, batch=None, opts=None, stream=None):
                             C.byref(o), _stream(stream)))
 
 
-def fit(ctx, model, batch, n_iter, tol=0.0, opts=None, stream=None):
+def estep_viterbi(ctx, model, batch, stats=None, stream=None):
+    """hmm_estep_viterbi: statistics of the Viterbi paths (Viterbi training);
+    returns (stats, per-sequence best-path log-probabilities)."""
+    torch = _torch()
+    stats = stats or Stats(ctx, model)
+    sc = torch.empty(batch.n_seq, dtype=torch.float64, device=batch.values.device)
+    b = batch.c()
+    check(ctx.lib.hmm_estep_viterbi(ctx.h, model.h, C.byref(b), stats.h, _ptr(sc), _stream(stream)))
+    return stats, sc
+
+
+def fit(ctx, model, batch, n_iter, tol=0.0, opts=None, stream=None, trainer="baum_welch"):
+    """hmm_fit: n_iter iterations of Baum-Welch (trainer "baum_welch"; MAP
+    with dirichlet_* in opts) or Viterbi training (trainer "viterbi")."""
     o = _lib.hmm_fit_opts()
     o.max_iter = n_iter
     o.tol = tol
+    o.trainer = {"baum_welch": 0, "viterbi": 1}[trainer]
     o.mstep = opts or mstep_opts()
     trace = np.zeros((max(n_iter, 1), model.n_models), np.float64)
     done = C.c_int32(0)

@@ -30,11 +30,13 @@ class hmm_batch(C.Structure):
 class hmm_mstep_opts(C.Structure):
     _fields_ = [("collapse_eps", C.c_double), ("tikhonov_eps", C.c_double),
                 ("newton_maxit", C.c_int32), ("newton_tol", C.c_double),
-                ("nu_mode", C.c_int32), ("update_transitions", C.c_int32)]
+                ("nu_mode", C.c_int32), ("update_transitions", C.c_int32),
+                ("dirichlet_A", C.c_double), ("dirichlet_pi", C.c_double)]
 
 
 class hmm_fit_opts(C.Structure):
-    _fields_ = [("max_iter", C.c_int32), ("tol", C.c_double), ("mstep", hmm_mstep_opts)]
+    _fields_ = [("max_iter", C.c_int32), ("tol", C.c_double), ("mstep", hmm_mstep_opts),
+                ("trainer", C.c_int32)]
 
 
 class hmm_serve_opts(C.Structure):
@@ -104,6 +106,8 @@ _SIGS = {
                                    C.POINTER(C.c_int32)]),
     "hmm_estep_stats": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(hmm_batch), C.c_void_p,
                                   C.c_void_p, C.c_void_p]),
+    "hmm_estep_viterbi": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(hmm_batch), C.c_void_p,
+                                    C.c_void_p, C.c_void_p]),
     "hmm_mstep": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(hmm_batch),
                             C.POINTER(hmm_mstep_opts), C.c_void_p]),
     "hmm_fit": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(hmm_batch), C.POINTER(hmm_fit_opts),

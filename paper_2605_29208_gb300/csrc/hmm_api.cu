@@ -744,6 +744,7 @@ void run_estep_large(hmm_ctx ctx, hmm_model model, const hmm_batch* b, hmm_plan 
                      float* gamma, double* ll, bool want_stats, hmm_stats stats, cudaStream_t st) {
   const int NP = model->NP, N = model->N;
   const int64_t S = b->n_seq, TT = std::max<int64_t>(b->total_T, 1);
+  if (want_stats && stats) stats->hard = false;
   if (ctx->plain_estep) throw Error{HMM_E_UNSUPPORTED, "the plain path covers padded N <= 32"};
   if (!logb) logb = mv_table(ctx, model, b, plan, st);
   ctx->scratch.ensure(TT * NP * 4 + 64);
@@ -903,6 +904,7 @@ void run_estep(hmm_ctx ctx, hmm_model model, const hmm_batch* b, hmm_plan plan, 
   if (model->table_family() && ctx->plain_estep)
     throw Error{HMM_E_UNSUPPORTED, "the plain path covers the scalar families only"};
   const int64_t S = b->n_seq;
+  if (want_stats && stats) stats->hard = false;
   const bool mv_stats = want_stats && stats && model->table_family();
   if (model->table_family() && !logb) logb = mv_table(ctx, model, b, plan, st);
   ctx->scratch.ensure(std::max<int64_t>(b->total_T, 1) * NP * 4 + 64);
@@ -994,6 +996,9 @@ MStepOpts to_opts(const hmm_mstep_opts* o) {
   r.newton_tol = (o && o->newton_tol > 0) ? o->newton_tol : 1e-10;
   r.nu_mode = o ? o->nu_mode : 0;
   r.update_transitions = o ? o->update_transitions : 1;
+  r.prior_A = o ? o->dirichlet_A : 0.0;
+  r.prior_pi = o ? o->dirichlet_pi : 0.0;
+  r.hard = 0;
   return r;
 }
 
@@ -1058,8 +1063,10 @@ void prepare_mstep(hmm_model model, hmm_stats stats, const hmm_batch* b, hmm_pla
   stats->dp_count.ensure(64 * sizeof(int));
 }
 
-void run_mstep(hmm_ctx ctx, hmm_model model, hmm_stats stats, const MStepOpts& o, const hmm_batch* b,
+void run_mstep(hmm_ctx ctx, hmm_model model, hmm_stats stats, const MStepOpts& o_in, const hmm_batch* b,
                hmm_plan plan, cudaStream_t st) {
+  MStepOpts o = o_in;
+  o.hard = stats->hard ? 1 : 0;   // statistics of Viterbi paths: transition counts
   if (model->table_family()) HMM_REQUIRE(stats->mv_rec.p != nullptr, "table-family statistics were never computed");
   const bool dpass = model->any_negbin || model->any_weibull;
   if (dpass && model->NP > 32)
@@ -1321,6 +1328,8 @@ hmm_status hmm_ctx_destroy(hmm_ctx ctx) {
     ctx->lg_xi.release();
     ctx->xi_xt.release();
     ctx->xi_yt.release();
+    ctx->vt_path.release();
+    ctx->vt_count.release();
     for (auto* bb : {&ctx->tp_Q, &ctx->tp_qexp, &ctx->tp_bvec, &ctx->tp_boff}) bb->release();
     delete ctx;
   });
@@ -1791,6 +1800,135 @@ hmm_status hmm_forward_backward(hmm_ctx ctx, hmm_model model, const hmm_batch* b
   });
 }
 
+namespace {
+// Viterbi decode of a batch (the body of hmm_viterbi) with a plan.
+void run_viterbi(hmm_ctx ctx, hmm_model model, const hmm_batch* batch, hmm_plan plan, const float* d_logb,
+                 int32_t* d_path, double* d_score, cudaStream_t st) {
+  const int64_t Sn = batch->n_seq;
+  if (Sn == 0) return;
+  if (model->NP > 32) {
+    if (!d_logb) d_logb = mv_table(ctx, model, batch, plan, st);
+    ctx->psi.ensure(std::max<int64_t>(batch->total_T, 1) * model->NP * 2 + 64);
+    LargeArgs a{};
+    a.logb = d_logb;
+    a.offsets = batch->offsets;
+    a.model_id = batch->model_id;
+    a.groups = plan->lg_groups.as<int32_t>();
+    a.n_groups = plan->n_groups;
+    a.mv = model->view();
+    a.psi = ctx->psi.as<uint16_t>();
+    a.path = d_path;
+    a.score = d_score;
+    KTimer kt(ctx, HMM_KT_VITERBI, st);
+    HMM_CUDA(launch_large_viterbi(model->NP, a, st));
+    return;
+  }
+  if (model->table_family() && !d_logb) d_logb = mv_table(ctx, model, batch, plan, st);
+  const int NP = model->NP;
+  ctx->psi.ensure(std::max<int64_t>(batch->total_T, 1) * NP + 64);
+  VitArgs a;
+  a.y = batch->values;
+  a.logb = d_logb;
+  a.offsets = batch->offsets;
+  a.model_id = batch->model_id;
+  a.order = plan->order.as<int32_t>();
+  a.n_seq = (int32_t)Sn;
+  int G = plan->viterbi_G > 0 ? plan->viterbi_G : default_viterbi_G(NP, Sn, ctx->n_sm);
+  if (ctx->viterbi_lanes && viterbi_small_supported(NP, ctx->viterbi_lanes)) G = ctx->viterbi_lanes;
+  a.n_items = (int32_t)((Sn + viterbi_seqs_per_item(G) - 1) / viterbi_seqs_per_item(G));
+  a.mv = model->view();
+  a.psi = ctx->psi.as<uint8_t>();
+  a.path = d_path;
+  a.score = d_score;
+  a.work_counter = ctx->counters + 1;
+  a.status = ctx->status;
+  HMM_CUDA(cudaMemsetAsync(ctx->counters + 1, 0, sizeof(int), st));
+  KTimer kt(ctx, HMM_KT_VITERBI, st);
+  const int fam = d_logb ? FAM_TABLE : (plan->uniform_family >= 0 ? plan->uniform_family : FAM_ANY);
+  HMM_CUDA(launch_viterbi_small(NP, G, a, fam, ctx->n_sm, st));
+}
+
+// One-hot occupancies of decoded paths: gamma[t][j] = 1[path_t = j].
+__global__ void onehot_kernel(const int32_t* __restrict__ path, int64_t total_T, int N, float* __restrict__ gamma) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= total_T * N) return;
+  gamma[i] = path[i / N] == (int32_t)(i % N) ? 1.f : 0.f;
+}
+
+// Transition counts of the decoded paths per 64-sequence chunk, as float64
+// blocks [n_chunks][NP][NP] (integer atomics: exact, order-independent).
+__global__ void path_xi_kernel(const int32_t* __restrict__ path, const int64_t* __restrict__ offsets,
+                               const int32_t* __restrict__ seq_by_model, const int32_t* __restrict__ chunk_lo,
+                               const int32_t* __restrict__ chunk_hi, int NP, int* __restrict__ counts,
+                               double* __restrict__ xi_chunk) {
+  const int c = blockIdx.x;
+  int* cnt = counts + (size_t)c * NP * NP;
+  for (int z = threadIdx.x; z < NP * NP; z += blockDim.x) cnt[z] = 0;
+  __syncthreads();
+  for (int qs = chunk_lo[c]; qs < chunk_hi[c]; ++qs) {
+    const int s = seq_by_model[qs];
+    const int64_t b = offsets[s], e = offsets[s + 1];
+    for (int64_t t = b + threadIdx.x; t + 1 < e; t += blockDim.x) {
+      const int i = path[t], j = path[t + 1];
+      if (i >= 0 && i < NP && j >= 0 && j < NP) atomicAdd(&cnt[i * NP + j], 1);
+    }
+  }
+  __syncthreads();
+  double* out = xi_chunk + (size_t)c * NP * NP;
+  for (int z = threadIdx.x; z < NP * NP; z += blockDim.x) out[z] = (double)cnt[z];
+}
+
+// Statistics of the Viterbi paths into `stats` (hmm_estep_viterbi).
+void run_estep_viterbi(hmm_ctx ctx, hmm_model model, const hmm_batch* b, hmm_plan plan, hmm_stats stats,
+                       double* d_score, cudaStream_t st) {
+  const int NP = model->NP, N = model->N;
+  const int64_t S = b->n_seq, TT = std::max<int64_t>(b->total_T, 1);
+  ctx->vt_path.ensure((size_t)TT * 4);
+  if (!d_score) {
+    ctx->loglik.ensure(std::max<int64_t>(S, 1) * 8);
+    d_score = ctx->loglik.as<double>();
+  }
+  run_viterbi(ctx, model, b, plan, nullptr, ctx->vt_path.as<int32_t>(), d_score, st);
+  stats->gamma.ensure((size_t)TT * N * 4);
+  stats->gamma_T = b->total_T;
+  ctx->partials.ensure((size_t)std::max<int64_t>(S, 1) * NP * NST * 4);
+  const int nc = plan->n_chunks;
+  ctx->lg_xi.ensure((size_t)std::max(nc, 1) * NP * NP * 8);
+  ctx->vt_count.ensure((size_t)std::max(nc, 1) * NP * NP * 4);
+  ctx->chunk_rec.ensure((size_t)std::max(nc, 1) * rec_size(NP) * 8);
+  KTimer kt(ctx, HMM_KT_REDUCE, st);
+  kt.kernels = 3;
+  const int64_t n = b->total_T * N;
+  if (n > 0) {
+    onehot_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(ctx->vt_path.as<int32_t>(), b->total_T, N,
+                                                              stats->gamma.as<float>());
+    HMM_CUDA(cudaGetLastError());
+    ++kt.kernels;
+  }
+  LargeArgs a{};
+  a.offsets = b->offsets;
+  a.model_id = b->model_id;
+  a.mv = model->view();
+  HMM_CUDA(launch_large_stats(a, b->values, stats->gamma.as<float>(), S, model->table_family(),
+                              ctx->partials.as<float>(), st));
+  if (nc > 0) {
+    path_xi_kernel<<<nc, 256, 0, st>>>(ctx->vt_path.as<int32_t>(), b->offsets, plan->seq_by_model.as<int32_t>(),
+                                       plan->chunk_lo.as<int32_t>(), plan->chunk_hi.as<int32_t>(), NP,
+                                       ctx->vt_count.as<int>(), ctx->lg_xi.as<double>());
+    HMM_CUDA(cudaGetLastError());
+    HMM_CUDA(launch_large_reduce(ctx->partials.as<float>(), d_score, ctx->lg_xi.as<double>(),
+                                 plan->seq_by_model.as<int32_t>(), plan->chunk_lo.as<int32_t>(),
+                                 plan->chunk_hi.as<int32_t>(), nc, NP, ctx->chunk_rec.as<double>(), st));
+  }
+  reduce_chunks_l2<<<model->M, 256, 0, st>>>(ctx->chunk_rec.as<double>(), plan->model_chunk_ptr.as<int32_t>(),
+                                             rec_size(NP), stats->rec.as<double>());
+  HMM_CUDA(cudaGetLastError());
+  if (model->table_family()) kt.kernels += mv_statistics(ctx, model, b, plan, stats, st);
+  stats->valid = true;
+  stats->hard = true;
+}
+}  // namespace
+
 hmm_status hmm_viterbi(hmm_ctx ctx, hmm_model model, const hmm_batch* batch, const float* d_logb,
                        int32_t* d_path, double* d_score, void* stream) {
   return guarded([&] {
@@ -1798,54 +1936,33 @@ hmm_status hmm_viterbi(hmm_ctx ctx, hmm_model model, const hmm_batch* batch, con
     check_batch(model, batch);
     PlanRef pr;
     get_plan(ctx, model, batch, S(stream), pr);
-    const int64_t Sn = batch->n_seq;
-    if (Sn == 0) return;
-    if (model->NP > 32) {
-      if (!d_logb) d_logb = mv_table(ctx, model, batch, pr.p, S(stream));
-      ctx->psi.ensure(std::max<int64_t>(batch->total_T, 1) * model->NP * 2 + 64);
-      LargeArgs a{};
-      a.logb = d_logb;
-      a.offsets = batch->offsets;
-      a.model_id = batch->model_id;
-      a.groups = pr.p->lg_groups.as<int32_t>();
-      a.n_groups = pr.p->n_groups;
-      a.mv = model->view();
-      a.psi = ctx->psi.as<uint16_t>();
-      a.path = d_path;
-      a.score = d_score;
-      {
-        KTimer kt(ctx, HMM_KT_VITERBI, S(stream));
-        HMM_CUDA(launch_large_viterbi(model->NP, a, S(stream)));
-      }
-      if (pr.owned) HMM_CUDA(cudaStreamSynchronize(S(stream)));
-      return;
-    }
-    if (model->table_family() && !d_logb) d_logb = mv_table(ctx, model, batch, pr.p, S(stream));
-    const int NP = model->NP;
-    ctx->psi.ensure(std::max<int64_t>(batch->total_T, 1) * NP + 64);
-    VitArgs a;
-    a.y = batch->values;
-    a.logb = d_logb;
-    a.offsets = batch->offsets;
-    a.model_id = batch->model_id;
-    a.order = pr.p->order.as<int32_t>();
-    a.n_seq = (int32_t)Sn;
-    int G = pr.p->viterbi_G > 0 ? pr.p->viterbi_G : default_viterbi_G(NP, Sn, ctx->n_sm);
-    if (ctx->viterbi_lanes && viterbi_small_supported(NP, ctx->viterbi_lanes)) G = ctx->viterbi_lanes;
-    a.n_items = (int32_t)((Sn + viterbi_seqs_per_item(G) - 1) / viterbi_seqs_per_item(G));
-    a.mv = model->view();
-    a.psi = ctx->psi.as<uint8_t>();
-    a.path = d_path;
-    a.score = d_score;
-    a.work_counter = ctx->counters + 1;
-    a.status = ctx->status;
-    HMM_CUDA(cudaMemsetAsync(ctx->counters + 1, 0, sizeof(int), S(stream)));
-    {
-      KTimer kt(ctx, HMM_KT_VITERBI, S(stream));
-      const int fam = d_logb ? FAM_TABLE : (pr.p->uniform_family >= 0 ? pr.p->uniform_family : FAM_ANY);
-      HMM_CUDA(launch_viterbi_small(NP, G, a, fam, ctx->n_sm, S(stream)));
-    }
+    run_viterbi(ctx, model, batch, pr.p, d_logb, d_path, d_score, S(stream));
     if (pr.owned) HMM_CUDA(cudaStreamSynchronize(S(stream)));
+  });
+}
+
+hmm_status hmm_estep_viterbi(hmm_ctx ctx, hmm_model model, const hmm_batch* batch, hmm_stats stats,
+                             double* d_score, void* stream) {
+  return guarded([&] {
+    HMM_REQUIRE(ctx && model && stats, "NULL argument");
+    HMM_REQUIRE(stats->model == model, "stats belong to another model");
+    check_batch(model, batch);
+    if (batch->n_seq == 0) {
+      zero_stats(model, stats, S(stream));
+      stats->hard = true;
+    } else {
+      PlanRef pr;
+      get_plan(ctx, model, batch, S(stream), pr);
+      run_estep_viterbi(ctx, model, batch, pr.p, stats, d_score, S(stream));
+      if (pr.owned) HMM_CUDA(cudaStreamSynchronize(S(stream)));
+    }
+    for (int i = 0; i < 3; ++i) {
+      void* p = nullptr;
+      int64_t n = 0;
+      int op = 0;
+      record_view(stats, i, &p, &n, &op);
+      call_reduce(stats, p, n, op, S(stream));
+    }
   });
 }
 
@@ -2193,8 +2310,17 @@ hmm_status hmm_fit(hmm_ctx ctx, hmm_model model, const hmm_batch* batch, const h
     run_estep(ctx, model, batch, pr.p, nullptr, nullptr, nullptr, true, stats, st);
     prepare_mstep(model, stats, batch, pr.p);
     HMM_CUDA(cudaStreamSynchronize(st));
+    const bool viterbi_training = opts->trainer == 1;
+    HMM_REQUIRE(opts->trainer == 0 || opts->trainer == 1, "trainer must be 0 (Baum-Welch) or 1 (Viterbi)");
+    if (viterbi_training) {   // size the Viterbi-training buffers before any capture
+      run_estep_viterbi(ctx, model, batch, pr.p, stats, nullptr, st);
+      HMM_CUDA(cudaStreamSynchronize(st));
+    }
     auto one_iter = [&]() {
-      run_estep(ctx, model, batch, pr.p, nullptr, nullptr, nullptr, true, stats, st);
+      if (viterbi_training)
+        run_estep_viterbi(ctx, model, batch, pr.p, stats, nullptr, st);
+      else
+        run_estep(ctx, model, batch, pr.p, nullptr, nullptr, nullptr, true, stats, st);
       trace_gather_kernel<<<(M + 255) / 256, 256, 0, st>>>(stats->rec.as<double>(), RS, M,
                                                           ctx->trace.as<double>(), it_dev);
       HMM_CUDA(cudaGetLastError());

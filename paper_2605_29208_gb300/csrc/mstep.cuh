@@ -464,14 +464,18 @@ __global__ void mstep_kernel(ModelBufs mb, const double* __restrict__ rec, MStep
         for (int z = 0; z < 4 && z < mb.P; ++z) th[z] = old[z];
     }
     if (o.update_transitions) {
+      // expected (Baum-Welch: a_ij X_ij) or counted (Viterbi training: X_ij)
+      // transitions, plus the Dirichlet pseudo-counts of the MAP reading
       double* Arow = mb.A + ((size_t)m * NP + k) * NP;
       const double* X = R + rec_xi(NP) + k * NP;
+      const double cA = o.prior_A > 1.0 ? o.prior_A - 1.0 : 0.0;
+      const double cp = o.prior_pi > 1.0 ? o.prior_pi - 1.0 : 0.0;
       double den = 0.0;
-      for (int j = 0; j < N; ++j) den += Arow[j] * X[j];
+      for (int j = 0; j < N; ++j) den += (o.hard ? X[j] : Arow[j] * X[j]) + cA;
       if (den >= o.collapse_eps)
-        for (int j = 0; j < N; ++j) Arow[j] = Arow[j] * X[j] / den;
+        for (int j = 0; j < N; ++j) Arow[j] = ((o.hard ? X[j] : Arow[j] * X[j]) + cA) / den;
       const double ns = R[0];
-      if (ns > 0.0) mb.pi[(size_t)m * NP + k] = R[rec_g1(NP) + k] / ns;
+      if (ns > 0.0) mb.pi[(size_t)m * NP + k] = (R[rec_g1(NP) + k] + cp) / (ns + N * cp);
     }
   }
   __syncthreads();

@@ -45,6 +45,9 @@ struct MStepOpts {
   double newton_tol;
   int nu_mode;
   int update_transitions;
+  double prior_A;         // Dirichlet concentration of the rows of A (MAP; <= 1: none)
+  double prior_pi;        // Dirichlet concentration of pi (MAP; <= 1: none)
+  int hard;               // the xi slots hold transition counts (Viterbi training)
 };
 
 // Per-(model, state) Newton state of the families whose M-step re-reads the

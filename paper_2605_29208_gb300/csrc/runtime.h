@@ -107,6 +107,8 @@ struct hmm_ctx_s {
   hmm::DevBuf lg_rz;             // [total_T] 1 / Z_t
   hmm::DevBuf lg_xi;             // [n_chunks][NP][NP] float64 xi blocks
   hmm::DevBuf xi_xt, xi_yt;      // [NP][xi_ktot] float32 operands of the tensor-core xi
+  hmm::DevBuf vt_path;           // [total_T] Viterbi paths of Viterbi training
+  hmm::DevBuf vt_count;          // [n_chunks][NP][NP] int32 transition counts
   // options
   int profile = 0;
   int estep_lanes = 0;
@@ -171,6 +173,7 @@ struct hmm_stats_s {
   hmm::DevBuf mv_chunk;          // [n_chunks][NP*KS] float64
   hmm::DevBuf mv_rec;            // [M][NP*KS] float64
   hmm::DevBuf ext_mm;            // [M][NP][2] int32 ordered keys of the support min / max
+  bool hard = false;             // made by hmm_estep_viterbi: xi slots hold counts
   // cross-process exchange (hmm_stats_set_allreduce)
   hmm_allreduce_fn reduce_fn = nullptr;
   void* reduce_user = nullptr;
