@@ -442,7 +442,8 @@ hmm_status hmm_estep_stats(hmm_ctx ctx, hmm_model model, const hmm_batch* batch,
  * first states, so that hmm_mstep then runs the Baum-Welch M-step on these
  * hard weights.  The statistic record's log-likelihood entry holds the sum
  * of the paths' log-probabilities max_q log P(q, y), the objective that
- * Viterbi training does not decrease.  d_score [n_seq] (may be NULL)
+ * Viterbi training does not decrease, and hmm_stats_get reports the
+ * transition counts in place of the expected transitions.  d_score [n_seq] (may be NULL)
  * receives them per sequence.  The installed all-reduce (if any) runs as
  * after hmm_estep_stats. */
 hmm_status hmm_estep_viterbi(hmm_ctx ctx, hmm_model model, const hmm_batch* batch, hmm_stats stats,

@@ -1059,7 +1059,13 @@ void prepare_mstep(hmm_model model, hmm_stats stats, const hmm_batch* b, hmm_pla
   stats->dp_part.ensure((size_t)std::max<int64_t>(b->n_seq, 1) * RS * 4);
   stats->dp_chunk.ensure((size_t)std::max(plan ? plan->n_chunks : 0, 1) * RS * 8);
   stats->dp_rec.ensure((size_t)model->M * RS * 8);
-  if (model->any_negbin) stats->nb_d.ensure((size_t)model->M * model->NP * 2 * NB_YMAX * 4);
+  if (model->any_negbin) {
+    stats->nb_d.ensure((size_t)model->M * model->NP * 2 * NB_YMAX * 4);
+    stats->nb_hist.ensure((size_t)model->M * model->NP * NB_YMAX * 8);
+    stats->nb_tail.ensure((size_t)std::max<int64_t>(b->n_seq, 1));
+    HMM_CUDA(ensure_max_dyn_smem(reinterpret_cast<const void*>(nb_hist_kernel),
+                                 (size_t)model->NP * NB_YMAX * 8));
+  }
   stats->dp_count.ensure(64 * sizeof(int));
 }
 
@@ -1144,8 +1150,20 @@ void run_mstep(hmm_ctx ctx, hmm_model model, hmm_stats stats, const MStepOpts& o
   const unsigned blocks = (unsigned)((S * 32 + 255) / 256);
   const int nthr = model->M * NP;
   KTimer kt(ctx, HMM_KT_MSTEP, st);
-  kt.kernels = 2 + (passes + 1) * ((int)model->any_negbin + (S > 0 ? 3 + (plan->n_chunks > 0) : 1));
+  kt.kernels = 2 + (passes + 1) * (2 * (int)model->any_negbin + (S > 0 ? 3 + (plan->n_chunks > 0) : 1));
   prepare_mstep(model, stats, b, plan);
+  if (model->any_negbin && S > 0) {   // weighted histograms of the small counts, once per M-step
+    HMM_CUDA(cudaMemsetAsync(stats->nb_hist.p, 0, (size_t)model->M * NP * NB_YMAX * 8, st));
+    HMM_CUDA(cudaMemsetAsync(stats->nb_tail.p, 0, (size_t)S, st));
+    if (plan->n_chunks > 0) {
+      nb_hist_kernel<<<plan->n_chunks, 256, (size_t)NP * NB_YMAX * 8, st>>>(
+          model->bufs(), b->values, stats->gamma.as<float>(), b->offsets, b->model_id,
+          plan->seq_by_model.as<int32_t>(), plan->chunk_lo.as<int32_t>(), plan->chunk_hi.as<int32_t>(),
+          stats->nb_hist.as<unsigned long long>(), stats->nb_tail.as<uint8_t>());
+      HMM_CUDA(cudaGetLastError());
+    }
+    kt.kernels += 3;
+  }
   // active-state counters, one per pass (the update of pass p fills p + 1);
   // passes with no active state return at once
   int* cnt = stats->dp_count.as<int>();
@@ -1159,8 +1177,8 @@ void run_mstep(hmm_ctx ctx, hmm_model model, hmm_stats stats, const MStepOpts& o
     }
     if (S > 0) {
       dp_sums_kernel<<<blocks, 256, 0, st>>>(model->bufs(), b->values, stats->gamma.as<float>(), b->offsets,
-                                             b->model_id, (int)S, dps, stats->nb_d.as<float>(), cnt + it,
-                                             stats->dp_part.as<float>());
+                                             b->model_id, (int)S, dps, stats->nb_d.as<float>(),
+                                             stats->nb_tail.as<uint8_t>(), cnt + it, stats->dp_part.as<float>());
       HMM_CUDA(cudaGetLastError());
       if (plan->n_chunks > 0) {
         reduce_records_l1<<<plan->n_chunks, 128, 0, st>>>(stats->dp_part.as<float>(), RS,
@@ -1172,6 +1190,13 @@ void run_mstep(hmm_ctx ctx, hmm_model model, hmm_stats stats, const MStepOpts& o
       reduce_chunks_l2<<<model->M, 128, 0, st>>>(stats->dp_chunk.as<double>(), plan->model_chunk_ptr.as<int32_t>(),
                                                  RS, stats->dp_rec.as<double>());
       HMM_CUDA(cudaGetLastError());
+      if (model->any_negbin) {   // the histogram rows of the negative-binomial sums
+        const int nw = model->M * NP;
+        nb_histdot_kernel<<<(unsigned)((nw * 32 + 255) / 256), 256, 0, st>>>(
+            model->bufs(), dps, cnt + it, stats->nb_d.as<float>(), stats->nb_hist.as<unsigned long long>(),
+            stats->dp_rec.as<double>());
+        HMM_CUDA(cudaGetLastError());
+      }
     } else {
       HMM_CUDA(cudaMemsetAsync(stats->dp_rec.p, 0, (size_t)model->M * RS * 8, st));
     }
@@ -1988,7 +2013,7 @@ hmm_status hmm_stats_destroy(hmm_stats stats) {
     if (!stats) return;
     for (auto* bb : {&stats->rec, &stats->gamma, &stats->dps, &stats->dp_part, &stats->dp_chunk, &stats->dp_rec,
                      &stats->nb_d, &stats->dp_count, &stats->mv_part, &stats->mv_chunk, &stats->mv_rec,
-                     &stats->ext_mm})
+                     &stats->ext_mm, &stats->nb_hist, &stats->nb_tail})
       bb->release();
     delete stats;
   });
@@ -2083,9 +2108,9 @@ hmm_status hmm_stats_get(hmm_stats stats, double* h_out, int64_t n_values) {
       *q++ = R[0];
       *q++ = R[1];
       for (int j = 0; j < N; ++j) *q++ = R[rec_g1(NP) + j];
-      for (int i = 0; i < N; ++i)
+      for (int i = 0; i < N; ++i)   // expected transitions a_ij X_ij (counts after hmm_estep_viterbi)
         for (int j = 0; j < N; ++j)
-          *q++ = A[((size_t)m * NP + i) * NP + j] * R[rec_xi(NP) + i * NP + j];
+          *q++ = (stats->hard ? 1.0 : A[((size_t)m * NP + i) * NP + j]) * R[rec_xi(NP) + i * NP + j];
       const int fam = md->h_family[m];
       for (int j = 0; j < N; ++j) {
         const double* St = R + rec_st(NP) + j * (NST - 1);

@@ -497,10 +497,15 @@ __global__ void mstep_kernel(ModelBufs mb, const double* __restrict__ rec, MStep
 // TPW consecutive occupancy rows per iteration; the TPW partial sums of a
 // state are combined with shuffles at the end.  Nothing runs once no state
 // of any model is active (count in *active_count).
+// Negative binomial: the rows with integer y < NB_YMAX enter through the
+// weighted histograms of nb_hist_kernel (sum_t gamma_t(j) f(y_t) =
+// sum_y h_j(y) f(y), nb_histdot_kernel), so the passes read only the
+// sequences that hold larger counts (tail[s] != 0) and add only those rows.
 __global__ void dp_sums_kernel(ModelBufs mb, const float* __restrict__ y, const float* __restrict__ gamma,
                                const int64_t* __restrict__ offsets, const int32_t* __restrict__ model_id,
                                int n_seq, const DPState* __restrict__ dps, const float* __restrict__ nbd,
-                               const int* __restrict__ active_count, float* __restrict__ part) {
+                               const uint8_t* __restrict__ tail, const int* __restrict__ active_count,
+                               float* __restrict__ part) {
   if (*active_count == 0) return;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
@@ -512,7 +517,7 @@ __global__ void dp_sums_kernel(ModelBufs mb, const float* __restrict__ y, const 
   const int m = model_id[s];
   const int fam = mb.family[m];
   float* out = part + (size_t)s * NP * 3;
-  const bool dpf = (fam == HMM_WEIBULL || fam == HMM_NEGBIN);
+  const bool dpf = fam == HMM_WEIBULL || (fam == HMM_NEGBIN && tail[s] != 0);
   const DPState* d = dps + (size_t)m * NP;
   const bool mine = dpf && k < N && tt < TPW && d[k].active != 0;
   const bool any = __any_sync(0xffffffffu, mine);
@@ -557,11 +562,8 @@ __global__ void dp_sums_kernel(ModelBufs mb, const float* __restrict__ y, const 
         const float g = gamma[t * N + k];
         const float yy = y[t];
         const int yi = (int)fminf(yy, 2.0e9f);
-        float d1, d2;
-        if (yi < NB_YMAX) {
-          d1 = __ldg(T1 + yi);
-          d2 = __ldg(T2 + yi);
-        } else {
+        float d1 = 0.f, d2 = 0.f;   // rows below NB_YMAX: in the histogram
+        if (yi >= NB_YMAX && g > 0.f) {
           d1 = digamma_f(yy + x) - digamma_f(x);
           d2 = trigamma_f(yy + x) - trigamma_f(x);
         }
@@ -615,6 +617,84 @@ __global__ void nb_table_kernel(ModelBufs mb, const DPState* __restrict__ dps, c
     d2 -= 1.0 / (x * x);
     T1[y] = (float)d1;
     T2[y] = (float)d2;
+  }
+}
+
+// Occupancy-weighted histograms of the integer observations below NB_YMAX
+// per negative-binomial state, H[m][NP][NB_YMAX]: fixed-point sums (2^32
+// units of gamma, unsigned 64-bit), so that the atomic additions are exact
+// and the result does not depend on their order.  One block per chunk of
+// the model-sorted sequence list; a shared-memory histogram (dynamic:
+// NP * NB_YMAX * 8 bytes) is flushed once per block.  tail[s] = 1 marks the
+// sequences holding a count >= NB_YMAX.
+constexpr double NB_HIST_ONE = 4294967296.0;
+__global__ void nb_hist_kernel(ModelBufs mb, const float* __restrict__ y, const float* __restrict__ gamma,
+                               const int64_t* __restrict__ offsets, const int32_t* __restrict__ model_id,
+                               const int32_t* __restrict__ seq_by_model, const int32_t* __restrict__ chunk_lo,
+                               const int32_t* __restrict__ chunk_hi, unsigned long long* __restrict__ H,
+                               uint8_t* __restrict__ tail) {
+  extern __shared__ unsigned long long hsh[];
+  const int c = blockIdx.x;
+  const int lo = chunk_lo[c], hi = chunk_hi[c];
+  if (lo >= hi) return;
+  const int m = model_id[seq_by_model[lo]];
+  if (mb.family[m] != HMM_NEGBIN) return;
+  const int NP = mb.NP, N = mb.N;
+  for (int z = threadIdx.x; z < NP * NB_YMAX; z += blockDim.x) hsh[z] = 0ull;
+  __syncthreads();
+  for (int q = lo; q < hi; ++q) {
+    const int s = seq_by_model[q];
+    const int64_t b = offsets[s], e = offsets[s + 1];
+    bool big = false;
+    for (int64_t idx = threadIdx.x; idx < (e - b) * N; idx += blockDim.x) {
+      const int64_t t = b + idx / N;
+      const int k = (int)(idx % N);
+      const float yy = y[t];
+      if (!is_count(yy)) continue;   // density 0: no occupancy
+      if (yy >= (float)NB_YMAX) {
+        big = true;
+        continue;
+      }
+      const float g = gamma[t * N + k];
+      if (g > 0.f) atomicAdd(&hsh[k * NB_YMAX + (int)yy], (unsigned long long)llrint((double)g * NB_HIST_ONE));
+    }
+    if (big) tail[s] = 1;
+  }
+  __syncthreads();
+  unsigned long long* Hm = H + (size_t)m * NP * NB_YMAX;
+  for (int z = threadIdx.x; z < NP * NB_YMAX; z += blockDim.x)
+    if (hsh[z]) atomicAdd(&Hm[z], hsh[z]);
+}
+
+// Histogram part of one data pass: for every active negative-binomial state
+// sum_y h(y) [psi(y + r) - psi(r)] and sum_y h(y) [psi'(y + r) - psi'(r)]
+// (the tables of nb_table_kernel), added to the pass's reduced sums.  One
+// warp per (model, state), fixed-order lane sums: deterministic.
+__global__ void nb_histdot_kernel(ModelBufs mb, const DPState* __restrict__ dps,
+                                  const int* __restrict__ active_count, const float* __restrict__ nbd,
+                                  const unsigned long long* __restrict__ H, double* __restrict__ dp_rec) {
+  if (*active_count == 0) return;
+  const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (w >= mb.M * mb.NP) return;
+  const int m = w / mb.NP, k = w % mb.NP;
+  if (k >= mb.N || mb.family[m] != HMM_NEGBIN || !dps[w].active) return;
+  const float* T1 = nbd + (size_t)w * 2 * NB_YMAX;
+  const float* T2 = T1 + NB_YMAX;
+  const unsigned long long* h = H + (size_t)w * NB_YMAX;
+  double a1 = 0.0, a2 = 0.0;
+  for (int yv = lane; yv < NB_YMAX; yv += 32) {
+    const double hv = (double)h[yv];
+    a1 += hv * (double)T1[yv];
+    a2 += hv * (double)T2[yv];
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    a1 += __shfl_xor_sync(0xffffffffu, a1, o);
+    a2 += __shfl_xor_sync(0xffffffffu, a2, o);
+  }
+  if (lane == 0) {
+    double* R = dp_rec + (size_t)m * mb.NP * 3 + k * 3;
+    R[0] += a1 / NB_HIST_ONE;
+    R[1] += a2 / NB_HIST_ONE;
   }
 }
 

@@ -339,3 +339,23 @@ def test_length_one_sequences_after_other_work(H, ctx):
     assert np.all(rec[2 + N:2 + N + N * N] == 0.0)
     fb = [O.forward_backward(om(models[0]), values[offsets[s]:offsets[s + 1]])["logL"] for s in range(40)]
     check_ll(ll.cpu().numpy(), np.array(fb))
+
+
+def test_negbin_mstep_with_counts_above_the_histogram(H, ctx):
+    """Negative-binomial states whose counts straddle the histogram range
+    (means 20 and 700): the M-step's Newton sums combine the weighted
+    histogram of the small counts with the data pass over the large ones."""
+    rng = np.random.default_rng(5)
+    r = np.array([5.0, 30.0])
+    mean = np.array([20.0, 700.0])
+    truth = [synth.make_model("negbin", np.array([0.5, 0.5]), np.array([[0.9, 0.1], [0.2, 0.8]]),
+                              r=r, p=r / (r + mean))]
+    values, offsets, mid = synth.make_batch(6, truth, [400, 250, 31, 500], [0, 0, 0, 0])
+    assert (values >= 512).any() and (values < 512).any()
+    init = [synth.perturb(rng, truth[0])]
+    model = H.Model(ctx, init)
+    batch = H.Batch(values, offsets, mid)
+    stats, _ = H.estep_stats(ctx, model, batch)
+    H.mstep(ctx, model, stats, batch=batch)
+    ref, _ = O.em_iteration([om(m) for m in init], values, offsets, mid)
+    assert_params_close(model.get(), ref)
