@@ -272,6 +272,27 @@ hmm_status hmm_model_set_params(hmm_model model, const double* h_blob, int64_t n
 /* Copies the current parameters back (synchronises the model's last stream). */
 hmm_status hmm_model_get_params(hmm_model model, double* h_blob, int64_t n_values);
 
+/* k-means++ seeding and Lloyd iterations for R restarts at once, on the
+ * device (the initialisation the paper names for Baum-Welch, Sec. 4.5,
+ * without constants; the rules are the library's reading).  d_x [T][F]
+ * float32 features (device, caller-owned); distances, sums and centres are
+ * float64.  h_u [R][K] (host) uniforms in [0, 1) drawn by the caller: the
+ * first centre of restart r is observation floor(u[r][0] T), centre j the
+ * first observation whose running sum of D2 (squared distance to the
+ * nearest centre so far) exceeds u[r][j] times the total (total 0:
+ * floor(u[r][j] T)).  Then at most max_iter Lloyd passes: every observation
+ * to its nearest centre (lowest index at ties), every non-empty cluster's
+ * centre to the mean of its observations, until a pass changes no
+ * assignment.  Outputs: d_centres [R][K][F] float64, d_labels [R][T] int32
+ * (the last pass's assignments; untouched when max_iter is 0) and h_passes
+ * [R] (host, may be NULL) the assignment passes run.  1 <= F <= 16,
+ * 1 <= K <= 64, 1 <= R <= 65535; HMM_E_ARG otherwise or for a uniform
+ * outside [0, 1).  Results are bitwise reproducible.  Synchronises
+ * `stream` every 8 passes to stop once every restart has converged. */
+hmm_status hmm_kmeans(hmm_ctx ctx, const float* d_x, int64_t T, int32_t F, int32_t K, int32_t R,
+                      const double* h_u, int32_t max_iter, double* d_centres, int32_t* d_labels,
+                      int32_t* h_passes, void* stream);
+
 /* ---------------------------------------------------------------- plans */
 /* Builds the schedule of a batch (processing order by family and length,
  * the per-model sequence lists used for the deterministic reductions).

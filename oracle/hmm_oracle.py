@@ -1091,3 +1091,49 @@ def brute_force(logpi, logA, logb):
     return dict(logL=logL, gamma=gamma, xi_sum=xi,
                 map_path=paths[best].astype(np.int32), map_score=float(lp[best]),
                 all_scores=lp, paths=paths)
+
+
+# --------------------------------------------------------------------------
+# k-means++ seeding and Lloyd iterations (Sec. 4.5 initialisation; the paper
+# gives no constants).  Reading: features are float32 values computed in
+# float64; the uniforms u_0..u_{K-1} in [0, 1) are inputs.  The first
+# centre is the observation floor(u_0 T); centre j is the first observation
+# i whose running sum of D2 (the squared distance to the nearest centre so
+# far) exceeds u_j times the total (if the total is 0: floor(u_j T)).  Lloyd
+# iterations assign every observation to its nearest centre (the lowest
+# index at ties) and move every non-empty cluster's centre to the mean of
+# its observations, until no assignment changes or max_iter assignment
+# passes.
+# --------------------------------------------------------------------------
+def kmeanspp(X, u, max_iter=100):
+    """Returns (centres [K, F] float64, labels [T] int32, assignment passes)."""
+    X = np.asarray(X, dtype=np.float64)
+    X = X[:, None] if X.ndim == 1 else X
+    T, F = X.shape
+    K = len(u)
+    C = np.empty((K, F))
+    C[0] = X[min(int(math.floor(u[0] * T)), T - 1)]
+    d2 = np.sum((X - C[0]) ** 2, axis=1)
+    for j in range(1, K):
+        tot = float(np.sum(d2))
+        if tot > 0:
+            cum = np.cumsum(d2)
+            i = int(np.searchsorted(cum, u[j] * tot, side="right"))
+            i = min(i, T - 1)
+        else:
+            i = min(int(math.floor(u[j] * T)), T - 1)
+        C[j] = X[i]
+        d2 = np.minimum(d2, np.sum((X - C[j]) ** 2, axis=1))
+    labels = None
+    passes = 0
+    for passes in range(1, max_iter + 1):
+        dist = np.sum((X[:, None, :] - C[None, :, :]) ** 2, axis=2)
+        new = np.argmin(dist, axis=1).astype(np.int32)     # first minimum: lowest index
+        if labels is not None and np.array_equal(new, labels):
+            break
+        labels = new
+        for j in range(K):
+            sel = labels == j
+            if sel.any():
+                C[j] = X[sel].mean(axis=0)
+    return C, labels, passes

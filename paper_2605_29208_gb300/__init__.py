@@ -297,6 +297,25 @@ def forward_backward_static(model, batch, gamma, loglik, logb=None, stream=None)
     return loglik, gamma
 
 
+def kmeans(ctx, X, u, max_iter=100, stream=None):
+    """hmm_kmeans: k-means++ seeding from the uniforms u [R][K] and Lloyd
+    iterations on the device for R restarts of the features X [T][F]
+    (float32, a torch tensor on the GPU or an array); returns (centres
+    [R][K][F] float64, labels [R][T] int32, passes [R])."""
+    torch = _torch()
+    X = torch.as_tensor(np.asarray(X, np.float32) if not torch.is_tensor(X) else X).to("cuda", torch.float32)
+    X = X.reshape(X.shape[0], -1).contiguous()
+    u = np.ascontiguousarray(np.atleast_2d(u), np.float64)
+    R, K = u.shape
+    T, F = X.shape
+    centres = torch.empty((R, K, F), dtype=torch.float64, device=X.device)
+    labels = torch.full((R, T), -1, dtype=torch.int32, device=X.device)
+    passes = np.zeros(R, np.int32)
+    check(ctx.lib.hmm_kmeans(ctx.h, _ptr(X), T, F, K, R, u.ctypes.data_as(C.c_void_p), max_iter, _ptr(centres),
+                             _ptr(labels), passes.ctypes.data_as(C.c_void_p), _stream(stream)))
+    return centres, labels, passes
+
+
 def viterbi(ctx, model, batch, logb=None, stream=None):
     torch = _torch()
     dev = batch.values.device

@@ -84,6 +84,8 @@ _SIGS = {
     "hmm_model_destroy": (C.c_int, [C.c_void_p]),
     "hmm_model_set_params": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64]),
     "hmm_model_get_params": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64]),
+    "hmm_kmeans": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int32, C.c_int32, C.c_int32, C.c_void_p,
+                             C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "hmm_plan_create": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(hmm_batch), C.c_void_p,
                                   C.c_void_p, C.POINTER(C.c_void_p)]),
     "hmm_plan_destroy": (C.c_int, [C.c_void_p]),

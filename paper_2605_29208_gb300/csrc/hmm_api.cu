@@ -1355,6 +1355,7 @@ hmm_status hmm_ctx_destroy(hmm_ctx ctx) {
     ctx->xi_yt.release();
     ctx->vt_path.release();
     ctx->vt_count.release();
+    for (auto* bb : {&ctx->km_u, &ctx->km_d2, &ctx->km_part, &ctx->km_flags}) bb->release();
     for (auto* bb : {&ctx->tp_Q, &ctx->tp_qexp, &ctx->tp_bvec, &ctx->tp_boff}) bb->release();
     delete ctx;
   });

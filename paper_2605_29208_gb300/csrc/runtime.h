@@ -109,6 +109,7 @@ struct hmm_ctx_s {
   hmm::DevBuf xi_xt, xi_yt;      // [NP][xi_ktot] float32 operands of the tensor-core xi
   hmm::DevBuf vt_path;           // [total_T] Viterbi paths of Viterbi training
   hmm::DevBuf vt_count;          // [n_chunks][NP][NP] int32 transition counts
+  hmm::DevBuf km_u, km_d2, km_part, km_flags;   // k-means++: uniforms, D2, block sums, flags
   // options
   int profile = 0;
   int estep_lanes = 0;

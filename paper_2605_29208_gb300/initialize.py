@@ -5,47 +5,61 @@ fixes one reading (it is an input to the fit, not a parity target, and both
 the CUDA path and the CPU checker receive its output as their starting
 model):
 
-* seeding: the first centre is a uniformly drawn observation, each further
-  centre an observation drawn with probability proportional to its squared
-  distance to the nearest centre so far (numpy ``default_rng(seed)``);
-* Lloyd iterations until no assignment changes or 100 iterations, ties to
-  the lowest cluster index, an empty cluster keeps its centre;
+* uniforms u_0..u_{N-1} from numpy ``default_rng(seed)``; the first centre
+  is observation floor(u_0 T), centre j the first observation whose running
+  sum of squared distances to the nearest centre so far exceeds u_j times
+  the total (floor(u_j T) when the total is 0);
+* Lloyd iterations until no assignment changes or 100 passes, ties to the
+  lowest cluster index, an empty cluster keeps its centre;
 * state j's emission from cluster j by moments (Gaussian mean / variance,
   Poisson mean, Gamma and Beta method of moments, ...), variances floored;
 * pi uniform, A from the label transitions inside each sequence with one
   added to every count (add-one smoothing), rows normalised.
 
-Host numpy: the initialisation runs once per fit.
+With a context the seeding and the Lloyd iterations run on the GPU
+(hmm_kmeans, every restart of ``kmeanspp_init_many`` in one call); without
+one, a host numpy version of the same rules runs.  The moments and the
+label transitions are host numpy over the labels.
 """
 from __future__ import annotations
+
+import math
 
 import numpy as np
 
 VAR_FLOOR = 1e-6
+MAX_ITER = 100
 
 
-def _kmeanspp(X, N, rng, max_iter=100):
+def _uniforms(seed, N):
+    return np.random.default_rng(seed).random(N)
+
+
+def _kmeanspp_host(X, u, max_iter=MAX_ITER):
     T = X.shape[0]
-    centres = np.empty((N, X.shape[1]))
-    centres[0] = X[rng.integers(T)]
-    d2 = np.sum((X - centres[0]) ** 2, axis=1)
-    for j in range(1, N):
-        tot = d2.sum()
-        i = rng.integers(T) if tot <= 0 else rng.choice(T, p=d2 / tot)
-        centres[j] = X[i]
-        d2 = np.minimum(d2, np.sum((X - centres[j]) ** 2, axis=1))
+    K = len(u)
+    C = np.empty((K, X.shape[1]))
+    C[0] = X[min(int(math.floor(u[0] * T)), T - 1)]
+    d2 = np.sum((X - C[0]) ** 2, axis=1)
+    for j in range(1, K):
+        tot = float(d2.sum())
+        if tot > 0:
+            i = min(int(np.searchsorted(np.cumsum(d2), u[j] * tot, side="right")), T - 1)
+        else:
+            i = min(int(math.floor(u[j] * T)), T - 1)
+        C[j] = X[i]
+        d2 = np.minimum(d2, np.sum((X - C[j]) ** 2, axis=1))
     labels = None
     for _ in range(max_iter):
-        dist = np.sum((X[:, None, :] - centres[None, :, :]) ** 2, axis=2)
-        new = np.argmin(dist, axis=1)            # first minimum: lowest cluster
+        new = np.argmin(np.sum((X[:, None, :] - C[None, :, :]) ** 2, axis=2), axis=1)
         if labels is not None and np.array_equal(new, labels):
             break
         labels = new
-        for j in range(N):
+        for j in range(K):
             sel = labels == j
             if sel.any():
-                centres[j] = X[sel].mean(axis=0)
-    return centres, labels
+                C[j] = X[sel].mean(axis=0)
+    return C, labels
 
 
 def _state_params(family, x, D):
@@ -86,22 +100,23 @@ def _state_params(family, x, D):
     raise ValueError(family)
 
 
-def kmeanspp_init(family, N, values, offsets, seed=0):
-    """Starting model dict for `family` with N states from the packed
-    observations (values [total_T] or [total_T, D], offsets [S+1])."""
-    rng = np.random.default_rng(seed)
+def _features(family, values):
     X = np.asarray(values, np.float64)
     X = X[:, None] if X.ndim == 1 else X
-    D = X.shape[1]
     feat = X
     if family == "vonmises":        # cluster angles on the unit circle
         feat = np.stack([np.cos(X[:, 0]), np.sin(X[:, 0])], axis=1)
-    centres, labels = _kmeanspp(feat, N, rng)
+    # the device clusters float32 features: round them once for both routes
+    return X, feat.astype(np.float32).astype(np.float64)
+
+
+def _model_from_labels(family, N, X, centres, labels, offsets):
+    D = X.shape[1]
     # order the states by their first centre coordinate (a stable labelling)
     order = np.argsort(centres[:, 0], kind="stable")
     rank = np.empty(N, np.int64)
     rank[order] = np.arange(N)
-    labels = rank[labels]
+    labels = rank[np.asarray(labels, np.int64)]
     per = [_state_params(family, X[labels == j], D) for j in range(N)]
     params = {k: np.array([p[k] for p in per]) for k in per[0]}
     counts = np.ones((N, N))
@@ -112,3 +127,25 @@ def kmeanspp_init(family, N, values, offsets, seed=0):
             np.add.at(counts, (lab[:-1], lab[1:]), 1.0)
     A = counts / counts.sum(axis=1, keepdims=True)
     return dict(family=family, pi=np.full(N, 1.0 / N), A=A, params=params)
+
+
+def kmeanspp_init_many(ctx, family, N, values, offsets, seeds):
+    """Starting models of several restarts (one per seed) with one device
+    k-means++ call for all of them (hmm_kmeans)."""
+    from . import kmeans
+    X, feat = _features(family, values)
+    u = np.stack([_uniforms(s, N) for s in seeds])
+    C, lab, _ = kmeans(ctx, feat.astype(np.float32), u, max_iter=MAX_ITER)
+    C, lab = C.cpu().numpy(), lab.cpu().numpy()
+    return [_model_from_labels(family, N, X, C[r], lab[r], offsets) for r in range(len(seeds))]
+
+
+def kmeanspp_init(family, N, values, offsets, seed=0, ctx=None):
+    """Starting model dict for `family` with N states from the packed
+    observations (values [total_T] or [total_T, D], offsets [S+1]); on the
+    GPU when a context is given."""
+    if ctx is not None:
+        return kmeanspp_init_many(ctx, family, N, values, offsets, [seed])[0]
+    X, feat = _features(family, values)
+    centres, labels = _kmeanspp_host(feat, _uniforms(seed, N))
+    return _model_from_labels(family, N, X, centres, labels, offsets)

@@ -6,7 +6,8 @@ Every restart (and every candidate state count) is its own model of one
 multi-model batch: the observations are repeated once per model with that
 model's id, so all restarts run in the same kernel launches as independent
 problems (the E-step, M-step and Viterbi kernels treat models separately).
-Each restart starts from k-means++ with its own seed (host, once per fit);
+Each restart starts from k-means++ with its own seed (all restarts in one
+device k-means++ call);
 after the fit, one forward pass gives every model's final log-likelihood,
 and the library's hmm_information_criteria scores it.
 """
@@ -15,7 +16,7 @@ from __future__ import annotations
 import numpy as np
 
 from . import Batch, Model, forward_backward, fit, information_criteria
-from .initialize import kmeanspp_init
+from .initialize import kmeanspp_init_many
 
 
 def _replicate(values, offsets, R):
@@ -34,7 +35,7 @@ def fit_restarts(ctx, family, n_states, values, offsets, n_restarts=8, n_iter=20
     of each restart); the best restart is the one with the largest
     log-likelihood (the criteria order restarts of one state count alike)."""
     R = int(n_restarts)
-    inits = [kmeanspp_init(family, n_states, values, offsets, seed=seed + r) for r in range(R)]
+    inits = kmeanspp_init_many(ctx, family, n_states, values, offsets, [seed + r for r in range(R)])
     vals, offs, mid = _replicate(values, offsets, R)
     model = Model(ctx, inits)
     batch = Batch(vals, offs, mid, dim=dim).make_plan(ctx, model)

@@ -25,8 +25,8 @@ def H():
 
 def test_tiny_gauss_fit_and_decode(H):
     truth, values, offsets, mid = synth.tiny_gauss()
-    init = initialize.kmeanspp_init("gauss", 2, values, offsets, seed=0)
     ctx = H.Context(0)
+    init = initialize.kmeanspp_init("gauss", 2, values, offsets, seed=0, ctx=ctx)
     model = H.Model(ctx, [init])
     batch = H.Batch(values, offsets, mid)
     trace, (ref_models, ref_trace) = check_fit_iterations(H, ctx, model, batch, values, offsets, mid, 20)

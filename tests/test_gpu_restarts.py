@@ -37,7 +37,7 @@ def test_restarts_match_the_oracle(H):
     models, ll, crit = restarts.fit_restarts(ctx, "gauss", 3, values, offsets, n_restarts=3, n_iter=5, seed=7)
     mid = np.zeros(len(offsets) - 1, np.int32)
     for r in range(3):
-        init = kmeanspp_init("gauss", 3, values, offsets, seed=7 + r)
+        init = kmeanspp_init("gauss", 3, values, offsets, seed=7 + r, ctx=ctx)
         ref, _ = O.fit([O.Model("gauss", init["pi"], init["A"], init["params"])], values, offsets, mid, 5)
         ref_ll = O.batch_loglik(ref, values, offsets, mid).sum()
         assert abs(ll[r] - ref_ll) <= 1e-5 * abs(ref_ll)
