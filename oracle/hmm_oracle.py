@@ -57,6 +57,9 @@ NU_TOL = 1e-6                # Sec. 4.3: |d nu| < 1e-6 stops the nu Newton
 NU_MIN, NU_MAX = 0.5, 1e4    # reading: nu kept in [0.5, 1e4]
 NEGBIN_RMAX = 1e6            # reading: no finite MLE when var <= mean
 KAPPA_MAX = 1e6              # reading: R -> 1 gives kappa -> inf
+VAR_RESOLUTION = 1e-6        # reading 14: a variance below this fraction of the
+                             # weighted mean square deviation from the current
+                             # location counts as zero (an undefined update)
 
 FAMILIES = ("gauss", "poisson", "gamma", "beta", "weibull", "negbin",
             "student_t", "vonmises", "diag_gauss", "full_gauss", "discrete",
@@ -499,6 +502,8 @@ def mstep_gauss(w, y, cur):
     Nj = w.sum()
     mu = np.sum(w * y) / Nj
     s2 = np.sum(w * (y - mu) ** 2) / Nj
+    if s2 <= VAR_RESOLUTION * np.sum(w * (y - cur.get("mu", mu)) ** 2) / Nj:
+        s2 = 0.0                    # e.g. one observation: undefined, theta_j kept
     return dict(mu=mu, sigma2=s2)
 
 
@@ -668,6 +673,8 @@ def mstep_student_t(w, y, cur, nu_mode="ecm"):
     wu = w * u
     mu = np.sum(wu * y) / np.sum(wu)                      # Eq. 15
     s2 = np.sum(wu * (y - mu) ** 2) / Nj                  # Eq. 16
+    if s2 <= VAR_RESOLUTION * np.sum(wu * (y - mu0) ** 2) / Nj:
+        s2 = 0.0                    # reading 14: undefined, theta_j kept
     C = np.sum(w * (np.log(u) - u))
     if nu_mode == "ecm":
         C += Nj * (digamma((nu0 + 1) / 2) - np.log((nu0 + 1) / 2))
@@ -722,7 +729,10 @@ def mstep_lognormal(w, y, cur):
     Nj = w.sum()
     ly = _safe_log(y)
     mu = np.sum(w * ly) / Nj
-    return dict(mu=mu, sigma2=np.sum(w * (ly - mu) ** 2) / Nj)
+    s2 = np.sum(w * (ly - mu) ** 2) / Nj
+    if s2 <= VAR_RESOLUTION * np.sum(w * (ly - cur.get("mu", mu)) ** 2) / Nj:
+        s2 = 0.0                    # reading 14: undefined, theta_j kept
+    return dict(mu=mu, sigma2=s2)
 
 
 def mstep_exponential(w, y, cur):

@@ -122,9 +122,9 @@ __global__ void ext_mstep_kernel(const int* __restrict__ family, double* __restr
   double nt[2] = {th[0], P > 1 ? th[1] : 0.0};
   switch (fam) {
     case HMM_LOGNORMAL: {                             // Gaussian M-step on log y
-      const double mu = R[1] / W;
+      const double mu = R[1] / W, m0 = th[0];
       nt[0] = mu;
-      nt[1] = R[2] / W - mu * mu;
+      nt[1] = resolved_var(R[2] / W - mu * mu, R[2] / W - 2.0 * m0 * R[1] / W + m0 * m0);
       break;
     }
     case HMM_EXPONENTIAL: nt[0] = W / R[1]; break;    // 1 / ybar

@@ -930,6 +930,13 @@ void run_estep(hmm_ctx ctx, hmm_model model, const hmm_batch* b, hmm_plan plan, 
     pa.beta = ctx->plain_beta.as<float>();
     pa.partials = ctx->partials.as<float>();
     pa.loglik = ll;
+    pa.gamma = nullptr;
+    if (want_stats && stats && (model->any_negbin || model->any_weibull)) {
+      // the data-pass M-steps re-read the occupancies of this E-step
+      stats->gamma.ensure(std::max<int64_t>(b->total_T, 1) * model->N * 4);
+      stats->gamma_T = b->total_T;
+      pa.gamma = stats->gamma.as<float>();
+    }
     {
       KTimer kt(ctx, HMM_KT_PLAIN, st);
       kt.kernels = 2;
@@ -1060,7 +1067,6 @@ void prepare_mstep(hmm_model model, hmm_stats stats, const hmm_batch* b, hmm_pla
   stats->dp_chunk.ensure((size_t)std::max(plan ? plan->n_chunks : 0, 1) * RS * 8);
   stats->dp_rec.ensure((size_t)model->M * RS * 8);
   if (model->any_negbin) {
-    stats->nb_d.ensure((size_t)model->M * model->NP * 2 * NB_YMAX * 4);
     stats->nb_hist.ensure((size_t)model->M * model->NP * NB_YMAX * 8);
     stats->nb_tail.ensure((size_t)std::max<int64_t>(b->n_seq, 1));
     HMM_CUDA(ensure_max_dyn_smem(reinterpret_cast<const void*>(nb_hist_kernel),
@@ -1150,7 +1156,7 @@ void run_mstep(hmm_ctx ctx, hmm_model model, hmm_stats stats, const MStepOpts& o
   const unsigned blocks = (unsigned)((S * 32 + 255) / 256);
   const int nthr = model->M * NP;
   KTimer kt(ctx, HMM_KT_MSTEP, st);
-  kt.kernels = 2 + (passes + 1) * (2 * (int)model->any_negbin + (S > 0 ? 3 + (plan->n_chunks > 0) : 1));
+  kt.kernels = 2 + (passes + 1) * ((int)model->any_negbin + (S > 0 ? 3 + (plan->n_chunks > 0) : 1));
   prepare_mstep(model, stats, b, plan);
   if (model->any_negbin && S > 0) {   // weighted histograms of the small counts, once per M-step
     HMM_CUDA(cudaMemsetAsync(stats->nb_hist.p, 0, (size_t)model->M * NP * NB_YMAX * 8, st));
@@ -1171,14 +1177,10 @@ void run_mstep(hmm_ctx ctx, hmm_model model, hmm_stats stats, const MStepOpts& o
   dp_count_kernel<<<(nthr + 127) / 128, 128, 0, st>>>(dps, nthr, cnt);
   HMM_CUDA(cudaGetLastError());
   for (int it = 0; it <= passes; ++it) {
-    if (model->any_negbin) {
-      nb_table_kernel<<<(nthr + 127) / 128, 128, 0, st>>>(model->bufs(), dps, cnt + it, stats->nb_d.as<float>());
-      HMM_CUDA(cudaGetLastError());
-    }
     if (S > 0) {
       dp_sums_kernel<<<blocks, 256, 0, st>>>(model->bufs(), b->values, stats->gamma.as<float>(), b->offsets,
-                                             b->model_id, (int)S, dps, stats->nb_d.as<float>(),
-                                             stats->nb_tail.as<uint8_t>(), cnt + it, stats->dp_part.as<float>());
+                                             b->model_id, (int)S, dps, stats->nb_tail.as<uint8_t>(), cnt + it,
+                                             stats->dp_part.as<float>());
       HMM_CUDA(cudaGetLastError());
       if (plan->n_chunks > 0) {
         reduce_records_l1<<<plan->n_chunks, 128, 0, st>>>(stats->dp_part.as<float>(), RS,
@@ -1193,8 +1195,7 @@ void run_mstep(hmm_ctx ctx, hmm_model model, hmm_stats stats, const MStepOpts& o
       if (model->any_negbin) {   // the histogram rows of the negative-binomial sums
         const int nw = model->M * NP;
         nb_histdot_kernel<<<(unsigned)((nw * 32 + 255) / 256), 256, 0, st>>>(
-            model->bufs(), dps, cnt + it, stats->nb_d.as<float>(), stats->nb_hist.as<unsigned long long>(),
-            stats->dp_rec.as<double>());
+            model->bufs(), dps, cnt + it, stats->nb_hist.as<unsigned long long>(), stats->dp_rec.as<double>());
         HMM_CUDA(cudaGetLastError());
       }
     } else {
@@ -2013,7 +2014,7 @@ hmm_status hmm_stats_destroy(hmm_stats stats) {
   return guarded([&] {
     if (!stats) return;
     for (auto* bb : {&stats->rec, &stats->gamma, &stats->dps, &stats->dp_part, &stats->dp_chunk, &stats->dp_rec,
-                     &stats->nb_d, &stats->dp_count, &stats->mv_part, &stats->mv_chunk, &stats->mv_rec,
+                     &stats->dp_count, &stats->mv_part, &stats->mv_chunk, &stats->mv_rec,
                      &stats->ext_mm, &stats->nb_hist, &stats->nb_tail})
       bb->release();
     delete stats;

@@ -260,7 +260,7 @@ __global__ void indep_mstep_kernel(const int* __restrict__ icomp, const float* _
     case HMM_LOGNORMAL: {
       const double d1 = S[0] / W;
       nt[0] = c + d1;
-      nt[1] = S[1] / W - d1 * d1;
+      nt[1] = resolved_var(S[1] / W - d1 * d1, S[1] / W);
       break;
     }
     case HMM_POISSON: nt[0] = S[0] / W; break;
@@ -281,7 +281,7 @@ __global__ void indep_mstep_kernel(const int* __restrict__ icomp, const float* _
     case HMM_STUDENT_T: {   // Eq. 15-19 with u from the current parameters
       const double d1 = S[1] / S[0];
       nt[0] = c + d1;
-      nt[1] = (S[2] - S[1] * d1) / W;
+      nt[1] = resolved_var((S[2] - S[1] * d1) / W, S[2] / W);
       nt[2] = student_nu(W, S[3], th[2], o);
       break;
     }

@@ -342,6 +342,14 @@ __device__ inline double student_nu(double W, double C, double nu0, const MStepO
   return nu;
 }
 
+// A weighted variance var from float32 sums about the current location
+// (msd = the weighted mean square deviation from it): below 1e-6 msd it is
+// not resolvable and counts as zero, an undefined update (one observation,
+// or all weight on equal values); the oracle applies the same rule.
+__host__ __device__ inline double resolved_var(double var, double msd) {
+  return var > 1e-6 * msd ? var : 0.0;
+}
+
 // Domain check of a closed-form / Newton update (data-pass families are
 // checked when their passes finish).
 __device__ inline bool valid_update(int fam, const double* th) {
@@ -387,7 +395,7 @@ __global__ void mstep_kernel(ModelBufs mb, const double* __restrict__ rec, MStep
         case HMM_GAUSS: {
           const double d1 = S[1] / W;
           th[0] = (double)cf[0] + d1;
-          th[1] = fmax(S[2] / W - d1 * d1, 0.0);
+          th[1] = resolved_var(S[2] / W - d1 * d1, S[2] / W);
           break;
         }
         case HMM_POISSON:
@@ -411,7 +419,7 @@ __global__ void mstep_kernel(ModelBufs mb, const double* __restrict__ rec, MStep
           const double d1 = Sud / Su;
           const double nu0 = th[2];
           th[0] = (double)cf[0] + d1;                 // Eq. 15
-          th[1] = (Sud2 - Sud * d1) / W;              // Eq. 16 (divides by N_j)
+          th[1] = resolved_var((Sud2 - Sud * d1) / W, Sud2 / W);   // Eq. 16 (divides by N_j)
           th[2] = student_nu(W, S[4], nu0, o);        // Eq. 18-19
           break;
         }
@@ -503,8 +511,8 @@ __global__ void mstep_kernel(ModelBufs mb, const double* __restrict__ rec, MStep
 // sequences that hold larger counts (tail[s] != 0) and add only those rows.
 __global__ void dp_sums_kernel(ModelBufs mb, const float* __restrict__ y, const float* __restrict__ gamma,
                                const int64_t* __restrict__ offsets, const int32_t* __restrict__ model_id,
-                               int n_seq, const DPState* __restrict__ dps, const float* __restrict__ nbd,
-                               const uint8_t* __restrict__ tail, const int* __restrict__ active_count,
+                               int n_seq, const DPState* __restrict__ dps, const uint8_t* __restrict__ tail,
+                               const int* __restrict__ active_count,
                                float* __restrict__ part) {
   if (*active_count == 0) return;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -554,10 +562,8 @@ __global__ void dp_sums_kernel(ModelBufs mb, const float* __restrict__ y, const 
         }
       }
     } else {
-      // psi(y + r) - psi(r) and psi'(y + r) - psi'(r) from the float64-built
-      // per-state tables for y < NB_YMAX; float32 evaluation above (rare)
-      const float* T1 = nbd + ((size_t)m * NP + k) * 2 * NB_YMAX;
-      const float* T2 = T1 + NB_YMAX;
+      // psi(y + r) - psi(r) and psi'(y + r) - psi'(r) in float32 for the
+      // counts >= NB_YMAX (the smaller ones are in the histogram)
       for (int64_t t = b + tt; t < e; t += TPW) {
         const float g = gamma[t * N + k];
         const float yy = y[t];
@@ -591,32 +597,6 @@ __global__ void dp_sums_kernel(ModelBufs mb, const float* __restrict__ y, const 
     out[lane * 3 + 0] = a0;
     out[lane * 3 + 1] = a1;
     out[lane * 3 + 2] = a2;
-  }
-}
-
-// Tables of psi(y + r) - psi(r) and psi'(y + r) - psi'(r) for integer
-// y < NB_YMAX at the current iterate r of every active negative-binomial
-// state, by the float64 recurrences psi(x + 1) = psi(x) + 1/x and
-// psi'(x + 1) = psi'(x) - 1/x^2 (exact up to rounding), stored as float32.
-__global__ void nb_table_kernel(ModelBufs mb, const DPState* __restrict__ dps, const int* __restrict__ active_count,
-                                float* __restrict__ nbd) {
-  if (*active_count == 0) return;
-  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= mb.M * mb.NP) return;
-  const int m = idx / mb.NP, k = idx % mb.NP;
-  if (k >= mb.N || mb.family[m] != HMM_NEGBIN || !dps[idx].active) return;
-  const double r = dps[idx].x;
-  float* T1 = nbd + (size_t)idx * 2 * NB_YMAX;
-  float* T2 = T1 + NB_YMAX;
-  double d1 = 0.0, d2 = 0.0;
-  T1[0] = 0.f;
-  T2[0] = 0.f;
-  for (int y = 1; y < NB_YMAX; ++y) {
-    const double x = r + (double)(y - 1);
-    d1 += 1.0 / x;
-    d2 -= 1.0 / (x * x);
-    T1[y] = (float)d1;
-    T2[y] = (float)d2;
   }
 }
 
@@ -666,26 +646,50 @@ __global__ void nb_hist_kernel(ModelBufs mb, const float* __restrict__ y, const 
     if (hsh[z]) atomicAdd(&Hm[z], hsh[z]);
 }
 
-// Histogram part of one data pass: for every active negative-binomial state
+// Histogram part of one data pass for every active negative-binomial state:
 // sum_y h(y) [psi(y + r) - psi(r)] and sum_y h(y) [psi'(y + r) - psi'(r)]
-// (the tables of nb_table_kernel), added to the pass's reduced sums.  One
-// warp per (model, state), fixed-order lane sums: deterministic.
+// over y < NB_YMAX, in float64 from psi(y + r) - psi(r) = sum_{k<y} 1/(r + k)
+// and psi'(y + r) - psi'(r) = -sum_{k<y} 1/(r + k)^2 (the recurrences of the
+// digamma / trigamma functions), added to the pass's reduced sums.  One warp
+// per (model, state): lane l covers y in [16 l, 16 l + 16), an exclusive
+// scan of the lanes' increments gives each lane its starting sums; fixed
+// order throughout, so the result is deterministic.
+static_assert(NB_YMAX == 512, "the histogram dot assumes 16 counts per lane");
 __global__ void nb_histdot_kernel(ModelBufs mb, const DPState* __restrict__ dps,
-                                  const int* __restrict__ active_count, const float* __restrict__ nbd,
-                                  const unsigned long long* __restrict__ H, double* __restrict__ dp_rec) {
+                                  const int* __restrict__ active_count, const unsigned long long* __restrict__ H,
+                                  double* __restrict__ dp_rec) {
   if (*active_count == 0) return;
   const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   if (w >= mb.M * mb.NP) return;
   const int m = w / mb.NP, k = w % mb.NP;
   if (k >= mb.N || mb.family[m] != HMM_NEGBIN || !dps[w].active) return;
-  const float* T1 = nbd + (size_t)w * 2 * NB_YMAX;
-  const float* T2 = T1 + NB_YMAX;
+  const double r = dps[w].x;
+  const int y0 = lane * 16;
+  double l1 = 0.0, l2 = 0.0;
+  for (int i = 0; i < 16; ++i) {
+    const double x = r + (double)(y0 + i);
+    l1 += 1.0 / x;
+    l2 += 1.0 / (x * x);
+  }
+  double p1 = l1, p2 = l2;   // inclusive scan over the lanes
+  for (int o = 1; o < 32; o <<= 1) {
+    const double t1 = __shfl_up_sync(0xffffffffu, p1, o), t2 = __shfl_up_sync(0xffffffffu, p2, o);
+    if (lane >= o) {
+      p1 += t1;
+      p2 += t2;
+    }
+  }
+  double run1 = __shfl_up_sync(0xffffffffu, p1, 1), run2 = __shfl_up_sync(0xffffffffu, p2, 1);
+  if (lane == 0) run1 = run2 = 0.0;
   const unsigned long long* h = H + (size_t)w * NB_YMAX;
   double a1 = 0.0, a2 = 0.0;
-  for (int yv = lane; yv < NB_YMAX; yv += 32) {
-    const double hv = (double)h[yv];
-    a1 += hv * (double)T1[yv];
-    a2 += hv * (double)T2[yv];
+  for (int i = 0; i < 16; ++i) {
+    const double hv = (double)h[y0 + i];
+    a1 += hv * run1;
+    a2 -= hv * run2;
+    const double x = r + (double)(y0 + i);
+    run1 += 1.0 / x;
+    run2 += 1.0 / (x * x);
   }
   for (int o = 16; o > 0; o >>= 1) {
     a1 += __shfl_xor_sync(0xffffffffu, a1, o);

@@ -25,6 +25,7 @@ struct PlainArgs {
   float* beta;        // [total_T][NP] log2 beta-hat
   float* partials;    // [S][2][NP][NP + NST]
   double* loglik;     // [S]
+  float* gamma;       // [total_T][N] occupancies, or nullptr (kept for the data-pass M-steps)
 };
 
 // lse in base 2 over i of x[i] + c[i]
@@ -142,6 +143,7 @@ __global__ void __launch_bounds__(128) plain_posterior_kernel(PlainArgs a) {
     const Feat f = feat_of(fam, a.y[base + t], a.mv.lfact2);
     const float* ar = a.alpha + (base + t) * NP;
     const float g = ex2f(ar[j] + a.beta[(base + t) * NP + j] - ll2);
+    if (a.gamma && j < N) a.gamma[(base + t) * N + j] = g;
     st[0] += g;
     accumulate_stats(fam, f, c, c2, g, st);
     if (t == 0) st[NST - 1] += g;

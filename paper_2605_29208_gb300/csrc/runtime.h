@@ -168,7 +168,6 @@ struct hmm_stats_s {
   hmm::DevBuf dp_part;           // [S][NP][3] float32
   hmm::DevBuf dp_chunk;          // [n_chunks][NP*3] float64
   hmm::DevBuf dp_rec;            // [M][NP*3] float64
-  hmm::DevBuf nb_d;              // [M][NP][2][NB_YMAX] float32 digamma tables
   hmm::DevBuf nb_hist;           // [M][NP][NB_YMAX] u64 fixed-point occupancy histograms
   hmm::DevBuf nb_tail;           // [S] u8: the sequence holds a count >= NB_YMAX
   hmm::DevBuf dp_count;          // active-state counters of the passes

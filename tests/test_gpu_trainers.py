@@ -10,7 +10,7 @@ import pytest
 
 from oracle import hmm_oracle as O
 from paper_2605_29208_gb300 import synth
-from parity import LL_RTOL, PARAM_RTOL, assert_params_close, check_fit_iterations, om
+from parity import LL_RTOL, PARAM_RTOL, assert_params_close, check_viterbi_fp64, om
 
 pytestmark = pytest.mark.gpu
 
@@ -131,9 +131,22 @@ def test_viterbi_training(H, ctx, family, N):
     obj = []
     for k in range(3):
         before = [om(m) for m in model2.get()]
+        # the paths of this iteration: equal to the float64 decoder's, else a
+        # logged near-tie, after which the two trajectories may part
+        p2, s2 = H.viterbi(ctx, model2, batch)
+        p2, s2 = p2.cpu().numpy(), s2.cpu().numpy()
+        tie = False
+        for s in range(len(offsets) - 1):
+            q, _ = O.viterbi(before[mid[s]], values[offsets[s]:offsets[s + 1]])
+            if not np.array_equal(p2[offsets[s]:offsets[s + 1]], q):
+                check_viterbi_fp64(p2[offsets[s]:offsets[s + 1]], s2[s], before[mid[s]],
+                                   values[offsets[s]:offsets[s + 1]], where=("viterbi training", k, s))
+                tie = True
+        if tie:
+            break
         tr, done = H.fit(ctx, model2, batch, n_iter=1, trainer="viterbi")
         ref, sc = O.viterbi_train_iteration(before, values, offsets, mid)
         np.testing.assert_allclose(tr[0], [sc[mid == m].sum() for m in range(len(init))], rtol=LL_RTOL)
         assert_params_close(model2.get(), ref, rtol=PARAM_RTOL)
         obj.append(tr[0].sum())
-    assert np.all(np.diff(obj) >= -1e-6 * abs(obj[0]))
+    assert len(obj) >= 2 and np.all(np.diff(obj) >= -1e-6 * abs(obj[0]))

@@ -392,3 +392,18 @@ def test_transition_and_initial_update_vs_brute_force(N):
         g1 += bf["gamma"][0]
     np.testing.assert_allclose(new[0].A, xi / den[:, None], rtol=1e-11, atol=1e-13)
     np.testing.assert_allclose(new[0].pi, g1 / len(seqs), rtol=1e-11, atol=1e-13)
+
+
+def test_unresolvable_variance_keeps_parameters():
+    """Reading 14: a variance that vanishes relative to the weighted mean
+    square deviation from the current location (here: one observation
+    carrying all the weight) is an undefined update; the state keeps its
+    parameters."""
+    y = np.array([3.0, -1.0, 7.0])
+    W = np.array([[1.0, 0.5], [0.0, 0.5], [0.0, 1.0]])
+    for fam, extra in (("gauss", {}), ("student_t", {"nu": [5.0, 5.0]}), ("lognormal", {})):
+        yy = np.abs(y) if fam == "lognormal" else y
+        m = M(fam, 2, mu=[0.5, 0.2], sigma2=[2.0, 3.0], **extra)
+        new, _ = O.mstep_emission(m, W, yy)
+        assert new.params["mu"][0] == 0.5 and new.params["sigma2"][0] == 2.0, fam
+        assert new.params["sigma2"][1] != 3.0, fam   # the other state is updated
