@@ -77,7 +77,9 @@ def dist_env():
 def workload(args, rank):
     from paper_2605_29208_gb300 import synth
     if args.workload == "batching":
-        truths, inits, values, offsets, mid = synth.batching_workload(seed=synth.MASTER_SEED + 2 + 1000 * rank)
+        # --quick: 10k sequences and 128 models of the same mix (profiling runs)
+        kw = dict(n_seq=10_000, n_models=128) if args.quick else {}
+        truths, inits, values, offsets, mid = synth.batching_workload(seed=synth.MASTER_SEED + 2 + 1000 * rank, **kw)
         return truths, inits, values, offsets, mid
     n_seq, T = (256, 500) if args.quick else (N_SEQ, T_LEN)
     # weak scaling: every rank holds its own full-size batch (seed per rank)
