@@ -57,6 +57,12 @@ cudaError_t launch_viterbi_small(int NP, int G, const VitArgs& a, int fam, int n
 // large-N kernels (padded N in {64, 128, 256, 512, 1024})
 cudaError_t launch_large_fb(int NP, const LargeArgs& a, cudaStream_t st);
 cudaError_t launch_large_viterbi(int NP, const LargeArgs& a, cudaStream_t st);
+// the same recursions for few groups at padded N = 256 on clusters of two
+// CTAs with A resident in shared memory (the single-sequence latency path)
+constexpr int LG_CL_MAX_GROUPS = 32;
+bool large_cl_supported(int NP, int n_groups);
+cudaError_t launch_large_fb_cl(const LargeArgs& a, cudaStream_t st);
+cudaError_t launch_large_viterbi_cl(const LargeArgs& a, cudaStream_t st);
 // tensor-core recursions (tcgen05, FP16 operands): padded N in {64, ..., 512},
 // tiles of tc_tile_rows() sequences of one model; same outputs as launch_large_fb
 bool tc_supported(int NP);

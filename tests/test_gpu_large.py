@@ -224,3 +224,30 @@ def test_large_weibull_mstep_unsupported(H, ctx):
     stats, _ = H.estep_stats(ctx, model, batch)
     with pytest.raises(Exception):
         H.mstep(ctx, model, stats, batch=batch)
+
+
+@pytest.mark.parametrize("n_seq", [1, 9, 300])
+def test_large_256_cluster_and_group_paths(H, ctx, n_seq):
+    """Padded N = 256 runs on clusters of two CTAs with A in shared memory
+    for up to 32 sequence groups (1 and 9 sequences here) and on the
+    one-block kernels above that (300 sequences, 38 groups): both against
+    the oracle (logL, gamma, Viterbi bit-exact on the float32 table and
+    against float64)."""
+    models = synth.small_models("gauss", 230, 1, seed=1234, conc=0.5)
+    rng = np.random.default_rng(n_seq)
+    lengths = list(rng.integers(1, 400, n_seq)) if n_seq > 1 else [2500]
+    values, offsets, mid = synth.make_batch(5 + n_seq, models, lengths, [0] * n_seq)
+    model = H.Model(ctx, models)
+    batch = H.Batch(values, offsets, mid)
+    ll, gamma, _ = H.forward_backward(ctx, model, batch)
+    ll, gamma = ll.cpu().numpy(), gamma.cpu().numpy()
+    path, score = H.viterbi(ctx, model, batch)
+    path, score = path.cpu().numpy(), score.cpu().numpy()
+    o = om(models[0])
+    for s in sorted({0, n_seq // 2, n_seq - 1}):
+        y = values[offsets[s]:offsets[s + 1]]
+        fb = O.forward_backward(o, y)
+        assert abs(ll[s] - fb["logL"]) <= LL_RTOL * max(1.0, abs(fb["logL"])), (s, ll[s], fb["logL"])
+        np.testing.assert_allclose(gamma[offsets[s]:offsets[s + 1]], fb["gamma"], atol=GAMMA_ATOL)
+        check_viterbi_fp64(path[offsets[s]:offsets[s + 1]], score[s], o, y, where=("N230", n_seq, s))
+    check_viterbi_table_batch(H, ctx, model, batch, models, values, offsets, mid, path, score)
