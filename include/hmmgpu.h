@@ -479,8 +479,10 @@ hmm_status hmm_estep_viterbi(hmm_ctx ctx, hmm_model model, const hmm_batch* batc
 hmm_status hmm_mstep(hmm_ctx ctx, hmm_model model, hmm_stats stats,
                      const hmm_batch* batch, const hmm_mstep_opts* opts, void* stream);
 
-/* max_iter Baum-Welch iterations (E-step, then M-step) on the batch, in place
- * on `model`.  h_loglik_trace (host, may be NULL) receives, for every
+/* max_iter Baum-Welch iterations (the EM of Sec. 3-4: the E-step of Sec. 3.2
+ * and Eq. 5, then the M-step of Sec. 4, Eq. 6; the paper's Baum-Welch, MAP
+ * Baum-Welch and Viterbi trainers, Sec. 5.6, select with opts) on the batch,
+ * in place on `model`.  h_loglik_trace (host, may be NULL) receives, for every
  * iteration k, the sum of log-likelihoods of each model under the parameters
  * entering iteration k: [max_iter][n_models].  *iters_done (may be NULL) gets
  * the number of iterations run.  The iterations run as one captured CUDA

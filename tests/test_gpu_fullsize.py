@@ -116,18 +116,35 @@ def test_precision_full_size(H):
     batch = H.Batch(values, offsets, mid, dim=values.shape[1]).make_plan(ctx, model)
     ll0, gamma, _ = H.forward_backward(ctx, model, batch)
     assert float((gamma.sum(dim=1) - 1).abs().max()) < 1e-4
+    o = om(init)
+    s = 517
+    y = np.asarray(values[offsets[s]:offsets[s + 1]], np.float64)
+    fb = O.forward_backward(o, y)              # the sampled sequence, element by element
+    g0 = gamma[offsets[s]:offsets[s + 1]].cpu().numpy()
+    np.testing.assert_allclose(g0, fb["gamma"], atol=GAMMA_ATOL)
     del gamma
     ctx.set_option(_lib.OPT_TENSOR_RECURRENCE, 1)
     ll1, gamma1, _ = H.forward_backward(ctx, model, batch)
     assert float((gamma1.sum(dim=1) - 1).abs().max()) < 1e-3
+    g1 = gamma1[offsets[s]:offsets[s + 1]].cpu().numpy()
+    # the FP16-operand path to its own stated bound
+    assert float(np.abs(g1 - fb["gamma"]).max()) < 1e-3
     del gamma1
     ll0, ll1 = ll0.cpu().numpy(), ll1.cpu().numpy()
-    o = om(init)
-    s = 517
-    y = np.asarray(values[offsets[s]:offsets[s + 1]], np.float64)
-    logb = O.emission_logpdf(o, y)
-    alpha = O.forward_log(np.log(o.pi), np.log(o.A), logb)
-    ref = float(O.lse(alpha[-1], axis=0))
+    ref = fb["logL"]
     assert abs(ll0[s] - ref) <= LL_RTOL * abs(ref)
     assert abs(ll1[s] - ref) <= 5e-5 * abs(ref)
     assert np.all(np.abs(ll1 - ll0) <= 5e-5 * np.abs(ll0))
+    # the statistics of the whole batch on the tensor path: totals equal the
+    # sequence, transition and row counts, the M-step keeps A stochastic
+    stats, _ = H.estep_stats(ctx, model, batch)
+    rec = stats.get()
+    N = 512
+    n_seq, g1s, xi = rec[0], rec[2:2 + N], rec[2 + N:2 + N + N * N]
+    W = rec[2 + N + N * N:].reshape(N, -1)[:, 0]
+    assert n_seq == 1024
+    assert abs(g1s.sum() - 1024) < 1e-2
+    assert abs(xi.sum() - 1024 * 4095) < 1e-3 * 1024 * 4095
+    assert abs(W.sum() - 1024 * 4096) < 1e-3 * 1024 * 4096
+    H.mstep(ctx, model, stats, batch=batch)
+    np.testing.assert_allclose(model.get()[0]["A"].sum(axis=1), 1.0, rtol=1e-9)
