@@ -22,12 +22,21 @@ struct Error {
   std::string msg;
 };
 
-#define HMM_CUDA(call)                                                              \
-  do {                                                                              \
-    cudaError_t e_ = (call);                                                        \
-    if (e_ != cudaSuccess)                                                          \
-      throw ::hmm::Error{HMM_E_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)}; \
+#define HMM_CUDA(call)                                                                               \
+  do {                                                                                               \
+    cudaError_t e_ = (call);                                                                         \
+    if (e_ != cudaSuccess)                                                                           \
+      throw ::hmm::Error{HMM_E_CUDA, std::string(#call) + " (" + ::hmm::src_base(__FILE__) + ":" +     \
+                                         std::to_string(__LINE__) + "): " + cudaGetErrorString(e_)}; \
   } while (0)
+
+// file name without its directories (error messages)
+inline const char* src_base(const char* f) {
+  const char* b = f;
+  for (const char* p = f; *p; ++p)
+    if (*p == '/') b = p + 1;
+  return b;
+}
 
 #define HMM_REQUIRE(cond, msg)                                            \
   do {                                                                    \
