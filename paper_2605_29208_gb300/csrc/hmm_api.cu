@@ -561,13 +561,13 @@ void launch_mv_emission(hmm_model model, const hmm_batch* b, hmm_plan plan, floa
     const size_t smem = ((size_t)32 * (D + 1) + (size_t)64 * (model->KM | 1)) * 4;
     if (fam == HMM_DIAG_GAUSS) {
       auto kern = mv_emission_tiled_kernel<HMM_DIAG_GAUSS>;
-      HMM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      HMM_CUDA(ensure_max_dyn_smem(reinterpret_cast<const void*>(kern), smem));
       kern<<<grid, 256, smem, st>>>(model->mvcoef.as<float>(), model->NP, model->N, D, model->KM, b->values,
                                     b->offsets, b->model_id, plan->tile_seq.as<int32_t>(),
                                     plan->tile_row.as<int32_t>(), out);
     } else {
       auto kern = mv_emission_tiled_kernel<HMM_FULL_GAUSS>;
-      HMM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      HMM_CUDA(ensure_max_dyn_smem(reinterpret_cast<const void*>(kern), smem));
       kern<<<grid, 256, smem, st>>>(model->mvcoef.as<float>(), model->NP, model->N, D, model->KM, b->values,
                                     b->offsets, b->model_id, plan->tile_seq.as<int32_t>(),
                                     plan->tile_row.as<int32_t>(), out);

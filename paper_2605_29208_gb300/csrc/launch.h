@@ -4,8 +4,8 @@
 
 #include <cuda_runtime.h>
 
+#include <map>
 #include <mutex>
-#include <set>
 #include <utility>
 
 #include "estep_small.cuh"
@@ -14,19 +14,23 @@
 
 namespace hmm {
 
-// Raises a kernel's dynamic shared-memory limit on the current device.  The
-// attribute is a per-device property of the kernel, so it is set once per
-// (kernel, device) pair; thread-safe.
+// Raises a kernel's dynamic shared-memory limit on the current device to at
+// least `bytes`.  The attribute is a per-device property of the kernel and
+// setting it also lowers the limit, so the largest size requested so far is
+// kept per (kernel, device) and the attribute only ever grows (a kernel whose
+// shared memory depends on its arguments asks for different sizes);
+// thread-safe.
 inline cudaError_t ensure_max_dyn_smem(const void* kernel, size_t bytes) {
   static std::mutex mu;
-  static std::set<std::pair<const void*, int>> done;
+  static std::map<std::pair<const void*, int>, size_t> limit;
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   std::lock_guard<std::mutex> lk(mu);
-  if (done.count({kernel, dev})) return cudaSuccess;
+  size_t& cur = limit[{kernel, dev}];
+  if (bytes <= cur) return cudaSuccess;
   e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-  if (e == cudaSuccess) done.insert({kernel, dev});
+  if (e == cudaSuccess) cur = bytes;
   return e;
 }
 
