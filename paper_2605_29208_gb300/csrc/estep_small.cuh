@@ -331,11 +331,8 @@ __device__ void estep_item(WarpSmem<C>& sm, const EStepArgs& a, int item, int la
     }
   };
 
-  // emission of the step whose data sit in ring slot `sl` -> lbn / ftn, and
-  // its scaled linear form en = 2^(lbn - Ln) with Ln = floor(max_j lbn_j)
-  // over the chain (an integer; 0 when every state is impossible), so that
-  // the step's new vector needs no exponential on its dependency chain
-  float lbn[R], en[R], Ln = 0.f;
+  // emission of the step whose data sit in ring slot `sl` -> lbn / ftn
+  float lbn[R];
   Feat ftn;
   auto emission = [&](int sl) {
     if constexpr (FAM == FAM_TABLE) {
@@ -355,13 +352,6 @@ __device__ void estep_item(WarpSmem<C>& sm, const EStepArgs& a, int item, int la
         lbn[q] = ftn.ok ? e : -INFINITY;
       }
     }
-    float lm = -INFINITY;
-#pragma unroll
-    for (int q = 0; q < R; ++q) lm = fmaxf(lm, lbn[q]);
-    lm = group_max<G>(lm);
-    Ln = (lm > -INFINITY && lm < INFINITY) ? floorf(lm) : 0.f;
-#pragma unroll
-    for (int q = 0; q < R; ++q) en[q] = ex2f(lbn[q] - Ln);
   };
 
   // one recursion step of phase PH2 (false: phase 1) at warp iteration k
@@ -381,13 +371,9 @@ __device__ void estep_item(WarpSmem<C>& sm, const EStepArgs& a, int item, int la
 
     // emission log2 b_k(y_t) of the owned states: computed one step ahead
     // (it does not depend on the recursion, so it overlaps the previous step)
-    float lb[R], eb[R];
+    float lb[R];
 #pragma unroll
-    for (int q = 0; q < R; ++q) {
-      lb[q] = lbn[q];
-      eb[q] = en[q];
-    }
-    const float Lb = Ln;
+    for (int q = 0; q < R; ++q) lb[q] = lbn[q];
     const Feat ft = ftn;
     emission((slot == PD - 1) ? 0 : slot + 1);
     // mat-vec s = M^T v_prev (or the initial vector), packed FP32x2 FMAs
@@ -464,40 +450,17 @@ __device__ void estep_item(WarpSmem<C>& sm, const EStepArgs& a, int item, int la
       }
     }
 
-    // new vector v = s * 2^(lb - E), E = floor(max_j(lb_j + log2 s_j)): from
-    // p = s * 2^(lb - Lb), E = Lb + floor(log2 max p) read off the exponent
-    // bits of max p, and v = p * 2^-(E - Lb) (exact scaling).  When max p is
-    // not a normal float in [2^-100, 2^126) (an improbable row, an impossible
-    // state set, non-finite values) the chain takes the log-space form.
-    float p[R], pm = 0.f;
+    // new vector: v = s * 2^(lb - E), E = floor(max_j(lb_j + log2 s_j))
+    float tm = -INFINITY;
+#pragma unroll
+    for (int q = 0; q < R; ++q) tm = fmaxf(tm, lb[q] + lg2a(s[q]));
+    tm = group_max<G>(tm);
+    const float E = (tm > -INFINITY) ? floorf(tm) : 0.f;
 #pragma unroll
     for (int q = 0; q < R; ++q) {
-      p[q] = s[q] * eb[q];
-      pm = fmaxf(pm, p[q]);
+      const float nv = s[q] * ex2f(lb[q] - E);
+      v[q] = act ? nv : v[q];
     }
-    pm = group_max<G>(pm);
-    const bool fast = pm >= 0x1p-100f && pm < 0x1p126f;
-    float E, nv[R];
-    {
-      const int ex = ((__float_as_int(pm) >> 23) & 0xff) - 127;   // floor(log2 pm) for a normal pm
-      const float sc = __int_as_float((127 - ex) << 23);            // 2^-ex
-      E = Lb + (float)ex;
-#pragma unroll
-      for (int q = 0; q < R; ++q) nv[q] = p[q] * sc;
-    }
-    if (__any_sync(0xffffffffu, !fast)) {   // warp-uniform: the shuffles below stay convergent
-      float tm = -INFINITY;
-#pragma unroll
-      for (int q = 0; q < R; ++q) tm = fmaxf(tm, lb[q] + lg2a(s[q]));
-      tm = group_max<G>(tm);
-      if (!fast) {
-        E = (tm > -INFINITY) ? floorf(tm) : 0.f;
-#pragma unroll
-        for (int q = 0; q < R; ++q) nv[q] = s[q] * ex2f(lb[q] - E);
-      }
-    }
-#pragma unroll
-    for (int q = 0; q < R; ++q) v[q] = act ? nv[q] : v[q];
     if (act) {
       offs += E;
       started = true;
