@@ -431,6 +431,12 @@ void hmm::fill_plan(hmm_plan p, hmm_ctx ctx, hmm_model model, const hmm_batch* b
       std::vector<int32_t> flat;
       for (auto& g : groups) flat.insert(flat.end(), g.begin(), g.end());
       p->n_groups = (int)groups.size();
+      p->lg_fill = 0;
+      for (auto& g : groups) {
+        int f = 0;
+        for (int32_t x : g) f += x >= 0;
+        p->lg_fill = std::max(p->lg_fill, f);
+      }
       p->lg_groups.ensure(flat.size() * 4);
       HMM_CUDA(cudaMemcpy(p->lg_groups.p, flat.data(), flat.size() * 4, cudaMemcpyHostToDevice));
       if (tc_supported(model->NP)) {
@@ -775,6 +781,8 @@ void run_estep_large(hmm_ctx ctx, hmm_model model, const hmm_batch* b, hmm_plan 
   a.model_id = b->model_id;
   a.groups = plan->lg_groups.as<int32_t>();
   a.n_groups = plan->n_groups;
+  a.group_fill = plan->lg_fill;
+  a.status = ctx->status;
   a.mv = model->view();
   a.fv = ctx->scratch.as<float>();
   a.bv = ctx->lg_bv.as<float>();
@@ -1842,6 +1850,8 @@ void run_viterbi(hmm_ctx ctx, hmm_model model, const hmm_batch* batch, hmm_plan 
     a.model_id = batch->model_id;
     a.groups = plan->lg_groups.as<int32_t>();
     a.n_groups = plan->n_groups;
+    a.group_fill = plan->lg_fill;
+    a.status = ctx->status;
     a.mv = model->view();
     a.psi = ctx->psi.as<uint16_t>();
     a.path = d_path;

@@ -222,6 +222,7 @@ cudaError_t launch_vit_np(const LargeArgs& a, cudaStream_t st) {
 
 cudaError_t launch_large_fb(int NP, const LargeArgs& a, cudaStream_t st) {
   if (a.n_groups == 0) return cudaSuccess;
+  if (a.status && large_cl1_supported(NP, a.group_fill)) return launch_large_fb_cl1(NP, a, st);
   if (large_cl_supported(NP, a.n_groups)) return launch_large_fb_cl(a, st);
   switch (NP) {
     case 64: return launch_fb_np<64>(a, st);
@@ -269,6 +270,7 @@ cudaError_t launch_large_reduce(const float* part, const double* loglik, const d
 
 cudaError_t launch_large_viterbi(int NP, const LargeArgs& a, cudaStream_t st) {
   if (a.n_groups == 0) return cudaSuccess;
+  if (a.status && large_cl1_supported(NP, a.group_fill)) return launch_large_viterbi_cl1(NP, a, st);
   if (large_cl_supported(NP, a.n_groups)) return launch_large_viterbi_cl(a, st);
   switch (NP) {
     case 64: return launch_vit_np<64>(a, st);

@@ -44,6 +44,7 @@ struct LargeArgs {
   const int32_t* model_id;     // [n_seq]
   const int32_t* groups;       // [n_groups][LG_SB] sequence ids (one model per group), -1 empty
   int32_t n_groups;
+  int32_t group_fill;          // most sequences in one group (1: the single-sequence cluster kernel)
   ModelView mv;
   float* fv;                   // [total_T][NP] forward vectors
   float* bv;                   // [total_T][NP] backward vectors (before the emission)
@@ -53,6 +54,7 @@ struct LargeArgs {
   uint16_t* psi;               // [total_T][NP] backpointers
   int32_t* path;               // [total_T]
   double* score;               // [n_seq]
+  int* status;                 // device status word (bounded waits)
 };
 
 __device__ __forceinline__ float warp_max_f(float x) {

@@ -376,6 +376,404 @@ __global__ void __launch_bounds__(CL_NT, 1) large_vit_cl_kernel(LargeArgs a) {
   }
 }
 
+// ---------------------------------------------------------------------------
+// One sequence per group (the request server's case: every request its own
+// model).  Per step the mat-vec is 65,536 FMAs, so the step time is the
+// latency of its dependency chain; this variant takes the cluster-wide
+// barrier out of that chain.  Each CTA scales its columns by its own power of
+// two E_r = floor(max of its u) and sends the scaled values v' and E_r to
+// every CTA of the cluster with st.async stores that complete a transaction
+// count on the receiver's mbarrier (two, by step parity); a receiver waits on
+// its own mbarrier only.  The step's shift is E = max_r E_r = floor(max u)
+// (floor is monotone), the shift of large_fb_kernel, and v = v' 2^(E_r - E)
+// is applied as an exact power-of-two scaling of each CTA's part of the
+// mat-vec and of the stored row.  The transition column block of a thread
+// lives in registers (64 rows), the vector in shared memory; lanes 8q + c of
+// a warp hold quarter q of the rows of column c, combined by shuffles.  One
+// __syncthreads per step (the CTA's row maximum).
+template <int NP_, int CLN>
+struct Cl1 {
+  static constexpr int NP = NP_;
+  static constexpr int CW = NP / CLN;    // columns per CTA
+  static constexpr int Q = 4;            // lanes per column (row quarters)
+  static constexpr int RPT = NP / Q;     // rows per thread
+  static constexpr int NW = CW / 8;      // warps per CTA (8 columns each)
+  static constexpr int NT = NW * 32;
+  static constexpr int VP = RPT + 4;     // padded quarter stride (bank offset)
+  static constexpr uint32_t RX = (uint32_t)(CLN - 1) * (CW + 1) * 4;   // bytes received per step
+  static_assert(CW % RPT == 0 || RPT % CW == 0, "a quarter must lie in one CTA's columns");
+  static_assert(RPT % 4 == 0, "rows per thread in float4 blocks");
+};
+
+template <class S, int CLN>
+struct Cl1Smem {
+  float v[2][S::Q * S::VP];   // v' of every state (padded by quarter), by step parity
+  float E[2][CLN];            // E_r of every CTA, by step parity
+  float wmax[2][S::NW];       // warp maxima, by step parity
+  uint64_t bar[2];            // completion of a step's vector, by parity
+};
+
+__device__ __forceinline__ void st_async_v4(uint32_t addr, float4 v, uint32_t bar) {
+  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v4.f32 [%0], {%1, %2, %3, %4}, [%5];" ::"r"(addr),
+               "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w), "r"(bar)
+               : "memory");
+}
+__device__ __forceinline__ void st_async_f32(uint32_t addr, float v, uint32_t bar) {
+  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.f32 [%0], %1, [%2];" ::"r"(addr), "f"(v), "r"(bar)
+               : "memory");
+}
+// bounded wait with cluster-scope acquire (the data of st.async stores)
+__device__ __forceinline__ bool mbar_wait_cl(uint64_t* b, uint32_t parity) {
+  const uint32_t addr = smem_u32(b);
+  const long long t0 = clock64();
+  for (;;) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, "
+        "p;\n\t}"
+        : "=r"(ok)
+        : "r"(addr), "r"(parity)
+        : "memory");
+    if (ok) return true;
+    if (clock64() - t0 > tc::TC_WAIT_CYCLES) return false;
+  }
+}
+// x 2^(Er - E) (0 for a CTA whose values are all zero)
+__device__ __forceinline__ float cl1_scale(float x, float Er, float E) {
+  return Er > -INFINITY ? ldexpf(x, (int)(Er - E)) : 0.f;
+}
+template <int RPT>
+__device__ __forceinline__ int cl1_vidx(int j) { return j + 4 * (j / RPT); }
+
+template <int NP_, int CLN>
+__global__ void __launch_bounds__(Cl1<NP_, CLN>::NT, 1) large_fb_cl1_kernel(LargeArgs a) {
+  using S = Cl1<NP_, CLN>;
+  constexpr int NP = S::NP, CW = S::CW, RPT = S::RPT, NW = S::NW;
+  __shared__ __align__(16) Cl1Smem<S, CLN> sm;
+  const uint32_t rank = cluster_rank();
+  const int g = blockIdx.y, dir = blockIdx.z;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int c8 = lane & 7, q = lane >> 3;
+  const int j = (int)rank * CW + warp * 8 + c8;     // state of this thread's column
+  const int N = a.mv.N;
+  const int s = a.groups[(size_t)g * LG_SB];
+  const int64_t base = a.offsets[s];
+  const int T = (int)(a.offsets[s + 1] - base);
+  const int m = a.model_id[s];
+  const int rq = (q * RPT) / CW;                    // CTA whose columns are this thread's rows
+  const float* Mg = (dir == 0 ? a.mv.A32 : a.mv.AT32) + (size_t)m * NP * NP;
+  float2 Ar[RPT / 2];
+#pragma unroll
+  for (int p = 0; p < RPT / 2; ++p)
+    Ar[p] = make_float2(__ldg(Mg + (size_t)(q * RPT + 2 * p) * NP + j), __ldg(Mg + (size_t)(q * RPT + 2 * p + 1) * NP + j));
+  if (tid == 0) {
+    tc::mbar_init(&sm.bar[0], 2 * NW + 2);
+    tc::mbar_init(&sm.bar[1], 2 * NW + 2);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (tid == 0) {
+    tc::mbar_expect_tx(&sm.bar[0], S::RX);
+    if (T > 1) tc::mbar_expect_tx(&sm.bar[1], S::RX);
+  }
+  cluster_sync();   // every CTA's barriers initialised before any remote store
+
+  auto tof = [&](int k) { return dir == 0 ? k : T - 1 - k; };
+  float lb_cur = (T > 0 && j < N) ? __ldg(a.logb + (base + tof(0)) * N + j) * kLog2ef : -INFINITY;
+  double O = 0.0;            // log2 offset after the previous step (thread 0)
+  bool dead = false;
+  float vprev = 0.f, Eprev = 0.f;
+  int64_t rowprev = 0;
+  for (int k = 0; k < T; ++k) {
+    const int par = k & 1;
+    const int64_t row = base + tof(k);
+    const float lb_next = (k + 1 < T && j < N) ? __ldg(a.logb + (base + tof(k + 1)) * N + j) * kLog2ef : -INFINITY;
+    float u;
+    if (k == 0) {
+      u = dir == 0 ? lb_cur + a.mv.logpi2[(size_t)m * NP + j] : lb_cur;
+      if (dir == 1 && q == 0) a.bv[row * NP + j] = j < N ? 1.f : 0.f;
+      if (dir == 1 && rank == 0 && tid == 0) a.ob[row] = 0.0;
+    } else {
+      const int pp = par ^ 1;
+      if (!dead && !mbar_wait_cl(&sm.bar[pp], (uint32_t)((k - 1) >> 1) & 1u)) {
+        set_status(a.status, ST_TIMEOUT);
+        dead = true;   // the protocol is broken: finish without waiting (results invalid, status set)
+      }
+      if (tid == 0 && k + 1 < T) tc::mbar_expect_tx(&sm.bar[pp], S::RX);   // its phase of step k + 1
+      float Er[CLN], E = -INFINITY;
+#pragma unroll
+      for (int r = 0; r < CLN; ++r) {
+        Er[r] = sm.E[pp][r];
+        E = fmaxf(E, Er[r]);
+      }
+      if (!(E > -INFINITY)) E = 0.f;
+      if (tid == 0) O += (double)E;
+      if (dir == 0) {   // the previous step's row, now that its shift is known
+        if (q == 0) a.fv[rowprev * NP + j] = cl1_scale(vprev, Eprev, E);
+        if (rank == 0 && tid == 0) a.oa[rowprev] = O;
+      }
+      const float* vb = &sm.v[pp][q * S::VP];
+      float2 acc0 = make_float2(0.f, 0.f), acc1 = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int p = 0; p < RPT / 4; ++p) {
+        const float4 x = *reinterpret_cast<const float4*>(vb + 4 * p);
+        acc0 = __ffma2_rn(make_float2(x.x, x.y), Ar[2 * p], acc0);
+        acc1 = __ffma2_rn(make_float2(x.z, x.w), Ar[2 * p + 1], acc1);
+      }
+      float Erq = Er[0];
+#pragma unroll
+      for (int r = 1; r < CLN; ++r)
+        if (r == rq) Erq = Er[r];
+      float part = cl1_scale((acc0.x + acc0.y) + (acc1.x + acc1.y), Erq, E);
+      part += __shfl_xor_sync(0xffffffffu, part, 8);
+      part += __shfl_xor_sync(0xffffffffu, part, 16);
+      if (dir == 1) {
+        if (q == 0) a.bv[row * NP + j] = part;
+        if (rank == 0 && tid == 0) a.ob[row] = O;
+      }
+      u = lb_cur + log2f(part);
+    }
+    float mx = u;
+    mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 1));
+    mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 2));
+    mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 4));
+    if (lane == 0) sm.wmax[par][warp] = mx;
+    __syncthreads();
+    float cm = -INFINITY;
+#pragma unroll
+    for (int w = 0; w < NW; ++w) cm = fmaxf(cm, sm.wmax[par][w]);
+    const float Eown = cm > -INFINITY ? floorf(cm) : -INFINITY;
+    const float vj = Eown > -INFINITY ? exp2f(u - Eown) : 0.f;
+    __syncwarp();
+    // lanes c8 = 0 and 4 of quarter q send four consecutive columns to CTA q
+    const float v1 = __shfl_down_sync(0xffffffffu, vj, 1);
+    const float v2 = __shfl_down_sync(0xffffffffu, vj, 2);
+    const float v3 = __shfl_down_sync(0xffffffffu, vj, 3);
+    if ((c8 & 3) == 0 && q < CLN) {
+      const float4 pk = make_float4(vj, v1, v2, v3);
+      float* dst = &sm.v[par][cl1_vidx<RPT>(j)];
+      if (q == (int)rank) {
+        *reinterpret_cast<float4*>(dst) = pk;
+        tc::mbar_arrive(&sm.bar[par]);
+      } else {
+        st_async_v4(mapa(smem_u32(dst), (uint32_t)q), pk, mapa(smem_u32(&sm.bar[par]), (uint32_t)q));
+      }
+    }
+    if (warp == 0 && lane < CLN) {
+      if (lane == (int)rank) {
+        sm.E[par][rank] = Eown;
+        tc::mbar_arrive(&sm.bar[par]);
+      } else {
+        st_async_f32(mapa(smem_u32(&sm.E[par][rank]), (uint32_t)lane), Eown,
+                     mapa(smem_u32(&sm.bar[par]), (uint32_t)lane));
+      }
+    }
+    vprev = vj;
+    Eprev = Eown;
+    rowprev = row;
+    lb_cur = lb_next;
+  }
+  if (T > 0) {   // the last step's vector: every incoming store has landed; forward: the last row
+    const int pp = (T - 1) & 1;
+    if (!dead && !mbar_wait_cl(&sm.bar[pp], (uint32_t)((T - 1) >> 1) & 1u)) set_status(a.status, ST_TIMEOUT);
+    if (dir == 0) {
+      float E = -INFINITY;
+#pragma unroll
+      for (int r = 0; r < CLN; ++r) E = fmaxf(E, sm.E[pp][r]);
+      if (!(E > -INFINITY)) E = 0.f;
+      if (q == 0) a.fv[rowprev * NP + j] = cl1_scale(vprev, Eprev, E);
+      if (rank == 0 && tid == 0) a.oa[rowprev] = O + (double)E;
+    }
+  }
+  cluster_sync();
+}
+
+// Viterbi for one sequence per group, the same exchange: each CTA sends its
+// columns' raw delta_k (the candidates' maximum plus ln b, before the step's
+// normalisation) and its maximum; a receiver takes the step maximum mx over
+// the CTAs, subtracts it from the rows it scans (the float32-mode order of
+// large_viterbi_kernel: (delta - mx) + ln a_ij, upward, strict '>'; the row
+// quarters of a column are joined in order, the lower keeping ties) and adds
+// mx to the float64 offset.  CTA 0 picks the final state and traces back.
+template <int NP_, int CLN>
+__global__ void __launch_bounds__(Cl1<NP_, CLN>::NT, 1) large_vit_cl1_kernel(LargeArgs a) {
+  using S = Cl1<NP_, CLN>;
+  constexpr int NP = S::NP, CW = S::CW, RPT = S::RPT, NW = S::NW, NT = S::NT;
+  constexpr int TB = 32768 / (2 * NP);   // traceback rows staged per chunk (32 KB)
+  __shared__ __align__(16) Cl1Smem<S, CLN> sm;
+  __shared__ __align__(16) uint16_t stage[TB * NP];
+  __shared__ int sidx[NW];
+  const uint32_t rank = cluster_rank();
+  const int g = blockIdx.y;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int c8 = lane & 7, q = lane >> 3;
+  const int j = (int)rank * CW + warp * 8 + c8;
+  const int N = a.mv.N;
+  const int s = a.groups[(size_t)g * LG_SB];
+  const int64_t base = a.offsets[s];
+  const int T = (int)(a.offsets[s + 1] - base);
+  const int m = a.model_id[s];
+  const float* Mg = a.mv.logAe + (size_t)m * NP * NP;
+  float2 Ar[RPT / 2];
+#pragma unroll
+  for (int p = 0; p < RPT / 2; ++p)
+    Ar[p] = make_float2(__ldg(Mg + (size_t)(q * RPT + 2 * p) * NP + j), __ldg(Mg + (size_t)(q * RPT + 2 * p + 1) * NP + j));
+  if (tid == 0) {
+    tc::mbar_init(&sm.bar[0], 2 * NW + 2);
+    tc::mbar_init(&sm.bar[1], 2 * NW + 2);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (tid == 0) {
+    tc::mbar_expect_tx(&sm.bar[0], S::RX);
+    if (T > 1) tc::mbar_expect_tx(&sm.bar[1], S::RX);
+  }
+  cluster_sync();
+
+  float lb_cur = (T > 0 && j < N) ? __ldg(a.logb + base * N + j) : -INFINITY;
+  double off = 0.0;   // thread 0
+  bool dead = false;
+  for (int k = 0; k < T; ++k) {
+    const int par = k & 1;
+    const int64_t row = base + k;
+    const float lb_next = (k + 1 < T && j < N) ? __ldg(a.logb + (row + 1) * N + j) : -INFINITY;
+    float dn;
+    if (k == 0) {
+      dn = a.mv.logpie[(size_t)m * NP + j] + lb_cur;
+    } else {
+      const int pp = par ^ 1;
+      if (!dead && !mbar_wait_cl(&sm.bar[pp], (uint32_t)((k - 1) >> 1) & 1u)) {
+        set_status(a.status, ST_TIMEOUT);
+        dead = true;
+      }
+      if (tid == 0 && k + 1 < T) tc::mbar_expect_tx(&sm.bar[pp], S::RX);
+      float mx = -INFINITY;
+#pragma unroll
+      for (int r = 0; r < CLN; ++r) mx = fmaxf(mx, sm.E[pp][r]);
+      const bool fin = mx > -INFINITY && mx < INFINITY;
+      if (tid == 0 && fin) off += (double)mx;
+      const float* vb = &sm.v[pp][q * S::VP];
+      float best = -INFINITY;
+      int arg = 0;
+#pragma unroll
+      for (int p = 0; p < RPT / 4; ++p) {
+        const float4 x = *reinterpret_cast<const float4*>(vb + 4 * p);
+        const float d0 = fin ? x.x - mx : x.x, d1 = fin ? x.y - mx : x.y;
+        const float d2 = fin ? x.z - mx : x.z, d3 = fin ? x.w - mx : x.w;
+        const float cv[4] = {d0 + Ar[2 * p].x, d1 + Ar[2 * p].y, d2 + Ar[2 * p + 1].x, d3 + Ar[2 * p + 1].y};
+#pragma unroll
+        for (int e = 0; e < 4; ++e)
+          if (cv[e] > best) {
+            best = cv[e];
+            arg = q * RPT + 4 * p + e;
+          }
+      }
+      // quarters in order: a later quarter wins only when strictly larger
+      float bo = __shfl_down_sync(0xffffffffu, best, 8);
+      int ao = __shfl_down_sync(0xffffffffu, arg, 8);
+      if (bo > best) best = bo, arg = ao;
+      bo = __shfl_down_sync(0xffffffffu, best, 16);
+      ao = __shfl_down_sync(0xffffffffu, arg, 16);
+      if (bo > best) best = bo, arg = ao;
+      // lanes of quarter 0 hold the joined result; every lane takes its column's
+      if (q == 0) a.psi[row * NP + j] = (uint16_t)arg;
+      best = __shfl_sync(0xffffffffu, best, c8);
+      dn = best + lb_cur;
+    }
+    float wm = dn;
+    wm = fmaxf(wm, __shfl_xor_sync(0xffffffffu, wm, 1));
+    wm = fmaxf(wm, __shfl_xor_sync(0xffffffffu, wm, 2));
+    wm = fmaxf(wm, __shfl_xor_sync(0xffffffffu, wm, 4));
+    if (lane == 0) sm.wmax[par][warp] = wm;
+    __syncthreads();
+    float cm = -INFINITY;
+#pragma unroll
+    for (int w = 0; w < NW; ++w) cm = fmaxf(cm, sm.wmax[par][w]);
+    __syncwarp();
+    const float v1 = __shfl_down_sync(0xffffffffu, dn, 1);
+    const float v2 = __shfl_down_sync(0xffffffffu, dn, 2);
+    const float v3 = __shfl_down_sync(0xffffffffu, dn, 3);
+    if ((c8 & 3) == 0 && q < CLN) {
+      const float4 pk = make_float4(dn, v1, v2, v3);
+      float* dst = &sm.v[par][cl1_vidx<RPT>(j)];
+      if (q == (int)rank) {
+        *reinterpret_cast<float4*>(dst) = pk;
+        tc::mbar_arrive(&sm.bar[par]);
+      } else {
+        st_async_v4(mapa(smem_u32(dst), (uint32_t)q), pk, mapa(smem_u32(&sm.bar[par]), (uint32_t)q));
+      }
+    }
+    if (warp == 0 && lane < CLN) {
+      if (lane == (int)rank) {
+        sm.E[par][rank] = cm;
+        tc::mbar_arrive(&sm.bar[par]);
+      } else {
+        st_async_f32(mapa(smem_u32(&sm.E[par][rank]), (uint32_t)lane), cm, mapa(smem_u32(&sm.bar[par]), (uint32_t)lane));
+      }
+    }
+    lb_cur = lb_next;
+  }
+  if (T > 0) {
+    const int pp = (T - 1) & 1;
+    if (!dead && !mbar_wait_cl(&sm.bar[pp], (uint32_t)((T - 1) >> 1) & 1u)) set_status(a.status, ST_TIMEOUT);
+  }
+  __threadfence();   // every CTA's pointer rows are visible before the traceback
+  cluster_sync();
+  if (rank != 0) return;
+  if (T == 0) {
+    if (tid == 0) a.score[s] = 0.0;
+    return;
+  }
+  // final state: the lowest index of the normalised last row's maximum
+  const int pp = (T - 1) & 1;
+  float mx = -INFINITY;
+#pragma unroll
+  for (int r = 0; r < CLN; ++r) mx = fmaxf(mx, sm.E[pp][r]);
+  const bool fin = mx > -INFINITY && mx < INFINITY;
+  if (tid == 0 && fin) off += (double)mx;
+  float dz = -INFINITY;
+  if (tid < NP) {
+    const float x = sm.v[pp][cl1_vidx<RPT>(tid)];
+    dz = fin ? x - mx : x;
+  }
+  float dmax = dz;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) dmax = fmaxf(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+  if (lane == 0) sm.wmax[0][warp] = dmax;
+  __syncthreads();
+  dmax = -INFINITY;
+  for (int w = 0; w < NW; ++w) dmax = fmaxf(dmax, sm.wmax[0][w]);
+  int lo = (tid < NP && dz == dmax) ? tid : NP;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+  if (lane == 0) sidx[warp] = lo;
+  __syncthreads();
+  int st = NP;
+  for (int w = 0; w < NW; ++w) st = min(st, sidx[w]);
+  if (st >= NP) st = 0;
+  if (tid == 0) {
+    const float d = sm.v[pp][cl1_vidx<RPT>(st)];
+    const float dd = fin ? d - mx : d;
+    a.score[s] = dd > -INFINITY ? off + (double)dd : -INFINITY;
+  }
+  int thi = T - 1;
+  while (thi > 0) {
+    const int tlo = max(0, thi - TB);
+    const int rows = thi - tlo;
+    __syncthreads();
+    for (int z = tid; z < rows * NP; z += NT) stage[z] = a.psi[(base + tlo + 1) * NP + z];
+    __syncthreads();
+    if (tid == 0) {
+      for (int t = thi; t > tlo; --t) {
+        a.path[base + t] = st;
+        st = stage[(t - tlo - 1) * NP + st];
+      }
+    }
+    thi = tlo;
+  }
+  if (tid == 0) a.path[base] = st;
+}
+
 template <class K>
 cudaError_t launch_cl(K kern, const LargeArgs& a, unsigned dirs, cudaStream_t st) {
   const size_t smem = sizeof(ClSmem);
@@ -404,6 +802,61 @@ cudaError_t launch_large_fb_cl(const LargeArgs& a, cudaStream_t st) { return lau
 
 cudaError_t launch_large_viterbi_cl(const LargeArgs& a, cudaStream_t st) {
   return launch_cl(large_vit_cl_kernel, a, 1, st);
+}
+
+template <int NP, int CLN>
+cudaError_t launch_fb_cl1(const LargeArgs& a, cudaStream_t st) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(CLN, (unsigned)a.n_groups, 2);
+  cfg.blockDim = dim3(Cl1<NP, CLN>::NT, 1, 1);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = CLN;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, large_fb_cl1_kernel<NP, CLN>, a);
+}
+
+bool large_cl1_supported(int NP, int group_fill) { return group_fill == 1 && (NP == 64 || NP == 128 || NP == 256); }
+
+template <int NP, int CLN>
+cudaError_t launch_vit_cl1(const LargeArgs& a, cudaStream_t st) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(CLN, (unsigned)a.n_groups, 1);
+  cfg.blockDim = dim3(Cl1<NP, CLN>::NT, 1, 1);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = CLN;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, large_vit_cl1_kernel<NP, CLN>, a);
+}
+
+cudaError_t launch_large_viterbi_cl1(int NP, const LargeArgs& a, cudaStream_t st) {
+  switch (NP) {
+    case 64: return launch_vit_cl1<64, 1>(a, st);
+    case 128: return launch_vit_cl1<128, 2>(a, st);
+    case 256: return launch_vit_cl1<256, 4>(a, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+// 64 columns per CTA: one CTA at padded N = 64, clusters of 2 and 4 above
+cudaError_t launch_large_fb_cl1(int NP, const LargeArgs& a, cudaStream_t st) {
+  switch (NP) {
+    case 64: return launch_fb_cl1<64, 1>(a, st);
+    case 128: return launch_fb_cl1<128, 2>(a, st);
+    case 256: return launch_fb_cl1<256, 4>(a, st);
+  }
+  return cudaErrorInvalidValue;
 }
 
 }  // namespace hmm

@@ -66,6 +66,9 @@ cudaError_t launch_large_viterbi(int NP, const LargeArgs& a, cudaStream_t st);
 constexpr int LG_CL_MAX_GROUPS = 32;
 bool large_cl_supported(int NP, int n_groups);
 cudaError_t launch_large_fb_cl(const LargeArgs& a, cudaStream_t st);
+bool large_cl1_supported(int NP, int group_fill);
+cudaError_t launch_large_fb_cl1(int NP, const LargeArgs& a, cudaStream_t st);
+cudaError_t launch_large_viterbi_cl1(int NP, const LargeArgs& a, cudaStream_t st);
 cudaError_t launch_large_viterbi_cl(const LargeArgs& a, cudaStream_t st);
 // tensor-core recursions (tcgen05, FP16 operands): padded N in {64, ..., 512},
 // tiles of tc_tile_rows() sequences of one model; same outputs as launch_large_fb

@@ -206,6 +206,7 @@ struct hmm_plan_s {
   int n_tiles = 0;
   hmm::DevBuf lg_groups;         // [n_groups][LG_SB] large-N sequence groups (one model each)
   int n_groups = 0;
+  int lg_fill = 0;               // most sequences in one large-N group
   hmm::DevBuf tc_tiles;          // [n_tc_tiles][tc_tile_rows()] tiles of the tensor-core recursions
   int n_tc_tiles = 0;
   // chunk-ordered K layout of the tensor-core xi (padded N > 32): row t of

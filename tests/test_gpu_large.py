@@ -251,3 +251,31 @@ def test_large_256_cluster_and_group_paths(H, ctx, n_seq):
         np.testing.assert_allclose(gamma[offsets[s]:offsets[s + 1]], fb["gamma"], atol=GAMMA_ATOL)
         check_viterbi_fp64(path[offsets[s]:offsets[s + 1]], score[s], o, y, where=("N230", n_seq, s))
     check_viterbi_table_batch(H, ctx, model, batch, models, values, offsets, mid, path, score)
+
+
+@pytest.mark.parametrize("N,lengths", [(230, [2500, 1, 2, 700, 33]), (129, [64, 65, 300]), (256, [1000, 5]),
+                                       (40, [3000, 1, 17]), (100, [1500, 2, 64, 128])])
+def test_large_single_sequence_groups(H, ctx, N, lengths):
+    """Padded N = 64, 128, 256 with one sequence per model (the request
+    server's case) run the single-sequence cluster kernels (64 columns per
+    CTA, per-CTA power-of-two shifts joined exactly, st.async vector
+    exchange).  logL and gamma per sequence against the oracle, the
+    statistics record against the oracle's sums (their xi is formed from the
+    stored forward / backward rows), Viterbi bit-identical to the
+    float32-mode oracle on the shared table and against float64."""
+    M = len(lengths)
+    models = synth.small_models("gauss", N, M, seed=4321 + N, conc=0.5)
+    mid = np.arange(M)
+    values, offsets, mid = synth.make_batch(17 + N, models, lengths, mid)
+    model = H.Model(ctx, models)
+    batch = H.Batch(values, offsets, mid)
+    ll, gamma, _ = H.forward_backward(ctx, model, batch)
+    check_fb(ll.cpu().numpy(), gamma.cpu().numpy(), models, values, offsets, mid)
+    stats, _ = H.estep_stats(ctx, model, batch)
+    np.testing.assert_allclose(stats.get(), oracle_stats(models, values, offsets, mid), rtol=2e-5, atol=2e-4)
+    path, score = H.viterbi(ctx, model, batch)
+    path, score = path.cpu().numpy(), score.cpu().numpy()
+    for s in range(M):
+        y = values[offsets[s]:offsets[s + 1]]
+        check_viterbi_fp64(path[offsets[s]:offsets[s + 1]], score[s], om(models[s]), y, where=("single", N, s))
+    check_viterbi_table_batch(H, ctx, model, batch, models, values, offsets, mid, path, score)
