@@ -62,7 +62,7 @@ def args_parse():
     p.add_argument("--slots", type=int, default=32, help="serving: concurrent batches")
     p.add_argument("--no-extras", action="store_true",
                    help="only the headline line (no batching / precision / serving sub-measurements)")
-    p.add_argument("--serve-rate", type=float, default=5.0, help="extras: the sustained serving rate")
+    p.add_argument("--serve-rate", type=float, default=20.0, help="extras: the sustained serving rate")
     p.add_argument("--serve-requests", type=int, default=150, help="extras: requests per serving run")
     return p.parse_args()
 
