@@ -260,4 +260,54 @@ __device__ __forceinline__ float ext_feature(int fam, int z, float y) {
 }
 
 
+// ---------------------------------------------------------------------------
+// Work distribution of the persistent small-N kernels.  Warps take work items
+// from global counters.  For batches that mix emission families the plan
+// lays the processing order out as one segment per family (each longest
+// first) and gives each segment a share of the SMs proportional to its time
+// steps: a warp starts on the segment of its SM and moves to the next
+// segment once its own is drained.  An SM then runs one family's loop at a
+// time (mixed SMs thrash the instruction cache with every family's unrolled
+// step), while each segment still starts with its longest sequences.
+// ---------------------------------------------------------------------------
+struct FamSched {
+  int32_t n_seg = 0;                 // 0: one counter over all items
+  const int32_t* seg_seq = nullptr;  // [n_seg + 1] segment boundaries in the order
+  const int32_t* seg_sm = nullptr;   // [n_seg + 1] SM boundaries: SM s starts on segment f when seg_sm[f] <= s
+};
+
+template <class Run>
+__device__ __forceinline__ void for_each_item(const FamSched& fs, int* counters, int n_items, int spw, int lane,
+                                              Run&& run) {
+  if (fs.n_seg <= 0) {
+    for (;;) {
+      int item = 0;
+      if (lane == 0) item = atomicAdd(counters, 1);
+      item = __shfl_sync(0xffffffffu, item, 0);
+      if (item >= n_items) return;
+      run(item);
+    }
+  }
+  uint32_t smid;
+  asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
+  const int nsm = max(fs.seg_sm[fs.n_seg], 1);
+  const int sm = (int)(smid % (uint32_t)nsm);
+  int home = 0;
+  for (int f = 1; f < fs.n_seg; ++f)
+    if (sm >= fs.seg_sm[f]) home = f;
+  for (int d = 0; d < fs.n_seg; ++d) {
+    const int f = (home + d) % fs.n_seg;
+    // item i belongs to the segment of its first sequence
+    const int ilo = (fs.seg_seq[f] + spw - 1) / spw;
+    const int ihi = min(n_items, (fs.seg_seq[f + 1] + spw - 1) / spw);
+    for (;;) {
+      int item = 0;
+      if (lane == 0) item = ilo + atomicAdd(counters + f, 1);
+      item = __shfl_sync(0xffffffffu, item, 0);
+      if (item >= ihi) break;
+      run(item);
+    }
+  }
+}
+
 }  // namespace hmm

@@ -58,8 +58,9 @@ struct EStepArgs {
   float* gamma;              // [total_T][N] or nullptr
   float* partials;           // [S][2][NP][NP + NST]
   double* loglik;            // [S] or nullptr
-  int* work_counter;
+  int* work_counter;         // [1], or [sched.n_seg]
   int* status;
+  FamSched sched;
 };
 
 template <int NP_, int G_>
@@ -544,9 +545,8 @@ __device__ void estep_item(WarpSmem<C>& sm, const EStepArgs& a, int item, int la
 
 namespace hmm {
 
-// Persistent launch: warps pull work items (SPW sequences each) from a
-// global counter; items are laid out in the plan's order (family, then
-// length descending) so that consecutive items are alike.
+// Persistent launch: warps pull work items (SPW sequences each) from global
+// counters (for_each_item); items are laid out in the plan's order.
 // FAMK: one emission family for the whole launch, FAM_TABLE for a log b
 // table, or FAM_ANY for batches that mix families (each work item then runs
 // the loop of its family; items mixing families switch per step).
@@ -557,11 +557,7 @@ __global__ void __launch_bounds__(WPB * 32) estep_small_kernel(EStepArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   WarpSmem<C>& sm = reinterpret_cast<WarpSmem<C>*>(smem_raw)[threadIdx.x >> 5];
   const int lane = threadIdx.x & 31;
-  for (;;) {
-    int item = 0;
-    if (lane == 0) item = atomicAdd(a.work_counter, 1);
-    item = __shfl_sync(0xffffffffu, item, 0);
-    if (item >= a.n_items) break;
+  for_each_item(a.sched, a.work_counter, a.n_items, C::SPW, lane, [&](int item) {
     if constexpr (FAMK != FAM_ANY) {
       estep_item<C, FAMK, MODE>(sm, a, item, lane);
     } else {
@@ -581,7 +577,7 @@ __global__ void __launch_bounds__(WPB * 32) estep_small_kernel(EStepArgs a) {
         default: estep_item<C, FAM_ANY, MODE>(sm, a, item, lane); break;
       }
     }
-  }
+  });
 }
 
 template <int NP, int G>

@@ -319,20 +319,58 @@ void hmm::fill_plan(hmm_plan p, hmm_ctx ctx, hmm_model model, const hmm_batch* b
     std::vector<int32_t> order(S), bym(S);
     std::iota(order.begin(), order.end(), 0);
     std::iota(bym.begin(), bym.end(), 0);
-    // processing order: longest first in buckets of ~9% length (so that the
+    // Processing order: longest first in buckets of ~9% length (so that the
     // persistent warps take the long sequences early), family inside a
-    // bucket (family-uniform warps), then exact length descending
+    // bucket (family-uniform warps), then exact length descending.  A batch
+    // that mixes the fused families (one kernel holding every family's loop)
+    // is laid out family first instead, one segment per family in that
+    // order, and the kernels give each segment its own SMs (FamSched).
     auto bucket = [&](int32_t q) {
       const int64_t L = ho[q + 1] - ho[q];
       return L <= 0 ? -1 : (int)std::floor(8.0 * std::log2((double)L));
     };
+    bool mixed = false;
+    for (int64_t q2 = 1; q2 < S && !mixed; ++q2) mixed = model->h_family[hm[q2]] != model->h_family[hm[0]];
+    const bool fam_major = mixed && model->NP <= 32 && !model->table_family();
     std::stable_sort(order.begin(), order.end(), [&](int32_t x, int32_t y) {
+      const int fx = model->h_family[hm[x]], fy = model->h_family[hm[y]];
+      if (fam_major && fx != fy) return fx < fy;
       const int bx = bucket(x), by = bucket(y);
       if (bx != by) return bx > by;
-      const int fx = model->h_family[hm[x]], fy = model->h_family[hm[y]];
       if (fx != fy) return fx < fy;
       return (ho[x + 1] - ho[x]) > (ho[y + 1] - ho[y]);
     });
+    p->n_fam_seg = 0;
+    if (fam_major) {
+      std::vector<int32_t> sseq{0};
+      std::vector<double> w;
+      double wsum = 0.0;
+      for (int64_t q2 = 0; q2 < S; ++q2) {
+        if (q2 > 0 && model->h_family[hm[order[q2]]] != model->h_family[hm[order[q2 - 1]]]) {
+          sseq.push_back((int32_t)q2);
+          w.push_back(0.0);
+        }
+        if (w.empty()) w.push_back(0.0);
+        const double L = (double)(ho[order[q2] + 1] - ho[order[q2]]);
+        w.back() += L;
+        wsum += L;
+      }
+      sseq.push_back((int32_t)S);
+      const int nseg = (int)w.size();
+      const int nsm = std::max(ctx->n_sm, 1);
+      std::vector<int32_t> ssm(nseg + 1, 0);
+      double cum = 0.0;
+      for (int f = 0; f < nseg; ++f) {
+        cum += w[f];
+        ssm[f + 1] = f + 1 == nseg ? nsm : (int32_t)std::llround(nsm * (wsum > 0 ? cum / wsum : 1.0));
+      }
+      HMM_REQUIRE(nseg <= 8, "more than 8 family segments");
+      p->n_fam_seg = nseg;
+      p->fam_seg_seq.ensure((size_t)(nseg + 1) * 4);
+      p->fam_seg_sm.ensure((size_t)(nseg + 1) * 4);
+      HMM_CUDA(cudaMemcpy(p->fam_seg_seq.p, sseq.data(), (nseg + 1) * 4, cudaMemcpyHostToDevice));
+      HMM_CUDA(cudaMemcpy(p->fam_seg_sm.p, ssm.data(), (nseg + 1) * 4, cudaMemcpyHostToDevice));
+    }
     std::stable_sort(bym.begin(), bym.end(), [&](int32_t x, int32_t y) { return hm[x] < hm[y]; });
     const int CH = 64;
     std::vector<int32_t> lo, hi, mptr(model->M + 1, 0);
@@ -509,7 +547,7 @@ void hmm::destroy_plan(hmm_plan p) {
   p->lg_groups.release();
   p->tc_tiles.release();
   for (auto* bb : {&p->xi_kseq, &p->xi_kc0, &p->xi_kused, &p->xi_kpad, &p->tp_chunk_seq, &p->tp_chunk_t0,
-                   &p->tp_seq_chunk0, &p->tp_seq_nchunk})
+                   &p->tp_seq_chunk0, &p->tp_seq_nchunk, &p->fam_seg_seq, &p->fam_seg_sm})
     bb->release();
   delete p;
 }
@@ -968,6 +1006,12 @@ void run_estep(hmm_ctx ctx, hmm_model model, const hmm_batch* b, hmm_plan plan, 
   a.loglik = ll;
   a.work_counter = ctx->counters;
   a.status = ctx->status;
+  if (plan->n_fam_seg > 0) {
+    a.sched.n_seg = plan->n_fam_seg;
+    a.sched.seg_seq = plan->fam_seg_seq.as<int32_t>();
+    a.sched.seg_sm = plan->fam_seg_sm.as<int32_t>();
+    a.work_counter = ctx->counters + 8;
+  }
   const bool dpass = want_stats && stats && (model->any_negbin || model->any_weibull || model->table_family());
   if (dpass && !gamma) {
     // the Weibull / negative-binomial M-steps re-read the occupancies, and
@@ -978,7 +1022,7 @@ void run_estep(hmm_ctx ctx, hmm_model model, const hmm_batch* b, hmm_plan plan, 
     a.gamma = gamma;
   }
   if (!ctx->plain_estep) {
-    HMM_CUDA(cudaMemsetAsync(ctx->counters, 0, sizeof(int), st));
+    HMM_CUDA(cudaMemsetAsync(a.work_counter, 0, sizeof(int) * std::max(a.sched.n_seg, 1), st));
     KTimer kt(ctx, HMM_KT_ESTEP, st);
     const int mode = (want_stats ? MODE_STATS : 0) | (gamma ? MODE_GAMMA : 0);
     const int fam = logb ? FAM_TABLE : (plan->uniform_family >= 0 ? plan->uniform_family : FAM_ANY);
@@ -1879,7 +1923,13 @@ void run_viterbi(hmm_ctx ctx, hmm_model model, const hmm_batch* batch, hmm_plan 
   a.score = d_score;
   a.work_counter = ctx->counters + 1;
   a.status = ctx->status;
-  HMM_CUDA(cudaMemsetAsync(ctx->counters + 1, 0, sizeof(int), st));
+  if (plan->n_fam_seg > 0) {
+    a.sched.n_seg = plan->n_fam_seg;
+    a.sched.seg_seq = plan->fam_seg_seq.as<int32_t>();
+    a.sched.seg_sm = plan->fam_seg_sm.as<int32_t>();
+    a.work_counter = ctx->counters + 16;
+  }
+  HMM_CUDA(cudaMemsetAsync(a.work_counter, 0, sizeof(int) * std::max(a.sched.n_seg, 1), st));
   KTimer kt(ctx, HMM_KT_VITERBI, st);
   const int fam = d_logb ? FAM_TABLE : (plan->uniform_family >= 0 ? plan->uniform_family : FAM_ANY);
   HMM_CUDA(launch_viterbi_small(NP, G, a, fam, ctx->n_sm, st));

@@ -196,6 +196,9 @@ struct hmm_plan_s {
   int M = 0;
   int64_t max_T = 0;
   hmm::DevBuf order;             // [S] int32 processing order
+  hmm::DevBuf fam_seg_seq;       // [n_fam_seg + 1] family segments of the order (mixed-family batches)
+  hmm::DevBuf fam_seg_sm;        // [n_fam_seg + 1] SM shares of the segments
+  int n_fam_seg = 0;
   hmm::DevBuf seq_by_model;      // [S] int32
   hmm::DevBuf chunk_lo, chunk_hi;// [n_chunks] int32
   hmm::DevBuf model_chunk_ptr;   // [M+1] int32

@@ -43,8 +43,9 @@ struct VitArgs {
   uint8_t* psi;               // [total_T][NP] (+16 bytes of slack)
   int32_t* path;              // [total_T]
   double* score;              // [S]
-  int* work_counter;
+  int* work_counter;          // [1], or [sched.n_seg]
   int* status;
+  FamSched sched;
 };
 
 template <int NP_, int G_>
@@ -339,11 +340,7 @@ __global__ void __launch_bounds__(WPB * 32) viterbi_small_kernel(VitArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   VitSmem<C>& sm = reinterpret_cast<VitSmem<C>*>(smem_raw)[threadIdx.x >> 5];
   const int lane = threadIdx.x & 31;
-  for (;;) {
-    int item = 0;
-    if (lane == 0) item = atomicAdd(a.work_counter, 1);
-    item = __shfl_sync(0xffffffffu, item, 0);
-    if (item >= a.n_items) break;
+  for_each_item(a.sched, a.work_counter, a.n_items, C::SPW, lane, [&](int item) {
     if constexpr (FAMK != FAM_ANY) {
       viterbi_item<C, FAMK>(sm, a, item, lane);
     } else {
@@ -360,7 +357,7 @@ __global__ void __launch_bounds__(WPB * 32) viterbi_small_kernel(VitArgs a) {
         default: viterbi_item<C, FAM_ANY>(sm, a, item, lane); break;
       }
     }
-  }
+  });
 }
 
 }  // namespace hmm
