@@ -479,15 +479,24 @@ __global__ void __launch_bounds__(Cl1<NP_, CLN>::NT, 1) large_fb_cl1_kernel(Larg
   cluster_sync();   // every CTA's barriers initialised before any remote store
 
   auto tof = [&](int k) { return dir == 0 ? k : T - 1 - k; };
-  float lb_cur = (T > 0 && j < N) ? __ldg(a.logb + (base + tof(0)) * N + j) * kLog2ef : -INFINITY;
+  // emissions two steps ahead in a register pair (the loop runs two steps per
+  // pass), raw loads from a clamped row so that nothing waits on them early
+  const int jc = min(j, N - 1);
+  auto lbraw = [&](int k) { return __ldg(a.logb + (base + tof(min(k, T - 1))) * N + jc); };
+  float lbA = 0.f, lbB = 0.f;
+  if (T > 0) {
+    lbA = lbraw(0);
+    lbB = lbraw(1);
+  }
   double O = 0.0;            // log2 offset after the previous step (thread 0)
   bool dead = false;
   float vprev = 0.f, Eprev = 0.f;
   int64_t rowprev = 0;
-  for (int k = 0; k < T; ++k) {
+  auto step = [&](const int k, float& lbr) {
     const int par = k & 1;
     const int64_t row = base + tof(k);
-    const float lb_next = (k + 1 < T && j < N) ? __ldg(a.logb + (base + tof(k + 1)) * N + j) * kLog2ef : -INFINITY;
+    const float lb_cur = j < N ? lbr * kLog2ef : -INFINITY;
+    if (k + 2 < T) lbr = lbraw(k + 2);
     float u;
     if (k == 0) {
       u = dir == 0 ? lb_cur + a.mv.logpi2[(size_t)m * NP + j] : lb_cur;
@@ -513,13 +522,17 @@ __global__ void __launch_bounds__(Cl1<NP_, CLN>::NT, 1) large_fb_cl1_kernel(Larg
         if (rank == 0 && tid == 0) a.oa[rowprev] = O;
       }
       const float* vb = &sm.v[pp][q * S::VP];
-      float2 acc0 = make_float2(0.f, 0.f), acc1 = make_float2(0.f, 0.f);
+      float2 acc[4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) acc[e] = make_float2(0.f, 0.f);
 #pragma unroll
       for (int p = 0; p < RPT / 4; ++p) {
         const float4 x = *reinterpret_cast<const float4*>(vb + 4 * p);
-        acc0 = __ffma2_rn(make_float2(x.x, x.y), Ar[2 * p], acc0);
-        acc1 = __ffma2_rn(make_float2(x.z, x.w), Ar[2 * p + 1], acc1);
+        acc[2 * (p & 1)] = __ffma2_rn(make_float2(x.x, x.y), Ar[2 * p], acc[2 * (p & 1)]);
+        acc[2 * (p & 1) + 1] = __ffma2_rn(make_float2(x.z, x.w), Ar[2 * p + 1], acc[2 * (p & 1) + 1]);
       }
+      const float2 acc0 = make_float2(acc[0].x + acc[2].x, acc[0].y + acc[2].y);
+      const float2 acc1 = make_float2(acc[1].x + acc[3].x, acc[1].y + acc[3].y);
       float Erq = Er[0];
 #pragma unroll
       for (int r = 1; r < CLN; ++r)
@@ -571,7 +584,10 @@ __global__ void __launch_bounds__(Cl1<NP_, CLN>::NT, 1) large_fb_cl1_kernel(Larg
     vprev = vj;
     Eprev = Eown;
     rowprev = row;
-    lb_cur = lb_next;
+  };
+  for (int k = 0; k < T; k += 2) {
+    step(k, lbA);
+    if (k + 1 < T) step(k + 1, lbB);
   }
   if (T > 0) {   // the last step's vector: every incoming store has landed; forward: the last row
     const int pp = (T - 1) & 1;
@@ -630,13 +646,20 @@ __global__ void __launch_bounds__(Cl1<NP_, CLN>::NT, 1) large_vit_cl1_kernel(Lar
   }
   cluster_sync();
 
-  float lb_cur = (T > 0 && j < N) ? __ldg(a.logb + base * N + j) : -INFINITY;
+  const int jc = min(j, N - 1);
+  auto lbraw = [&](int k) { return __ldg(a.logb + (base + min(k, T - 1)) * N + jc); };
+  float lbA = 0.f, lbB = 0.f;
+  if (T > 0) {
+    lbA = lbraw(0);
+    lbB = lbraw(1);
+  }
   double off = 0.0;   // thread 0
   bool dead = false;
-  for (int k = 0; k < T; ++k) {
+  auto step = [&](const int k, float& lbr) {
     const int par = k & 1;
     const int64_t row = base + k;
-    const float lb_next = (k + 1 < T && j < N) ? __ldg(a.logb + (row + 1) * N + j) : -INFINITY;
+    const float lb_cur = j < N ? lbr : -INFINITY;
+    if (k + 2 < T) lbr = lbraw(k + 2);
     float dn;
     if (k == 0) {
       dn = a.mv.logpie[(size_t)m * NP + j] + lb_cur;
@@ -653,21 +676,32 @@ __global__ void __launch_bounds__(Cl1<NP_, CLN>::NT, 1) large_vit_cl1_kernel(Lar
       const bool fin = mx > -INFINITY && mx < INFINITY;
       if (tid == 0 && fin) off += (double)mx;
       const float* vb = &sm.v[pp][q * S::VP];
-      float best = -INFINITY;
-      int arg = 0;
+      // four sub-ranges of the quarter scanned side by side (shorter chains),
+      // then joined in order: a later sub-range only when strictly larger
+      constexpr int PS = RPT / 16;   // float4 blocks per sub-range
+      float bs[4];
+      int as[4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) bs[r] = -INFINITY, as[r] = 0;
 #pragma unroll
       for (int p = 0; p < RPT / 4; ++p) {
+        const int r = p / PS;
         const float4 x = *reinterpret_cast<const float4*>(vb + 4 * p);
         const float d0 = fin ? x.x - mx : x.x, d1 = fin ? x.y - mx : x.y;
         const float d2 = fin ? x.z - mx : x.z, d3 = fin ? x.w - mx : x.w;
         const float cv[4] = {d0 + Ar[2 * p].x, d1 + Ar[2 * p].y, d2 + Ar[2 * p + 1].x, d3 + Ar[2 * p + 1].y};
 #pragma unroll
         for (int e = 0; e < 4; ++e)
-          if (cv[e] > best) {
-            best = cv[e];
-            arg = q * RPT + 4 * p + e;
+          if (cv[e] > bs[r]) {
+            bs[r] = cv[e];
+            as[r] = q * RPT + 4 * p + e;
           }
       }
+      float best = bs[0];
+      int arg = as[0];
+#pragma unroll
+      for (int r = 1; r < 4; ++r)
+        if (bs[r] > best) best = bs[r], arg = as[r];
       // quarters in order: a later quarter wins only when strictly larger
       float bo = __shfl_down_sync(0xffffffffu, best, 8);
       int ao = __shfl_down_sync(0xffffffffu, arg, 8);
@@ -711,7 +745,10 @@ __global__ void __launch_bounds__(Cl1<NP_, CLN>::NT, 1) large_vit_cl1_kernel(Lar
         st_async_f32(mapa(smem_u32(&sm.E[par][rank]), (uint32_t)lane), cm, mapa(smem_u32(&sm.bar[par]), (uint32_t)lane));
       }
     }
-    lb_cur = lb_next;
+  };
+  for (int k = 0; k < T; k += 2) {
+    step(k, lbA);
+    if (k + 1 < T) step(k + 1, lbB);
   }
   if (T > 0) {
     const int pp = (T - 1) & 1;
