@@ -683,13 +683,15 @@ __global__ void __launch_bounds__(Cl1<NP_, CLN>::NT, 1) large_vit_cl1_kernel(Lar
       int as[4];
 #pragma unroll
       for (int r = 0; r < 4; ++r) bs[r] = -INFINITY, as[r] = 0;
+      // x - mx as x + (-mx), and x + (-0) = x exactly when the step is not normalised
+      const float2 neg = fin ? make_float2(-mx, -mx) : make_float2(-0.f, -0.f);
 #pragma unroll
       for (int p = 0; p < RPT / 4; ++p) {
         const int r = p / PS;
         const float4 x = *reinterpret_cast<const float4*>(vb + 4 * p);
-        const float d0 = fin ? x.x - mx : x.x, d1 = fin ? x.y - mx : x.y;
-        const float d2 = fin ? x.z - mx : x.z, d3 = fin ? x.w - mx : x.w;
-        const float cv[4] = {d0 + Ar[2 * p].x, d1 + Ar[2 * p].y, d2 + Ar[2 * p + 1].x, d3 + Ar[2 * p + 1].y};
+        const float2 c01 = __fadd2_rn(__fadd2_rn(make_float2(x.x, x.y), neg), Ar[2 * p]);
+        const float2 c23 = __fadd2_rn(__fadd2_rn(make_float2(x.z, x.w), neg), Ar[2 * p + 1]);
+        const float cv[4] = {c01.x, c01.y, c23.x, c23.y};
 #pragma unroll
         for (int e = 0; e < 4; ++e)
           if (cv[e] > bs[r]) {
