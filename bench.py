@@ -606,6 +606,7 @@ def run_precision(args, emit=True):
                               peak_note="measured bf16 dense GEMM peak (FP16 runs at the BF16 rate)"),
                 breakdown=dict(recursion_ms=rec_ms, emission_ms=per(prof_tc, "emission", steps),
                                posterior_stats_xi_ms=per(prof_tc, "reduce", steps),
+                               xi_gemm_ms=per(prof_tc, "xi", steps),
                                mstep_ms=per(prof_tc, "mstep", steps), viterbi_ms=per(prof_tc, "viterbi", steps)),
                 fp32_path=dict(ms_per_step=ms_32,
                                recursion_ms=prof_32["estep"][0] / max(prof_32["estep"][1], 1),

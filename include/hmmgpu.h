@@ -206,6 +206,7 @@ typedef enum {
   HMM_KT_VITERBI = 3,         /* Viterbi forward + traceback             */
   HMM_KT_EMISSION = 4,        /* emission log-density tables             */
   HMM_KT_PLAIN = 5,           /* plain float32 log-space E-step kernels  */
+  HMM_KT_XI = 6,              /* tensor-core xi GEMM (inside HMM_KT_REDUCE) */
   HMM_KT_SLOTS = 8
 } hmm_kernel_slot;
 

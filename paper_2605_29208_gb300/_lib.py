@@ -13,7 +13,7 @@ STATUS_NAMES = {0: "HMM_OK", 1: "HMM_E_ARG", 2: "HMM_E_NOMEM", 3: "HMM_E_CUDA",
 
 OPT_PROFILE, OPT_ESTEP_LANES, OPT_VITERBI_LANES, OPT_PLAIN_ESTEP, OPT_TENSOR_RECURRENCE = 1, 2, 3, 4, 5
 OPT_TIME_PARALLEL = 6
-KT_SLOTS = ("estep", "reduce", "mstep", "viterbi", "emission", "plain", "slot6", "slot7")
+KT_SLOTS = ("estep", "reduce", "mstep", "viterbi", "emission", "plain", "xi", "slot7")
 
 FAMILY = {"gauss": 0, "poisson": 1, "gamma": 2, "beta": 3, "weibull": 4, "negbin": 5,
           "student_t": 6, "vonmises": 7, "diag_gauss": 8, "full_gauss": 9, "discrete": 10,

@@ -843,6 +843,8 @@ void run_estep_large(hmm_ctx ctx, hmm_model model, const hmm_batch* b, hmm_plan 
     kt.kernels += 2 + (plan->n_tiles > 0);   // prep (+ pad) + GEMM in place of the CUDA-core xi
     ctx->xi_xt.ensure((size_t)NP * plan->xi_ktot * 4);
     ctx->xi_yt.ensure((size_t)NP * plan->xi_ktot * 4);
+    KTimer kx(ctx, HMM_KT_XI, st);
+    kx.kernels = 2 + (plan->n_tiles > 0);
     HMM_CUDA(launch_tc_xi(a, ctx->lg_rz.as<float>(), plan->tile_seq.as<int32_t>(), plan->tile_row.as<int32_t>(),
                           plan->n_tiles, plan->xi_kseq.as<int64_t>(), plan->xi_kc0.as<int64_t>(),
                           plan->xi_kused.as<int32_t>(), plan->xi_kpad.as<int32_t>(), plan->n_chunks, plan->xi_ktot,

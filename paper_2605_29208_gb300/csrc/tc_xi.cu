@@ -7,12 +7,19 @@
 //    contiguous) in a chunk-ordered K layout: the rows of a chunk's
 //    sequences are consecutive, each chunk's range padded to a multiple of 32
 //    with zeros; a 32 x 32 shared-memory transpose per block.
-// 2. xi_tc_kernel: one CTA per (128 i, up to 256 j, chunk) tile, K-blocks of
-//    32 (128 bytes) staged by cp.async into the 128-byte-swizzled K-major
-//    layout, 4 stages; one thread issues tcgen05.mma.kind::tf32 (M = 128,
-//    N = 256, K = 8) into TMEM; the epilogue writes the float64 block.
+// 2. xi_tc_kernel: one CTA per (128 i, up to 256 j, chunk) tile; K-blocks of
+//    32 (128 bytes) of X and Y move by TMA (2D tensor maps, 128-byte swizzle:
+//    the K-major layout the MMA reads) into a ring of 4 stages with full /
+//    empty mbarriers; one thread issues the copies, one thread issues
+//    tcgen05.mma.kind::tf32 (M = 128, N = 256, K = 8) into TMEM; the
+//    epilogue writes the float64 block.
 // TF32 keeps float32's exponent range (1/Z_t can be large) with 10
 // significant bits, the same as the FP16 recursions.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <mutex>
+
 #include "launch.h"
 #include "tc_common.cuh"
 
@@ -79,20 +86,35 @@ __global__ void xi_pad_kernel(const int64_t* __restrict__ kc0, const int32_t* __
   }
 }
 
-__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+// one 2D tensor-map tile (x = K element, y = state row) into shared memory,
+// completing `bar`'s transaction count
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+      : "memory");
 }
 
+// Stage ring: thread 0 loads K-block kb of the X tile (128 states) and the
+// Y tile (TN states) with two TMA copies into stage kb % XI_STAGES once the
+// MMAs of block kb - XI_STAGES have released it (`empty`); thread 32 issues
+// the four MMAs of a block once its copies have landed (`full`) and releases
+// the stage with tcgen05.commit.  The tensor maps' 128-byte swizzle is the
+// K-major layout sw128_desc describes.
 template <int TN>
-__global__ void __launch_bounds__(128, 1) xi_tc_kernel(const float* __restrict__ XT, const float* __restrict__ YT,
-                                                       int64_t ktot, const int64_t* __restrict__ kc0,
+__global__ void __launch_bounds__(128, 1) xi_tc_kernel(const __grid_constant__ CUtensorMap tmX,
+                                                       const __grid_constant__ CUtensorMap tmY,
+                                                       const int64_t* __restrict__ kc0,
                                                        const int32_t* __restrict__ kpad, int NP,
                                                        double* __restrict__ xi_chunk, int* status) {
   constexpr uint32_t A_BYTES = XI_TM * 128, B_BYTES = TN * 128, STAGE = A_BYTES + B_BYTES;
   extern __shared__ uint8_t xr[];
   uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(xr) + 1023) & ~uintptr_t(1023));
-  uint64_t* mb = reinterpret_cast<uint64_t*>(sm + XI_STAGES * STAGE);   // [XI_STAGES] MMA done per stage
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(mb + XI_STAGES);
+  uint64_t* full = reinterpret_cast<uint64_t*>(sm + XI_STAGES * STAGE);   // [XI_STAGES] copies landed
+  uint64_t* empty = full + XI_STAGES;                                     // [XI_STAGES] MMAs of the stage done
+  uint64_t* done = empty + XI_STAGES;                                     // every MMA done
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(done + 1);
   const int tid = threadIdx.x, warp = tid >> 5;
   const int tj_count = NP / TN;
   const int ti = blockIdx.x / tj_count, tj = blockIdx.x % tj_count;
@@ -100,8 +122,14 @@ __global__ void __launch_bounds__(128, 1) xi_tc_kernel(const float* __restrict__
   const int64_t k0 = kc0[c];
   const int nkb = kpad[c] / XI_KB;
   if (tid == 0) {
-    for (int z = 0; z < XI_STAGES; ++z) mbar_init(&mb[z], 1);
+    for (int z = 0; z < XI_STAGES; ++z) {
+      mbar_init(&full[z], 1);
+      mbar_init(&empty[z], 1);
+    }
+    mbar_init(done, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmX)) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmY)) : "memory");
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
@@ -112,47 +140,22 @@ __global__ void __launch_bounds__(128, 1) xi_tc_kernel(const float* __restrict__
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tslot;
-  const float* Ab = XT + (size_t)(ti * XI_TM) * ktot + k0;
-  const float* Bb = YT + (size_t)(tj * TN) * ktot + k0;
-  auto load_stage = [&](int kb, int st) {
-    const uint32_t sa = smem_u32(sm + st * STAGE), sb = sa + A_BYTES;
-    const int64_t ko = (int64_t)kb * XI_KB;
-    for (int z = tid; z < XI_TM * 8; z += 128) {
-      const int row = z >> 3, q = z & 7;
-      cp_async16(sa + sw128_chunk(row, q), Ab + (size_t)row * ktot + ko + q * 4);
+  if (tid == 0) {
+    for (int kb = 0; kb < nkb; ++kb) {
+      const int st = kb % XI_STAGES;
+      if (kb >= XI_STAGES && !mbar_wait(&empty[st], (uint32_t)((kb / XI_STAGES - 1) & 1)))
+        set_status(status, ST_TIMEOUT);
+      mbar_expect_tx(&full[st], STAGE);
+      const uint32_t sa = smem_u32(sm + st * STAGE);
+      const int x = (int)(k0 + (int64_t)kb * XI_KB);
+      tma_load_2d(sa, &tmX, x, ti * XI_TM, smem_u32(&full[st]));
+      tma_load_2d(sa + A_BYTES, &tmY, x, tj * TN, smem_u32(&full[st]));
     }
-    for (int z = tid; z < TN * 8; z += 128) {
-      const int row = z >> 3, q = z & 7;
-      cp_async16(sb + sw128_chunk(row, q), Bb + (size_t)row * ktot + ko + q * 4);
-    }
-    asm volatile("cp.async.commit_group;" ::: "memory");
-  };
-  const uint32_t idesc = tc_idesc_tf32(XI_TM, TN);
-  // prologue: stages 0 .. XI_STAGES-2
-  for (int z = 0; z < XI_STAGES - 1; ++z) {
-    if (z < nkb) load_stage(z, z);
-    else asm volatile("cp.async.commit_group;" ::: "memory");
-  }
-  for (int kb = 0; kb < nkb; ++kb) {
-    const int st = kb % XI_STAGES;
-    // refill the stage that the MMA of kb - 1 used once that MMA is done
-    const int nk = kb + XI_STAGES - 1;
-    if (nk < nkb) {
-      const int ns = nk % XI_STAGES;
-      if (kb >= 1) {
-        // the stage ns was last read by the MMAs of block nk - XI_STAGES = kb - 1
-        if (!mbar_wait(&mb[ns], (uint32_t)(((kb - 1) / XI_STAGES) & 1))) {
-          if (tid == 0) set_status(status, ST_TIMEOUT);
-        }
-      }
-      load_stage(nk, ns);
-    } else {
-      asm volatile("cp.async.commit_group;" ::: "memory");
-    }
-    asm volatile("cp.async.wait_group %0;" ::"n"(XI_STAGES - 1) : "memory");
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    __syncthreads();
-    if (tid == 0) {
+  } else if (tid == 32) {
+    const uint32_t idesc = tc_idesc_tf32(XI_TM, TN);
+    for (int kb = 0; kb < nkb; ++kb) {
+      const int st = kb % XI_STAGES;
+      if (!mbar_wait(&full[st], (uint32_t)((kb / XI_STAGES) & 1))) set_status(status, ST_TIMEOUT);
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const uint32_t sa = smem_u32(sm + st * STAGE), sb = sa + A_BYTES;
 #pragma unroll
@@ -166,17 +169,17 @@ __global__ void __launch_bounds__(128, 1) xi_tc_kernel(const float* __restrict__
             : "memory");
       }
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                       smem_u32(&mb[st]))
+                       smem_u32(&empty[st]))
                    : "memory");
     }
+    if (nkb > 0)
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                       smem_u32(done))
+                   : "memory");
   }
-  // wait for the last block's MMAs (its commit covers every earlier MMA)
-  if (nkb > 0) {
-    const int st = (nkb - 1) % XI_STAGES;
-    if (!mbar_wait(&mb[st], (uint32_t)(((nkb - 1) / XI_STAGES) & 1)))
-      if (tid == 0) set_status(status, ST_TIMEOUT);
-  }
-  asm volatile("cp.async.wait_group 0;" ::: "memory");
+  __syncwarp();
+  if (nkb > 0 && !mbar_wait(done, 0u))
+    if ((tid & 31) == 0) set_status(status, ST_TIMEOUT);
   __syncwarp();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   // epilogue: lane = row i of the tile, 32 columns per load
@@ -207,17 +210,51 @@ __global__ void __launch_bounds__(128, 1) xi_tc_kernel(const float* __restrict__
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TN));
 }
 
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link
+// against the driver library)
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  });
+  return fn;
+}
+
+// [rows][ktot] float32, K contiguous; box of 32 K elements (128 bytes) x box_rows
+// states with 128-byte swizzle
+cudaError_t make_xi_map(CUtensorMap* m, const float* base, int64_t ktot, int rows, int box_rows) {
+  auto enc = tensor_map_encoder();
+  if (!enc) return cudaErrorNotSupported;
+  const cuuint64_t dims[2] = {(cuuint64_t)ktot, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)ktot * sizeof(float)};
+  const cuuint32_t box[2] = {(cuuint32_t)XI_KB, (cuuint32_t)box_rows};
+  const cuuint32_t estr[2] = {1, 1};
+  const CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base), dims, strides, box, estr,
+                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
 template <int TN>
 cudaError_t launch_xi_tn(const float* XT, const float* YT, int64_t ktot, const int64_t* kc0, const int32_t* kpad,
                          int n_chunks, int NP, double* xi_chunk, int* status, cudaStream_t st) {
-  constexpr size_t smem = 1024 + (size_t)XI_STAGES * (XI_TM * 128 + TN * 128) + XI_STAGES * 8 + 16;
+  constexpr size_t smem = 1024 + (size_t)XI_STAGES * (XI_TM * 128 + TN * 128) + (2 * XI_STAGES + 1) * 8 + 16;
+  // TMA coordinates are 32-bit; the K extent is a multiple of 32 (16-byte rows)
+  if (ktot >= (int64_t(1) << 31) || ktot % XI_KB != 0) return cudaErrorInvalidValue;
+  CUtensorMap mx, my;
+  cudaError_t e = make_xi_map(&mx, XT, ktot, NP, XI_TM);
+  if (e == cudaSuccess) e = make_xi_map(&my, YT, ktot, NP, TN);
+  if (e != cudaSuccess) return e;
   auto kern = xi_tc_kernel<TN>;
-  {
-    cudaError_t e = ensure_max_dyn_smem(reinterpret_cast<const void*>(kern), smem);
-    if (e != cudaSuccess) return e;
-  }
+  e = ensure_max_dyn_smem(reinterpret_cast<const void*>(kern), smem);
+  if (e != cudaSuccess) return e;
   const dim3 grid((unsigned)((NP / XI_TM) * (NP / TN)), (unsigned)n_chunks);
-  kern<<<grid, 128, smem, st>>>(XT, YT, ktot, kc0, kpad, NP, xi_chunk, status);
+  kern<<<grid, 128, smem, st>>>(mx, my, kc0, kpad, NP, xi_chunk, status);
   return cudaGetLastError();
 }
 
