@@ -186,9 +186,13 @@ typedef enum {
                                  exp-space form) as tcgen05 GEMMs with FP16
                                  operands and FP32 accumulation; the shift and
                                  the log-likelihood stay in float64.  0 (default):
-                                 float32 CUDA-core recursions.  The FP16 path's
-                                 error against float64 is larger than the float32
-                                 path's (about 1e-3 absolute on gamma).          */
+                                 float32 CUDA-core recursions.  2: the same with
+                                 TF32 operands (10 significant bits as FP16, the
+                                 float32 exponent range) where padded N <= 256;
+                                 at 512 the FP16 recursion runs.  The FP16 and
+                                 TF32 paths' error against float64 is larger than
+                                 the float32 path's (about 1e-3 absolute on
+                                 gamma).                                          */
   HMM_OPT_TIME_PARALLEL = 6     /* forward-backward without statistics at padded
                                  N <= 32: 0 (default) runs the time-parallel form
                                  (chunk transfer matrices, boundary vectors,

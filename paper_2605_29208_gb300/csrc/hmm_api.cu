@@ -829,7 +829,8 @@ void run_estep_large(hmm_ctx ctx, hmm_model model, const hmm_batch* b, hmm_plan 
   {
     KTimer kt(ctx, HMM_KT_ESTEP, st);
     if (ctx->tensor_rec && tc_supported(NP))
-      HMM_CUDA(launch_tc_fb(NP, a, plan->tc_tiles.as<int32_t>(), plan->n_tc_tiles, ctx->status, st));
+      HMM_CUDA(launch_tc_fb(NP, a, plan->tc_tiles.as<int32_t>(), plan->n_tc_tiles, ctx->status,
+                            ctx->tensor_rec == 2 && tc_tf32_supported(NP), st));
     else
       HMM_CUDA(launch_large_fb(NP, a, st));
   }
@@ -1439,7 +1440,7 @@ hmm_status hmm_ctx_set_option(hmm_ctx ctx, int32_t key, int64_t value) {
       case HMM_OPT_ESTEP_LANES: ctx->estep_lanes = (int)value; break;
       case HMM_OPT_VITERBI_LANES: ctx->viterbi_lanes = (int)value; break;
       case HMM_OPT_PLAIN_ESTEP: ctx->plain_estep = value != 0; break;
-      case HMM_OPT_TENSOR_RECURRENCE: ctx->tensor_rec = value != 0; break;
+      case HMM_OPT_TENSOR_RECURRENCE: ctx->tensor_rec = value == 2 ? 2 : (value != 0 ? 1 : 0); break;
       case HMM_OPT_TIME_PARALLEL: ctx->time_parallel = (int)value; break;
       default: throw Error{HMM_E_ARG, "unknown option"};
     }

@@ -73,8 +73,9 @@ cudaError_t launch_large_viterbi_cl(const LargeArgs& a, cudaStream_t st);
 // tensor-core recursions (tcgen05, FP16 operands): padded N in {64, ..., 512},
 // tiles of tc_tile_rows() sequences of one model; same outputs as launch_large_fb
 bool tc_supported(int NP);
+bool tc_tf32_supported(int NP);
 int tc_tile_rows();
-cudaError_t launch_tc_fb(int NP, const LargeArgs& a, const int32_t* tiles, int n_tiles, int* status,
+cudaError_t launch_tc_fb(int NP, const LargeArgs& a, const int32_t* tiles, int n_tiles, int* status, bool tf32,
                          cudaStream_t st);
 // xi blocks on the tensor cores (TF32, K = time), padded N 128-1024: the
 // transposed operands XT / YT [NP][ktot] float32 in the chunk-ordered K layout

@@ -57,12 +57,19 @@ struct TcArgs {
   int* status;
 };
 
-template <int NP>
+// TF: TF32 operands (float32 rounded to 10 significant bits, float32's
+// exponent range) instead of FP16; 32 K elements per 128-byte row, so a
+// CTA's 64-state slice is two K-blocks.
+template <int NP, bool TF>
 struct TcShape {
-  static constexpr int CL = NP / TC_NC;      // CTAs per cluster = K-blocks
-  static constexpr uint32_t V_BYTES = (uint32_t)CL * TC_M * 128;
-  static constexpr uint32_t B_BYTES = (uint32_t)CL * TC_NC * 128;
-  static constexpr uint32_t KB_V = TC_M * 128;   // one K-block of V
+  static constexpr int CL = NP / TC_NC;      // CTAs per cluster = state slices
+  static constexpr int KPB = TF ? 32 : 64;   // K elements per 128-byte K-block row
+  static constexpr int KBS = TC_NC / KPB;    // K-blocks per slice
+  static constexpr uint32_t KB_V = TC_M * 128;          // one K-block of V
+  static constexpr uint32_t SLICE_V = KB_V * KBS;       // one CTA's slice of V
+  static constexpr uint32_t KB_B = TC_NC * 128;         // one K-block of B
+  static constexpr uint32_t V_BYTES = (uint32_t)CL * SLICE_V;
+  static constexpr uint32_t B_BYTES = (uint32_t)(NP / KPB) * KB_B;
   // at least 32 KB so that at most 7 CTAs (448 TMEM columns) share an SM
   static constexpr size_t smem_bytes() {
     const size_t b = 1024 + V_BYTES + B_BYTES + (size_t)CL * TC_M * 4 + 2 * 64 * 4 + (CL + 2) * 8 + 16;
@@ -70,9 +77,19 @@ struct TcShape {
   }
 };
 
-template <int NP>
+__device__ __forceinline__ uint32_t to_tf32(float v) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(v));
+  return r;
+}
+// Byte offset of element (row, k) in a [rows][32] TF32 K-block tile.
+__device__ __forceinline__ uint32_t sw128_off32(int row, int k) {
+  return sw128_chunk(row, k >> 2) + ((k & 3) << 2);
+}
+
+template <int NP, bool TF>
 __global__ void __launch_bounds__(TC_THREADS, 1) tc_fb_kernel(TcArgs a) {
-  using S = TcShape<NP>;
+  using S = TcShape<NP, TF>;
   constexpr int CL = S::CL;
   extern __shared__ uint8_t tc_raw[];
   uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(tc_raw) + 1023) & ~uintptr_t(1023));
@@ -129,7 +146,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_fb_kernel(TcArgs a) {
   for (int idx = tid; idx < TC_NC * NP; idx += TC_THREADS) {
     const int n = idx / NP, k = idx % NP;
     const float v = src[(size_t)(n0 + n) * NP + k] * exp2f(csc[n]);
-    *reinterpret_cast<__half*>(Bs + (k >> 6) * (TC_NC * 128) + sw128_off(n, k & 63)) = __float2half_rn(v);
+    if constexpr (TF)
+      *reinterpret_cast<uint32_t*>(Bs + (k >> 5) * S::KB_B + sw128_off32(n, k & 31)) = to_tf32(v);
+    else
+      *reinterpret_cast<__half*>(Bs + (k >> 6) * S::KB_B + sw128_off(n, k & 63)) = __float2half_rn(v);
   }
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -161,7 +181,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_fb_kernel(TcArgs a) {
   };
   load_lb(0);
   double O = 0.0;
-  const uint32_t idesc = tc_idesc(TC_M, TC_NC);
+  const uint32_t idesc = TF ? tc_idesc_tf32(TC_M, TC_NC) : tc_idesc(TC_M, TC_NC);
   const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16);
 
   for (int k = 0; k < tmax; ++k) {
@@ -173,16 +193,27 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_fb_kernel(TcArgs a) {
         for (int kb = 0; kb < CL; ++kb) {
           if (!mbar_wait(&kbar[kb], (uint32_t)((k - 1) & 1))) set_status(a.status, ST_TIMEOUT);
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-          const uint32_t va = smem_u32(Vs + kb * S::KB_V), ba = smem_u32(Bs + kb * (TC_NC * 128));
 #pragma unroll
-          for (int kk = 0; kk < 4; ++kk) {
-            const uint64_t ad = sw128_desc(va + kk * 32), bd = sw128_desc(ba + kk * 32);
-            const uint32_t acc = (kb | kk) ? 1u : 0u;
-            asm volatile(
-                "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-                "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
-                "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
-                : "memory");
+          for (int sb = 0; sb < S::KBS; ++sb) {
+            const uint32_t va = smem_u32(Vs + kb * S::SLICE_V + sb * S::KB_V);
+            const uint32_t ba = smem_u32(Bs + (kb * S::KBS + sb) * S::KB_B);
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk) {
+              const uint64_t ad = sw128_desc(va + kk * 32), bd = sw128_desc(ba + kk * 32);
+              const uint32_t acc = (kb | sb | kk) ? 1u : 0u;
+              if constexpr (TF)
+                asm volatile(
+                    "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                    "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+                    "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+                    : "memory");
+              else
+                asm volatile(
+                    "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                    "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+                    "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+                    : "memory");
+            }
           }
         }
         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
@@ -249,8 +280,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_fb_kernel(TcArgs a) {
     if (dir == 1 && rank == 0 && act) a.ob[grow] = O;
     O = (k == 0 ? 0.0 : O) + (double)E;
     if (dir == 0 && rank == 0 && act) a.oa[grow] = O;
-    // new vector: float32 rows to global, FP16 slice into K-block `rank`
-    uint8_t* vrow = Vs + rank * S::KB_V;
+    // new vector: float32 rows to global, the FP16 / TF32 slice into slice `rank`
+    uint8_t* vrow = Vs + rank * S::SLICE_V;
 #pragma unroll
     for (int c = 0; c < TC_NC; c += 8) {
       float v[8];
@@ -261,10 +292,19 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_fb_kernel(TcArgs a) {
         *reinterpret_cast<float4*>(g) = make_float4(v[0], v[1], v[2], v[3]);
         *reinterpret_cast<float4*>(g + 4) = make_float4(v[4], v[5], v[6], v[7]);
       }
-      __half2 h[4];
+      if constexpr (TF) {
+        uint8_t* blk = vrow + (c >> 5) * S::KB_V;
+        const int q0 = (c & 31) >> 2;
+        *reinterpret_cast<uint4*>(blk + sw128_chunk(tid, q0)) =
+            make_uint4(to_tf32(v[0]), to_tf32(v[1]), to_tf32(v[2]), to_tf32(v[3]));
+        *reinterpret_cast<uint4*>(blk + sw128_chunk(tid, q0 + 1)) =
+            make_uint4(to_tf32(v[4]), to_tf32(v[5]), to_tf32(v[6]), to_tf32(v[7]));
+      } else {
+        __half2 h[4];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) h[q] = __floats2half2_rn(v[2 * q], v[2 * q + 1]);
-      *reinterpret_cast<uint4*>(vrow + sw128_off(tid, c)) = *reinterpret_cast<uint4*>(h);
+        for (int q = 0; q < 4; ++q) h[q] = __floats2half2_rn(v[2 * q], v[2 * q + 1]);
+        *reinterpret_cast<uint4*>(vrow + sw128_off(tid, c)) = *reinterpret_cast<uint4*>(h);
+      }
     }
     // this warp's 32 rows of the slice (4 KB, contiguous in the swizzled
     // layout) go to the other CTAs; the local K-block counts one arrival per warp
@@ -272,20 +312,22 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_fb_kernel(TcArgs a) {
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncwarp();
     if (k + 1 < tmax && (tid & 31) == 0) {
-      const uint32_t srcv = smem_u32(vrow + warp * 4096);
       for (int p = 0; p < CL; ++p) {
         if (p == (int)rank) continue;
-        const uint32_t dst = mapa(srcv, (uint32_t)p);
         const uint32_t bar = mapa(smem_u32(&kbar[rank]), (uint32_t)p);
-        asm volatile(
-            "cp.async.bulk.shared::cluster.shared::cta.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
-            "r"(srcv), "r"(4096), "r"(bar)
-            : "memory");
+        for (int sb = 0; sb < S::KBS; ++sb) {
+          const uint32_t srcv = smem_u32(vrow + sb * S::KB_V + warp * 4096);
+          asm volatile(
+              "cp.async.bulk.shared::cluster.shared::cta.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                  mapa(srcv, (uint32_t)p)),
+              "r"(srcv), "r"(4096), "r"(bar)
+              : "memory");
+        }
       }
       mbar_arrive(&kbar[rank]);
       if (tid == 0)
         for (int kb = 0; kb < CL; ++kb)
-          if (kb != (int)rank) mbar_expect_tx(&kbar[kb], S::KB_V);
+          if (kb != (int)rank) mbar_expect_tx(&kbar[kb], S::SLICE_V);
     }
     if (k + 1 < tmax) load_lb(k + 1);
   }
@@ -295,10 +337,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_fb_kernel(TcArgs a) {
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_NC));
 }
 
-template <int NP>
+template <int NP, bool TF>
 cudaError_t launch_tc_np(const TcArgs& a, cudaStream_t st) {
-  using S = TcShape<NP>;
-  auto kern = tc_fb_kernel<NP>;
+  using S = TcShape<NP, TF>;
+  auto kern = tc_fb_kernel<NP, TF>;
   {
     cudaError_t e = ensure_max_dyn_smem(reinterpret_cast<const void*>(kern), S::smem_bytes());
     if (e != cudaSuccess) return e;
@@ -324,7 +366,11 @@ int tc_tile_rows() { return TC_M; }
 
 bool tc_supported(int NP) { return NP >= 64 && NP <= 512; }
 
-cudaError_t launch_tc_fb(int NP, const LargeArgs& la, const int32_t* tiles, int n_tiles, int* status,
+// the TF32 vector of a 128-sequence tile is 512 B per sequence at N = 512:
+// with A's columns it no longer fits in shared memory
+bool tc_tf32_supported(int NP) { return NP >= 64 && NP <= 256; }
+
+cudaError_t launch_tc_fb(int NP, const LargeArgs& la, const int32_t* tiles, int n_tiles, int* status, bool tf32,
                          cudaStream_t st) {
   if (n_tiles == 0) return cudaSuccess;
   TcArgs a;
@@ -339,11 +385,19 @@ cudaError_t launch_tc_fb(int NP, const LargeArgs& la, const int32_t* tiles, int 
   a.oa = la.oa;
   a.ob = la.ob;
   a.status = status;
+  if (tf32) {
+    switch (NP) {
+      case 64: return launch_tc_np<64, true>(a, st);
+      case 128: return launch_tc_np<128, true>(a, st);
+      case 256: return launch_tc_np<256, true>(a, st);
+    }
+    return cudaErrorInvalidValue;
+  }
   switch (NP) {
-    case 64: return launch_tc_np<64>(a, st);
-    case 128: return launch_tc_np<128>(a, st);
-    case 256: return launch_tc_np<256>(a, st);
-    case 512: return launch_tc_np<512>(a, st);
+    case 64: return launch_tc_np<64, false>(a, st);
+    case 128: return launch_tc_np<128, false>(a, st);
+    case 256: return launch_tc_np<256, false>(a, st);
+    case 512: return launch_tc_np<512, false>(a, st);
   }
   return cudaErrorInvalidValue;
 }

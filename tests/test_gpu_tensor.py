@@ -144,3 +144,50 @@ def test_tensor_xi_statistics(H, ctx, N):
         np.testing.assert_allclose(rec[2:2 + N], g1, atol=TC_GAMMA_ATOL * len(idx))
         np.testing.assert_allclose(rec[2 + N:2 + N + N * N].reshape(N, N), xi, rtol=5e-3, atol=5e-3)
         np.testing.assert_allclose(rec[2 + N + N * N::3], W, rtol=2e-3, atol=2e-3)
+
+
+# TF32 operands (HMM_OPT_TENSOR_RECURRENCE = 2, padded N <= 256): the same
+# 10 significant bits as FP16 with float32's exponent range, held to the same
+# stated bounds.
+
+@pytest.fixture()
+def ctx32(H):
+    from paper_2605_29208_gb300 import _lib
+    c = H.Context(0)
+    c.set_option(_lib.OPT_TENSOR_RECURRENCE, 2)
+    return c
+
+
+@pytest.mark.parametrize("family,N,D,conc,lengths,n_models", [
+    ("diag_gauss", 64, 4, 1.0, [1, 2, 50, 130, 0, 7], 1),
+    ("gauss", 100, 1, 1.0, MANY, 2),
+    ("gamma", 200, 1, 1.0, [33, 90, 5, 1], 2),
+    ("diag_gauss", 256, 8, 0.1, [1, 40, 97, 150], 1),
+])
+def test_tf32_forward_backward(H, ctx32, family, N, D, conc, lengths, n_models):
+    test_tensor_forward_backward(H, ctx32, family, N, D, conc, lengths, n_models)
+
+
+def test_tf32_em_iteration(H, ctx32):
+    test_tensor_em_iteration(H, ctx32, "gauss", 64, 1)
+
+
+def test_tf32_xi_statistics(H, ctx32):
+    test_tensor_xi_statistics(H, ctx32, 128)
+
+
+def test_tf32_matches_float32_path_and_differs_from_fp16(H, ctx32):
+    """N = 256, 260 sequences, Dirichlet(0.1) rows: the TF32 recursion stays
+    within the bounds of the float32 path, and its log-likelihoods are not
+    the FP16 path's (the operand type really changed)."""
+    from paper_2605_29208_gb300 import _lib
+    models, values, offsets, mid, model, batch = build(H, ctx32, "diag_gauss", 256, 16, 0.1, [64] * 260, 1, 1250)
+    ll2, g2, _ = H.forward_backward(ctx32, model, batch)
+    ctx32.set_option(_lib.OPT_TENSOR_RECURRENCE, 1)
+    ll1, _, _ = H.forward_backward(ctx32, model, batch)
+    ctx32.set_option(_lib.OPT_TENSOR_RECURRENCE, 0)
+    ll0, g0, _ = H.forward_backward(ctx32, model, batch)
+    ll0, ll1, ll2 = ll0.cpu().numpy(), ll1.cpu().numpy(), ll2.cpu().numpy()
+    assert np.all(np.abs(ll2 - ll0) <= TC_LL_RTOL * np.maximum(1.0, np.abs(ll0)))
+    assert float((g2 - g0).abs().max()) <= TC_GAMMA_ATOL
+    assert np.any(ll2 != ll1)
