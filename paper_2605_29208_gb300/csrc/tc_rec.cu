@@ -1,8 +1,9 @@
 // Tensor-core forward / backward recursions for large N (padded N = 64 ...
 // 512): each step of Eq. 2 (and of the backward recursion) in the shifted
 // exp-space form is a GEMM of the tile's 128 scaled vectors with A (or A^T),
-// run by tcgen05.mma (FP16 operands, FP32 accumulator in TMEM); the power-
-// of-two row shift is added back in float64, as on the CUDA-core path.
+// run by tcgen05.mma (FP16 operands, or TF32 for padded N <= 256; FP32
+// accumulator in TMEM); the power-of-two row shift is added back in float64,
+// as on the CUDA-core path.
 //
 // Work layout: a cluster of CL = NP / 64 CTAs owns a tile of 128 sequences
 // of one model; CTA r computes the output states [64 r, 64 r + 64) of every
