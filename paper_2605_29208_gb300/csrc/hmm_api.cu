@@ -1404,6 +1404,7 @@ hmm_status hmm_ctx_destroy(hmm_ctx ctx) {
     ctx->tune_out.release();
     ctx->mvlogb.release();
     ctx->lg_bv.release();
+    ctx->lg_logAT.release();
     ctx->lg_off.release();
     ctx->lg_rz.release();
     ctx->lg_xi.release();
@@ -1890,7 +1891,8 @@ void run_viterbi(hmm_ctx ctx, hmm_model model, const hmm_batch* batch, hmm_plan 
   if (Sn == 0) return;
   if (model->NP > 32) {
     if (!d_logb) d_logb = mv_table(ctx, model, batch, plan, st);
-    ctx->psi.ensure(std::max<int64_t>(batch->total_T, 1) * model->NP * 2 + 64);
+    ctx->psi.ensure(std::max<int64_t>(batch->total_T, 1) * model->NP * 4 + 64);
+    ctx->lg_logAT.ensure((size_t)model->M * model->NP * model->NP * 4);
     LargeArgs a{};
     a.logb = d_logb;
     a.offsets = batch->offsets;
@@ -1901,6 +1903,8 @@ void run_viterbi(hmm_ctx ctx, hmm_model model, const hmm_batch* batch, hmm_plan 
     a.status = ctx->status;
     a.mv = model->view();
     a.psi = ctx->psi.as<uint16_t>();
+    a.drow = ctx->psi.as<float>();
+    a.logAT = ctx->lg_logAT.as<float>();
     a.path = d_path;
     a.score = d_score;
     KTimer kt(ctx, HMM_KT_VITERBI, st);

@@ -208,11 +208,24 @@ cudaError_t launch_fb_np(const LargeArgs& a, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+// out[m][j][i] = ln a_ij (32 x 32 tiles through shared memory)
+__global__ void logA_transpose_kernel(const float* __restrict__ in, int NP, float* __restrict__ out) {
+  __shared__ float tile[32][33];
+  const size_t off = (size_t)blockIdx.z * NP * NP;
+  const int i0 = blockIdx.y * 32, j0 = blockIdx.x * 32;
+  for (int r = threadIdx.y; r < 32; r += 8) tile[r][threadIdx.x] = in[off + (size_t)(i0 + r) * NP + j0 + threadIdx.x];
+  __syncthreads();
+  for (int r = threadIdx.y; r < 32; r += 8) out[off + (size_t)(j0 + r) * NP + i0 + threadIdx.x] = tile[threadIdx.x][r];
+}
+
 template <int NP>
 cudaError_t launch_vit_np(const LargeArgs& a, cudaStream_t st) {
   const size_t smem = LgVitShape<NP>::smem_bytes();
   auto kern = large_viterbi_kernel<NP>;
   cudaError_t e = ensure_max_dyn_smem(reinterpret_cast<const void*>(kern), smem);
+  if (e != cudaSuccess) return e;
+  logA_transpose_kernel<<<dim3(NP / 32, NP / 32, (unsigned)a.mv.M), dim3(32, 8), 0, st>>>(a.mv.logAe, NP, a.logAT);
+  e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   kern<<<(unsigned)a.n_groups, LG_NT, smem, st>>>(a);
   return cudaGetLastError();

@@ -51,7 +51,9 @@ struct LargeArgs {
   double* oa;                  // [total_T] log2 offsets of fv rows
   double* ob;                  // [total_T] log2 offsets of bv rows
   // Viterbi
-  uint16_t* psi;               // [total_T][NP] backpointers
+  uint16_t* psi;               // [total_T][NP] backpointers (cluster kernels)
+  float* drow;                 // [total_T][NP] normalised delta rows (grouped kernel)
+  float* logAT;                // [M][NP][NP] ln a transposed (grouped kernel's traceback)
   int32_t* path;               // [total_T]
   double* score;               // [n_seq]
   int* status;                 // device status word (bounded waits)
@@ -241,10 +243,14 @@ __global__ void __launch_bounds__(LG_NT) large_fb_kernel(LargeArgs a) {
 }
 
 // Max-plus recursion (Eq. 3-4) of one group with the operation order of the
-// float32-mode reading: c = delta(i) + ln a_ij scanned upward with a strict
-// '>', delta_t(j) = best + ln b_j(t), then the step maximum is subtracted and
-// added to a float64 score offset.  Backpointers are 16-bit; the traceback
-// stages LG_TB rows at a time in shared memory.
+// float32-mode reading: c = delta(i) + ln a_ij, delta_t(j) = max_i c + ln b_j(t),
+// then the step maximum is subtracted and added to a float64 score offset.
+// The recursion keeps values only (one add and one maximum per candidate)
+// and stores every step's normalised row d_t [total_T][NP] (float32); the
+// traceback recomputes the one backpointer it needs per step,
+// psi_t(q_t) = the lowest i attaining max_i d_{t-1}(i) + ln a_{i q_t}, from
+// the same float32 operands, which is what an upward strict-'>' scan gives.
+// One warp per sequence of the group walks its path.
 template <int NP>
 struct LgVitShape {
   static constexpr size_t smem_bytes() {
@@ -255,7 +261,6 @@ struct LgVitShape {
 template <int NP>
 __global__ void __launch_bounds__(LG_NT) large_viterbi_kernel(LargeArgs a) {
   using S = LgShape<NP>;
-  static_assert(LG_TB * NP * 2 <= 2 * LG_SB * NP * 4, "traceback stage must fit the recursion buffers");
   extern __shared__ __align__(16) float lsm[];
   __shared__ LgMeta md;
   __shared__ double soff[LG_SB];
@@ -304,46 +309,58 @@ __global__ void __launch_bounds__(LG_NT) large_viterbi_kernel(LargeArgs a) {
 #pragma unroll
         for (int c = 0; c < S::JC; ++c) dn[r][c] = a.mv.logpie[(size_t)m * NP + cg + c * S::CG] + lb[r][c];
     } else {
-      float best[S::SBT][S::JC];
-      int arg[S::SBT][S::JC];
+      // candidates in 8-row blocks of A, the next block's rows loaded while the
+      // current one is used; adds two rows per instruction, two running maxima
+      // per (sequence, column) (the maximum does not depend on the order)
+      float b0[S::SBT][S::JC], b1[S::SBT][S::JC];
 #pragma unroll
       for (int r = 0; r < S::SBT; ++r)
 #pragma unroll
-        for (int c = 0; c < S::JC; ++c) best[r][c] = -INFINITY, arg[r][c] = 0;
+        for (int c = 0; c < S::JC; ++c) b0[r][c] = -INFINITY, b1[r][c] = -INFINITY;
       const float* dp = d0 + ts * S::SBT * NP;
-#pragma unroll 2
-      for (int i = 0; i < NP; i += 4) {
-        float am[4][S::JC];
+      auto load8 = [&](float2 (&am)[4][S::JC], int i) {
 #pragma unroll
-        for (int q = 0; q < 4; ++q)
+        for (int q2 = 0; q2 < 4; ++q2)
 #pragma unroll
           for (int c = 0; c < S::JC; ++c) {
-            const float* p = Mp + (size_t)(i + q) * NP + cg + c * S::CG;
-            am[q][c] = S::A_SMEM ? *p : __ldg(p);
+            const float* p = Mp + (size_t)(i + 2 * q2) * NP + cg + c * S::CG;
+            am[q2][c] = S::A_SMEM ? make_float2(p[0], p[NP]) : make_float2(__ldg(p), __ldg(p + NP));
           }
+      };
+      auto comp8 = [&](const float2 (&am)[4][S::JC], int i) {
 #pragma unroll
         for (int r = 0; r < S::SBT; ++r) {
-          const float4 x = *reinterpret_cast<const float4*>(dp + r * NP + i);
-          const float xs[4] = {x.x, x.y, x.z, x.w};
+          const float4 x0 = *reinterpret_cast<const float4*>(dp + r * NP + i);
+          const float4 x1 = *reinterpret_cast<const float4*>(dp + r * NP + i + 4);
+          const float2 xv[4] = {make_float2(x0.x, x0.y), make_float2(x0.z, x0.w), make_float2(x1.x, x1.y),
+                                make_float2(x1.z, x1.w)};
 #pragma unroll
-          for (int q = 0; q < 4; ++q)
+          for (int q2 = 0; q2 < 4; ++q2)
 #pragma unroll
             for (int c = 0; c < S::JC; ++c) {
-              const float cand = xs[q] + am[q][c];
-              if (cand > best[r][c]) {
-                best[r][c] = cand;
-                arg[r][c] = i + q;
-              }
+              const float2 cc = __fadd2_rn(xv[q2], am[q2][c]);
+              b0[r][c] = fmaxf(b0[r][c], cc.x);
+              b1[r][c] = fmaxf(b1[r][c], cc.y);
             }
         }
+      };
+      float2 amA[4][S::JC], amB[4][S::JC];
+      load8(amA, 0);
+      for (int i = 0; i < NP; i += 16) {
+        load8(amB, i + 8);
+        comp8(amA, i);
+        if (i + 16 < NP) load8(amA, i + 16);
+        comp8(amB, i + 8);
       }
+      float best[S::SBT][S::JC];
 #pragma unroll
       for (int r = 0; r < S::SBT; ++r)
 #pragma unroll
-        for (int c = 0; c < S::JC; ++c) {
-          dn[r][c] = best[r][c] + lb[r][c];
-          if (act[r]) a.psi[row[r] * NP + cg + c * S::CG] = (uint16_t)arg[r][c];
-        }
+        for (int c = 0; c < S::JC; ++c) best[r][c] = fmaxf(b0[r][c], b1[r][c]);
+#pragma unroll
+      for (int r = 0; r < S::SBT; ++r)
+#pragma unroll
+        for (int c = 0; c < S::JC; ++c) dn[r][c] = best[r][c] + lb[r][c];
     }
 #pragma unroll
     for (int r = 0; r < S::SBT; ++r) {
@@ -367,6 +384,7 @@ __global__ void __launch_bounds__(LG_NT) large_viterbi_kernel(LargeArgs a) {
       for (int c = 0; c < S::JC; ++c) {
         const float d = fin ? dn[r][c] - mx : dn[r][c];
         d1[b * NP + cg + c * S::CG] = d;
+        if (act[r]) a.drow[row[r] * NP + cg + c * S::CG] = d;
         if (last) dfin[b * NP + cg + c * S::CG] = d;
       }
       if (last && cg == 0) soff[b] = off[r];
@@ -377,8 +395,8 @@ __global__ void __launch_bounds__(LG_NT) large_viterbi_kernel(LargeArgs a) {
     d1 = tmp;
   }
 
-  // final states and tracebacks, one sequence after another
-  uint16_t* stage = reinterpret_cast<uint16_t*>(vbuf);
+  // final states (the lowest index attaining the maximum of the last row)
+  __shared__ int qfin[LG_SB];
   for (int b = 0; b < LG_SB; ++b) {
     const int s = md.seq[b], T = md.len[b];
     if (s < 0) continue;
@@ -386,7 +404,6 @@ __global__ void __launch_bounds__(LG_NT) large_viterbi_kernel(LargeArgs a) {
       if (tid == 0) a.score[s] = 0.0;
       continue;
     }
-    // lowest index attaining the maximum of the last row
     float mx = -INFINITY;
     for (int j = tid; j < NP; j += LG_NT) mx = fmaxf(mx, dfin[b * NP + j]);
     mx = warp_max_f(mx);
@@ -407,26 +424,55 @@ __global__ void __launch_bounds__(LG_NT) large_viterbi_kernel(LargeArgs a) {
     if (tid == 0) {
       const float d = dfin[b * NP + q];
       a.score[s] = d > -INFINITY ? soff[b] + (double)d : -INFINITY;
+      qfin[b] = q;
     }
-    const int64_t base = md.base[b];
-    int thi = T - 1;
-    while (thi > 0) {
-      const int tlo = max(0, thi - LG_TB);
-      const int rows = thi - tlo;          // rows tlo+1 .. thi
-      __syncthreads();
-      for (int z = tid; z < rows * NP; z += LG_NT)
-        stage[z] = a.psi[(base + tlo + 1) * NP + z];
-      __syncthreads();
-      if (tid == 0) {
-        for (int t = thi; t > tlo; --t) {
-          a.path[base + t] = q;
-          q = stage[(t - tlo - 1) * NP + q];
-        }
-      }
-      thi = tlo;
-    }
-    if (tid == 0) a.path[base] = q;
     __syncthreads();
+  }
+  // tracebacks, warp b on sequence b: lane l scans rows i = l + 32 m upward
+  // (strict '>'), the warp keeps the largest value and, among equal values,
+  // the lowest index.  The next step's row d_{t-2} is loaded while step t is
+  // reduced; ln a_{i q} is read as row q of the transposed table.
+  static_assert(LG_NT / 32 == LG_SB, "one warp per sequence of the group");
+  constexpr int PL = NP / 32;   // rows per lane
+  {
+    const int b = warp, s = md.seq[b], T = md.len[b];
+    if (s >= 0 && T > 0) {
+      const int64_t base = md.base[b];
+      const float* AT = a.logAT + (size_t)m * NP * NP;
+      int q = qfin[b];
+      if (lane == 0) a.path[base + T - 1] = q;
+      float dr[PL];
+      if (T > 1) {
+#pragma unroll
+        for (int p = 0; p < PL; ++p) dr[p] = a.drow[(base + T - 2) * NP + lane + 32 * p];
+      }
+      for (int t = T - 1; t > 0; --t) {
+        float cur[PL];
+#pragma unroll
+        for (int p = 0; p < PL; ++p) cur[p] = dr[p];
+        if (t > 1) {
+#pragma unroll
+          for (int p = 0; p < PL; ++p) dr[p] = a.drow[(base + t - 2) * NP + lane + 32 * p];
+        }
+        const float* arow = AT + (size_t)q * NP;
+        float bv = -INFINITY;
+        int bi = 0;
+#pragma unroll
+        for (int p = 0; p < PL; ++p) {
+          const float c = cur[p] + __ldg(arow + lane + 32 * p);
+          if (c > bv) {
+            bv = c;
+            bi = lane + 32 * p;
+          }
+        }
+        const float wv = warp_max_f(bv);
+        int wi = bv == wv ? bi : NP;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) wi = min(wi, __shfl_xor_sync(0xffffffffu, wi, o));
+        q = wi >= NP ? 0 : wi;
+        if (lane == 0) a.path[base + t - 1] = q;
+      }
+    }
   }
 }
 

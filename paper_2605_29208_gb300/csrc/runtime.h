@@ -112,6 +112,7 @@ struct hmm_ctx_s {
   hmm::DevBuf tune_out;          // outputs of the autotuner's trial runs
   hmm::DevBuf mvlogb;            // [total_T][N] log b table (multivariate and large-N models)
   hmm::DevBuf lg_bv;             // [total_T][NP] large-N backward rows
+  hmm::DevBuf lg_logAT;          // [M][NP][NP] ln a transposed (large-N Viterbi traceback)
   hmm::DevBuf lg_off;            // [2][total_T] float64 log2 offsets (forward, backward)
   hmm::DevBuf lg_rz;             // [total_T] 1 / Z_t
   hmm::DevBuf lg_xi;             // [n_chunks][NP][NP] float64 xi blocks
