@@ -387,6 +387,20 @@ void hmm::fill_plan(hmm_plan p, hmm_ctx ctx, hmm_model model, const hmm_batch* b
     }
     mptr[model->M] = (int32_t)lo.size();
     p->n_chunks = (int)lo.size();
+    {
+      std::vector<int64_t> crow(std::max<int64_t>(S, 1), 0);
+      p->max_chunk_rows = 0;
+      for (size_t c = 0; c < lo.size(); ++c) {
+        int64_t acc = 0;
+        for (int32_t q2 = lo[c]; q2 < hi[c]; ++q2) {
+          crow[q2] = acc;
+          acc += ho[bym[q2] + 1] - ho[bym[q2]];
+        }
+        p->max_chunk_rows = std::max(p->max_chunk_rows, acc);
+      }
+      p->chunk_row0.ensure(crow.size() * 8);
+      HMM_CUDA(cudaMemcpy(p->chunk_row0.p, crow.data(), crow.size() * 8, cudaMemcpyHostToDevice));
+    }
     p->order.ensure(std::max<int64_t>(S, 1) * 4);
     p->seq_by_model.ensure(std::max<int64_t>(S, 1) * 4);
     p->chunk_lo.ensure(std::max<size_t>(lo.size(), 1) * 4);
@@ -546,7 +560,7 @@ void hmm::destroy_plan(hmm_plan p) {
   p->tile_row.release();
   p->lg_groups.release();
   p->tc_tiles.release();
-  for (auto* bb : {&p->xi_kseq, &p->xi_kc0, &p->xi_kused, &p->xi_kpad, &p->tp_chunk_seq, &p->tp_chunk_t0,
+  for (auto* bb : {&p->chunk_row0, &p->xi_kseq, &p->xi_kc0, &p->xi_kused, &p->xi_kpad, &p->tp_chunk_seq, &p->tp_chunk_t0,
                    &p->tp_seq_chunk0, &p->tp_seq_nchunk, &p->fam_seg_seq, &p->fam_seg_sm})
     bb->release();
   delete p;
@@ -725,18 +739,27 @@ int mv_statistics(hmm_ctx ctx, hmm_model model, const hmm_batch* b, hmm_plan pla
     // tiled raw moments per chunk (symbol counts for the discrete family),
     // fixed-order model sums, then the shift to the current means
     if (plan->n_chunks > 0) {
+      // row splits of about 4096 rows (at most 64) so that long chunks run on
+      // many blocks
       const int ftiles = (KS + MVM_TILE - 1) / MVM_TILE;
-      mv_moments_kernel<<<dim3((unsigned)(((NP + MVM_TILE - 1) / MVM_TILE) * ftiles), (unsigned)plan->n_chunks), 256, 0,
-                          st>>>(
-          model->family.as<int>(), NP, model->N, model->D, KS, b->values, stats->gamma.as<float>(), b->offsets,
-          b->model_id, plan->seq_by_model.as<int32_t>(), plan->chunk_lo.as<int32_t>(), plan->chunk_hi.as<int32_t>(),
-          stats->mv_chunk.as<double>());
+      const int split = (int)std::min<int64_t>(64, std::max<int64_t>(1, (plan->max_chunk_rows + 4095) / 4096));
+      stats->mv_split.ensure((size_t)plan->n_chunks * split * RS * 8);
+      mv_moments_kernel<<<dim3((unsigned)(((NP + MVM_TILE - 1) / MVM_TILE) * ftiles), (unsigned)plan->n_chunks,
+                               (unsigned)split),
+                          256, 0, st>>>(model->family.as<int>(), NP, model->N, model->D, KS, b->values,
+                                        stats->gamma.as<float>(), b->offsets, b->model_id,
+                                        plan->seq_by_model.as<int32_t>(), plan->chunk_lo.as<int32_t>(),
+                                        plan->chunk_hi.as<int32_t>(), plan->chunk_row0.as<int64_t>(), split,
+                                        stats->mv_split.as<double>());
+      HMM_CUDA(cudaGetLastError());
+      mv_split_combine_kernel<<<dim3((unsigned)std::min<int64_t>((RS + 255) / 256, 64), (unsigned)plan->n_chunks), 256,
+                                0, st>>>(stats->mv_split.as<double>(), split, RS, stats->mv_chunk.as<double>());
       HMM_CUDA(cudaGetLastError());
     }
     reduce_chunks_l2<<<model->M, 128, 0, st>>>(stats->mv_chunk.as<double>(), plan->model_chunk_ptr.as<int32_t>(), RS,
                                                stats->mv_rec.as<double>());
     HMM_CUDA(cudaGetLastError());
-    nk = (plan->n_chunks > 0) + 1;
+    nk = 2 * (plan->n_chunks > 0) + 1;
   }
   if (raw) {   // counts and feature sums need no shift
     if (model->any_support) {   // support min / max of the uniform and Pareto states
@@ -761,7 +784,7 @@ int mv_statistics(hmm_ctx ctx, hmm_model model, const hmm_batch* b, hmm_plan pla
                                                      NP, model->N, model->D, model->KM, KS,
                                                      stats->mv_rec.as<double>());
     HMM_CUDA(cudaGetLastError());
-    return (plan->n_chunks > 0) + 2;
+    return 2 * (plan->n_chunks > 0) + 2;
   }
   if (S > 0) {
     mv_stats_kernel<<<(unsigned)S, 128, 0, st>>>(model->family.as<int>(), model->mvcoef.as<float>(), NP, model->N,
@@ -1148,7 +1171,8 @@ void run_mstep(hmm_ctx ctx, hmm_model model, hmm_stats stats, const MStepOpts& o
   }
   {
     KTimer kt(ctx, HMM_KT_MSTEP, st);
-    kt.kernels = 1 + 2 * (int)model->any_discrete + 2 * (int)model->any_mv + (int)model->any_ext +
+    kt.kernels = 1 + 2 * (model->NP > 32) + 2 * (int)model->any_discrete + 2 * (int)model->any_mv +
+                 (int)model->any_ext +
                  2 * (int)model->any_indep;
     if (model->any_indep) {   // Sec. 4.5: every component's scalar update with the state's weights
       const int n = model->M * model->NP * model->D;
@@ -1166,8 +1190,20 @@ void run_mstep(hmm_ctx ctx, hmm_model model, hmm_stats stats, const MStepOpts& o
                                                         model->M, model->NP, model->N, model->P, model->KS, o);
       HMM_CUDA(cudaGetLastError());
     }
-    mstep_kernel<<<model->M, model->NP, 0, st>>>(model->bufs(), stats->rec.as<double>(), o, dps);
+    // above 32 states the transition rows and their float32 tables run as
+    // their own kernels (one block per row, one thread per entry): one thread
+    // per state would leave a single model's M-step on one SM, dominated by
+    // its N float64 logarithms
+    const bool rows_split = model->NP > 32;
+    mstep_kernel<<<model->M, model->NP, 0, st>>>(model->bufs(), stats->rec.as<double>(), o, dps, rows_split);
     HMM_CUDA(cudaGetLastError());
+    if (rows_split) {
+      mstep_rows_kernel<<<model->M * model->NP, 128, 0, st>>>(model->bufs(), stats->rec.as<double>(), o);
+      HMM_CUDA(cudaGetLastError());
+      const int64_t ne = (int64_t)model->M * model->NP * model->NP;
+      derive_tables_kernel<<<(unsigned)((ne + 255) / 256), 256, 0, st>>>(model->bufs());
+      HMM_CUDA(cudaGetLastError());
+    }
     if (model->any_indep) {
       const int n = model->M * model->NP * model->D;
       indep_derive_kernel<<<(n + 127) / 128, 128, 0, st>>>(model->icomp.as<int>(), model->theta.as<double>(),
@@ -2081,7 +2117,7 @@ hmm_status hmm_stats_destroy(hmm_stats stats) {
   return guarded([&] {
     if (!stats) return;
     for (auto* bb : {&stats->rec, &stats->gamma, &stats->dps, &stats->dp_part, &stats->dp_chunk, &stats->dp_rec,
-                     &stats->dp_count, &stats->mv_part, &stats->mv_chunk, &stats->mv_rec,
+                     &stats->dp_count, &stats->mv_part, &stats->mv_split, &stats->mv_chunk, &stats->mv_rec,
                      &stats->ext_mm, &stats->nb_hist, &stats->nb_tail})
       bb->release();
     delete stats;

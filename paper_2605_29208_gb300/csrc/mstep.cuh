@@ -204,16 +204,23 @@ __device__ inline int additive_slot(int fam) {
 }
 
 // One thread per (model, state row): refresh every derived table of the row.
-__device__ inline void derive_row(const ModelBufs& mb, int m, int k) {
+// the float32 transition tables of entry (m, k, j): linear, transposed, log2, ln
+__device__ __forceinline__ void derive_entry(const ModelBufs& mb, int m, int k, int j) {
   const int NP = mb.NP, N = mb.N;
   const size_t row = ((size_t)m * NP + k) * NP;
-  for (int j = 0; j < NP; ++j) {
-    const double a = (k < N && j < N) ? mb.A[row + j] : 0.0;
-    mb.A32[row + j] = (float)a;
-    if (mb.AT32) mb.AT32[((size_t)m * NP + j) * NP + k] = (float)a;
-    mb.logA2[row + j] = a > 0.0 ? (float)log2(a) : -INFINITY;
-    mb.logAe[row + j] = a > 0.0 ? (float)log(a) : -INFINITY;
-  }
+  const double a = (k < N && j < N) ? mb.A[row + j] : 0.0;
+  mb.A32[row + j] = (float)a;
+  if (mb.AT32) mb.AT32[((size_t)m * NP + j) * NP + k] = (float)a;
+  mb.logA2[row + j] = a > 0.0 ? (float)log2(a) : -INFINITY;
+  mb.logAe[row + j] = a > 0.0 ? (float)log(a) : -INFINITY;
+}
+
+// tables: also the row's transition tables (float64 logarithms: at large N
+// the M-step leaves them to derive_tables_kernel, one thread per entry)
+__device__ inline void derive_row(const ModelBufs& mb, int m, int k, bool tables = true) {
+  const int NP = mb.NP, N = mb.N;
+  if (tables)
+    for (int j = 0; j < NP; ++j) derive_entry(mb, m, k, j);
   const double p = k < N ? mb.pi[(size_t)m * NP + k] : 0.0;
   mb.pi32[(size_t)m * NP + k] = (float)p;
   mb.logpi2[(size_t)m * NP + k] = p > 0.0 ? (float)log2(p) : -INFINITY;
@@ -236,6 +243,13 @@ __global__ void derive_kernel(ModelBufs mb) {
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= mb.M * mb.NP) return;
   derive_row(mb, idx / mb.NP, idx % mb.NP);
+}
+
+__global__ void derive_tables_kernel(ModelBufs mb) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t NP = mb.NP;
+  if (idx >= (int64_t)mb.M * NP * NP) return;
+  derive_entry(mb, (int)(idx / (NP * NP)), (int)(idx / NP % NP), (int)(idx % NP));
 }
 
 __global__ void lfact_kernel(float* lfact2) {
@@ -376,7 +390,7 @@ __device__ inline bool valid_update(int fam, const double* th) {
 // then the derived tables of row k.  Families whose Newton step needs data
 // passes (Weibull, negative binomial) get their seed here and are finished by
 // the data-pass kernels.
-__global__ void mstep_kernel(ModelBufs mb, const double* __restrict__ rec, MStepOpts o, DPState* dps) {
+__global__ void mstep_kernel(ModelBufs mb, const double* __restrict__ rec, MStepOpts o, DPState* dps, bool rows_split) {
   const int m = blockIdx.x, k = threadIdx.x;
   const int NP = mb.NP, N = mb.N;
   if (k >= NP) return;
@@ -473,21 +487,50 @@ __global__ void mstep_kernel(ModelBufs mb, const double* __restrict__ rec, MStep
     }
     if (o.update_transitions) {
       // expected (Baum-Welch: a_ij X_ij) or counted (Viterbi training: X_ij)
-      // transitions, plus the Dirichlet pseudo-counts of the MAP reading
-      double* Arow = mb.A + ((size_t)m * NP + k) * NP;
-      const double* X = R + rec_xi(NP) + k * NP;
+      // transitions, plus the Dirichlet pseudo-counts of the MAP reading;
+      // above 32 states mstep_rows_kernel updates the rows
       const double cA = o.prior_A > 1.0 ? o.prior_A - 1.0 : 0.0;
       const double cp = o.prior_pi > 1.0 ? o.prior_pi - 1.0 : 0.0;
-      double den = 0.0;
-      for (int j = 0; j < N; ++j) den += (o.hard ? X[j] : Arow[j] * X[j]) + cA;
-      if (den >= o.collapse_eps)
-        for (int j = 0; j < N; ++j) Arow[j] = ((o.hard ? X[j] : Arow[j] * X[j]) + cA) / den;
+      if (!rows_split) {
+        double* Arow = mb.A + ((size_t)m * NP + k) * NP;
+        const double* X = R + rec_xi(NP) + k * NP;
+        double den = 0.0;
+        for (int j = 0; j < N; ++j) den += (o.hard ? X[j] : Arow[j] * X[j]) + cA;
+        if (den >= o.collapse_eps)
+          for (int j = 0; j < N; ++j) Arow[j] = ((o.hard ? X[j] : Arow[j] * X[j]) + cA) / den;
+      }
       const double ns = R[0];
       if (ns > 0.0) mb.pi[(size_t)m * NP + k] = (R[rec_g1(NP) + k] + cp) / (ns + N * cp);
     }
   }
   __syncthreads();
-  derive_row(mb, m, k);
+  derive_row(mb, m, k, !rows_split);
+}
+
+// Transition row k of model m: expected (Baum-Welch: a_ij X_ij) or counted
+// (Viterbi training: X_ij) transitions plus the Dirichlet pseudo-counts of
+// the MAP reading, over their sum (128 strided partial sums added by a fixed
+// tree).  One block of 128 threads per row; derive_tables_kernel follows.
+__global__ void __launch_bounds__(128) mstep_rows_kernel(ModelBufs mb, const double* __restrict__ rec, MStepOpts o) {
+  const int NP = mb.NP, N = mb.N;
+  const int m = blockIdx.x / NP, k = blockIdx.x % NP, tid = threadIdx.x;
+  if (k >= N || !o.update_transitions) return;
+  const double* R = rec + (size_t)m * rec_size(NP);
+  double* Arow = mb.A + ((size_t)m * NP + k) * NP;
+  const double* X = R + rec_xi(NP) + k * NP;
+  const double cA = o.prior_A > 1.0 ? o.prior_A - 1.0 : 0.0;
+  __shared__ double red[128];
+  double part = 0.0;
+  for (int j = tid; j < N; j += 128) part += (o.hard ? X[j] : Arow[j] * X[j]) + cA;
+  red[tid] = part;
+  __syncthreads();
+  for (int w = 64; w > 0; w >>= 1) {
+    if (tid < w) red[tid] += red[tid + w];
+    __syncthreads();
+  }
+  const double den = red[0];
+  if (den >= o.collapse_eps)
+    for (int j = tid; j < N; j += 128) Arow[j] = ((o.hard ? X[j] : Arow[j] * X[j]) + cA) / den;
 }
 
 // ---------------------------------------------------------------------------

@@ -264,6 +264,12 @@ __device__ __forceinline__ float mv_feature(int fam, int D, int z, const float* 
   return q < D * D ? yr[q / D] * yr[q % D] : 0.f;
 }
 
+// Block (tile, c, z): rows [z per, (z + 1) per) of chunk c's rows taken in
+// seq_by_model order (crow[q] = the chunk rows before position q), in slabs
+// of MVM_KT rows; the next slab's values are loaded into registers while the
+// current one is accumulated (double-buffered shared memory, one barrier per
+// slab).  part[(c split + z)][NP][KS] float64; mv_split_combine_kernel adds
+// the splits of a chunk in order.
 __global__ void __launch_bounds__(256) mv_moments_kernel(const int* __restrict__ family, int NP, int N, int D, int KS,
                                                          const float* __restrict__ y, const float* __restrict__ gamma,
                                                          const int64_t* __restrict__ offsets,
@@ -271,51 +277,71 @@ __global__ void __launch_bounds__(256) mv_moments_kernel(const int* __restrict__
                                                          const int32_t* __restrict__ seq_by_model,
                                                          const int32_t* __restrict__ chunk_lo,
                                                          const int32_t* __restrict__ chunk_hi,
-                                                         double* __restrict__ out) {
-  __shared__ __align__(16) float Xs[MVM_KT][MVM_TILE];
-  __shared__ __align__(16) float Fs[MVM_KT][MVM_TILE];
+                                                         const int64_t* __restrict__ crow, int split,
+                                                         double* __restrict__ part) {
+  __shared__ __align__(16) float Xs[2][MVM_KT][MVM_TILE];
+  __shared__ __align__(16) float Fs[2][MVM_KT][MVM_TILE];
   const int ftiles = (KS + MVM_TILE - 1) / MVM_TILE;
   const int ti = blockIdx.x / ftiles, tf = blockIdx.x % ftiles;
-  const int c = blockIdx.y;
+  const int c = blockIdx.y, zsp = blockIdx.z;
   const int tid = threadIdx.x, ty = tid / 16, tx = tid % 16;
   const int lo = chunk_lo[c], hi = chunk_hi[c];
   const int fam = family[model_id[seq_by_model[lo]]];
   const int nf = fam == HMM_DISCRETE ? KS : (is_ext_family(fam) ? ext_stat_count(fam) : mv_stat_count(fam, D));
+  const int slast = seq_by_model[hi - 1];
+  const int64_t rows = crow[hi - 1] + (offsets[slast + 1] - offsets[slast]);
+  const int64_t per = (rows + split - 1) / split;
+  const int64_t r0 = (int64_t)zsp * per < rows ? (int64_t)zsp * per : rows, r1 = r0 + per < rows ? r0 + per : rows;
   float acc[4][4];
   double dacc[4][4];
 #pragma unroll
   for (int p = 0; p < 4; ++p)
 #pragma unroll
     for (int q = 0; q < 4; ++q) acc[p][q] = 0.f, dacc[p][q] = 0.0;
-  int since = 0;
-  for (int qs = lo; qs < hi; ++qs) {
+  int since = 0, buf = 0;
+  constexpr int PER_T = MVM_KT * MVM_TILE / 256;   // slab entries per thread
+  for (int qs = lo; qs < hi && r0 < r1; ++qs) {
     const int s = seq_by_model[qs];
-    const int64_t b = offsets[s], e = offsets[s + 1];
-    for (int64_t t0 = b; t0 < e; t0 += MVM_KT) {
-      for (int z = tid; z < MVM_KT * MVM_TILE; z += 256) {
-        const int r = z / MVM_TILE, col = z % MVM_TILE;
+    const int64_t b = offsets[s], len = offsets[s + 1] - b, cs = crow[qs];
+    const int64_t ta = r0 - cs > 0 ? r0 - cs : 0, tb = r1 - cs < len ? r1 - cs : len;
+    if (ta >= tb) continue;
+    float px[PER_T], pf[PER_T];
+    auto fetch = [&](int64_t t0) {
+#pragma unroll
+      for (int e = 0; e < PER_T; ++e) {
+        const int z = tid + 256 * e, r = z / MVM_TILE, col = z % MVM_TILE;
         const int64_t t = t0 + r;
         float xv = 0.f, fv = 0.f;
-        if (t < e) {
+        if (t < tb) {
           const int j = ti * MVM_TILE + col, f = tf * MVM_TILE + col;
-          if (j < N) xv = gamma[t * N + j];
-          if (f < nf) fv = mv_feature(fam, D, f, y + t * D);
+          if (j < N) xv = gamma[(b + t) * N + j];
+          if (f < nf) fv = mv_feature(fam, D, f, y + (b + t) * D);
         }
-        Xs[r][col] = xv;
-        Fs[r][col] = fv;
+        px[e] = xv;
+        pf[e] = fv;
       }
+    };
+    fetch(ta);
+    for (int64_t t0 = ta; t0 < tb; t0 += MVM_KT) {
+#pragma unroll
+      for (int e = 0; e < PER_T; ++e) {
+        const int z = tid + 256 * e, r = z / MVM_TILE, col = z % MVM_TILE;
+        Xs[buf][r][col] = px[e];
+        Fs[buf][r][col] = pf[e];
+      }
+      if (t0 + MVM_KT < tb) fetch(t0 + MVM_KT);
       __syncthreads();
 #pragma unroll
       for (int r = 0; r < MVM_KT; ++r) {
-        const float4 x = *reinterpret_cast<const float4*>(&Xs[r][ty * 4]);
-        const float4 f4 = *reinterpret_cast<const float4*>(&Fs[r][tx * 4]);
+        const float4 x = *reinterpret_cast<const float4*>(&Xs[buf][r][ty * 4]);
+        const float4 f4 = *reinterpret_cast<const float4*>(&Fs[buf][r][tx * 4]);
         const float xa[4] = {x.x, x.y, x.z, x.w}, fa[4] = {f4.x, f4.y, f4.z, f4.w};
 #pragma unroll
         for (int p = 0; p < 4; ++p)
 #pragma unroll
           for (int q = 0; q < 4; ++q) acc[p][q] = fmaf(xa[p], fa[q], acc[p][q]);
       }
-      __syncthreads();
+      buf ^= 1;
       since += MVM_KT;
       if (since >= 256) {
 #pragma unroll
@@ -326,7 +352,7 @@ __global__ void __launch_bounds__(256) mv_moments_kernel(const int* __restrict__
       }
     }
   }
-  double* o = out + (size_t)c * NP * KS;
+  double* o = part + ((size_t)c * split + zsp) * NP * KS;
 #pragma unroll
   for (int p = 0; p < 4; ++p)
 #pragma unroll
@@ -334,6 +360,17 @@ __global__ void __launch_bounds__(256) mv_moments_kernel(const int* __restrict__
       const int j = ti * MVM_TILE + ty * 4 + p, f = tf * MVM_TILE + tx * 4 + q;
       if (j < NP && f < KS) o[(size_t)j * KS + f] = dacc[p][q] + (double)acc[p][q];
     }
+}
+
+// out[c][e] = sum over z = 0, 1, .. of part[c split + z][e] (fixed order)
+__global__ void mv_split_combine_kernel(const double* __restrict__ part, int split, int64_t rec,
+                                        double* __restrict__ out) {
+  const int c = blockIdx.y;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < rec; e += (int64_t)gridDim.x * blockDim.x) {
+    double v = 0.0;
+    for (int z = 0; z < split; ++z) v += part[((size_t)c * split + z) * rec + e];
+    out[(size_t)c * rec + e] = v;
+  }
 }
 
 // Raw feature sums per sequence for padded N <= 32 and few features

@@ -182,6 +182,7 @@ struct hmm_stats_s {
   hmm::DevBuf nb_tail;           // [S] u8: the sequence holds a count >= NB_YMAX
   hmm::DevBuf dp_count;          // active-state counters of the passes
   hmm::DevBuf mv_part;           // [S][NP][KS] float32 multivariate moments
+  hmm::DevBuf mv_split;          // [n_chunks][split][NP][KS] float64 row-split partial moments
   hmm::DevBuf mv_chunk;          // [n_chunks][NP*KS] float64
   hmm::DevBuf mv_rec;            // [M][NP*KS] float64
   hmm::DevBuf ext_mm;            // [M][NP][2] int32 ordered keys of the support min / max
@@ -203,6 +204,8 @@ struct hmm_plan_s {
   hmm::DevBuf seq_by_model;      // [S] int32
   hmm::DevBuf chunk_lo, chunk_hi;// [n_chunks] int32
   hmm::DevBuf model_chunk_ptr;   // [M+1] int32
+  hmm::DevBuf chunk_row0;        // [S] int64: rows of the chunk's earlier sequences (seq_by_model order)
+  int64_t max_chunk_rows = 0;    // rows of the longest chunk
   int n_chunks = 0;
   int uniform_family = -1;       // the one family of all sequences, or -1
   int estep_G = 0;               // chain widths chosen by hmm_plan_autotune (0: default)
