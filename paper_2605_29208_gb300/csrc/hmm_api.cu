@@ -1244,19 +1244,23 @@ void run_mstep(hmm_ctx ctx, hmm_model model, hmm_stats stats, const MStepOpts& o
   stats->dp_chunk.ensure((size_t)std::max(plan ? plan->n_chunks : 0, 1) * RS * 8);
   stats->dp_rec.ensure((size_t)model->M * RS * 8);
   const int passes = std::min(o.newton_maxit, 24);   // + one final pass
-  const unsigned blocks = (unsigned)((S * 32 + 255) / 256);
+  // a warp per sequence, grid-stride: passes after convergence exit in few blocks
+  const unsigned blocks = (unsigned)std::min<int64_t>((S * 32 + 255) / 256, (int64_t)ctx->n_sm * 8);
   const int nthr = model->M * NP;
   KTimer kt(ctx, HMM_KT_MSTEP, st);
-  kt.kernels = 2 + (passes + 1) * ((int)model->any_negbin + (S > 0 ? 3 + (plan->n_chunks > 0) : 1));
+  kt.kernels = 2 + (int)model->any_negbin +
+               (passes + 1) * ((int)model->any_negbin + (S > 0 ? 3 + (plan->n_chunks > 0) : 1));
   prepare_mstep(model, stats, b, plan);
   if (model->any_negbin && S > 0) {   // weighted histograms of the small counts, once per M-step
     HMM_CUDA(cudaMemsetAsync(stats->nb_hist.p, 0, (size_t)model->M * NP * NB_YMAX * 8, st));
     HMM_CUDA(cudaMemsetAsync(stats->nb_tail.p, 0, (size_t)S, st));
     if (plan->n_chunks > 0) {
-      nb_hist_kernel<<<plan->n_chunks, 256, (size_t)NP * NB_YMAX * 8, st>>>(
+      // row splits of about 4096 rows per chunk (at most 64)
+      const int split = (int)std::min<int64_t>(64, std::max<int64_t>(1, (plan->max_chunk_rows + 4095) / 4096));
+      nb_hist_kernel<<<dim3((unsigned)plan->n_chunks, (unsigned)split), 256, (size_t)NP * NB_YMAX * 8, st>>>(
           model->bufs(), b->values, stats->gamma.as<float>(), b->offsets, b->model_id,
           plan->seq_by_model.as<int32_t>(), plan->chunk_lo.as<int32_t>(), plan->chunk_hi.as<int32_t>(),
-          stats->nb_hist.as<unsigned long long>(), stats->nb_tail.as<uint8_t>());
+          plan->chunk_row0.as<int64_t>(), split, stats->nb_hist.as<unsigned long long>(), stats->nb_tail.as<uint8_t>());
       HMM_CUDA(cudaGetLastError());
     }
     kt.kernels += 3;
@@ -1277,11 +1281,11 @@ void run_mstep(hmm_ctx ctx, hmm_model model, hmm_stats stats, const MStepOpts& o
         reduce_records_l1<<<plan->n_chunks, 128, 0, st>>>(stats->dp_part.as<float>(), RS,
                                                         plan->seq_by_model.as<int32_t>(),
                                                         plan->chunk_lo.as<int32_t>(), plan->chunk_hi.as<int32_t>(),
-                                                        stats->dp_chunk.as<double>());
+                                                        stats->dp_chunk.as<double>(), cnt + it);
         HMM_CUDA(cudaGetLastError());
       }
       reduce_chunks_l2<<<model->M, 128, 0, st>>>(stats->dp_chunk.as<double>(), plan->model_chunk_ptr.as<int32_t>(),
-                                                 RS, stats->dp_rec.as<double>());
+                                                 RS, stats->dp_rec.as<double>(), cnt + it);
       HMM_CUDA(cudaGetLastError());
       if (model->any_negbin) {   // the histogram rows of the negative-binomial sums
         const int nw = model->M * NP;
@@ -1300,6 +1304,10 @@ void run_mstep(hmm_ctx ctx, hmm_model model, hmm_stats stats, const MStepOpts& o
   }
   dp_finish_kernel<<<(nthr + 127) / 128, 128, 0, st>>>(model->bufs());
   HMM_CUDA(cudaGetLastError());
+  if (model->any_negbin) {   // the count tables of the new r, one warp per state
+    nb_table_kernel<<<(unsigned)((nthr * 32 + 255) / 256), 256, 0, st>>>(model->bufs());
+    HMM_CUDA(cudaGetLastError());
+  }
 }
 
 }  // namespace

@@ -52,9 +52,12 @@ __global__ void reduce_estep_l1(const float* __restrict__ partials, const double
 }
 
 // Level 2: a model's chunk records in order -> the model's record.
+// active (optional): nothing to do when *active == 0 (a Newton data pass
+// after every state converged; its update reads nothing)
 __global__ void reduce_chunks_l2(const double* __restrict__ chunk_rec,
                                  const int32_t* __restrict__ model_chunk_ptr, int RS,
-                                 double* __restrict__ rec) {
+                                 double* __restrict__ rec, const int* __restrict__ active = nullptr) {
+  if (active && *active == 0) return;
   const int m = blockIdx.x;
   const int c0 = model_chunk_ptr[m], c1 = model_chunk_ptr[m + 1];
   for (int f = threadIdx.x; f < RS; f += blockDim.x) {
@@ -217,7 +220,9 @@ __device__ __forceinline__ void derive_entry(const ModelBufs& mb, int m, int k, 
 
 // tables: also the row's transition tables (float64 logarithms: at large N
 // the M-step leaves them to derive_tables_kernel, one thread per entry)
-__device__ inline void derive_row(const ModelBufs& mb, int m, int k, bool tables = true) {
+// nbtab: also the negative-binomial count table (511 float64 logarithms; the
+// M-step leaves it to nb_table_kernel, one warp per state)
+__device__ inline void derive_row(const ModelBufs& mb, int m, int k, bool tables = true, bool nbtab = true) {
   const int NP = mb.NP, N = mb.N;
   if (tables)
     for (int j = 0; j < NP; ++j) derive_entry(mb, m, k, j);
@@ -228,7 +233,7 @@ __device__ inline void derive_row(const ModelBufs& mb, int m, int k, bool tables
   if (k < N) {
     float* nbt = mb.nbtab ? mb.nbtab + ((size_t)m * NP + k) * NB_YMAX : nullptr;
     derive_coef(mb.family[m], mb.theta + ((size_t)m * NP + k) * mb.P,
-                mb.coef + ((size_t)m * NP + k) * KC, mb.family[m] == HMM_NEGBIN ? nbt : nullptr);
+                mb.coef + ((size_t)m * NP + k) * KC, (nbtab && mb.family[m] == HMM_NEGBIN) ? nbt : nullptr);
   } else {
     // padding state: zero multipliers and a -inf additive constant give
     // log b = -inf for every observation inside the support
@@ -504,7 +509,40 @@ __global__ void mstep_kernel(ModelBufs mb, const double* __restrict__ rec, MStep
     }
   }
   __syncthreads();
-  derive_row(mb, m, k, !rows_split);
+  derive_row(mb, m, k, !rows_split, false);
+}
+
+// T(y) = [lgamma(y + r) - lgamma(r) - lgamma(y + 1)] log2 e for y < NB_YMAX of
+// every negative-binomial state: T(y) = sum_{i=1..y} log((r + i - 1) / i),
+// lane l of the state's warp adds the terms of y in [16 l, 16 l + 16) and an
+// exclusive warp scan (fixed order, float64) gives each lane its start.
+static_assert(NB_YMAX == 512, "the count table assumes 16 counts per lane");
+__global__ void nb_table_kernel(ModelBufs mb) {
+  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (gw >= mb.M * mb.NP || !mb.nbtab) return;
+  const int m = gw / mb.NP, k = gw % mb.NP;
+  if (mb.family[m] != HMM_NEGBIN || k >= mb.N) return;
+  const double r = mb.theta[((size_t)m * mb.NP + k) * mb.P];
+  double term[16], tot = 0.0;
+#pragma unroll
+  for (int e = 0; e < 16; ++e) {
+    const int yv = 16 * lane + e;
+    term[e] = yv == 0 ? 0.0 : log((r + yv - 1.0) / (double)yv);
+    tot += term[e];
+  }
+  double pre = tot;   // inclusive scan of the lane totals
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const double u = __shfl_up_sync(0xffffffffu, pre, o);
+    if (lane >= o) pre += u;
+  }
+  double acc = pre - tot;
+  float* nbt = mb.nbtab + ((size_t)m * mb.NP + k) * NB_YMAX;
+#pragma unroll
+  for (int e = 0; e < 16; ++e) {
+    acc += term[e];
+    nbt[16 * lane + e] = (float)(acc * kLog2e);
+  }
 }
 
 // Transition row k of model m: expected (Baum-Welch: a_ij X_ij) or counted
@@ -552,16 +590,11 @@ __global__ void __launch_bounds__(128) mstep_rows_kernel(ModelBufs mb, const dou
 // weighted histograms of nb_hist_kernel (sum_t gamma_t(j) f(y_t) =
 // sum_y h_j(y) f(y), nb_histdot_kernel), so the passes read only the
 // sequences that hold larger counts (tail[s] != 0) and add only those rows.
-__global__ void dp_sums_kernel(ModelBufs mb, const float* __restrict__ y, const float* __restrict__ gamma,
-                               const int64_t* __restrict__ offsets, const int32_t* __restrict__ model_id,
-                               int n_seq, const DPState* __restrict__ dps, const uint8_t* __restrict__ tail,
-                               const int* __restrict__ active_count,
-                               float* __restrict__ part) {
-  if (*active_count == 0) return;
-  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (warp >= n_seq) return;
-  const int s = warp;
+__device__ __forceinline__ void dp_sums_seq(const ModelBufs& mb, const float* __restrict__ y,
+                                            const float* __restrict__ gamma, const int64_t* __restrict__ offsets,
+                                            const int32_t* __restrict__ model_id, const DPState* __restrict__ dps,
+                                            const uint8_t* __restrict__ tail, float* __restrict__ part, int s,
+                                            int lane) {
   const int NP = mb.NP, N = mb.N;
   const int TPW = 32 / NP;
   const int tt = lane / NP, k = lane % NP;
@@ -643,19 +676,32 @@ __global__ void dp_sums_kernel(ModelBufs mb, const float* __restrict__ y, const 
   }
 }
 
+__global__ void dp_sums_kernel(ModelBufs mb, const float* __restrict__ y, const float* __restrict__ gamma,
+                               const int64_t* __restrict__ offsets, const int32_t* __restrict__ model_id,
+                               int n_seq, const DPState* __restrict__ dps, const uint8_t* __restrict__ tail,
+                               const int* __restrict__ active_count,
+                               float* __restrict__ part) {
+  if (*active_count == 0) return;
+  const int lane = threadIdx.x & 31;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  for (int s = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; s < n_seq; s += nwarps)
+    dp_sums_seq(mb, y, gamma, offsets, model_id, dps, tail, part, s, lane);
+}
+
 // Occupancy-weighted histograms of the integer observations below NB_YMAX
 // per negative-binomial state, H[m][NP][NB_YMAX]: fixed-point sums (2^32
-// units of gamma, unsigned 64-bit), so that the atomic additions are exact
-// and the result does not depend on their order.  One block per chunk of
-// the model-sorted sequence list; a shared-memory histogram (dynamic:
-// NP * NB_YMAX * 8 bytes) is flushed once per block.  tail[s] = 1 marks the
-// sequences holding a count >= NB_YMAX.
+// units of gamma, unsigned 64-bit), so that every addition is exact and the
+// result does not depend on their order.  One block per row range (about
+// 4096 rows) of a chunk of the model-sorted sequence list; a shared-memory
+// histogram (dynamic: NP * NB_YMAX * 8 bytes) is flushed once per block with
+// global atomics.  tail[s] = 1 marks the sequences holding a count >=
+// NB_YMAX.
 constexpr double NB_HIST_ONE = 4294967296.0;
 __global__ void nb_hist_kernel(ModelBufs mb, const float* __restrict__ y, const float* __restrict__ gamma,
                                const int64_t* __restrict__ offsets, const int32_t* __restrict__ model_id,
                                const int32_t* __restrict__ seq_by_model, const int32_t* __restrict__ chunk_lo,
-                               const int32_t* __restrict__ chunk_hi, unsigned long long* __restrict__ H,
-                               uint8_t* __restrict__ tail) {
+                               const int32_t* __restrict__ chunk_hi, const int64_t* __restrict__ crow, int split,
+                               unsigned long long* __restrict__ H, uint8_t* __restrict__ tail) {
   extern __shared__ unsigned long long hsh[];
   const int c = blockIdx.x;
   const int lo = chunk_lo[c], hi = chunk_hi[c];
@@ -663,25 +709,55 @@ __global__ void nb_hist_kernel(ModelBufs mb, const float* __restrict__ y, const 
   const int m = model_id[seq_by_model[lo]];
   if (mb.family[m] != HMM_NEGBIN) return;
   const int NP = mb.NP, N = mb.N;
+  // block (c, z): rows [z per, (z + 1) per) of the chunk's rows in
+  // seq_by_model order (crow[q]: the chunk rows before position q)
+  const int slast = seq_by_model[hi - 1];
+  const int64_t rows = crow[hi - 1] + (offsets[slast + 1] - offsets[slast]);
+  const int64_t per = (rows + split - 1) / split;
+  const int64_t zr = (int64_t)blockIdx.y * per;
+  const int64_t r0 = zr < rows ? zr : rows, r1 = r0 + per < rows ? r0 + per : rows;
+  if (r0 >= r1) return;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int z = threadIdx.x; z < NP * NB_YMAX; z += blockDim.x) hsh[z] = 0ull;
   __syncthreads();
-  for (int q = lo; q < hi; ++q) {
-    const int s = seq_by_model[q];
-    const int64_t b = offsets[s], e = offsets[s + 1];
-    bool big = false;
-    for (int64_t idx = threadIdx.x; idx < (e - b) * N; idx += blockDim.x) {
-      const int64_t t = b + idx / N;
-      const int k = (int)(idx % N);
-      const float yy = y[t];
-      if (!is_count(yy)) continue;   // density 0: no occupancy
-      if (yy >= (float)NB_YMAX) {
-        big = true;
-        continue;
+  // warp w owns the histograms of states w, w + nw, ..: no other warp writes
+  // them, and lanes of the warp that hit the same count are merged first, so
+  // every update is a plain add of the group's exact fixed-point sum
+  for (int k = warp; k < N; k += nw) {
+    unsigned long long* hk = hsh + (size_t)k * NB_YMAX;
+    for (int q = lo; q < hi; ++q) {
+      const int s = seq_by_model[q];
+      const int64_t len = offsets[s + 1] - offsets[s], cs = crow[q];
+      const int64_t ta = r0 - cs > 0 ? r0 - cs : 0, tb = r1 - cs < len ? r1 - cs : len;
+      if (ta >= tb) continue;
+      const int64_t b = offsets[s] + ta, e = offsets[s] + tb;
+      bool big = false;
+      for (int64_t t0 = b; t0 < e; t0 += 32) {
+        const int64_t t = t0 + lane;
+        int bin = -1;
+        unsigned long long v = 0ull;
+        if (t < e) {
+          const float yy = y[t];
+          if (is_count(yy)) {   // density 0 outside the support: no occupancy
+            if (yy >= (float)NB_YMAX) {
+              big = true;
+            } else {
+              const float g = gamma[t * N + k];
+              if (g > 0.f) {
+                bin = (int)yy;
+                v = (unsigned long long)llrint((double)g * NB_HIST_ONE);
+              }
+            }
+          }
+        }
+        const unsigned grp = __match_any_sync(0xffffffffu, bin);
+        unsigned long long sum = 0ull;
+        for (unsigned mm = grp; mm; mm &= mm - 1) sum += __shfl_sync(grp, v, __ffs(mm) - 1);
+        if (bin >= 0 && lane == __ffs(grp) - 1) hk[bin] += sum;
+        __syncwarp();
       }
-      const float g = gamma[t * N + k];
-      if (g > 0.f) atomicAdd(&hsh[k * NB_YMAX + (int)yy], (unsigned long long)llrint((double)g * NB_HIST_ONE));
+      if (big) tail[s] = 1;
     }
-    if (big) tail[s] = 1;
   }
   __syncthreads();
   unsigned long long* Hm = H + (size_t)m * NP * NB_YMAX;
@@ -749,7 +825,8 @@ __global__ void nb_histdot_kernel(ModelBufs mb, const DPState* __restrict__ dps,
 // model-sorted sequence list
 __global__ void reduce_records_l1(const float* __restrict__ part, int RS, const int32_t* __restrict__ seq_by_model,
                                   const int32_t* __restrict__ chunk_lo, const int32_t* __restrict__ chunk_hi,
-                                  double* __restrict__ chunk_rec) {
+                                  double* __restrict__ chunk_rec, const int* __restrict__ active = nullptr) {
+  if (active && *active == 0) return;
   const int c = blockIdx.x;
   const int lo = chunk_lo[c], hi = chunk_hi[c];
   for (int f = threadIdx.x; f < RS; f += blockDim.x) {
@@ -832,7 +909,7 @@ __global__ void dp_finish_kernel(ModelBufs mb) {
   if (idx >= mb.M * mb.NP) return;
   const int m = idx / mb.NP, k = idx % mb.NP;
   const int fam = mb.family[m];
-  if (fam == HMM_WEIBULL || fam == HMM_NEGBIN) derive_row(mb, m, k);
+  if (fam == HMM_WEIBULL || fam == HMM_NEGBIN) derive_row(mb, m, k, true, false);
 }
 
 }  // namespace hmm
