@@ -1171,7 +1171,7 @@ void run_mstep(hmm_ctx ctx, hmm_model model, hmm_stats stats, const MStepOpts& o
   }
   {
     KTimer kt(ctx, HMM_KT_MSTEP, st);
-    kt.kernels = 1 + 2 * (model->NP > 32) + 2 * (int)model->any_discrete + 2 * (int)model->any_mv +
+    kt.kernels = 1 + 2 * (model->NP >= 16) + 2 * (int)model->any_discrete + 2 * (int)model->any_mv +
                  (int)model->any_ext +
                  2 * (int)model->any_indep;
     if (model->any_indep) {   // Sec. 4.5: every component's scalar update with the state's weights
@@ -1190,11 +1190,11 @@ void run_mstep(hmm_ctx ctx, hmm_model model, hmm_stats stats, const MStepOpts& o
                                                         model->M, model->NP, model->N, model->P, model->KS, o);
       HMM_CUDA(cudaGetLastError());
     }
-    // above 32 states the transition rows and their float32 tables run as
+    // from 16 states the transition rows and their float32 tables run as
     // their own kernels (one block per row, one thread per entry): one thread
     // per state would leave a single model's M-step on one SM, dominated by
-    // its N float64 logarithms
-    const bool rows_split = model->NP > 32;
+    // the serial chain of its N float64 logarithms
+    const bool rows_split = model->NP >= 16;
     mstep_kernel<<<model->M, model->NP, 0, st>>>(model->bufs(), stats->rec.as<double>(), o, dps, rows_split);
     HMM_CUDA(cudaGetLastError());
     if (rows_split) {

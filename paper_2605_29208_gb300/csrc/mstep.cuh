@@ -285,7 +285,10 @@ __device__ inline double positive_step(double x, double step) {
 __device__ inline double gamma_shape(double ybar, double var, double c, const MStepOpts& o) {
   // c > 0 unless every weighted observation is equal (no MLE then)
   if (!(c > 0.0) || !(ybar > 0.0)) return NAN;
-  double a = (var > 0.0) ? ybar * ybar / var : 0.5 / c;
+  // start from the closed-form approximation of the shape MLE given by
+  // Minka ("Estimating a Gamma distribution", 2002): within a few per cent,
+  // so Newton needs two or three steps
+  double a = (3.0 - c + sqrt((c - 3.0) * (c - 3.0) + 24.0 * c)) / (12.0 * c);
   for (int it = 0; it < o.newton_maxit; ++it) {
     const double s = log(a) - digamma_d(a) - c;
     const double ds = 1.0 / a - trigamma_d(a);
@@ -493,7 +496,7 @@ __global__ void mstep_kernel(ModelBufs mb, const double* __restrict__ rec, MStep
     if (o.update_transitions) {
       // expected (Baum-Welch: a_ij X_ij) or counted (Viterbi training: X_ij)
       // transitions, plus the Dirichlet pseudo-counts of the MAP reading;
-      // above 32 states mstep_rows_kernel updates the rows
+      // from 16 states mstep_rows_kernel updates the rows
       const double cA = o.prior_A > 1.0 ? o.prior_A - 1.0 : 0.0;
       const double cp = o.prior_pi > 1.0 ? o.prior_pi - 1.0 : 0.0;
       if (!rows_split) {
