@@ -1060,13 +1060,13 @@ void run_estep(hmm_ctx ctx, hmm_model model, const hmm_batch* b, hmm_plan plan, 
     const int RS = rec_size(NP);
     ctx->chunk_rec.ensure((size_t)std::max(plan->n_chunks, 1) * RS * 8);
     if (plan->n_chunks > 0) {
-      reduce_estep_l1<<<plan->n_chunks, 256, 0, st>>>(a.partials, ll, plan->seq_by_model.as<int32_t>(),
-                                                     plan->chunk_lo.as<int32_t>(), plan->chunk_hi.as<int32_t>(),
-                                                     NP, ctx->chunk_rec.as<double>());
+      reduce_estep_l1<<<dim3((unsigned)plan->n_chunks, (unsigned)((RS + 127) / 128)), 128, 0, st>>>(
+          a.partials, ll, plan->seq_by_model.as<int32_t>(), plan->chunk_lo.as<int32_t>(),
+          plan->chunk_hi.as<int32_t>(), NP, ctx->chunk_rec.as<double>());
       HMM_CUDA(cudaGetLastError());
     }
-    reduce_chunks_l2<<<model->M, 256, 0, st>>>(ctx->chunk_rec.as<double>(), plan->model_chunk_ptr.as<int32_t>(),
-                                               RS, stats->rec.as<double>());
+    reduce_chunks_l2<<<dim3((unsigned)model->M, (unsigned)((RS + 127) / 128)), 128, 0, st>>>(
+        ctx->chunk_rec.as<double>(), plan->model_chunk_ptr.as<int32_t>(), RS, stats->rec.as<double>());
     HMM_CUDA(cudaGetLastError());
     if (mv_stats) kt.kernels += mv_statistics(ctx, model, b, plan, stats, st);
     stats->valid = true;

@@ -19,30 +19,38 @@ __global__ void reduce_estep_l1(const float* __restrict__ partials, const double
   const int F = NP + NST;
   const int RS = rec_size(NP);
   double* out = chunk_rec + (size_t)c * RS;
-  for (int f = threadIdx.x; f < RS; f += blockDim.x) {
+  // the chunk's sequence ids staged once; the sums keep their sequential
+  // order (unrolled so that the loads are issued ahead of the additions);
+  // gridDim.y blocks share the fields of a chunk
+  __shared__ int sidx[64];
+  for (int z = threadIdx.x; z < hi - lo && z < 64; z += blockDim.x) sidx[z] = seq_by_model[lo + z];
+  __syncthreads();
+  auto sq = [&](int q) -> size_t { return q - lo < 64 ? (size_t)sidx[q - lo] : (size_t)seq_by_model[q]; };
+  for (int f = blockIdx.y * blockDim.x + threadIdx.x; f < RS; f += gridDim.y * blockDim.x) {
     double acc = 0.0;
     if (f == 0) {
       acc = (double)(hi - lo);
     } else if (f == 1) {
-      for (int q = lo; q < hi; ++q) acc += loglik[seq_by_model[q]];
+#pragma unroll 8
+      for (int q = lo; q < hi; ++q) acc += loglik[sq(q)];
     } else if (f < rec_xi(NP)) {
       const int k = f - rec_g1(NP);
-      for (int q = lo; q < hi; ++q) {
-        const size_t s = seq_by_model[q];
-        acc += (double)partials[((s * 2 + 1) * NP + k) * F + NP + NST - 1];
-      }
+#pragma unroll 8
+      for (int q = lo; q < hi; ++q) acc += (double)partials[((sq(q) * 2 + 1) * NP + k) * F + NP + NST - 1];
     } else if (f < rec_st(NP)) {
       const int i = (f - rec_xi(NP)) / NP, j = (f - rec_xi(NP)) % NP;
+#pragma unroll 8
       for (int q = lo; q < hi; ++q) {
-        const size_t s = seq_by_model[q];
+        const size_t s = sq(q);
         // forward chains accumulate xi with state j as the owned index
         acc += (double)partials[((s * 2 + 0) * NP + j) * F + i];
         acc += (double)partials[((s * 2 + 1) * NP + i) * F + j];
       }
     } else {
       const int k = (f - rec_st(NP)) / (NST - 1), z = (f - rec_st(NP)) % (NST - 1);
+#pragma unroll 8
       for (int q = lo; q < hi; ++q) {
-        const size_t s = seq_by_model[q];
+        const size_t s = sq(q);
         acc += (double)partials[((s * 2 + 0) * NP + k) * F + NP + z];
         acc += (double)partials[((s * 2 + 1) * NP + k) * F + NP + z];
       }
@@ -60,8 +68,9 @@ __global__ void reduce_chunks_l2(const double* __restrict__ chunk_rec,
   if (active && *active == 0) return;
   const int m = blockIdx.x;
   const int c0 = model_chunk_ptr[m], c1 = model_chunk_ptr[m + 1];
-  for (int f = threadIdx.x; f < RS; f += blockDim.x) {
+  for (int f = blockIdx.y * blockDim.x + threadIdx.x; f < RS; f += gridDim.y * blockDim.x) {
     double acc = 0.0;
+#pragma unroll 8
     for (int c = c0; c < c1; ++c) acc += chunk_rec[(size_t)c * RS + f];
     rec[(size_t)m * RS + f] = acc;
   }
