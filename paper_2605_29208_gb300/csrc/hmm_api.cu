@@ -106,6 +106,13 @@ static void check_scalar_params(int fam, const double* q) {
 
 // Records a pair of CUDA events around the launches made in its scope when
 // the context's profiling option is on (not inside a graph capture).
+// Grid of reduce_chunks_l2: one block row per model, the record's fields
+// spread over blocks (each field is still one thread's fixed-order sum).
+inline dim3 l2_grid(int M, int64_t RS, int threads) {
+  const int64_t y = std::min<int64_t>(std::max<int64_t>((RS + threads - 1) / threads, 1), 4096);
+  return dim3((unsigned)M, (unsigned)y);
+}
+
 struct KTimer {
   hmm_ctx ctx;
   int slot;
@@ -702,7 +709,8 @@ int mv_statistics(hmm_ctx ctx, hmm_model model, const hmm_batch* b, hmm_plan pla
       HMM_CUDA(cudaGetLastError());
       ++nk;
     }
-    reduce_chunks_l2<<<model->M, 128, 0, st>>>(stats->mv_chunk.as<double>(), plan->model_chunk_ptr.as<int32_t>(), RS,
+    reduce_chunks_l2<<<l2_grid(model->M, RS, 128), 128, 0, st>>>(stats->mv_chunk.as<double>(),
+                                                                 plan->model_chunk_ptr.as<int32_t>(), RS,
                                                stats->mv_rec.as<double>());
     HMM_CUDA(cudaGetLastError());
     return nk;
@@ -730,7 +738,8 @@ int mv_statistics(hmm_ctx ctx, hmm_model model, const hmm_batch* b, hmm_plan pla
       HMM_CUDA(cudaGetLastError());
       ++nk;
     }
-    reduce_chunks_l2<<<model->M, 128, 0, st>>>(stats->mv_chunk.as<double>(), plan->model_chunk_ptr.as<int32_t>(), RS,
+    reduce_chunks_l2<<<l2_grid(model->M, RS, 128), 128, 0, st>>>(stats->mv_chunk.as<double>(),
+                                                                 plan->model_chunk_ptr.as<int32_t>(), RS,
                                                stats->mv_rec.as<double>());
     HMM_CUDA(cudaGetLastError());
     ++nk;
@@ -756,7 +765,8 @@ int mv_statistics(hmm_ctx ctx, hmm_model model, const hmm_batch* b, hmm_plan pla
                                 0, st>>>(stats->mv_split.as<double>(), split, RS, stats->mv_chunk.as<double>());
       HMM_CUDA(cudaGetLastError());
     }
-    reduce_chunks_l2<<<model->M, 128, 0, st>>>(stats->mv_chunk.as<double>(), plan->model_chunk_ptr.as<int32_t>(), RS,
+    reduce_chunks_l2<<<l2_grid(model->M, RS, 128), 128, 0, st>>>(stats->mv_chunk.as<double>(),
+                                                                 plan->model_chunk_ptr.as<int32_t>(), RS,
                                                stats->mv_rec.as<double>());
     HMM_CUDA(cudaGetLastError());
     nk = 2 * (plan->n_chunks > 0) + 1;
@@ -798,7 +808,8 @@ int mv_statistics(hmm_ctx ctx, hmm_model model, const hmm_batch* b, hmm_plan pla
                                                     stats->mv_chunk.as<double>());
     HMM_CUDA(cudaGetLastError());
   }
-  reduce_chunks_l2<<<model->M, 128, 0, st>>>(stats->mv_chunk.as<double>(), plan->model_chunk_ptr.as<int32_t>(), RS,
+  reduce_chunks_l2<<<l2_grid(model->M, RS, 128), 128, 0, st>>>(stats->mv_chunk.as<double>(),
+                                                                 plan->model_chunk_ptr.as<int32_t>(), RS,
                                              stats->mv_rec.as<double>());
   HMM_CUDA(cudaGetLastError());
   return (S > 0) + (plan->n_chunks > 0) + 1;
@@ -881,7 +892,8 @@ void run_estep_large(hmm_ctx ctx, hmm_model model, const hmm_batch* b, hmm_plan 
   HMM_CUDA(launch_large_reduce(ctx->partials.as<float>(), ll, ctx->lg_xi.as<double>(),
                                plan->seq_by_model.as<int32_t>(), plan->chunk_lo.as<int32_t>(),
                                plan->chunk_hi.as<int32_t>(), plan->n_chunks, NP, ctx->chunk_rec.as<double>(), st));
-  reduce_chunks_l2<<<model->M, 256, 0, st>>>(ctx->chunk_rec.as<double>(), plan->model_chunk_ptr.as<int32_t>(),
+  reduce_chunks_l2<<<l2_grid(model->M, rec_size(NP), 256), 256, 0, st>>>(ctx->chunk_rec.as<double>(),
+                                                                         plan->model_chunk_ptr.as<int32_t>(),
                                              rec_size(NP), stats->rec.as<double>());
   HMM_CUDA(cudaGetLastError());
   kt.kernels += 1;   // the xi kernel of either form
@@ -1065,7 +1077,7 @@ void run_estep(hmm_ctx ctx, hmm_model model, const hmm_batch* b, hmm_plan plan, 
           plan->chunk_hi.as<int32_t>(), NP, ctx->chunk_rec.as<double>());
       HMM_CUDA(cudaGetLastError());
     }
-    reduce_chunks_l2<<<dim3((unsigned)model->M, (unsigned)((RS + 127) / 128)), 128, 0, st>>>(
+    reduce_chunks_l2<<<l2_grid(model->M, RS, 128), 128, 0, st>>>(
         ctx->chunk_rec.as<double>(), plan->model_chunk_ptr.as<int32_t>(), RS, stats->rec.as<double>());
     HMM_CUDA(cudaGetLastError());
     if (mv_stats) kt.kernels += mv_statistics(ctx, model, b, plan, stats, st);
@@ -1284,7 +1296,8 @@ void run_mstep(hmm_ctx ctx, hmm_model model, hmm_stats stats, const MStepOpts& o
                                                         stats->dp_chunk.as<double>(), cnt + it);
         HMM_CUDA(cudaGetLastError());
       }
-      reduce_chunks_l2<<<model->M, 128, 0, st>>>(stats->dp_chunk.as<double>(), plan->model_chunk_ptr.as<int32_t>(),
+      reduce_chunks_l2<<<l2_grid(model->M, RS, 128), 128, 0, st>>>(stats->dp_chunk.as<double>(),
+                                                                   plan->model_chunk_ptr.as<int32_t>(),
                                                  RS, stats->dp_rec.as<double>(), cnt + it);
       HMM_CUDA(cudaGetLastError());
       if (model->any_negbin) {   // the histogram rows of the negative-binomial sums
@@ -1727,8 +1740,15 @@ hmm_status hmm_model_set_params(hmm_model model, const double* h_blob, int64_t n
     HMM_CUDA(cudaMemcpy(model->A.p, A.data(), A.size() * 8, cudaMemcpyHostToDevice));
     HMM_CUDA(cudaMemcpy(model->theta.p, th.data(), th.size() * 8, cudaMemcpyHostToDevice));
     const int n = M * NP;
-    derive_kernel<<<(n + 127) / 128, 128>>>(model->bufs());
+    // from 16 states the transition tables run one thread per entry (as in
+    // the M-step) instead of a float64 logarithm chain per state
+    derive_kernel<<<(n + 127) / 128, 128>>>(model->bufs(), NP < 16);
     HMM_CUDA(cudaGetLastError());
+    if (NP >= 16) {
+      const int64_t ne = (int64_t)M * NP * NP;
+      derive_tables_kernel<<<(unsigned)((ne + 255) / 256), 256>>>(model->bufs());
+      HMM_CUDA(cudaGetLastError());
+    }
     if (model->any_mv) {
       mv_derive_kernel<<<(n + 127) / 128, 128>>>(model->family.as<int>(), model->theta.as<double>(), M, NP, N, P, D,
                                                  model->KM, model->mvcoef.as<float>());
@@ -2058,7 +2078,8 @@ void run_estep_viterbi(hmm_ctx ctx, hmm_model model, const hmm_batch* b, hmm_pla
                                  plan->seq_by_model.as<int32_t>(), plan->chunk_lo.as<int32_t>(),
                                  plan->chunk_hi.as<int32_t>(), nc, NP, ctx->chunk_rec.as<double>(), st));
   }
-  reduce_chunks_l2<<<model->M, 256, 0, st>>>(ctx->chunk_rec.as<double>(), plan->model_chunk_ptr.as<int32_t>(),
+  reduce_chunks_l2<<<l2_grid(model->M, rec_size(NP), 256), 256, 0, st>>>(ctx->chunk_rec.as<double>(),
+                                                                         plan->model_chunk_ptr.as<int32_t>(),
                                              rec_size(NP), stats->rec.as<double>());
   HMM_CUDA(cudaGetLastError());
   if (model->table_family()) kt.kernels += mv_statistics(ctx, model, b, plan, stats, st);

@@ -176,7 +176,8 @@ __global__ void large_reduce_l1(const float* __restrict__ part, const double* __
   const int lo = chunk_lo[c], hi = chunk_hi[c];
   const int RS = rec_size(NP);
   double* out = chunk_rec + (size_t)c * RS;
-  for (int f = threadIdx.x; f < RS; f += blockDim.x) {
+  // gridDim.y blocks share a chunk's fields (the xi block is a copy)
+  for (int f = blockIdx.y * blockDim.x + threadIdx.x; f < RS; f += gridDim.y * blockDim.x) {
     double acc = 0.0;
     if (f == 0) {
       acc = (double)(hi - lo);
@@ -276,8 +277,9 @@ cudaError_t launch_large_reduce(const float* part, const double* loglik, const d
                                 const int32_t* seq_by_model, const int32_t* chunk_lo, const int32_t* chunk_hi,
                                 int n_chunks, int NP, double* chunk_rec, cudaStream_t st) {
   if (n_chunks == 0) return cudaSuccess;
-  large_reduce_l1<<<(unsigned)n_chunks, 256, 0, st>>>(part, loglik, xi_chunk, seq_by_model, chunk_lo, chunk_hi, NP,
-                                                      chunk_rec);
+  const unsigned fy = (unsigned)std::min(std::max((rec_size(NP) + 255) / 256, 1), 1024);
+  large_reduce_l1<<<dim3((unsigned)n_chunks, fy), 256, 0, st>>>(part, loglik, xi_chunk, seq_by_model, chunk_lo,
+                                                                  chunk_hi, NP, chunk_rec);
   return cudaGetLastError();
 }
 

@@ -253,10 +253,10 @@ __device__ inline void derive_row(const ModelBufs& mb, int m, int k, bool tables
   }
 }
 
-__global__ void derive_kernel(ModelBufs mb) {
+__global__ void derive_kernel(ModelBufs mb, bool tables = true) {
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= mb.M * mb.NP) return;
-  derive_row(mb, idx / mb.NP, idx % mb.NP);
+  derive_row(mb, idx / mb.NP, idx % mb.NP, tables);
 }
 
 __global__ void derive_tables_kernel(ModelBufs mb) {
