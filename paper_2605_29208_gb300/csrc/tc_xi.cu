@@ -211,7 +211,7 @@ __global__ void __launch_bounds__(128, 1) xi_tc_kernel(const __grid_constant__ C
 }
 
 // cuTensorMapEncodeTiled through the runtime's driver entry point (no link
-// against the driver library)
+// against libcuda)
 PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
   static std::once_flag once;
