@@ -13,6 +13,8 @@ STATUS_NAMES = {0: "HMM_OK", 1: "HMM_E_ARG", 2: "HMM_E_NOMEM", 3: "HMM_E_CUDA",
 
 OPT_PROFILE, OPT_ESTEP_LANES, OPT_VITERBI_LANES, OPT_PLAIN_ESTEP, OPT_TENSOR_RECURRENCE = 1, 2, 3, 4, 5
 OPT_TIME_PARALLEL = 6
+# values of OPT_TENSOR_RECURRENCE: float32 CUDA cores, FP16 tensor cores, TF32 (padded N <= 256)
+TENSOR_REC_OFF, TENSOR_REC_FP16, TENSOR_REC_TF32 = 0, 1, 2
 KT_SLOTS = ("estep", "reduce", "mstep", "viterbi", "emission", "plain", "xi", "slot7")
 
 FAMILY = {"gauss": 0, "poisson": 1, "gamma": 2, "beta": 3, "weibull": 4, "negbin": 5,
